@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark: time to relative residual 1e-6 per LM normal-equation solve, PCG and MCG.
+
+One step is one pass of the whole hot path over one synthetic problem at the first
+LM iteration (lambda = 1e-4): linearisation and reduced camera system (build), a
+block-Jacobi PCG solve to |r| < 1e-6 |r_0| (Algorithm 1), an MCG solve to the same
+tolerance (Algorithm 2), and the float64 true residual of each.  ``value`` is
+milliseconds per step (lower is better); with N ranks each rank solves its own
+problem (replicas, no collective on the data path) and value = T_max / (N * K).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload dense-1936]
+                    [--precision fp64|mixed] [--impl ours|reference]
+
+``--impl reference`` times the float64 CPU oracle instead (host cores only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_04015_gb300 import synthetic  # noqa: E402
+
+WORKLOADS = {
+    # name: (generator, kwargs, description)
+    "dense-1936": ("dense", {}, "1936 cameras on a sphere, 1.3M landmarks, ~5.2M observations, "
+                                "64 co-visibility clusters, d~0.94 (F-1936-shaped)"),
+    "sequential-1000": ("sequential", {}, "1000 cameras on a helix, 100k landmarks, ~700k observations, "
+                                          "window 32 (banded S, d~0.04)"),
+    "tiny-16": ("tiny", {}, "16 cameras on a circle, 1000 landmarks, ~4.5k observations"),
+}
+LAMBDA = 1e-4
+TOL = 1e-6
+MAX_ITERS = 1000
+METRIC = "time to rel. residual 1e-6 per LM solve (MCG vs PCG, FP64 vs mixed); HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense-1936", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n-dirs", type=int, default=16)
+    ap.add_argument("--tau", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# FP64 arithmetic peak of a GB300 (nominal 1.25 TFLOP/s dense, NVIDIA's figure for the part).
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (the baseline and the reference arm)
+
+def oracle_sample_step(sc, frac: int = 32) -> dict:
+    """The float64 oracle on a bounded sample of the workload, scaled to the full problem.
+
+    Sample: every frac-th landmark of the same scene with all its observations.  The
+    oracle linearises and forms S, b~ (Eqs. 2-14), then solves to 1e-6 by PCG and MCG.
+    Build time is scaled by the observation ratio, solve times by the ratio of nonzero
+    9x9 blocks of S (the cost of one product with S).
+    """
+    from oracle import camera as ocam
+    from oracle import lm as olm
+    from oracle import schur as osch
+    from oracle import solvers as osol
+
+    keep = (sc.obs_pt % frac) == 0
+    oc, op = sc.obs_cam[keep], sc.obs_pt[keep]
+    m = ocam.project(sc.cams_true, sc.pts_true, oc, op) + sc.noise[keep]
+    t0 = time.perf_counter()
+    lin = olm.linearise(sc.cams0, sc.pts0, oc, op, m, LAMBDA)
+    Dinv = osol.block_jacobi_inverse(lin.S, sc.n_cams)
+    t1 = time.perf_counter()
+    pcg = osol.pcg(lin.S, lin.btilde, Dinv, TOL, MAX_ITERS)
+    t2 = time.perf_counter()
+    mcg = osol.mcg(lin.S, lin.btilde, Dinv, 16, 10.0, TOL, MAX_ITERS)
+    t3 = time.perf_counter()
+    nnzb_s = osch.density(lin.S, sc.n_cams) * sc.n_cams ** 2
+    return {"t_build": t1 - t0, "t_pcg": t2 - t1, "t_mcg": t3 - t2, "n_obs_sample": int(keep.sum()),
+            "n_obs": sc.n_obs, "nnzb_sample": nnzb_s, "pcg_iters": pcg.iters, "mcg_iters": mcg.iters,
+            "n_cams": sc.n_cams, "frac": frac}
+
+
+def sample_text(s: dict, nnzb_full) -> str:
+    return (f"landmarks with index % {s['frac']} == 0 ({s['n_obs_sample']} of {s['n_obs']} observations): oracle "
+            f"build + PCG ({s['pcg_iters']} it) + MCG N=16 tau=10 ({s['mcg_iters']} it) to 1e-6 in "
+            f"{s['t_build'] + s['t_pcg'] + s['t_mcg']:.1f} s; build scaled by observations, solves by nonzero "
+            f"blocks of S ({s['nnzb_sample']:.0f} -> {nnzb_full:.0f})")
+
+
+def scale_oracle(s: dict, nnzb_full: float) -> float:
+    """Estimated ms of one full step from a sample step."""
+    b = s["t_build"] * s["n_obs"] / s["n_obs_sample"]
+    r = nnzb_full / s["nnzb_sample"]
+    return 1e3 * (b + (s["t_pcg"] + s["t_mcg"]) * r)
+
+
+def cpu_threads() -> int:
+    try:
+        import threadpoolctl
+
+        info = threadpoolctl.threadpool_info()
+        n = max((d.get("num_threads", 1) for d in info), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def nnzb_estimate(sc) -> float:
+    """Nonzero 9x9 blocks of S for the full scene: camera pairs sharing a landmark."""
+    import scipy.sparse as sp
+
+    A = sp.csr_matrix((np.ones(sc.n_obs, np.float32), (sc.obs_cam, sc.obs_pt)), shape=(sc.n_cams, sc.n_pts))
+    return float((A @ A.T).nnz)
+
+
+def run_reference(a, rank: int, world: int):
+    if rank != 0:
+        return
+    gen, kw, desc = WORKLOADS[a.workload]
+    sc = synthetic.make(gen, 0, **kw)
+    nnzb = nnzb_estimate(sc)
+    for _ in range(a.warmup):
+        oracle_sample_step(sc)
+    vals, samples = [], []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        s = oracle_sample_step(sc)
+        samples.append(s)
+        vals.append(scale_oracle(s, nnzb))
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/step", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator; BAL/1dSfM datasets absent)",
+            "config": {"workload": a.workload, "description": desc, "lambda": LAMBDA, "tol": TOL},
+            "cpu_baseline": {"value": v, "unit": "ms/step", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample_text(samples[-1], nnzb)},
+            "e2e": {"value": v, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+
+def run_ours(a, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_2110_04015_gb300 import problem
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gen, kw, desc = WORKLOADS[a.workload]
+    sc = synthetic.make(gen, seed=rank, **kw)
+    xy = problem.device_measurements(sc, device=str(dev))
+    p = problem.from_scene(sc, precision=a.precision, xy=xy)
+    stream = torch.cuda.current_stream()
+    p.ba_set_stream(stream)
+
+    def step():
+        p.ba_build_normal(LAMBDA)
+        s1 = p.ba_solve_pcg(TOL, MAX_ITERS)
+        s2 = p.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
+        return s1, s2
+
+    for _ in range(a.warmup):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = p.ba_get_launch_count()
+    times, stats = [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    launches = p.ba_get_launch_count() - l0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    T = float(sum(times))
+    if dist:
+        t = torch.tensor([T], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+    value = T / (a.steps * world)
+
+    # breakdown of the last step
+    s_pcg, s_mcg = stats[-1]
+    for s1, s2 in stats:
+        assert s1["true_rel_residual"] <= 1.5e-6 and s2["true_rel_residual"] <= 1.5e-6, (s1, s2)
+
+    # roofline of the dominant kernel: the product q = S p of the Krylov solves
+    nnzb = p.ba_get_schur_nnzb()
+    n = 9 * sc.n_cams
+    t_spmv = p.ba_time_kernel("spmv", reps=10)
+    t_schur = p.ba_time_kernel("schur", reps=3)
+    peaks = load_peaks()
+    elt = 8 if a.precision == "fp64" else 4
+    spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
+    spmv_flops = 162.0 * nnzb
+    if a.precision == "fp64":
+        roof = {"kernel": "k_pcg_spmv<double> (q = S p)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "ms_per_launch": t_spmv,
+                "achieved_gbs": spmv_bytes / t_spmv / 1e6, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof = {"kernel": "k_pcg_spmv<float> (q = S p)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "bytes_per_launch": spmv_bytes,
+                "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
+    roof_schur = {"kernel": "k_schur (S block build)", "ms_per_launch": t_schur}
+
+    # end to end through the host-buffer API: parameters in, both solutions out
+    e2e = None
+    if not a.no_e2e:
+        cams_h = np.ascontiguousarray(sc.cams0)
+        pts_h = np.ascontiguousarray(sc.pts0)
+        dx_h = np.empty((sc.n_cams, 9))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            p.ba_set_params(cams_h, pts_h)
+            p.ba_build_normal(LAMBDA)
+            p.ba_solve_pcg(TOL, MAX_ITERS)
+            p.ba_get_delta(dx_h)
+            p.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
+            p.ba_get_delta(dx_h)
+        torch.cuda.synchronize()
+        Te = (time.perf_counter() - t0) * 1e3
+        if dist:
+            t = torch.tensor([Te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            Te = float(t.item())
+        e2e = {"value": Te / (a.steps * world), "unit": "ms/step",
+               "h2d_bytes_per_step": int(cams_h.nbytes + pts_h.nbytes), "d2h_bytes_per_step": int(2 * dx_h.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        s = oracle_sample_step(sc)
+        cpu = {"value": scale_oracle(s, nnzb), "unit": "ms/step", "cores": cpu_threads(), "kind": "oracle",
+               "sample": sample_text(s, nnzb)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms/step", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": T / a.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded generator; BAL/1dSfM datasets absent)",
+            "config": {"workload": a.workload, "description": desc, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
+                       "n_obs": sc.n_obs, "nnzb": nnzb, "lambda": LAMBDA, "tol": TOL, "max_iters": MAX_ITERS,
+                       "mcg": {"n_dirs": a.n_dirs, "tau": a.tau}, "precision": a.precision,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MiB buffer written before every timed step; S and the observation arrays exceed L2"},
+            "breakdown": {
+                "step_ms": [round(x, 4) for x in times],
+                "pcg": {k: s_pcg[k] for k in ("iters", "ms", "true_rel_residual", "status")},
+                "mcg": {k: s_mcg[k] for k in ("iters", "local_steps", "ms", "true_rel_residual", "status",
+                                              "history_cols", "n_dirs_eff")},
+                "build_ms": T / a.steps - s_pcg["ms"] - s_mcg["ms"],
+            },
+            "roofline": roof,
+            "roofline_build": roof_schur,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    p.close()
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    try:
+        run_ours(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

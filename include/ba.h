@@ -1,0 +1,269 @@
+/*
+ * ba.h - C ABI of the GB300 bundle-adjustment normal-equation solver.
+ *
+ * The library solves the reduced camera system of one Levenberg-Marquardt
+ * (LM) iteration of bundle adjustment,
+ *
+ *     S dx_p = -b~,   S = U_lambda - W V_lambda^{-1} W^T,   b~ = b_p - W V_lambda^{-1} b_l
+ *
+ * (Weber, Demmel, Cremers, "Multidirectional Conjugate Gradients for Scalable
+ * Bundle Adjustment", GCPR 2021: Section 3.1, Eqs. 6-14), by block-Jacobi
+ * preconditioned conjugate gradients (Algorithm 1) or by multidirectional
+ * conjugate gradients (Algorithm 2, Section 3.2), on one CUDA device.
+ *
+ * Conventions for every call:
+ *  - Return value: BA_OK (0) or a negative ba_status.  No C++ exception
+ *    crosses this boundary.  After a failure ba_last_error() describes it.
+ *  - A ba_problem handle is not thread-safe; distinct handles are
+ *    independent.  All device work of a handle is ordered on its stream
+ *    (ba_set_stream); calls return after that work has finished unless
+ *    stated otherwise.
+ *  - Pointer arguments marked "host or device" may point to host memory
+ *    (pageable or pinned) or to device memory of the handle's device: the
+ *    library copies with cudaMemcpyDefault.  The caller keeps ownership of
+ *    every buffer it passes; the library keeps its own copies.
+ *  - Arrays are dense, row-major, float64 unless stated.
+ *
+ * Camera model (BAL, d_p = 9): a camera row is (omega[3], t[3], f, k1, k2),
+ * omega an angle-axis rotation; a landmark X projects to
+ *     P = R(omega) X + t,  p = -(P_x, P_y) / P_z,
+ *     pi = f (1 + k1 |p|^2 + k2 |p|^4) p,
+ * and the residual of an observation with measurement m is pi - m (Eq. 1).
+ * The paper estimates these 9 parameters per pose but does not print the
+ * formula; this is the model of the BAL datasets it uses.
+ */
+#ifndef BA_H_
+#define BA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ba_status {
+    BA_OK = 0,
+    BA_ERR_INVALID_ARG = -1,   /* bad size, index, pointer or option */
+    BA_ERR_OOM = -2,           /* device or host allocation failed */
+    BA_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    BA_ERR_SINGULAR = -4,      /* a damped 3x3 V_lambda or a 9x9 block of S is not positive definite */
+    BA_ERR_BREAKDOWN = -5,     /* NaN/Inf or a non-positive curvature in the Krylov solve */
+    BA_ERR_NOT_CONVERGED = -6, /* max_iters reached; the iterate is still returned */
+    BA_ERR_TIMEOUT = -7,       /* reserved for bounded device-side waits */
+    BA_ERR_STATE = -8          /* call out of order, e.g. a solve before ba_build_normal */
+} ba_status;
+
+typedef enum ba_damping {
+    BA_DAMPING_MARQUARDT = 0,  /* D^T D = diag(J^T J), entries clamped to [1e-6, 1e32] */
+    BA_DAMPING_IDENTITY = 1    /* D = I */
+} ba_damping;
+
+typedef enum ba_precision {
+    BA_PRECISION_FP64 = 0,     /* every array and product in float64 */
+    BA_PRECISION_MIXED = 1     /* float32 S, directions and Krylov products; float64 outer
+                                  refinement on the true residual, small solves in float64 */
+} ba_precision;
+
+typedef enum ba_solver {
+    BA_SOLVER_PCG = 0,
+    BA_SOLVER_MCG = 1
+} ba_solver;
+
+/* Options fixed at ba_problem_create. */
+typedef struct ba_options {
+    int32_t damping;           /* ba_damping; the paper's D_p, D_l of Eq. 5 are unspecified */
+    int32_t precision;         /* ba_precision */
+    int32_t chunk_iters;       /* Krylov iterations per captured CUDA graph between host checks of
+                                  the device stop flag (default 8, 1..256) */
+    int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1) */
+    double inner_tol;          /* MIXED: relative residual reduction of one inner solve (default 1e-3) */
+    int32_t max_refine;        /* MIXED: maximum outer refinement sweeps (default 12) */
+    int32_t reserved[7];
+} ba_options;
+
+/* Filled by ba_solve_pcg / ba_solve_mcg. */
+typedef struct ba_solve_stats {
+    int32_t status;            /* same as the call's return value */
+    int32_t iters;             /* Krylov steps taken (summed over refinement sweeps) */
+    int32_t local_steps;       /* MCG steps whose tau-test chose the local directions */
+    int32_t n_dirs_eff;        /* MCG: non-empty pose subsets actually used */
+    int32_t refinements;       /* MIXED: outer sweeps; 1 for FP64 */
+    int32_t history_cols;      /* MCG: direction columns stored at exit */
+    double rel_residual;       /* recursive |r_i| / |r_0| at exit (of the last sweep for MIXED) */
+    double true_rel_residual;  /* |-b~ - S x| / |b~| recomputed in float64 at exit */
+    double ms;                 /* device time of the solve, CUDA events on the handle's stream */
+} ba_solve_stats;
+
+/* Filled by ba_lm_step. */
+typedef struct ba_lm_stats {
+    int32_t status;
+    int32_t accepted;          /* 1 if F(x + dx) < F(x) and x was updated */
+    int32_t converged;         /* 1 if the relative decrease of F fell below 1e-6 (Section 4.1) */
+    int32_t solver_iters;
+    double cost_before;        /* F(x) (Eq. 1) at entry */
+    double cost_after;         /* F(x + dx) of the trial step */
+    double lambda_used;
+    double lambda_next;
+    double ms;
+} ba_lm_stats;
+
+typedef struct ba_problem ba_problem;
+
+/* Fill *opt with the defaults listed in ba_options. */
+void ba_default_options(ba_options* opt);
+
+/*
+ * Create a problem from cameras, landmarks and observations (Section 3:
+ * n_p poses with d_p = 9, n_l landmarks, one 2-D residual per observation).
+ *   opt        options, or NULL for the defaults
+ *   cams       n_cams x 9, host or device
+ *   pts        n_pts x 3, host or device
+ *   obs_cam    n_obs camera indices in [0, n_cams), host or device, int32
+ *   obs_pt     n_obs landmark indices in [0, n_pts), host or device, int32
+ *   obs_xy     n_obs x 2 measured pixel positions m, host or device
+ *   out        receives the handle
+ * Observations may come in any order.  A landmark may have a single
+ * observation (V_lambda stays definite through the damping).  Errors:
+ * INVALID_ARG for non-positive sizes, n_obs >= 2^31, or an index out of
+ * range; OOM; CUDA.  Uses the current CUDA device and the legacy default
+ * stream until ba_set_stream.
+ */
+int ba_problem_create(const ba_options* opt, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                      const double* cams, const double* pts, const int32_t* obs_cam,
+                      const int32_t* obs_pt, const double* obs_xy, ba_problem** out);
+
+/* Free every device and host allocation of the handle.  NULL is ignored. */
+void ba_problem_destroy(ba_problem* p);
+
+/* Text of the last error of this handle ("" if none).  NULL handle: the last
+ * error of a failed ba_problem_create on this thread. */
+const char* ba_last_error(const ba_problem* p);
+
+/* Order all later work of the handle on `stream` (a cudaStream_t; NULL = legacy default). */
+int ba_set_stream(ba_problem* p, void* stream);
+
+/* Replace the current parameters x = (x_p, x_l) (cams n_cams x 9, pts n_pts x 3; host or
+ * device).  Either pointer may be NULL to keep that part. */
+int ba_set_params(ba_problem* p, const double* cams, const double* pts);
+
+/* Copy the current parameters out (host or device; NULL skips a part). */
+int ba_get_params(const ba_problem* p, double* cams, double* pts);
+
+/*
+ * Linearise at the current parameters and build the reduced camera system for
+ * damping lambda > 0 (Eqs. 2-14): residuals and Jacobians per observation, U_lambda,
+ * V_lambda (Marquardt or identity damping), b_p, b_l, the block-sparse S with its
+ * 9x9 blocks for every co-visible camera pair, b~, and the inverses of the diagonal
+ * blocks of S for the block-Jacobi preconditioner (Section 3.2).  In MIXED precision
+ * a float32 copy of S is made as well (the preconditioner stays float64).  Errors:
+ * INVALID_ARG (lambda <= 0 or not finite), SINGULAR (a V_lambda or S_jj not positive
+ * definite; the system is left unusable), CUDA.
+ */
+int ba_build_normal(ba_problem* p, double lambda);
+
+/*
+ * Solve S dx_p = -b~ by Algorithm 1 (block-Jacobi PCG) from x_0 = 0, stopping when the
+ * recursive residual satisfies |r_{i+1}| < tol |r_0| (the paper's eps, 1e-6 in Section 4.1)
+ * or after max_iters steps (1000 in the paper).  MIXED precision runs float32 PCG sweeps
+ * inside a float64 iterative refinement that stops on the true residual.  The result stays
+ * on the device (ba_get_delta).  Returns OK, NOT_CONVERGED (result still valid), BREAKDOWN,
+ * STATE (no ba_build_normal yet), INVALID_ARG, CUDA.  st may be NULL.
+ */
+int ba_solve_pcg(ba_problem* p, double tol, int32_t max_iters, ba_solve_stats* st);
+
+/*
+ * Solve S dx_p = -b~ by Algorithm 2 (MCG): the poses are split into n_dirs subsets of
+ * ceil(n_cams / n_dirs) consecutive poses (the last holds the remainder); after each
+ * step the tau-test t_i = gamma_i^T alpha_i / (r_{i+1}^T D(S)^{-1} r_{i+1}) < tau selects
+ * one search direction per subset, otherwise one global direction; the small systems
+ * use a float64 pseudo-inverse and every new block is reorthogonalised against all
+ * previous ones (Section 3.2, Eq. 18).  n_dirs = 1 or tau = 0 reduce to PCG plus
+ * reorthogonalisation.  Stop test and returns as ba_solve_pcg; also OOM when the
+ * direction history exceeds max_history columns.
+ */
+int ba_solve_mcg(ba_problem* p, double tol, int32_t max_iters, int32_t n_dirs, double tau,
+                 ba_solve_stats* st);
+
+/*
+ * Copy the last solution out: dxp (n_cams x 9) and, if dxl != NULL, the landmark
+ * update dx_l = -V_lambda^{-1} (b_l + W^T dx_p) (n_pts x 3).  The paper prints
+ * -V^{-1}(-b_l + W^T dx_p) in Eq. 15; the sign used here follows from the second
+ * block row of Eq. 6.  Host or device pointers.  STATE if nothing was solved.
+ */
+int ba_get_delta(ba_problem* p, double* dxp, double* dxl);
+
+/*
+ * One LM iteration (Section 4.1): build at the current lambda (the first call uses
+ * lambda0), solve with `solver` (BA_SOLVER_PCG, or BA_SOLVER_MCG with n_dirs, tau),
+ * back-substitute, evaluate F(x + dx) (Eq. 1), accept when it decreases
+ * (lambda <- max(lambda / 10, 1e-12)) or reject (lambda <- min(10 lambda, 1e16)).
+ * The paper does not state its lambda update; this is the rule used.  st->converged
+ * reports a relative decrease below ftol.  st may be NULL.
+ */
+int ba_lm_step(ba_problem* p, int32_t solver, double lambda0, double tol, int32_t max_iters,
+               int32_t n_dirs, double tau, double ftol, ba_lm_stats* st);
+
+/* F(x) = sum_i |r_i(x)|^2 at the current parameters (Eq. 1). */
+int ba_cost(ba_problem* p, double* cost);
+
+/* ---- standalone camera model and inspection of the built system ---------------------- */
+
+/*
+ * pi(c_j, X_l) for n_obs observations (the camera model above), device pointers only:
+ * cams n_cams x 9, pts n_pts x 3, obs_cam/obs_pt int32 n_obs, out_xy n_obs x 2.
+ * Indices are not checked.  Enqueued on `stream` (cudaStream_t, NULL = legacy default);
+ * returns after enqueueing.
+ */
+int ba_project(int32_t n_cams, int32_t n_pts, int64_t n_obs, const double* cams, const double* pts,
+               const int32_t* obs_cam, const int32_t* obs_pt, double* out_xy, void* stream);
+
+/* Residuals r (n_obs x 2), J_p (n_obs x 2 x 9), J_l (n_obs x 2 x 3) of the last build,
+ * in the caller's observation order (Eqs. 2-4).  Host or device; NULL skips. */
+int ba_get_linearization(const ba_problem* p, double* r, double* Jp, double* Jl);
+
+/* U_lambda (n_cams x 9 x 9), V_lambda (n_pts x 3 x 3), b_p (n_cams x 9), b_l (n_pts x 3)
+ * of the last build (Eqs. 8-11).  Host or device; NULL skips. */
+int ba_get_normal(const ba_problem* p, double* U, double* V, double* b_p, double* b_l);
+
+/* Number of nonzero 9x9 blocks of S (both triangles and the diagonal). */
+int ba_get_schur_nnzb(const ba_problem* p, int64_t* nnzb);
+
+/* S in block-CSR form: row_ptr (n_cams + 1, int64), col (nnzb, int32, ascending within a
+ * row), blocks (nnzb x 9 x 9, row-major), and b~ (n_cams x 9) (Eqs. 13-14).  Host or
+ * device; NULL skips. */
+int ba_get_schur(const ba_problem* p, int64_t* row_ptr, int32_t* col, double* blocks, double* btilde);
+
+/* The inverse diagonal blocks D(S)^{-1} (n_cams x 9 x 9) used by the preconditioner. */
+int ba_get_preconditioner(const ba_problem* p, double* Dinv);
+
+/* Recursive relative residuals |r_{i+1}| / |r_0| of the last solve, one per step; at most
+ * `cap` values are written to `hist` (host or device) and the count to *n. */
+int ba_get_residual_history(const ba_problem* p, double* hist, int32_t cap, int32_t* n);
+
+/* ---- measurement ------------------------------------------------------------------------ */
+
+/* Cumulative number of kernel executions this handle has issued on the device (kernels run
+ * from a replayed CUDA graph count one each). */
+int ba_get_launch_count(const ba_problem* p, int64_t* n);
+
+typedef enum ba_kernel {
+    BA_KERNEL_SPMV = 0,        /* q = S p of Algorithm 1 line 3, at the handle's precision */
+    BA_KERNEL_SCHUR = 1,       /* the S_jk = delta U_j - sum G G^T block build (Eq. 13) */
+    BA_KERNEL_LINEARIZE = 2    /* residuals and Jacobians of every observation (Eqs. 2-4) */
+} ba_kernel;
+
+/*
+ * Mean duration in milliseconds of one launch of `kernel` (ba_kernel), from CUDA events recorded
+ * on the handle's stream around each of `reps` launches; a 256 MiB buffer is written between
+ * launches so that no launch starts with its operands in L2.  Needs ba_build_normal; every
+ * kernel here recomputes the same values, so the built system is unchanged.  STATE before a
+ * build, INVALID_ARG for an unknown kernel or reps < 1.
+ */
+int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BA_H_ */

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libba (include/ba.h): same names, argument marshalling only.
+
+Every computation happens in the CUDA library.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); they are passed by pointer.
+When the library is missing this module raises instead of falling back to
+anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB, ROOT
+
+BA_OK = 0
+BA_ERR_INVALID_ARG = -1
+BA_ERR_OOM = -2
+BA_ERR_CUDA = -3
+BA_ERR_SINGULAR = -4
+BA_ERR_BREAKDOWN = -5
+BA_ERR_NOT_CONVERGED = -6
+BA_ERR_TIMEOUT = -7
+BA_ERR_STATE = -8
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "SINGULAR", -5: "BREAKDOWN",
+                -6: "NOT_CONVERGED", -7: "TIMEOUT", -8: "STATE"}
+
+DAMPING = {"marquardt": 0, "identity": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+SOLVER = {"pcg": 0, "mcg": 1}
+
+
+class ba_options(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_iters", ctypes.c_int32),
+                ("max_history", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class ba_solve_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("local_steps", ctypes.c_int32),
+                ("n_dirs_eff", ctypes.c_int32), ("refinements", ctypes.c_int32), ("history_cols", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ba_lm_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("accepted", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("solver_iters", ctypes.c_int32), ("cost_before", ctypes.c_double), ("cost_after", ctypes.c_double),
+                ("lambda_used", ctypes.c_double), ("lambda_next", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGNATURES = {
+    "ba_default_options": (None, [_P]),
+    "ba_problem_create": (_I32, [_P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P]),
+    "ba_problem_destroy": (None, [_P]),
+    "ba_last_error": (ctypes.c_char_p, [_P]),
+    "ba_set_stream": (_I32, [_P, _P]),
+    "ba_set_params": (_I32, [_P, _P, _P]),
+    "ba_get_params": (_I32, [_P, _P, _P]),
+    "ba_build_normal": (_I32, [_P, _D]),
+    "ba_solve_pcg": (_I32, [_P, _D, _I32, _P]),
+    "ba_solve_mcg": (_I32, [_P, _D, _I32, _I32, _D, _P]),
+    "ba_get_delta": (_I32, [_P, _P, _P]),
+    "ba_lm_step": (_I32, [_P, _I32, _D, _D, _I32, _I32, _D, _D, _P]),
+    "ba_cost": (_I32, [_P, _P]),
+    "ba_project": (_I32, [_I32, _I32, _I64, _P, _P, _P, _P, _P, _P]),
+    "ba_get_linearization": (_I32, [_P, _P, _P, _P]),
+    "ba_get_normal": (_I32, [_P, _P, _P, _P, _P]),
+    "ba_get_schur_nnzb": (_I32, [_P, _P]),
+    "ba_get_schur": (_I32, [_P, _P, _P, _P, _P]),
+    "ba_get_preconditioner": (_I32, [_P, _P]),
+    "ba_get_residual_history": (_I32, [_P, _P, _I32, _P]),
+    "ba_get_launch_count": (_I32, [_P, _P]),
+    "ba_time_kernel": (_I32, [_P, _I32, _I32, _P]),
+}
+KERNEL = {"spmv": 0, "schur": 1, "linearize": 2}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/ba.h."""
+    with open(os.path.join(ROOT, "include", "ba.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ba_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libba; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_2110_04015_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(code: int, handle=None, allow=(BA_OK,)) -> int:
+    if code in allow:
+        return code
+    msg = lib().ba_last_error(handle).decode() if handle is not None or code != BA_OK else ""
+    raise BAError(code, msg)
+
+
+def _f64(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _i32(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.int32)
+    return a
+
+
+def ba_project(cams, pts, obs_cam, obs_pt, out, stream=None) -> None:
+    """pi(c_j, X_l) per observation on the device (all arguments CUDA tensors)."""
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    code = lib().ba_project(int(cams.shape[0]), int(pts.shape[0]), int(obs_cam.shape[0]), _ptr(cams), _ptr(pts),
+                            _ptr(obs_cam), _ptr(obs_pt), _ptr(out), st)
+    _check(code)
+
+
+class Problem:
+    """One bundle-adjustment problem held by the library (a ``ba_problem`` handle)."""
+
+    def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, damping="marquardt", precision="fp64",
+                 chunk_iters=8, max_history=0, inner_tol=1e-3, max_refine=12):
+        L = lib()
+        opt = ba_options()
+        L.ba_default_options(ctypes.byref(opt))
+        opt.damping = DAMPING[damping]
+        opt.precision = PRECISION[precision]
+        opt.chunk_iters = chunk_iters
+        opt.max_history = max_history
+        opt.inner_tol = inner_tol
+        opt.max_refine = max_refine
+        self._keep = [_f64(cams), _f64(pts), _i32(obs_cam), _i32(obs_pt), _f64(obs_xy)]
+        cams, pts, obs_cam, obs_pt, obs_xy = self._keep
+        self.n_cams = int(cams.shape[0])
+        self.n_pts = int(pts.shape[0])
+        self.n_obs = int(obs_cam.shape[0])
+        h = ctypes.c_void_p()
+        code = L.ba_problem_create(ctypes.byref(opt), self.n_cams, self.n_pts, self.n_obs, _ptr(cams), _ptr(pts),
+                                   _ptr(obs_cam), _ptr(obs_pt), _ptr(obs_xy), ctypes.byref(h))
+        self._keep = None
+        if code != BA_OK:
+            raise BAError(code, L.ba_last_error(None).decode())
+        self.h = h
+        self.precision = precision
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the calls of include/ba.h
+    def ba_set_stream(self, stream):
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(lib().ba_set_stream(self.h, st), self.h)
+
+    def ba_set_params(self, cams=None, pts=None):
+        cams, pts = _f64(cams), _f64(pts)
+        _check(lib().ba_set_params(self.h, _ptr(cams), _ptr(pts)), self.h)
+
+    def ba_get_params(self, cams=None, pts=None):
+        if cams is None and pts is None:
+            cams = np.empty((self.n_cams, 9))
+            pts = np.empty((self.n_pts, 3))
+        _check(lib().ba_get_params(self.h, _ptr(cams), _ptr(pts)), self.h)
+        return cams, pts
+
+    def ba_build_normal(self, lam: float):
+        _check(lib().ba_build_normal(self.h, float(lam)), self.h)
+
+    def ba_solve_pcg(self, tol=1e-6, max_iters=1000) -> dict:
+        st = ba_solve_stats()
+        code = lib().ba_solve_pcg(self.h, float(tol), int(max_iters), ctypes.byref(st))
+        _check(code, self.h, allow=(BA_OK, BA_ERR_NOT_CONVERGED))
+        return st.as_dict()
+
+    def ba_solve_mcg(self, tol=1e-6, max_iters=1000, n_dirs=8, tau=3.0) -> dict:
+        st = ba_solve_stats()
+        code = lib().ba_solve_mcg(self.h, float(tol), int(max_iters), int(n_dirs), float(tau), ctypes.byref(st))
+        _check(code, self.h, allow=(BA_OK, BA_ERR_NOT_CONVERGED))
+        return st.as_dict()
+
+    def ba_get_delta(self, dxp=None, dxl=None, landmarks=False):
+        if dxp is None:
+            dxp = np.empty((self.n_cams, 9))
+        if dxl is None and landmarks:
+            dxl = np.empty((self.n_pts, 3))
+        _check(lib().ba_get_delta(self.h, _ptr(dxp), _ptr(dxl)), self.h)
+        return (dxp, dxl) if landmarks else dxp
+
+    def ba_lm_step(self, solver="pcg", lambda0=1e-4, tol=1e-6, max_iters=1000, n_dirs=8, tau=3.0,
+                   ftol=1e-6) -> dict:
+        st = ba_lm_stats()
+        code = lib().ba_lm_step(self.h, SOLVER[solver], float(lambda0), float(tol), int(max_iters), int(n_dirs),
+                                float(tau), float(ftol), ctypes.byref(st))
+        _check(code, self.h)
+        return st.as_dict()
+
+    def ba_cost(self) -> float:
+        c = ctypes.c_double()
+        _check(lib().ba_cost(self.h, ctypes.byref(c)), self.h)
+        return c.value
+
+    def ba_get_linearization(self):
+        r = np.empty((self.n_obs, 2))
+        Jp = np.empty((self.n_obs, 2, 9))
+        Jl = np.empty((self.n_obs, 2, 3))
+        _check(lib().ba_get_linearization(self.h, _ptr(r), _ptr(Jp), _ptr(Jl)), self.h)
+        return r, Jp, Jl
+
+    def ba_get_normal(self):
+        U = np.empty((self.n_cams, 9, 9))
+        V = np.empty((self.n_pts, 3, 3))
+        bp = np.empty((self.n_cams, 9))
+        bl = np.empty((self.n_pts, 3))
+        _check(lib().ba_get_normal(self.h, _ptr(U), _ptr(V), _ptr(bp), _ptr(bl)), self.h)
+        return U, V, bp, bl
+
+    def ba_get_schur_nnzb(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().ba_get_schur_nnzb(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def ba_get_schur(self, blocks=True):
+        nnzb = self.ba_get_schur_nnzb()
+        row_ptr = np.empty(self.n_cams + 1, np.int64)
+        col = np.empty(nnzb, np.int32)
+        B = np.empty((nnzb, 9, 9)) if blocks else None
+        bt = np.empty((self.n_cams, 9))
+        _check(lib().ba_get_schur(self.h, _ptr(row_ptr), _ptr(col), _ptr(B), _ptr(bt)), self.h)
+        return row_ptr, col, B, bt
+
+    def ba_get_preconditioner(self):
+        D = np.empty((self.n_cams, 9, 9))
+        _check(lib().ba_get_preconditioner(self.h, _ptr(D)), self.h)
+        return D
+
+    def ba_get_residual_history(self, cap=100000):
+        h = np.empty(cap)
+        n = ctypes.c_int32()
+        _check(lib().ba_get_residual_history(self.h, _ptr(h), int(cap), ctypes.byref(n)), self.h)
+        return h[:min(n.value, cap)].copy()
+
+    def ba_get_launch_count(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().ba_get_launch_count(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def ba_time_kernel(self, kernel="spmv", reps=10) -> float:
+        ms = ctypes.c_double()
+        _check(lib().ba_time_kernel(self.h, KERNEL[kernel], int(reps), ctypes.byref(ms)), self.h)
+        return ms.value
+
+    # short aliases
+    build_normal = ba_build_normal
+    solve_pcg = ba_solve_pcg
+    solve_mcg = ba_solve_mcg
+    get_delta = ba_get_delta
+    lm_step = ba_lm_step
+    cost = ba_cost

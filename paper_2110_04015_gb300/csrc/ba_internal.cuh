@@ -1,0 +1,157 @@
+// Internal declarations shared by the translation units of libba.
+//
+// Data layout in device memory (one problem):
+//   observations are kept sorted by landmark ("point order"); perm maps a
+//   point-order slot back to the caller's observation index.
+//   per observation : r (2), Jc (2x9), Jl (2x3), G = W_o L_l^{-T} (9x3)
+//   per landmark    : V_lambda (3x3), its Cholesky factor L (6 packed),
+//                     b_l (3), e = L^{-1} b_l (3)
+//   per camera      : U_lambda (9x9), b_p (9), b~ (9), D_j^{-1} (9x9)
+//   S               : block-CSR over cameras, every nonzero 9x9 block of both
+//                     triangles.  The blocks of block-row j are stored as a
+//                     slab of 81 x nnz_j values, entry-major: entry e of the
+//                     q-th block of the row sits at slab_j[e * nnz_j + q], so a
+//                     warp whose lanes take consecutive blocks of a row reads
+//                     consecutive words.
+// With G_o = W_o L_l^{-T} (V_l = L_l L_l^T) the Schur complement of Eq. 13 is
+//   S_jk = delta_jk U_j - sum_{l seen by j and k} G_jl G_kl^T,
+// and b~_j = b_p,j - sum_{o in camera j} G_o e_l (Eq. 14).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/ba.h"
+
+namespace ba {
+
+constexpr int kThreads = 256;
+constexpr int kMaxDirs = 16;   // widest direction block held by the small FP64 solves
+
+#define BA_CUDA_TRY(expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            throw ::ba::Error(BA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                   \
+    } while (0)
+
+struct Error {
+    int code;
+    std::string msg;
+    Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+// Immutable structure of a problem (built once at create).
+struct Structure {
+    int32_t n_c = 0, n_l = 0;
+    int64_t n_o = 0;
+    // observations in point order
+    int32_t* obs_cam = nullptr;   // n_o
+    int32_t* obs_pt = nullptr;    // n_o
+    int32_t* perm = nullptr;      // n_o: point-order slot -> caller index
+    double* obs_xy = nullptr;     // n_o x 2
+    int64_t* pt_ptr = nullptr;    // n_l + 1
+    int64_t* cam_ptr = nullptr;   // n_c + 1
+    int32_t* cam_obs = nullptr;   // n_o: point-order slots grouped by camera
+    // S pattern (full)
+    int64_t nnzb = 0;
+    int64_t* row_ptr = nullptr;   // n_c + 1
+    int32_t* col = nullptr;       // nnzb
+    int32_t* diag_pos = nullptr;  // n_c: block index of S_jj
+    // upper blocks (j <= k) with the observation pairs that feed them
+    int64_t n_up = 0;
+    int64_t n_pairs = 0;
+    int32_t* up_j = nullptr;      // n_up
+    int32_t* up_k = nullptr;      // n_up
+    int64_t* up_pos = nullptr;    // n_up: block index of (j, k)
+    int64_t* up_mir = nullptr;    // n_up: block index of (k, j), -1 on the diagonal
+    int64_t* up_pair_ptr = nullptr;  // n_up + 1
+    int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
+};
+
+// The linearised system at the current parameters (rebuilt by ba_build_normal).
+struct System {
+    double* cams = nullptr;   // n_c x 9 current parameters
+    double* pts = nullptr;    // n_l x 3
+    double* r = nullptr;      // n_o x 2
+    double* Jc = nullptr;     // n_o x 18
+    double* Jl = nullptr;     // n_o x 6
+    double* G = nullptr;      // n_o x 27
+    double* V = nullptr;      // n_l x 9
+    double* L = nullptr;      // n_l x 6
+    double* bl = nullptr;     // n_l x 3
+    double* e = nullptr;      // n_l x 3
+    double* U = nullptr;      // n_c x 81
+    double* bp = nullptr;     // n_c x 9
+    double* bt = nullptr;     // n_c x 9
+    double* S = nullptr;      // nnzb x 81 (slab layout)
+    double* Dinv = nullptr;   // n_c x 81
+    float* S32 = nullptr;     // float copy of S for the mixed-precision inner solves
+    int* status = nullptr;    // device error word of the build
+    double lambda = 0.0;
+    bool built = false;
+};
+
+// ---- launch wrappers (k_build.cu) -----------------------------------------------------
+void launch_project(int64_t n_o, const double* cams, const double* pts, const int32_t* oc,
+                    const int32_t* op, double* out, cudaStream_t st);
+void launch_linearize(const Structure& s, System& y, cudaStream_t st);
+void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+void launch_obs_G(const Structure& s, System& y, cudaStream_t st);
+void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+void launch_schur(const Structure& s, System& y, cudaStream_t st);
+void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st);
+void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st);
+void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl,
+                            cudaStream_t st);
+void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial,
+                 int nparts, cudaStream_t st);
+void launch_add_params(const double* a, const double* da, double* out, int64_t n, cudaStream_t st);
+void launch_unpermute(const double* in, const int32_t* perm, double* out, int64_t n_o, int width,
+                      cudaStream_t st);
+void launch_unslab(const Structure& s, const double* S, double* out, cudaStream_t st);
+
+// ---- solver (k_solve.cu) -------------------------------------------------------------------
+struct SolveArgs {
+    int mcg = 0;            // 0: Algorithm 1, 1: Algorithm 2
+    double tol = 1e-6;
+    int max_iters = 1000;
+    int n_dirs = 1;
+    double tau = 0.0;
+    int chunk = 8;
+    int precision = BA_PRECISION_FP64;
+    double inner_tol = 1e-3;
+    int max_refine = 12;
+    int64_t max_history = 0;
+};
+
+struct SolveOut {
+    int status = BA_OK;
+    int iters = 0;
+    int local_steps = 0;
+    int n_eff = 1;
+    int refinements = 0;
+    int64_t history_cols = 0;
+    double rel_residual = 0.0;
+    double true_rel_residual = 0.0;
+    double ms = 0.0;
+    int64_t launches = 0;   // kernel executions issued by the solve
+};
+
+struct Solver;   // workspace, defined in k_solve.cu
+Solver* solver_create();
+void solver_destroy(Solver* w);
+// Solve S x = -b~ into x (device, 9 n_c); history of recursive residuals kept in the workspace.
+void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x,
+                SolveOut& out, cudaStream_t st);
+int solver_history(const Solver* w, const double** hist);
+// Mean ms of one launch of the PCG product q = S p (float64 or float32 system), L2 flushed between launches.
+double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, cudaStream_t st);
+void flush_l2(cudaStream_t st);
+
+int num_sms();
+
+}  // namespace ba

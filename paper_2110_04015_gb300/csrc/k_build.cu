@@ -1,0 +1,613 @@
+// Linearisation and reduced-camera-system build (Section 3.1, Eqs. 2-14).
+//
+//   k_linearize     one thread per observation: r, J_p (2x9), J_l (2x3)
+//   k_landmarks     one thread per landmark: V_lambda, b_l, Cholesky V = L L^T, e = L^{-1} b_l
+//   k_obs_G         one thread per observation: G_o = (J_p^T J_l) L^{-T}
+//   k_cameras       one CTA per camera: U_lambda, b_p, b~ = b_p - sum G_o e_l
+//   k_schur         one warp per upper block (j <= k): S_jk = delta U_j - sum G_o G_o'^T,
+//                   written to (j, k) and transposed to (k, j)
+//   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
+// Every kernel uses grid-stride loops and 64-bit indices.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ba_internal.cuh"
+
+namespace ba {
+
+namespace {
+
+inline int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    int cap = num_sms() * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return static_cast<int>(g);
+}
+
+__device__ __forceinline__ int64_t gtid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
+
+// Rodrigues coefficients A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3,
+// by their Taylor series below th = 1e-4 where the closed forms cancel.
+__device__ __forceinline__ void rot_coeffs(double th2, double& A, double& B, double& C) {
+    if (th2 < 1e-8) {
+        A = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0);
+        B = 0.5 - th2 / 24.0 * (1.0 - th2 / 30.0);
+        C = 1.0 / 6.0 - th2 / 120.0 * (1.0 - th2 / 42.0);
+    } else {
+        double th = sqrt(th2);
+        double s, c;
+        sincos(th, &s, &c);
+        A = s / th;
+        B = (1.0 - c) / th2;
+        C = (th - s) / (th2 * th);
+    }
+}
+
+// R = I + A [w]x + B [w]x^2 with [w]x^2 = w w^T - th^2 I, row-major.
+__device__ __forceinline__ void rot_matrix(const double* w, double A, double B, double th2, double* R) {
+    R[0] = 1.0 + B * (w[0] * w[0] - th2);
+    R[1] = -A * w[2] + B * w[0] * w[1];
+    R[2] = A * w[1] + B * w[0] * w[2];
+    R[3] = A * w[2] + B * w[0] * w[1];
+    R[4] = 1.0 + B * (w[1] * w[1] - th2);
+    R[5] = -A * w[0] + B * w[1] * w[2];
+    R[6] = -A * w[1] + B * w[0] * w[2];
+    R[7] = A * w[0] + B * w[1] * w[2];
+    R[8] = 1.0 + B * (w[2] * w[2] - th2);
+}
+
+__device__ __forceinline__ void bal_project(const double* c, const double* X, double* out) {
+    double w[3] = {c[0], c[1], c[2]};
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double A, B, C, R[9];
+    rot_coeffs(th2, A, B, C);
+    rot_matrix(w, A, B, th2, R);
+    double P0 = R[0] * X[0] + R[1] * X[1] + R[2] * X[2] + c[3];
+    double P1 = R[3] * X[0] + R[4] * X[1] + R[5] * X[2] + c[4];
+    double P2 = R[6] * X[0] + R[7] * X[1] + R[8] * X[2] + c[5];
+    double p0 = -P0 / P2, p1 = -P1 / P2;
+    double n2 = p0 * p0 + p1 * p1;
+    double rho = 1.0 + c[7] * n2 + c[8] * n2 * n2;
+    out[0] = c[6] * rho * p0;
+    out[1] = c[6] * rho * p1;
+}
+
+// Residual and Jacobian blocks of one observation.  d(R X)/d omega = -R [X]x J_r(omega),
+// J_r = I - B [w]x + C [w]x^2 the right Jacobian of the rotation exponential.
+__device__ __forceinline__ void bal_linearize(const double* c, const double* X, const double* m,
+                                              double* r, double* Jc, double* Jl) {
+    double w[3] = {c[0], c[1], c[2]};
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double A, B, C, R[9];
+    rot_coeffs(th2, A, B, C);
+    rot_matrix(w, A, B, th2, R);
+    double P[3];
+    for (int a = 0; a < 3; ++a) P[a] = R[3 * a] * X[0] + R[3 * a + 1] * X[1] + R[3 * a + 2] * X[2] + c[3 + a];
+
+    // J_r
+    double Jr[9];
+    Jr[0] = 1.0 + C * (w[0] * w[0] - th2);
+    Jr[1] = B * w[2] + C * w[0] * w[1];
+    Jr[2] = -B * w[1] + C * w[0] * w[2];
+    Jr[3] = -B * w[2] + C * w[0] * w[1];
+    Jr[4] = 1.0 + C * (w[1] * w[1] - th2);
+    Jr[5] = B * w[0] + C * w[1] * w[2];
+    Jr[6] = B * w[1] + C * w[0] * w[2];
+    Jr[7] = -B * w[0] + C * w[1] * w[2];
+    Jr[8] = 1.0 + C * (w[2] * w[2] - th2);
+    // M = [X]x J_r ; rows of [X]x: (0, -X2, X1), (X2, 0, -X0), (-X1, X0, 0)
+    double M[9];
+    for (int b = 0; b < 3; ++b) {
+        M[b] = -X[2] * Jr[3 + b] + X[1] * Jr[6 + b];
+        M[3 + b] = X[2] * Jr[b] - X[0] * Jr[6 + b];
+        M[6 + b] = -X[1] * Jr[b] + X[0] * Jr[3 + b];
+    }
+    // dP/dw = -R M
+    double dPdw[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            dPdw[3 * a + b] = -(R[3 * a] * M[b] + R[3 * a + 1] * M[3 + b] + R[3 * a + 2] * M[6 + b]);
+
+    double iz = 1.0 / P[2];
+    double p0 = -P[0] * iz, p1 = -P[1] * iz;
+    double f = c[6], k1 = c[7], k2 = c[8];
+    double n2 = p0 * p0 + p1 * p1;
+    double rho = 1.0 + k1 * n2 + k2 * n2 * n2;
+    double drho = 2.0 * (k1 + 2.0 * k2 * n2);
+    // dpi/dp = f (rho I + drho p p^T)
+    double E00 = f * (rho + drho * p0 * p0), E01 = f * drho * p0 * p1, E11 = f * (rho + drho * p1 * p1);
+    // dp/dP = [[-iz, 0, -p0 iz], [0, -iz, -p1 iz]]  (P_x iz^2 = -p0 iz)
+    double D[6];
+    D[0] = -E00 * iz;
+    D[1] = -E01 * iz;
+    D[2] = -(E00 * p0 + E01 * p1) * iz;
+    D[3] = -E01 * iz;
+    D[4] = -E11 * iz;
+    D[5] = -(E01 * p0 + E11 * p1) * iz;
+
+    r[0] = f * rho * p0 - m[0];
+    r[1] = f * rho * p1 - m[1];
+    for (int a = 0; a < 2; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            Jc[9 * a + b] = D[3 * a] * dPdw[b] + D[3 * a + 1] * dPdw[3 + b] + D[3 * a + 2] * dPdw[6 + b];
+            Jc[9 * a + 3 + b] = D[3 * a + b];
+            Jl[3 * a + b] = D[3 * a] * R[b] + D[3 * a + 1] * R[3 + b] + D[3 * a + 2] * R[6 + b];
+        }
+    }
+    Jc[6] = rho * p0;
+    Jc[15] = rho * p1;
+    Jc[7] = f * n2 * p0;
+    Jc[16] = f * n2 * p1;
+    Jc[8] = f * n2 * n2 * p0;
+    Jc[17] = f * n2 * n2 * p1;
+}
+
+__device__ __forceinline__ double damp(double d, int damping, double lambda) {
+    if (damping == BA_DAMPING_IDENTITY) return d + lambda;
+    double c = fmin(fmax(d, 1e-6), 1e32);
+    return d + lambda * c;
+}
+
+__global__ void k_project(int64_t n_o, const double* __restrict__ cams, const double* __restrict__ pts,
+                          const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                          double* __restrict__ out) {
+    for (int64_t i = gtid(); i < n_o; i += gstride()) {
+        double c[9], X[3], pr[2];
+        const double* cp = cams + int64_t(oc[i]) * 9;
+        const double* xp = pts + int64_t(op[i]) * 3;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c[k] = __ldg(cp + k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) X[k] = __ldg(xp + k);
+        bal_project(c, X, pr);
+        out[2 * i] = pr[0];
+        out[2 * i + 1] = pr[1];
+    }
+}
+
+__global__ void k_linearize(int64_t n_o, const double* __restrict__ cams, const double* __restrict__ pts,
+                            const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                            const double* __restrict__ xy, double* __restrict__ r, double* __restrict__ Jc,
+                            double* __restrict__ Jl) {
+    for (int64_t i = gtid(); i < n_o; i += gstride()) {
+        double c[9], X[3], m[2], rr[2], jc[18], jl[6];
+        const double* cp = cams + int64_t(oc[i]) * 9;
+        const double* xp = pts + int64_t(op[i]) * 3;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c[k] = __ldg(cp + k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) X[k] = __ldg(xp + k);
+        m[0] = xy[2 * i];
+        m[1] = xy[2 * i + 1];
+        bal_linearize(c, X, m, rr, jc, jl);
+        r[2 * i] = rr[0];
+        r[2 * i + 1] = rr[1];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) Jc[18 * i + k] = jc[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Jl[6 * i + k] = jl[k];
+    }
+}
+
+// V_lambda = sum J_l^T J_l + damping, b_l = sum J_l^T r, V = L L^T, e = L^{-1} b_l.
+__global__ void k_landmarks(int32_t n_l, const int64_t* __restrict__ pt_ptr, const double* __restrict__ r,
+                            const double* __restrict__ Jl, int damping, double lambda, double* __restrict__ Vout,
+                            double* __restrict__ Lout, double* __restrict__ blout, double* __restrict__ eout,
+                            int* status) {
+    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+        double v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, b0 = 0, b1 = 0, b2 = 0;
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
+            const double* j = Jl + 6 * o;
+            double a0 = j[0], a1 = j[1], a2 = j[2], c0 = j[3], c1 = j[4], c2 = j[5];
+            double r0 = r[2 * o], r1 = r[2 * o + 1];
+            v00 += a0 * a0 + c0 * c0;
+            v01 += a0 * a1 + c0 * c1;
+            v02 += a0 * a2 + c0 * c2;
+            v11 += a1 * a1 + c1 * c1;
+            v12 += a1 * a2 + c1 * c2;
+            v22 += a2 * a2 + c2 * c2;
+            b0 += a0 * r0 + c0 * r1;
+            b1 += a1 * r0 + c1 * r1;
+            b2 += a2 * r0 + c2 * r1;
+        }
+        v00 = damp(v00, damping, lambda);
+        v11 = damp(v11, damping, lambda);
+        v22 = damp(v22, damping, lambda);
+        double* V = Vout + 9 * l;
+        V[0] = v00; V[1] = v01; V[2] = v02;
+        V[3] = v01; V[4] = v11; V[5] = v12;
+        V[6] = v02; V[7] = v12; V[8] = v22;
+        // Cholesky
+        double l00 = v00 > 0 ? sqrt(v00) : 0.0;
+        double l10 = v01 / l00, l20 = v02 / l00;
+        double d11 = v11 - l10 * l10;
+        double l11 = d11 > 0 ? sqrt(d11) : 0.0;
+        double l21 = (v12 - l20 * l10) / l11;
+        double d22 = v22 - l20 * l20 - l21 * l21;
+        double l22 = d22 > 0 ? sqrt(d22) : 0.0;
+        if (!(l00 > 0 && l11 > 0 && l22 > 0)) atomicExch(status, BA_ERR_SINGULAR);
+        double* L = Lout + 6 * l;
+        L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = l22;
+        blout[3 * l] = b0;
+        blout[3 * l + 1] = b1;
+        blout[3 * l + 2] = b2;
+        double e0 = b0 / l00;
+        double e1 = (b1 - l10 * e0) / l11;
+        double e2 = (b2 - l20 * e0 - l21 * e1) / l22;
+        eout[3 * l] = e0;
+        eout[3 * l + 1] = e1;
+        eout[3 * l + 2] = e2;
+    }
+}
+
+// G_o = W_o L^{-T}, W_o = J_p^T J_l (9x3); each row g solves L g^T = w^T.
+__global__ void k_obs_G(int64_t n_o, const int32_t* __restrict__ op, const double* __restrict__ Jc,
+                        const double* __restrict__ Jl, const double* __restrict__ Lall, double* __restrict__ G) {
+    for (int64_t o = gtid(); o < n_o; o += gstride()) {
+        const double* L = Lall + 6 * int64_t(op[o]);
+        double l00 = L[0], l10 = L[1], l11 = L[2], l20 = L[3], l21 = L[4], l22 = L[5];
+        double jl[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) jl[k] = Jl[6 * o + k];
+        const double* jc = Jc + 18 * o;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            double ca = jc[a], cb = jc[9 + a];
+            double w0 = ca * jl[0] + cb * jl[3];
+            double w1 = ca * jl[1] + cb * jl[4];
+            double w2 = ca * jl[2] + cb * jl[5];
+            double g0 = w0 / l00;
+            double g1 = (w1 - l10 * g0) / l11;
+            double g2 = (w2 - l20 * g0 - l21 * g1) / l22;
+            G[27 * o + 3 * a] = g0;
+            G[27 * o + 3 * a + 1] = g1;
+            G[27 * o + 3 * a + 2] = g2;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    return v;
+}
+
+constexpr int kCamThreads = 128;
+
+// U_lambda, b_p and b~ of one camera per CTA.
+__global__ void __launch_bounds__(kCamThreads) k_cameras(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const int32_t* __restrict__ op, const double* __restrict__ r, const double* __restrict__ Jc,
+    const double* __restrict__ G, const double* __restrict__ e, int damping, double lambda,
+    double* __restrict__ Uout, double* __restrict__ bpout, double* __restrict__ btout) {
+    __shared__ double red[kCamThreads / 32][64];
+    __shared__ double fin[64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        double u[45], b[9];
+#pragma unroll
+        for (int k = 0; k < 45; ++k) u[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b[k] = 0.0;
+        const int64_t beg = cam_ptr[j], end = cam_ptr[j + 1];
+        for (int64_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            double c0[9], c1[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                c0[k] = Jc[18 * o + k];
+                c1[k] = Jc[18 * o + 9 + k];
+            }
+            double r0 = r[2 * o], r1 = r[2 * o + 1];
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+#pragma unroll
+                for (int bb = a; bb < 9; ++bb) u[t++] += c0[a] * c0[bb] + c1[a] * c1[bb];
+                b[a] += c0[a] * r0 + c1[a] * r1;
+            }
+        }
+        // reduce the 54 sums
+#pragma unroll
+        for (int k = 0; k < 54; ++k) {
+            double v = warp_sum(k < 45 ? u[k] : b[k - 45]);
+            if (lane == 0) red[wid][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 54) {
+            double v = 0;
+            for (int w = 0; w < kCamThreads / 32; ++w) v += red[w][threadIdx.x];
+            fin[threadIdx.x] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 81) {
+            int a = threadIdx.x / 9, bb = threadIdx.x % 9;
+            int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+            int idx = lo * 9 - lo * (lo - 1) / 2 + (hi - lo);
+            double v = fin[idx];
+            if (a == bb) v = damp(v, damping, lambda);
+            Uout[81 * int64_t(j) + threadIdx.x] = v;
+        }
+        __syncthreads();
+        // b~ = b_p - sum_o G_o e_l
+        double t9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) t9[k] = 0.0;
+        for (int64_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const double* el = e + 3 * int64_t(op[o]);
+            double e0 = el[0], e1 = el[1], e2 = el[2];
+            const double* g = G + 27 * o;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) t9[a] += g[3 * a] * e0 + g[3 * a + 1] * e1 + g[3 * a + 2] * e2;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double v = warp_sum(t9[k]);
+            if (lane == 0) red[wid][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            double v = 0;
+            for (int w = 0; w < kCamThreads / 32; ++w) v += red[w][threadIdx.x];
+            double bpv = fin[45 + threadIdx.x];
+            bpout[9 * int64_t(j) + threadIdx.x] = bpv;
+            btout[9 * int64_t(j) + threadIdx.x] = bpv - v;
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per upper block (j, k): acc = sum over observation pairs of G_o G_o'^T.
+__global__ void k_schur(int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
+                        const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir,
+                        const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
+                        const double* __restrict__ G, const double* __restrict__ U,
+                        const int64_t* __restrict__ row_ptr, double* __restrict__ S) {
+    __shared__ double sg[kThreads / 32][2][28];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = gstride() >> 5;
+    // entries handled by this lane: e = lane, lane + 32, lane + 64 (< 81)
+    const int e0 = lane, e1 = lane + 32, e2 = lane + 64;
+    const int a0 = e0 / 9, b0 = e0 % 9, a1 = e1 / 9, b1 = e1 % 9;
+    const int a2 = e2 < 81 ? e2 / 9 : 0, b2 = e2 < 81 ? e2 % 9 : 0;
+    for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        const int64_t pb = pair_ptr[u], pe = pair_ptr[u + 1];
+        for (int64_t q = pb; q < pe; ++q) {
+            const int2 pr = pairs[q];
+            __syncwarp();
+            if (lane < 27) {
+                sg[wid][0][lane] = G[27 * int64_t(pr.x) + lane];
+                sg[wid][1][lane] = G[27 * int64_t(pr.y) + lane];
+            }
+            __syncwarp();
+            const double* g1 = sg[wid][0];
+            const double* g2 = sg[wid][1];
+            s0 += g1[3 * a0] * g2[3 * b0] + g1[3 * a0 + 1] * g2[3 * b0 + 1] + g1[3 * a0 + 2] * g2[3 * b0 + 2];
+            s1 += g1[3 * a1] * g2[3 * b1] + g1[3 * a1 + 1] * g2[3 * b1 + 1] + g1[3 * a1 + 2] * g2[3 * b1 + 2];
+            s2 += g1[3 * a2] * g2[3 * b2] + g1[3 * a2 + 1] * g2[3 * b2 + 1] + g1[3 * a2 + 2] * g2[3 * b2 + 2];
+        }
+        const int j = up_j[u], k = up_k[u];
+        const int64_t pos = up_pos[u], mir = up_mir[u];
+        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
+        double* slab = S + rj * 81 + (pos - rj);
+        const double* Uj = U + 81 * int64_t(j);
+        const bool diag = (j == k);
+        slab[e0 * nj] = (diag ? Uj[e0] : 0.0) - s0;
+        slab[e1 * nj] = (diag ? Uj[e1] : 0.0) - s1;
+        if (e2 < 81) slab[e2 * nj] = (diag ? Uj[e2] : 0.0) - s2;
+        if (!diag) {
+            const int64_t rk = row_ptr[k], nk = row_ptr[k + 1] - rk;
+            double* mslab = S + rk * 81 + (mir - rk);
+            mslab[(b0 * 9 + a0) * nk] = -s0;
+            mslab[(b1 * 9 + a1) * nk] = -s1;
+            if (e2 < 81) mslab[(b2 * 9 + a2) * nk] = -s2;
+        }
+    }
+}
+
+// D_j^{-1} = (S_jj)^{-1} = L^{-T} L^{-1} from the Cholesky factor of the diagonal block.
+__global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ diag_pos,
+                               const double* __restrict__ S, double* __restrict__ Dinv, int* status) {
+    for (int64_t j = gtid(); j < n_c; j += gstride()) {
+        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
+        const double* slab = S + rj * 81 + (diag_pos[j] - rj);
+        double L[81];
+        for (int a = 0; a < 9; ++a)
+            for (int b = 0; b < 9; ++b) L[9 * a + b] = slab[(9 * a + b) * nj];
+        bool ok = true;
+        for (int c = 0; c < 9; ++c) {
+            double d = L[9 * c + c];
+            for (int k = 0; k < c; ++k) d -= L[9 * c + k] * L[9 * c + k];
+            if (!(d > 0.0)) { ok = false; d = 1.0; }
+            double lc = sqrt(d);
+            L[9 * c + c] = lc;
+            for (int a = c + 1; a < 9; ++a) {
+                double v = L[9 * a + c];
+                for (int k = 0; k < c; ++k) v -= L[9 * a + k] * L[9 * c + k];
+                L[9 * a + c] = v / lc;
+            }
+        }
+        if (!ok) atomicExch(status, BA_ERR_SINGULAR);
+        // Li = L^{-1} (lower), column by column
+        double Li[81];
+        for (int k = 0; k < 81; ++k) Li[k] = 0.0;
+        for (int c = 0; c < 9; ++c) {
+            Li[9 * c + c] = 1.0 / L[9 * c + c];
+            for (int a = c + 1; a < 9; ++a) {
+                double v = 0.0;
+                for (int k = c; k < a; ++k) v -= L[9 * a + k] * Li[9 * k + c];
+                Li[9 * a + c] = v / L[9 * a + a];
+            }
+        }
+        double* D = Dinv + 81 * j;
+        for (int a = 0; a < 9; ++a) {
+            for (int b = a; b < 9; ++b) {
+                double v = 0.0;
+                for (int k = b; k < 9; ++k) v += Li[9 * k + a] * Li[9 * k + b];
+                D[9 * a + b] = v;
+                D[9 * b + a] = v;
+            }
+        }
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) out[i] = static_cast<float>(in[i]);
+}
+
+// dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
+__global__ void k_back_substitute(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
+                                  const double* __restrict__ G, const double* __restrict__ Lall,
+                                  const double* __restrict__ e, const double* __restrict__ dxp,
+                                  double* __restrict__ dxl) {
+    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+        double a0 = e[3 * l], a1 = e[3 * l + 1], a2 = e[3 * l + 2];
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
+            const double* g = G + 27 * o;
+            const double* x = dxp + 9 * int64_t(oc[o]);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                double xa = x[a];
+                a0 += g[3 * a] * xa;
+                a1 += g[3 * a + 1] * xa;
+                a2 += g[3 * a + 2] * xa;
+            }
+        }
+        const double* L = Lall + 6 * l;
+        double y2 = a2 / L[5];
+        double y1 = (a1 - L[4] * y2) / L[2];
+        double y0 = (a0 - L[1] * y1 - L[3] * y2) / L[0];
+        dxl[3 * l] = -y0;
+        dxl[3 * l + 1] = -y1;
+        dxl[3 * l + 2] = -y2;
+    }
+}
+
+// partial[b] = sum over this CTA's observations of |pi - m|^2
+__global__ void k_cost(int64_t n_o, const double* __restrict__ cams, const double* __restrict__ pts,
+                       const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                       const double* __restrict__ xy, double* __restrict__ partial) {
+    __shared__ double red[kThreads / 32];
+    double acc = 0.0;
+    for (int64_t i = gtid(); i < n_o; i += gstride()) {
+        double c[9], X[3], pr[2];
+        const double* cp = cams + int64_t(oc[i]) * 9;
+        const double* xp = pts + int64_t(op[i]) * 3;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c[k] = cp[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) X[k] = xp[k];
+        bal_project(c, X, pr);
+        double d0 = pr[0] - xy[2 * i], d1 = pr[1] - xy[2 * i + 1];
+        acc += d0 * d0 + d1 * d1;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0;
+        for (int w = 0; w < kThreads / 32; ++w) v += red[w];
+        partial[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_add(const double* __restrict__ a, const double* __restrict__ da, double* __restrict__ out, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) out[i] = a[i] + da[i];
+}
+
+__global__ void k_unpermute(const double* __restrict__ in, const int32_t* __restrict__ perm, double* __restrict__ out,
+                            int64_t n_o, int width) {
+    for (int64_t i = gtid(); i < n_o * width; i += gstride()) {
+        int64_t o = i / width;
+        int c = static_cast<int>(i - o * width);
+        out[int64_t(perm[o]) * width + c] = in[i];
+    }
+}
+
+// slab layout -> row-major 9x9 blocks
+__global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const double* __restrict__ S,
+                         double* __restrict__ out) {
+    const int64_t total = row_ptr[n_c] * 81;
+    for (int64_t i = gtid(); i < total; i += gstride()) {
+        const int64_t q = i / 81;
+        const int e = static_cast<int>(i - q * 81);
+        // row of block q by binary search
+        int lo = 0, hi = n_c;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (row_ptr[mid] <= q) lo = mid; else hi = mid;
+        }
+        const int64_t rj = row_ptr[lo], nj = row_ptr[lo + 1] - rj;
+        out[i] = S[rj * 81 + int64_t(e) * nj + (q - rj)];
+    }
+}
+
+}  // namespace
+
+void launch_project(int64_t n_o, const double* cams, const double* pts, const int32_t* oc, const int32_t* op,
+                    double* out, cudaStream_t st) {
+    if (n_o <= 0) return;
+    k_project<<<grid_for(n_o, kThreads), kThreads, 0, st>>>(n_o, cams, pts, oc, op, out);
+}
+
+void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
+    k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.cams, y.pts, s.obs_cam, s.obs_pt,
+                                                                 s.obs_xy, y.r, y.Jc, y.Jl);
+}
+
+void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
+    k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, y.r, y.Jl, damping, lambda, y.V,
+                                                                 y.L, y.bl, y.e, y.status);
+}
+
+void launch_obs_G(const Structure& s, System& y, cudaStream_t st) {
+    k_obs_G<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_pt, y.Jc, y.Jl, y.L, y.G);
+}
+
+void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
+    int g = s.n_c < num_sms() * 8 ? s.n_c : num_sms() * 8;
+    k_cameras<<<g, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, y.G, y.e, damping,
+                                         lambda, y.U, y.bp, y.bt);
+}
+
+void launch_schur(const Structure& s, System& y, cudaStream_t st) {
+    k_schur<<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir,
+                                                                   s.up_pair_ptr, s.pairs, y.G, y.U, s.row_ptr, y.S);
+}
+
+void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
+    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.diag_pos, y.S, y.Dinv, y.status);
+}
+
+void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st) {
+    k_to_float<<<grid_for(n, kThreads), kThreads, 0, st>>>(in, out, n);
+}
+
+void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl, cudaStream_t st) {
+    k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, y.L, y.e,
+                                                                       dxp, dxl);
+}
+
+void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial, int nparts,
+                 cudaStream_t st) {
+    k_cost<<<nparts, kThreads, 0, st>>>(s.n_o, cams, pts, s.obs_cam, s.obs_pt, s.obs_xy, partial);
+}
+
+void launch_add_params(const double* a, const double* da, double* out, int64_t n, cudaStream_t st) {
+    k_add<<<grid_for(n, kThreads), kThreads, 0, st>>>(a, da, out, n);
+}
+
+void launch_unpermute(const double* in, const int32_t* perm, double* out, int64_t n_o, int width, cudaStream_t st) {
+    k_unpermute<<<grid_for(n_o * width, kThreads), kThreads, 0, st>>>(in, perm, out, n_o, width);
+}
+
+void launch_unslab(const Structure& s, const double* S, double* out, cudaStream_t st) {
+    k_unslab<<<grid_for(s.nnzb * 81, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, S, out);
+}
+
+}  // namespace ba

@@ -1,0 +1,51 @@
+"""The C ABI library builds, loads without a GPU and exports every call of include/ba.h."""
+import ctypes
+import os
+
+import pytest
+
+from paper_2110_04015_gb300 import binding
+from paper_2110_04015_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def libba():
+    if not os.path.exists(B.LIB):
+        B.build()
+    return ctypes.CDLL(B.LIB)
+
+
+def test_header_declares_the_boundary_calls():
+    names = binding.header_functions()
+    for required in ["ba_problem_create", "ba_set_stream", "ba_build_normal", "ba_solve_pcg", "ba_solve_mcg",
+                     "ba_get_delta", "ba_lm_step", "ba_problem_destroy", "ba_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_call(libba):
+    missing = [n for n in binding.header_functions() if not hasattr(libba, n)]
+    assert not missing
+
+
+def test_binding_covers_every_declared_call():
+    assert sorted(binding._SIGNATURES) == binding.header_functions()
+
+
+def test_struct_layouts_match_header():
+    # sizes implied by include/ba.h (int32 fields, then doubles, natural alignment)
+    assert ctypes.sizeof(binding.ba_options) == 4 * 4 + 8 + 4 * 8
+    assert ctypes.sizeof(binding.ba_solve_stats) == 6 * 4 + 3 * 8
+    assert ctypes.sizeof(binding.ba_lm_stats) == 4 * 4 + 5 * 8
+
+
+def test_default_options_and_errors_without_device(libba):
+    L = binding.lib()
+    opt = binding.ba_options()
+    L.ba_default_options(ctypes.byref(opt))
+    assert opt.precision == 0 and opt.damping == 0 and opt.chunk_iters == 8 and opt.inner_tol == 1e-3
+    # argument checks run before any device work
+    out = ctypes.c_void_p()
+    code = L.ba_problem_create(None, 0, 1, 1, None, None, None, None, None, ctypes.byref(out))
+    assert code == binding.BA_ERR_INVALID_ARG
+    assert b"n_cams" in L.ba_last_error(None)
+    assert L.ba_project(0, 1, 1, None, None, None, None, None, None) == binding.BA_ERR_INVALID_ARG
