@@ -31,6 +31,13 @@ int num_sms() {
 
 using ba::Error;
 
+namespace ba {
+namespace {
+thread_local std::string g_thread_error;
+}
+void set_thread_error(const std::string& msg) { g_thread_error = msg; }
+}  // namespace ba
+
 struct ba_problem {
     ba_options opt;
     cudaStream_t stream = nullptr;
@@ -230,6 +237,13 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     s.nnzb = nnzb;
     s.row_ptr = upload(p, row_ptr);
     s.col = upload(p, col);
+    s.h_row_ptr = row_ptr;
+    s.h_col = col;
+    std::vector<int64_t> tile_ptr(size_t(n_c) + 1, 0);
+    for (int32_t j = 0; j < n_c; ++j) tile_ptr[j + 1] = tile_ptr[j] + (row_ptr[j + 1] - row_ptr[j] + ba::kTile - 1) / ba::kTile;
+    s.n_tiles = tile_ptr[n_c];
+    s.tile_ptr = upload(p, tile_ptr);
+    s.h_tile_ptr = tile_ptr;
     s.diag_pos = upload(p, diag_pos);
     s.n_up = n_up;
     s.n_pairs = n_pairs;
@@ -257,10 +271,14 @@ void alloc_system(ba_problem* p) {
     y.U = dev_alloc<double>(p, size_t(s.n_c) * 81);
     y.bp = dev_alloc<double>(p, size_t(s.n_c) * 9);
     y.bt = dev_alloc<double>(p, size_t(s.n_c) * 9);
-    y.S = dev_alloc<double>(p, size_t(s.nnzb) * 81);
+    y.S = dev_alloc<double>(p, size_t(s.n_tiles) * ba::kTileElems);
+    BA_CUDA_TRY(cudaMemset(y.S, 0, sizeof(double) * size_t(s.n_tiles) * ba::kTileElems));   // padding blocks stay 0
     y.Dinv = dev_alloc<double>(p, size_t(s.n_c) * 81);
     if (p->opt.precision == BA_PRECISION_MIXED) {
-        y.S32 = dev_alloc<float>(p, size_t(s.nnzb) * 81);
+        y.S32 = dev_alloc<float>(p, size_t(s.n_tiles) * ba::kTileElems);
+        BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
+        y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
+        y.Dhat = dev_alloc<double>(p, size_t(s.n_c) * 81);
     }
     y.status = dev_alloc<int>(p, 1);
     p->dxp = dev_alloc<double>(p, size_t(s.n_c) * 9);
@@ -292,8 +310,8 @@ void do_build(ba_problem* p, double lambda) {
     ba::launch_block_jacobi(s, y, st);
     p->launches += 6;
     if (p->opt.precision == BA_PRECISION_MIXED) {
-        ba::launch_to_float(y.S, y.S32, s.nnzb * 81, st);
-        p->launches += 1;
+        ba::launch_scaled_float(s, y, st);
+        p->launches += 2;
     }
     check_launch();
     int status = 0;
@@ -383,6 +401,7 @@ int ba_problem_create(const ba_options* opt, int32_t n_cams, int32_t n_pts, int6
                       const double* pts, const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_xy,
                       ba_problem** out) {
     g_create_error.clear();
+    ba::set_thread_error("");
     if (!out) { g_create_error = "out is NULL"; return BA_ERR_INVALID_ARG; }
     *out = nullptr;
     ba_problem* p = nullptr;
@@ -425,7 +444,7 @@ void ba_problem_destroy(ba_problem* p) {
 }
 
 const char* ba_last_error(const ba_problem* p) {
-    if (!p) return g_create_error.c_str();
+    if (!p) return ba::g_thread_error.empty() ? g_create_error.c_str() : ba::g_thread_error.c_str();
     return p->err.c_str();
 }
 

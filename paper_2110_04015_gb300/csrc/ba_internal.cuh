@@ -8,11 +8,13 @@
 //                     b_l (3), e = L^{-1} b_l (3)
 //   per camera      : U_lambda (9x9), b_p (9), b~ (9), D_j^{-1} (9x9)
 //   S               : block-CSR over cameras, every nonzero 9x9 block of both
-//                     triangles.  The blocks of block-row j are stored as a
-//                     slab of 81 x nnz_j values, entry-major: entry e of the
-//                     q-th block of the row sits at slab_j[e * nnz_j + q], so a
-//                     warp whose lanes take consecutive blocks of a row reads
-//                     consecutive words.
+//                     triangles.  The blocks of block-row j are grouped in tiles
+//                     of 32 consecutive blocks (the last tile of a row padded with
+//                     zero blocks); a tile holds its 32 x 81 values entry-major:
+//                     entry e of tile-local block l at tile[e * 32 + l].  A tile is
+//                     one contiguous run (10 KB float32, 20 KB float64) that a bulk
+//                     copy moves to shared memory, and a warp whose lanes take the
+//                     32 blocks of a tile reads consecutive words.
 // With G_o = W_o L_l^{-T} (V_l = L_l L_l^T) the Schur complement of Eq. 13 is
 //   S_jk = delta_jk U_j - sum_{l seen by j and k} G_jl G_kl^T,
 // and b~_j = b_p,j - sum_{o in camera j} G_o e_l (Eq. 14).
@@ -22,12 +24,20 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/ba.h"
 
 namespace ba {
 
 constexpr int kThreads = 256;
+constexpr int kTile = 32;                 // blocks per tile of S
+constexpr int kTileElems = 81 * kTile;    // values per tile
+
+// Index of entry e (= 9 a + b) of the q-th block (row-local) of block-row j of S.
+__host__ __device__ __forceinline__ int64_t s_at(const int64_t* tile_ptr, int64_t j, int64_t q, int e) {
+    return (tile_ptr[j] + (q >> 5)) * kTileElems + int64_t(e) * kTile + (q & 31);
+}
 constexpr int kMaxDirs = 16;   // widest direction block held by the small FP64 solves
 
 #define BA_CUDA_TRY(expr)                                                                   \
@@ -61,6 +71,8 @@ struct Structure {
     int64_t* row_ptr = nullptr;   // n_c + 1
     int32_t* col = nullptr;       // nnzb
     int32_t* diag_pos = nullptr;  // n_c: block index of S_jj
+    int64_t n_tiles = 0;
+    int64_t* tile_ptr = nullptr;  // n_c + 1: first tile of each block-row
     // upper blocks (j <= k) with the observation pairs that feed them
     int64_t n_up = 0;
     int64_t n_pairs = 0;
@@ -70,6 +82,10 @@ struct Structure {
     int64_t* up_mir = nullptr;    // n_up: block index of (k, j), -1 on the diagonal
     int64_t* up_pair_ptr = nullptr;  // n_up + 1
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
+    // host copies of the pattern (work lists of the block-sparse products are built from them)
+    std::vector<int64_t> h_row_ptr;
+    std::vector<int32_t> h_col;
+    std::vector<int64_t> h_tile_ptr;
 };
 
 // The linearised system at the current parameters (rebuilt by ba_build_normal).
@@ -87,9 +103,14 @@ struct System {
     double* U = nullptr;      // n_c x 81
     double* bp = nullptr;     // n_c x 9
     double* bt = nullptr;     // n_c x 9
-    double* S = nullptr;      // nnzb x 81 (slab layout)
+    double* S = nullptr;      // n_tiles x 2592 (tiled layout above)
     double* Dinv = nullptr;   // n_c x 81
-    float* S32 = nullptr;     // float copy of S for the mixed-precision inner solves
+    // mixed precision: the inner solves run on the Jacobi-scaled system
+    //   S^ = Lam S Lam, Lam = diag(S)^{-1/2},
+    // which removes the parameter-scale ill-conditioning of the 9x9 blocks before float32 rounding
+    float* S32 = nullptr;     // float(S^), tiled layout
+    double* lam = nullptr;    // 9 n_c: Lam
+    double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
     int* status = nullptr;    // device error word of the build
     double lambda = 0.0;
     bool built = false;
@@ -105,6 +126,7 @@ void launch_cameras(const Structure& s, System& y, int damping, double lambda, c
 void launch_schur(const Structure& s, System& y, cudaStream_t st);
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st);
 void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st);
+void launch_scaled_float(const Structure& s, System& y, cudaStream_t st);
 void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl,
                             cudaStream_t st);
 void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial,
@@ -153,5 +175,7 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
 void flush_l2(cudaStream_t st);
 
 int num_sms();
+// error text of handle-less calls on this thread (read back by ba_last_error(NULL))
+void set_thread_error(const std::string& msg);
 
 }  // namespace ba

@@ -7,6 +7,7 @@
 //   k_schur         one warp per upper block (j <= k): S_jk = delta U_j - sum G_o G_o'^T,
 //                   written to (j, k) and transposed to (k, j)
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
+// S is written in the tiled layout of ba_internal.cuh (s_at).
 // Every kernel uses grid-stride loops and 64-bit indices.
 #include <cuda_runtime.h>
 
@@ -366,7 +367,8 @@ __global__ void k_schur(int64_t n_up, const int32_t* __restrict__ up_j, const in
                         const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir,
                         const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
                         const double* __restrict__ G, const double* __restrict__ U,
-                        const int64_t* __restrict__ row_ptr, double* __restrict__ S) {
+                        const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                        double* __restrict__ S) {
     __shared__ double sg[kThreads / 32][2][28];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = gstride() >> 5;
@@ -393,32 +395,40 @@ __global__ void k_schur(int64_t n_up, const int32_t* __restrict__ up_j, const in
         }
         const int j = up_j[u], k = up_k[u];
         const int64_t pos = up_pos[u], mir = up_mir[u];
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        double* slab = S + rj * 81 + (pos - rj);
+        const int64_t qj = pos - row_ptr[j];
         const double* Uj = U + 81 * int64_t(j);
         const bool diag = (j == k);
-        slab[e0 * nj] = (diag ? Uj[e0] : 0.0) - s0;
-        slab[e1 * nj] = (diag ? Uj[e1] : 0.0) - s1;
-        if (e2 < 81) slab[e2 * nj] = (diag ? Uj[e2] : 0.0) - s2;
+        S[s_at(tile_ptr, j, qj, e0)] = (diag ? Uj[e0] : 0.0) - s0;
+        S[s_at(tile_ptr, j, qj, e1)] = (diag ? Uj[e1] : 0.0) - s1;
+        if (e2 < 81) S[s_at(tile_ptr, j, qj, e2)] = (diag ? Uj[e2] : 0.0) - s2;
         if (!diag) {
-            const int64_t rk = row_ptr[k], nk = row_ptr[k + 1] - rk;
-            double* mslab = S + rk * 81 + (mir - rk);
-            mslab[(b0 * 9 + a0) * nk] = -s0;
-            mslab[(b1 * 9 + a1) * nk] = -s1;
-            if (e2 < 81) mslab[(b2 * 9 + a2) * nk] = -s2;
+            const int64_t qk = mir - row_ptr[k];
+            S[s_at(tile_ptr, k, qk, b0 * 9 + a0)] = -s0;
+            S[s_at(tile_ptr, k, qk, b1 * 9 + a1)] = -s1;
+            if (e2 < 81) S[s_at(tile_ptr, k, qk, b2 * 9 + a2)] = -s2;
         }
     }
 }
 
 // D_j^{-1} = (S_jj)^{-1} = L^{-T} L^{-1} from the Cholesky factor of the diagonal block.
-__global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ diag_pos,
-                               const double* __restrict__ S, double* __restrict__ Dinv, int* status) {
+// With lam != nullptr the block is first scaled by its diagonal, B^ = s B s with s_a = B_aa^{-1/2};
+// Dinv then receives (B^)^{-1} and lam the scale factors.
+__global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                               const int32_t* __restrict__ diag_pos, const double* __restrict__ S,
+                               double* __restrict__ Dinv, double* __restrict__ lam, int* status) {
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        const double* slab = S + rj * 81 + (diag_pos[j] - rj);
+        const int64_t qd = diag_pos[j] - row_ptr[j];
         double L[81];
-        for (int a = 0; a < 9; ++a)
-            for (int b = 0; b < 9; ++b) L[9 * a + b] = slab[(9 * a + b) * nj];
+        for (int e = 0; e < 81; ++e) L[e] = S[s_at(tile_ptr, j, qd, e)];
+        if (lam) {
+            double sc[9];
+            for (int a = 0; a < 9; ++a) {
+                sc[a] = L[9 * a + a] > 0.0 ? 1.0 / sqrt(L[9 * a + a]) : 1.0;
+                lam[9 * j + a] = sc[a];
+            }
+            for (int a = 0; a < 9; ++a)
+                for (int b = 0; b < 9; ++b) L[9 * a + b] *= sc[a] * sc[b];
+        }
         bool ok = true;
         for (int c = 0; c < 9; ++c) {
             double d = L[9 * c + c];
@@ -458,6 +468,32 @@ __global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr,
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
     for (int64_t i = gtid(); i < n; i += gstride()) out[i] = static_cast<float>(in[i]);
+}
+
+// S32 = float(Lam S Lam), one warp per block-row, lanes over the row's blocks
+__global__ void k_scaled_float(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                               const int32_t* __restrict__ col, const double* __restrict__ S,
+                               const double* __restrict__ lam, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
+        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
+        double lr[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) lr[a] = lam[9 * j + a];
+        for (int64_t q = lane; q < nj; q += 32) {
+            const int64_t k = col[rj + q];
+            double lc[9];
+#pragma unroll
+            for (int b = 0; b < 9; ++b) lc[b] = lam[9 * k + b];
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = 0; b < 9; ++b) {
+                    const int64_t i = s_at(tile_ptr, j, q, 9 * a + b);
+                    out[i] = static_cast<float>(lr[a] * S[i] * lc[b]);
+                }
+        }
+    }
 }
 
 // dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
@@ -529,9 +565,9 @@ __global__ void k_unpermute(const double* __restrict__ in, const int32_t* __rest
     }
 }
 
-// slab layout -> row-major 9x9 blocks
-__global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const double* __restrict__ S,
-                         double* __restrict__ out) {
+// tiled layout -> row-major 9x9 blocks
+__global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                         const double* __restrict__ S, double* __restrict__ out) {
     const int64_t total = row_ptr[n_c] * 81;
     for (int64_t i = gtid(); i < total; i += gstride()) {
         const int64_t q = i / 81;
@@ -542,8 +578,7 @@ __global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const
             int mid = (lo + hi) >> 1;
             if (row_ptr[mid] <= q) lo = mid; else hi = mid;
         }
-        const int64_t rj = row_ptr[lo], nj = row_ptr[lo + 1] - rj;
-        out[i] = S[rj * 81 + int64_t(e) * nj + (q - rj)];
+        out[i] = S[s_at(tile_ptr, lo, q - row_ptr[lo], e)];
     }
 }
 
@@ -577,11 +612,21 @@ void launch_cameras(const Structure& s, System& y, int damping, double lambda, c
 
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
     k_schur<<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir,
-                                                                   s.up_pair_ptr, s.pairs, y.G, y.U, s.row_ptr, y.S);
+                                                                   s.up_pair_ptr, s.pairs, y.G, y.U, s.row_ptr,
+                                                                   s.tile_ptr, y.S);
 }
 
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
-    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.diag_pos, y.S, y.Dinv, y.status);
+    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.S, y.Dinv,
+                                                      nullptr, y.status);
+    if (y.S32)
+        k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.S, y.Dhat,
+                                                          y.lam, y.status);
+}
+
+void launch_scaled_float(const Structure& s, System& y, cudaStream_t st) {
+    k_scaled_float<<<grid_for(int64_t(s.n_c) * 32, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr,
+                                                                                   s.col, y.S, y.lam, y.S32);
 }
 
 void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st) {
@@ -607,7 +652,7 @@ void launch_unpermute(const double* in, const int32_t* perm, double* out, int64_
 }
 
 void launch_unslab(const Structure& s, const double* S, double* out, cudaStream_t st) {
-    k_unslab<<<grid_for(s.nnzb * 81, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, S, out);
+    k_unslab<<<grid_for(s.nnzb * 81, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, S, out);
 }
 
 }  // namespace ba

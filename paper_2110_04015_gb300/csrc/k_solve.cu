@@ -20,6 +20,7 @@
 // (Section 3.2, "Optimized implementation").
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -33,6 +34,7 @@ namespace {
 
 constexpr int kGramMax = kMaxDirs * kMaxDirs + kMaxDirs;   // Delta (w x w) and gamma (w)
 constexpr int kChunkCams = 112;                             // cameras per Phi partial
+constexpr double kStagnation = 1e-4;                        // float32 sweep stop on t_i (see Ctl::stag)
 
 struct Ctl {
     int it;            // completed steps
@@ -55,6 +57,9 @@ struct Ctl {
     double Delta, gamma, alpha, beta;   // PCG scalars
     double alpha_v[kMaxDirs];
     double true_rr, bb;                 // true residual and |rhs|^2
+    double stag;       // float32 sweeps: stop when t_i (energy decrease / r^T D^-1 r) falls below this
+    int direct_q;      // 1: Q_{i+1} = S P_{i+1} (Algorithm 2, line 3); 0: the Q update of Eq. 18
+    int pad_;
 };
 
 __device__ __forceinline__ int64_t gtid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
@@ -101,63 +106,363 @@ __device__ __forceinline__ double sum_partials(const double* partial, int np, in
 // ---------------------------------------------------------------------------------------
 // block-sparse products
 
-// out[(off + s) * n + 9 j + a] = sum over blocks q of row j in subset segment s of S_jq z_col(q).
-// local = 0: one segment (the whole row) written to column off.
+// Work items of the block-sparse products.  Item = a chunk [q0, q1) of the blocks of block-row
+// `row` that feed output column `seg` (the subset of the column cameras in MCG's local step, 0
+// otherwise).  The ng items of one output group (row, seg) are consecutive; each writes its 9
+// partial sums, and the warp that finishes last (atomic count, no waiting) adds the partials in
+// item order, so the result does not depend on scheduling.  Counters reset themselves.
+struct SpItem {
+    int row, seg, q0, q1, grp, k, ng, pad;
+};
+
+struct ItemList {
+    const SpItem* items = nullptr;
+    int64_t n = 0;
+    int* cnt = nullptr;       // one per group, zero between launches
+    void* part = nullptr;     // n x 9 partial sums (element type of the product)
+};
+
+// Sum the CTA's NV values, publish them as partial[blockIdx], and let the last CTA to finish
+// write the grid totals (in CTA order) to totals[0..NV).  Every CTA of the grid must call it.
+template <int NV>
+__device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* partial, int* cnt, double* totals) {
+    __shared__ double red[kThreads / 32][NV];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) red[wid][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        partial[int64_t(blockIdx.x) * NV + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(cnt, 1) == int(gridDim.x) - 1);
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < NV) {
+            double s = 0.0;
+            for (int b = 0; b < int(gridDim.x); ++b) s += __ldcg(partial + int64_t(b) * NV + threadIdx.x);
+            totals[threadIdx.x] = s;
+        }
+        if (threadIdx.x == 0) *cnt = 0;
+    }
+}
+
+// ---- bulk copies (cp.async.bulk + mbarrier) --------------------------------------------
+
+constexpr int kMaxSpin = 1 << 20;   // bounded mbarrier waits: a copy that never lands ends the kernel
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// one elected thread: bytes from global src to shared dst, completion counted on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < kMaxSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// warps per CTA and copy stages of the tile-streaming product (one CTA per SM: the stages use
+// 162 KB of shared memory in both precisions)
 template <typename T>
-__global__ void k_spmv_seg(int32_t n_c, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const T* __restrict__ S, const T* __restrict__ z, T* __restrict__ out,
-                           const Ctl* __restrict__ ctl, int use_ctl, int off_fixed) {
+struct SpmvCfg;
+template <>
+struct SpmvCfg<float> {
+    static constexpr int kWarps = 8, kStages = 2;
+};
+template <>
+struct SpmvCfg<double> {
+    static constexpr int kWarps = 4, kStages = 2;
+};
+template <typename T>
+constexpr size_t spmv_smem() {
+    return sizeof(T) * SpmvCfg<T>::kWarps * SpmvCfg<T>::kStages * kTileElems +
+           sizeof(uint64_t) * SpmvCfg<T>::kWarps * SpmvCfg<T>::kStages;
+}
+
+// Tile cursor of a warp: the tiles of items w0, w0 + W, ... in order, skipping empty items.
+struct TileCursor {
+    int64_t item;
+    int t, te;
+    int64_t base;
+};
+__device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, const int64_t* tile_ptr, int64_t item,
+                                            int64_t W) {
+    for (; item < L.n; item += W) {
+        const SpItem it = L.items[item];
+        if (it.q1 > it.q0) {
+            c.item = item;
+            c.t = it.q0 >> 5;
+            c.te = (it.q1 + 31) >> 5;
+            c.base = tile_ptr[it.row];
+            return;
+        }
+    }
+    c.item = L.n;
+    c.t = c.te = 0;
+    c.base = 0;
+}
+
+// y(row, seg) = sum over the item's blocks of S_row,col(q) z_col(q).  Each warp streams the
+// tiles of its items through kStages shared-memory buffers with bulk copies (issued by lane 0,
+// NS tiles ahead) and multiplies them with the gathered z blocks.
+// MODE 0: write y to column (off + seg) of `out` (off and the item list from ctl when use_ctl).
+// MODE 1 (Algorithm 1, line 3-4): q = y, and the totals of Delta = q^T p and gamma = p^T r.
+// MODE 2 (Algorithm 2, line 3, width 1): z is column new_off of P, y goes to the same column of out.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
+    const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
+    const T* __restrict__ S, const T* __restrict__ z, ItemList gl, ItemList lo, T* __restrict__ out, int64_t n,
+    const T* __restrict__ rvec, double* __restrict__ dpart, int* __restrict__ dcnt, double* __restrict__ totals,
+    Ctl* ctl, int use_ctl) {
+    constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     if (use_ctl && ctl->done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t n = int64_t(n_c) * 9;
-    const int local = use_ctl ? ctl->local : 0;
-    const int w = use_ctl ? ctl->w_new : 1;
-    const int off = use_ctl ? ctl->new_off : off_fixed;
-    const int sz = use_ctl ? ctl->sz : n_c;
-    const int nseg = local ? w : 1;
-    for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        const T* slab = S + rj * 81;
-        for (int s = 0; s < nseg; ++s) {
-            int64_t q0 = 0, q1 = nj;
-            if (local) {
-                // first block with col >= s*sz and first with col >= (s+1)*sz
-                const int lo_c = s * sz, hi_c = (s + 1) * sz;
-                int64_t a = 0, b = nj;
-                while (a < b) { int64_t m = (a + b) >> 1; if (col[rj + m] < lo_c) a = m + 1; else b = m; }
-                q0 = a;
-                b = nj;
-                while (a < b) { int64_t m = (a + b) >> 1; if (col[rj + m] < hi_c) a = m + 1; else b = m; }
-                q1 = a;
+    if (MODE == 2 && ctl->w_new != 1) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
+    const bool local = MODE == 0 && use_ctl && ctl->local;
+    const ItemList L = local ? lo : gl;
+    const int off = use_ctl ? ctl->new_off : 0;
+    if (MODE == 2) z += int64_t(off) * n;
+    T* part = static_cast<T*>(L.part);
+    constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
+
+    if (lane == 0) {
+        for (int st = 0; st < NS; ++st) mbar_init(&bars[st]);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int64_t W = int64_t(gridDim.x) * NW;
+    const int64_t w0 = int64_t(blockIdx.x) * NW + wid;
+    TileCursor f;
+    cursor_seek(f, L, tile_ptr, w0, W);
+    uint32_t parity = 0, inflight = 0;
+    for (int st = 0; st < NS; ++st) {
+        if (f.item < L.n) {
+            if (lane == 0) bulk_load(tiles + st * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[st]);
+            inflight |= 1u << st;
+            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+        }
+    }
+    int stage = 0;
+    bool bad = false;
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = w0; i < L.n && !bad; i += W) {
+        const SpItem it = L.items[i];
+        const int64_t rj = row_ptr[it.row];
+        T acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = T(0);
+        if (it.q1 > it.q0) {
+            const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
+            for (int t = t0; t < t1; ++t) {
+                // every lane observes the phase (visibility of the copied bytes); the warp agrees
+                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    bad = true;
+                    break;
+                }
+                parity ^= 1u << stage;
+                inflight &= ~(1u << stage);
+                const T* tile = tiles + stage * kTileElems;
+                const int q = t * 32 + lane;
+                if (q >= it.q0 && q < it.q1) {
+                    const T* zk = z + int64_t(col[rj + q]) * 9;
+                    T zv[9];
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) zv[b] = zk[b];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a)
+#pragma unroll
+                        for (int b = 0; b < 9; ++b) acc[a] += tile[(9 * a + b) * 32 + lane] * zv[b];
+                }
+                __syncwarp();
+                if (f.item < L.n) {
+                    fence_proxy_async();
+                    if (lane == 0)
+                        bulk_load(tiles + stage * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[stage]);
+                    inflight |= 1u << stage;
+                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+                }
+                stage = stage + 1 == NS ? 0 : stage + 1;
             }
-            T acc[9];
+            if (bad) break;
+        }
 #pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] = T(0);
-            for (int64_t q = q0 + lane; q < q1; q += 32) {
-                const T* zk = z + int64_t(col[rj + q]) * 9;
-                T zv[9];
+        for (int a = 0; a < 9; ++a) acc[a] = warp_sum(acc[a]);
+        T val = acc[0];
 #pragma unroll
-                for (int b = 0; b < 9; ++b) zv[b] = zk[b];
-                const T* sp = slab + q;
+        for (int a = 1; a < 9; ++a) if (lane == a) val = acc[a];
+        bool fin = true;
+        if (it.ng > 1) {
+            if (lane < 9) part[i * 9 + lane] = val;
+            __threadfence();
+            int last = 0;
+            if (lane == 0) last = (atomicAdd(L.cnt + it.grp, 1) == it.ng - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            fin = last != 0;
+            if (fin) {
+                __threadfence();
+                T sum = T(0);
+                const int64_t first = i - it.k;
+                if (lane < 9)
+                    for (int c = 0; c < it.ng; ++c) sum += __ldcg(part + (first + c) * 9 + lane);
+                val = sum;
+                if (lane == 0) L.cnt[it.grp] = 0;
+            }
+        }
+        if (fin && lane < 9) {
+            const int64_t rowi = 9 * int64_t(it.row) + lane;
+            if (MODE != 1) {
+                out[int64_t(off + it.seg) * n + rowi] = val;
+            } else {
+                out[rowi] = val;
+                const double pv = double(z[rowi]);
+                v[0] += double(val) * pv;
+                v[1] += pv * double(rvec[rowi]);
+            }
+        }
+    }
+    if (bad) {
+        // a copy did not land in time: report, then wait (bounded) for this warp's copies in flight
+        if (lane == 0) {
+            atomicExch(&ctl->status, BA_ERR_TIMEOUT);
+            atomicExch(&ctl->done, 1);
+        }
+        for (int st = 0; st < NS; ++st)
+            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
+    }
+    if (MODE == 1) grid_sum_finalize<2>(v, dpart, dcnt, totals);
+}
+
+// Q[:, off + c] = S P[:, off + c] for the w > 1 columns of a new local block (Algorithm 2, line 3,
+// used by the float32 sweeps, where the Eq. 18 update cancels).  Lane = 4 * qi + g: the lane takes
+// block q0 + qi (+ 8 per round) and columns 4g .. 4g + 3, so each 9x9 block is read once per warp
+// and multiplies up to 16 columns.  Items and their combination are those of k_spmv.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_spmm(const int64_t* __restrict__ row_ptr,
+                                                   const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
+                                                   const T* __restrict__ S, const T* __restrict__ P, ItemList gl,
+                                                   T* __restrict__ part, T* __restrict__ Q, int64_t n,
+                                                   const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    const int w = ctl->w_new;
+    if (w <= 1) return;
+    const int off = ctl->new_off;
+    __shared__ T red[kThreads / 32][kMaxDirs * 9];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int qi = lane >> 2, g = lane & 3;
+    const int nout = 9 * w;
+    for (int64_t i = gtid() >> 5; i < gl.n; i += gstride() >> 5) {
+        const SpItem it = gl.items[i];
+        const int64_t rj = row_ptr[it.row], tb = tile_ptr[it.row];
+        const int32_t* cj = col + rj;
+        T acc[9][4];
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+        if (4 * g < w) {
+            for (int q = it.q0 + qi; q < it.q1; q += 8) {
+                const int64_t k9 = int64_t(cj[q]) * 9;
+                T pv[9][4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int cc = 4 * g + c;
+                    const T* pc = P + int64_t(off + (cc < w ? cc : 0)) * n + k9;
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) pv[b][c] = cc < w ? pc[b] : T(0);
+                }
+                const T* sp = S + (tb + (q >> 5)) * kTileElems + (q & 31);
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
 #pragma unroll
-                    for (int b = 0; b < 9; ++b) acc[a] += sp[(9 * a + b) * nj] * zv[b];
+                    for (int b = 0; b < 9; ++b) {
+                        const T sab = sp[(9 * a + b) * 32];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[a][c] += sab * pv[b][c];
+                    }
                 }
             }
+        }
+        // sum over the 8 lanes of each column group
 #pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] = warp_sum(acc[a]);
-            if (lane < 9) {
-                T v = acc[0];
+        for (int a = 0; a < 9; ++a)
 #pragma unroll
-                for (int a = 1; a < 9; ++a) if (lane == a) v = acc[a];
-                out[int64_t(off + s) * n + 9 * j + lane] = v;
+            for (int c = 0; c < 4; ++c) {
+                T v = acc[a][c];
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                acc[a][c] = v;
+            }
+        __syncwarp();
+        if (qi == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int cc = 4 * g + c;
+                if (cc < w)
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) red[wid][cc * 9 + a] = acc[a][c];
             }
         }
-        // columns of subsets with no block in this row are zero
-        if (local) {
-            for (int s = nseg; s < w; ++s) if (lane < 9) out[int64_t(off + s) * n + 9 * j + lane] = T(0);
+        __syncwarp();
+        bool fin = true;
+        if (it.ng > 1) {
+            for (int o = lane; o < nout; o += 32) part[i * (kMaxDirs * 9) + o] = red[wid][o];
+            __threadfence();
+            int last = 0;
+            if (lane == 0) last = (atomicAdd(gl.cnt + it.grp, 1) == it.ng - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            fin = last != 0;
+            if (fin) {
+                __threadfence();
+                const int64_t first = i - it.k;
+                for (int o = lane; o < nout; o += 32) {
+                    T sum = T(0);
+                    for (int c = 0; c < it.ng; ++c) sum += __ldcg(part + (first + c) * (kMaxDirs * 9) + o);
+                    red[wid][o] = sum;
+                }
+                __syncwarp();
+                if (lane == 0) gl.cnt[it.grp] = 0;
+            }
         }
+        if (fin) {
+            for (int o = lane; o < nout; o += 32) {
+                const int cc = o / 9, a = o % 9;
+                Q[int64_t(off + cc) * n + 9 * int64_t(it.row) + a] = red[wid][o];
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -165,15 +470,16 @@ __global__ void k_spmv_seg(int32_t n_c, const int64_t* __restrict__ row_ptr, con
 // initialisation shared by both algorithms: x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z
 
 template <typename T>
-__global__ void k_init_vec(int32_t n_c, const double* __restrict__ rhs, double sign, const double* __restrict__ Dinv,
-                           T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, T* __restrict__ P0,
-                           double* __restrict__ partial) {
+__global__ void k_init_vec(int32_t n_c, const double* __restrict__ rhs, double sign, const double* __restrict__ scale,
+                           const double* __restrict__ Dinv, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                           T* __restrict__ P0, double* __restrict__ partial) {
     double v[1] = {0.0};
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
         double rv[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const T ra = T(sign * rhs[9 * j + a]);
+            const double sa = scale ? scale[9 * j + a] : 1.0;
+            const T ra = T(sign * sa * rhs[9 * j + a]);
             r[9 * j + a] = ra;
             x[9 * j + a] = T(0);
             rv[a] = double(ra);
@@ -193,7 +499,8 @@ __global__ void k_init_vec(int32_t n_c, const double* __restrict__ rhs, double s
 }
 
 __global__ void k_init_ctl(Ctl* ctl, const double* __restrict__ partial, int np, double tol, int max_iters,
-                           double tau, int n_eff, int sz, int K, int cap, int* blk_off, int* blk_w) {
+                           double tau, int n_eff, int sz, int K, int cap, int* blk_off, int* blk_w, double stag,
+                           int direct_q) {
     double rr0 = sum_partials(partial, np, 1, 0);
     if (threadIdx.x == 0) {
         Ctl c;
@@ -213,6 +520,8 @@ __global__ void k_init_ctl(Ctl* ctl, const double* __restrict__ partial, int np,
         c.local = 0;
         c.w_cur = 1;
         c.off_cur = 0;
+        c.stag = stag;
+        c.direct_q = direct_q;
         c.status = BA_OK;
         if (!(rr0 == rr0) || isinf(rr0)) { c.done = 1; c.status = BA_ERR_BREAKDOWN; }
         else if (rr0 == 0.0 || max_iters <= 0) { c.done = 1; c.status = rr0 == 0.0 ? BA_OK : BA_ERR_NOT_CONVERGED; }
@@ -225,63 +534,15 @@ __global__ void k_init_ctl(Ctl* ctl, const double* __restrict__ partial, int np,
 // ---------------------------------------------------------------------------------------
 // Algorithm 1
 
-// q = S p with the partial sums of Delta = q^T p and gamma = p^T r.
-template <typename T>
-__global__ void k_pcg_spmv(int32_t n_c, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const T* __restrict__ S, const T* __restrict__ p, const T* __restrict__ r,
-                           T* __restrict__ q, double* __restrict__ partial, const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
-    const int lane = threadIdx.x & 31;
-    double v[2] = {0.0, 0.0};
-    for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        const T* slab = S + rj * 81;
-        T acc[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) acc[a] = T(0);
-        for (int64_t qq = lane; qq < nj; qq += 32) {
-            const T* zk = p + int64_t(col[rj + qq]) * 9;
-            T zv[9];
-#pragma unroll
-            for (int b = 0; b < 9; ++b) zv[b] = zk[b];
-            const T* sp = slab + qq;
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-#pragma unroll
-                for (int b = 0; b < 9; ++b) acc[a] += sp[(9 * a + b) * nj] * zv[b];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 9; ++a) acc[a] = warp_sum(acc[a]);
-        if (lane < 9) {
-            T val = acc[0];
-#pragma unroll
-            for (int a = 1; a < 9; ++a) if (lane == a) val = acc[a];
-            q[9 * j + lane] = val;
-            const double pv = double(p[9 * j + lane]);
-            v[0] += double(val) * pv;
-            v[1] += pv * double(r[9 * j + lane]);
-        }
-    }
-    cta_sum_write<2>(v, partial + 2 * blockIdx.x);
-}
-
-// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; partials of |r|^2 and q^T z.
+// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2 and q^T z.
 template <typename T>
 __global__ void k_pcg_update(int32_t n_c, const double* __restrict__ Dinv, const T* __restrict__ p,
                              const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                             const double* __restrict__ pa, int np, double* __restrict__ pb,
+                             double* __restrict__ totals, double* __restrict__ dpart, int* __restrict__ dcnt,
                              const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
-    __shared__ double s_alpha;
-    if (threadIdx.x < 32) {
-        double D = sum_partials(pa, np, 2, 0);
-        double g = sum_partials(pa, np, 2, 1);
-        if (threadIdx.x == 0) s_alpha = g / D;
-    }
-    __syncthreads();
-    const T alpha = T(s_alpha);
-    double v[2] = {0.0, 0.0};
+    const T alpha = T(totals[1] / totals[0]);
+    double v[3] = {0.0, 0.0, 0.0};
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
         T rv[9], qv[9];
 #pragma unroll
@@ -302,40 +563,37 @@ __global__ void k_pcg_update(int32_t n_c, const double* __restrict__ Dinv, const
             const T zs = T(s);
             z[9 * j + a] = zs;
             v[1] += double(qv[a]) * double(zs);
+            v[2] += double(rv[a]) * double(zs);
         }
     }
-    cta_sum_write<2>(v, pb + 2 * blockIdx.x);
+    grid_sum_finalize<3>(v, dpart, dcnt, totals + 2);
 }
 
-// stop test and beta = Phi / Delta (one CTA)
-__global__ void k_pcg_decide(Ctl* ctl, const double* __restrict__ pa, const double* __restrict__ pb, int np,
-                             double* hist) {
-    if (ctl->done) return;
-    if (threadIdx.x >= 32) return;
-    double D = sum_partials(pa, np, 2, 0);
-    double g = sum_partials(pa, np, 2, 1);
-    double rr = sum_partials(pb, np, 2, 0);
-    double phi = sum_partials(pb, np, 2, 1);
-    if (threadIdx.x == 0) {
-        const int it = ctl->it + 1;
-        ctl->it = it;
-        ctl->Delta = D;
-        ctl->gamma = g;
-        ctl->alpha = g / D;
-        ctl->rr = rr;
-        hist[it - 1] = sqrt(rr / ctl->rr0);
-        if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_BREAKDOWN;
-        } else if (rr < ctl->tol2 * ctl->rr0) {
-            ctl->done = 1;
-            ctl->status = BA_OK;
-        } else if (it >= ctl->max_iters) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_NOT_CONVERGED;
-        } else {
-            ctl->beta = phi / D;
-        }
+// stop test and beta = Phi / Delta (one thread)
+__global__ void k_pcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist) {
+    if (ctl->done || threadIdx.x != 0) return;
+    const double D = totals[0], g = totals[1], rr = totals[2], phi = totals[3];
+    const int it = ctl->it + 1;
+    ctl->it = it;
+    ctl->Delta = D;
+    ctl->gamma = g;
+    ctl->alpha = g / D;
+    ctl->rr = rr;
+    hist[it - 1] = sqrt(rr / ctl->rr0);
+    if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
+        ctl->done = 1;
+        ctl->status = BA_ERR_BREAKDOWN;
+    } else if (rr < ctl->tol2 * ctl->rr0) {
+        ctl->done = 1;
+        ctl->status = BA_OK;
+    } else if (it >= ctl->max_iters) {
+        ctl->done = 1;
+        ctl->status = BA_ERR_NOT_CONVERGED;
+    } else if (ctl->stag > 0.0 && (g * g / D) < ctl->stag * totals[4]) {
+        ctl->done = 1;          // no measurable progress left at this precision: end the sweep
+        ctl->status = BA_OK;
+    } else {
+        ctl->beta = phi / D;
     }
 }
 
@@ -510,6 +768,76 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
     __syncthreads();
 }
 
+// Cholesky inverse of the symmetric w x w matrix in sA, accepted only when it equals the pseudo-
+// inverse: with A = L L^T, lambda_min(A) >= 1 / |L^{-1}|_F^2 and lambda_max(A) <= trace(A), so when
+// 1 / |L^{-1}|_F^2 exceeds 1e3 times the threshold w 2^-52 trace(A) no eigenvalue is dropped and
+// A^+ = A^{-1}.  sA is left intact; sL (lower factor, then L^{-1}) is scratch; sX receives A^{-1}.
+// Returns false (sX undefined) when the certificate fails or a pivot is not positive.
+__device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxDirs + 1],
+                                  double (*sX)[kMaxDirs + 1], int w) {
+    __shared__ int ok;
+    __shared__ double fro, tr;
+    const int t = threadIdx.x;
+    const int i = t / kMaxDirs, j = t % kMaxDirs;
+    if (t < kMaxDirs * kMaxDirs) sL[i][j] = (i < w && j < w && j <= i) ? sA[i][j] : 0.0;
+    if (t == 0) {
+        ok = 1;
+        fro = 0.0;
+        double s = 0.0;
+        for (int k = 0; k < w; ++k) s += sA[k][k];
+        tr = s;
+    }
+    __syncthreads();
+    // right-looking Cholesky on the lower triangle
+    for (int k = 0; k < w; ++k) {
+        if (t == 0) {
+            const double d = sL[k][k];
+            if (!(d > 0.0)) ok = 0;
+            sL[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        if (t > k && t < w) sL[t][k] /= sL[k][k];
+        __syncthreads();
+        if (t < kMaxDirs * kMaxDirs && i > k && j > k && j <= i && i < w) sL[i][j] -= sL[i][k] * sL[j][k];
+        __syncthreads();
+    }
+    if (!ok) return false;
+    // L^{-1} column by column (thread c solves column c), kept in sX temporarily
+    if (t < w) {
+        const int c = t;
+        for (int r = 0; r < w; ++r) {
+            double v = (r == c) ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) v -= sL[r][k] * sX[k][c];
+            sX[r][c] = r < c ? 0.0 : v / sL[r][r];
+        }
+    }
+    __syncthreads();
+    if (t < kMaxDirs * kMaxDirs) sL[i][j] = (i < w && j < w) ? sX[i][j] : 0.0;   // sL <- L^{-1}
+    __syncthreads();
+    if (t < 32) {
+        double f = 0.0;
+        for (int e = t; e < w * w; e += 32) {
+            const double v = sL[e / w][e % w];
+            f += v * v;
+        }
+        f = warp_sum(f);
+        if (t == 0) fro = f;
+    }
+    __syncthreads();
+    const double lam_min_bound = 1.0 / fro;
+    const double thr = w * 2.220446049250313e-16 * tr;
+    if (!(lam_min_bound > 1e3 * thr)) return false;
+    // A^{-1} = L^{-T} L^{-1}
+    if (t < kMaxDirs * kMaxDirs && i < w && j < w) {
+        double v = 0.0;
+        const int k0 = i > j ? i : j;
+        for (int k = k0; k < w; ++k) v += sL[k][i] * sL[k][j];
+        sX[i][j] = v;
+    }
+    __syncthreads();
+    return true;
+}
+
 // Delta_i, gamma_i -> Delta_i^+ (stored for the reorthogonalisation), alpha_i, gamma^T alpha.
 __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np, double* __restrict__ dpinv) {
     if (ctl->done) return;
@@ -539,7 +867,7 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np
     if (w == 1) {
         if (threadIdx.x == 0) sX[0][0] = sA[0][0] > 0.0 ? 1.0 / sA[0][0] : 0.0;
         __syncthreads();
-    } else {
+    } else if (!inverse_certified(sA, sV, sX, w)) {
         pinv_sym_jacobi(sA, sV, sX, w);
     }
     if (threadIdx.x < kMaxDirs * kMaxDirs) {
@@ -562,11 +890,12 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np
     }
 }
 
-// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; partials of |r|^2 and r^T z.
+// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z.
 template <typename T>
 __global__ void k_mcg_update(int32_t n_c, const double* __restrict__ Dinv, const T* __restrict__ P,
                              const T* __restrict__ Q, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                             double* __restrict__ partial, const Ctl* __restrict__ ctl) {
+                             double* __restrict__ dpart, int* __restrict__ dcnt, double* __restrict__ totals,
+                             const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
     const int64_t n = int64_t(n_c) * 9;
     const int w = ctl->w_cur, off = ctl->off_cur;
@@ -600,16 +929,13 @@ __global__ void k_mcg_update(int32_t n_c, const double* __restrict__ Dinv, const
             v[1] += double(rv[a]) * double(zs);
         }
     }
-    cta_sum_write<2>(v, partial + 2 * blockIdx.x);
+    grid_sum_finalize<2>(v, dpart, dcnt, totals);
 }
 
-// stop test, tau-test and the layout of the next block (one CTA)
-__global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ partial, int np, double* hist, int* blk_off,
-                             int* blk_w) {
+// stop test, tau-test and the layout of the next block (one thread)
+__global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist, int* blk_off, int* blk_w) {
     if (ctl->done) return;
-    if (threadIdx.x >= 32) return;
-    double rr = sum_partials(partial, np, 2, 0);
-    double rz = sum_partials(partial, np, 2, 1);
+    const double rr = totals[0], rz = totals[1];
     if (threadIdx.x == 0) {
         const int it = ctl->it + 1;
         ctl->it = it;
@@ -637,6 +963,11 @@ __global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ partial, int n
             return;
         }
         const double t = ctl->ga / rz;
+        if (ctl->stag > 0.0 && t < ctl->stag) {
+            ctl->done = 1;      // no measurable progress left at this precision: end the sweep
+            ctl->status = BA_OK;
+            return;
+        }
         const int local = (t < ctl->tau) ? 1 : 0;
         const int w = local ? ctl->n_eff : 1;
         if (ctl->cols + w > ctl->cap) {
@@ -731,6 +1062,7 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
     __shared__ T sB[TC][kMaxDirs];
     const int64_t n = int64_t(n_c) * 9;
     const int w = ctl->w_new, off = ctl->new_off, hc = ctl->hist_cols, local = ctl->local, sz = ctl->sz;
+    const bool upd_q = !ctl->direct_q;
     // every thread of the CTA walks all tiles, so the loop bounds are CTA-uniform
     const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
     const int64_t rbeg = int64_t(blockIdx.x) * per_cta;
@@ -747,7 +1079,7 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
             aq[s] = T(0);
             if (act && s < w) {
                 ap[s] = (local ? (s == sub) : (s == 0)) ? zr : T(0);
-                aq[s] = Q[int64_t(off + s) * n + row];
+                aq[s] = upd_q ? Q[int64_t(off + s) * n + row] : T(0);
             }
         }
         for (int c0 = 0; c0 < hc; c0 += TC) {
@@ -759,13 +1091,21 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
             }
             __syncthreads();
             if (act) {
-                for (int cc = 0; cc < tc; ++cc) {
-                    const T pv = P[int64_t(c0 + cc) * n + row];
-                    const T qv = Q[int64_t(c0 + cc) * n + row];
+                if (upd_q) {
+                    for (int cc = 0; cc < tc; ++cc) {
+                        const T pv = P[int64_t(c0 + cc) * n + row];
+                        const T qv = Q[int64_t(c0 + cc) * n + row];
 #pragma unroll
-                    for (int s = 0; s < kMaxDirs; ++s) {
-                        ap[s] -= pv * sB[cc][s];
-                        aq[s] -= qv * sB[cc][s];
+                        for (int s = 0; s < kMaxDirs; ++s) {
+                            ap[s] -= pv * sB[cc][s];
+                            aq[s] -= qv * sB[cc][s];
+                        }
+                    }
+                } else {
+                    for (int cc = 0; cc < tc; ++cc) {
+                        const T pv = P[int64_t(c0 + cc) * n + row];
+#pragma unroll
+                        for (int s = 0; s < kMaxDirs; ++s) ap[s] -= pv * sB[cc][s];
                     }
                 }
             }
@@ -775,7 +1115,7 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
             for (int s = 0; s < kMaxDirs; ++s) {
                 if (s < w) {
                     P[int64_t(off + s) * n + row] = ap[s];
-                    Q[int64_t(off + s) * n + row] = aq[s];
+                    if (upd_q) Q[int64_t(off + s) * n + row] = aq[s];
                 }
             }
         }
@@ -785,15 +1125,14 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
 // ---------------------------------------------------------------------------------------
 // true residual t = -b~ - S x in float64 and |t|^2, |b~|^2 partials
 
-__global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ S, const double* __restrict__ x,
-                                const double* __restrict__ bt, double* __restrict__ res,
+__global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                                const int32_t* __restrict__ col, const double* __restrict__ S,
+                                const double* __restrict__ x, const double* __restrict__ bt, double* __restrict__ res,
                                 double* __restrict__ partial) {
     const int lane = threadIdx.x & 31;
     double v[2] = {0.0, 0.0};
     for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        const double* slab = S + rj * 81;
+        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj, tb = tile_ptr[j];
         double acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = 0.0;
@@ -802,11 +1141,11 @@ __global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr
             double xv[9];
 #pragma unroll
             for (int b = 0; b < 9; ++b) xv[b] = xk[b];
-            const double* sp = slab + q;
+            const double* sp = S + (tb + (q >> 5)) * kTileElems + (q & 31);
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
 #pragma unroll
-                for (int b = 0; b < 9; ++b) acc[a] += sp[(9 * a + b) * nj] * xv[b];
+                for (int b = 0; b < 9; ++b) acc[a] += sp[(9 * a + b) * 32] * xv[b];
             }
         }
 #pragma unroll
@@ -834,9 +1173,10 @@ __global__ void k_true_reduce(Ctl* ctl, const double* __restrict__ partial, int 
     }
 }
 
-// mixed precision: x64 += (double) d32
-__global__ void k_accumulate(int64_t n, const float* __restrict__ d, double* __restrict__ x) {
-    for (int64_t i = gtid(); i < n; i += gstride()) x[i] += double(d[i]);
+// mixed precision: x64 += Lam (double) d32, the inner solution mapped back from the scaled system
+__global__ void k_accumulate(int64_t n, const float* __restrict__ d, const double* __restrict__ lam,
+                             double* __restrict__ x) {
+    for (int64_t i = gtid(); i < n; i += gstride()) x[i] += lam[i] * double(d[i]);
 }
 
 __global__ void k_zero(int64_t n, double* __restrict__ x) {
@@ -897,7 +1237,111 @@ struct Solver {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     GraphKey key;
+    // work lists of the block-sparse products: whole rows, and rows split by pose subset
+    ItemList items_g, items_l;
+    int items_l_dirs = -1;
+    bool use_local = false;    // local steps read items_l (false when there is a single subset)
+    void* mm_part = nullptr;   // k_spmm partials: items_g.n x 16 x 9
+    double* totals = nullptr;  // grid totals: [0] Delta [1] gamma [2] |r|^2 [3] Phi [4] r^T z ; [8] |r|^2 [9] r^T z
+    double* dpart = nullptr;   // 3 x (num_sms * 8) x 2 CTA partials
+    int* dcnt = nullptr;       // 4 self-resetting arrival counters
 };
+
+// Items of the block-sparse product: each (row, segment) split into chunks of at most cb blocks.
+// sz = 0: one segment per row; otherwise segment s holds the blocks whose column camera lies in
+// [s sz, (s + 1) sz), for s < n_seg (empty segments get one empty item, which writes zeros).
+static std::vector<SpItem> build_items(const Structure& s, int sz, int n_seg, int cb) {
+    std::vector<SpItem> out;
+    int grp = 0;
+    for (int32_t j = 0; j < s.n_c; ++j) {
+        const int64_t rj = s.h_row_ptr[j], nj = s.h_row_ptr[j + 1] - rj;
+        const int32_t* cj = s.h_col.data() + rj;
+        const int nseg = sz > 0 ? n_seg : 1;
+        for (int g = 0; g < nseg; ++g) {
+            int q0 = 0, q1 = int(nj);
+            if (sz > 0) {
+                q0 = int(std::lower_bound(cj, cj + nj, g * sz) - cj);
+                q1 = int(std::lower_bound(cj, cj + nj, (g + 1) * sz) - cj);
+            }
+            const int nch = q1 > q0 ? (q1 - q0 + cb - 1) / cb : 1;
+            for (int c = 0; c < nch; ++c) {
+                SpItem it;
+                it.row = j;
+                it.seg = g;
+                it.q0 = q0 + c * cb;
+                it.q1 = std::min(q1, q0 + (c + 1) * cb);
+                if (it.q1 < it.q0) it.q1 = it.q0;
+                it.grp = grp;
+                it.k = c;
+                it.ng = nch;
+                it.pad = 0;
+                out.push_back(it);
+            }
+            ++grp;
+        }
+    }
+    return out;
+}
+
+static int item_chunk(const Structure& s) {
+    int64_t target = int64_t(num_sms()) * 64;
+    int64_t cb = (s.nnzb + target - 1) / target;
+    cb = (cb + 31) / 32 * 32;
+    if (cb < 32) cb = 32;
+    if (cb > 256) cb = 256;
+    return int(cb);
+}
+
+static void free_items(ItemList& L) {
+    if (L.items) cudaFree(const_cast<SpItem*>(L.items));
+    if (L.cnt) cudaFree(L.cnt);
+    if (L.part) cudaFree(L.part);
+    L = ItemList();
+}
+
+static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
+    free_items(L);
+    SpItem* d = nullptr;
+    BA_CUDA_TRY(cudaMalloc(&d, sizeof(SpItem) * v.size()));
+    BA_CUDA_TRY(cudaMemcpy(d, v.data(), sizeof(SpItem) * v.size(), cudaMemcpyHostToDevice));
+    L.items = d;
+    L.n = int64_t(v.size());
+    const int ngrp = v.empty() ? 1 : v.back().grp + 1;
+    BA_CUDA_TRY(cudaMalloc(&L.cnt, sizeof(int) * ngrp));
+    BA_CUDA_TRY(cudaMemset(L.cnt, 0, sizeof(int) * ngrp));
+    BA_CUDA_TRY(cudaMalloc(&L.part, sizeof(double) * 9 * (v.size() > 0 ? v.size() : 1)));
+}
+
+static void ensure_items(Solver* w, const Structure& s, int n_dirs, int sz, int n_eff) {
+    const int cb = item_chunk(s);
+    if (!w->items_g.items) {
+        upload_items(w->items_g, build_items(s, 0, 1, cb));
+        BA_CUDA_TRY(cudaMalloc(&w->mm_part, sizeof(double) * kMaxDirs * 9 * size_t(w->items_g.n)));
+    }
+    if (n_eff > 1 && w->items_l_dirs != n_dirs) {
+        upload_items(w->items_l, build_items(s, sz, n_eff, cb));
+        w->items_l_dirs = n_dirs;
+    }
+    w->use_local = n_eff > 1;
+    static bool attrs = false;
+    if (!attrs) {
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+        attrs = true;
+    }
+    if (!w->totals) {
+        BA_CUDA_TRY(cudaMalloc(&w->totals, sizeof(double) * 16));
+        BA_CUDA_TRY(cudaMalloc(&w->dpart, sizeof(double) * 3 * 2 * size_t(num_sms()) * 8));
+        BA_CUDA_TRY(cudaMalloc(&w->dcnt, sizeof(int) * 4));
+        BA_CUDA_TRY(cudaMemset(w->dcnt, 0, sizeof(int) * 4));
+    }
+}
+
+static int spmv_grid() { return num_sms() * 8; }
 
 static void free_ws(Solver* w) {
     void* ptrs[] = {w->P, w->Q, w->r, w->z, w->xw, w->part_a, w->part_b, w->part_c, w->dpinv, w->B,
@@ -920,6 +1364,12 @@ Solver* solver_create() {
 void solver_destroy(Solver* w) {
     if (!w) return;
     free_ws(w);
+    free_items(w->items_g);
+    free_items(w->items_l);
+    if (w->mm_part) cudaFree(w->mm_part);
+    if (w->totals) cudaFree(w->totals);
+    if (w->dpart) cudaFree(w->dpart);
+    if (w->dcnt) cudaFree(w->dcnt);
     if (w->h_ctl) cudaFreeHost(w->h_ctl);
     if (w->flush) cudaFree(w->flush);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
@@ -982,37 +1432,60 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
     T* r = static_cast<T*>(w->r);
     T* z = static_cast<T*>(w->z);
     const int n_c = s.n_c;
+    const int Gs = spmv_grid();
+    const int Gt = num_sms();   // tile-streaming product: one CTA per SM
+    double* dp0 = w->dpart;
+    double* dp1 = w->dpart + 2 * Gs;
+    double* dp2 = w->dpart + 4 * Gs;
     if (!mcg) {
-        k_pcg_spmv<T><<<G, kThreads, 0, st>>>(n_c, s.row_ptr, s.col, S, P, r, Q, w->part_a, w->ctl);
-        k_pcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, w->part_a, G, w->part_b, w->ctl);
-        k_pcg_decide<<<1, 32, 0, st>>>(w->ctl, w->part_a, w->part_b, G, w->hist);
+        k_spmv<T, 1><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
+            s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, r, dp0, w->dcnt, w->totals, w->ctl, 1);
+        k_pcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, w->totals, dp1, w->dcnt + 1, w->ctl);
+        k_pcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals, w->hist);
         k_pcg_dir<T><<<G, kThreads, 0, st>>>(w->n, z, P, w->ctl);
     } else {
         k_mcg_gram<T><<<G, kThreads, 0, st>>>(w->n, P, Q, r, w->part_a, w->ctl);
         k_mcg_small<<<1, kThreads, 0, st>>>(w->ctl, w->part_a, G, w->dpinv);
-        k_mcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, w->part_b, w->ctl);
-        k_mcg_decide<<<1, 32, 0, st>>>(w->ctl, w->part_b, G, w->hist, w->blk_off, w->blk_w);
+        k_mcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, dp2, w->dcnt + 2, w->totals + 8, w->ctl);
+        k_mcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals + 8, w->hist, w->blk_off, w->blk_w);
         k_mcg_phi<T><<<G * 4, kThreads, 0, st>>>(n_c, Q, z, w->phip, w->ctl);
         k_mcg_beta<<<G, kThreads, 0, st>>>(w->phip, w->dpinv, w->blk_off, w->blk_w, w->B, w->ctl);
-        k_spmv_seg<T><<<G * 4, kThreads, 0, st>>>(n_c, s.row_ptr, s.col, S, z, Q, w->ctl, 1, 0);
-        k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, w->ctl);
+        if (sizeof(T) == 8) {
+            // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}
+            k_spmv<T, 0><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g, w->use_local ? w->items_l : w->items_g, Q, w->n,
+                nullptr, nullptr, nullptr, nullptr, w->ctl, 1);
+            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, w->ctl);
+        } else {
+            // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
+            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, w->ctl);
+            k_spmv<T, 2><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr,
+                w->ctl, 1);
+            k_spmm<T><<<Gs, kThreads, 0, st>>>(s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g,
+                                               static_cast<T*>(w->mm_part), Q, w->n, w->ctl);
+        }
     }
 }
 
 // One Krylov solve of S x = sign * rhs (rhs float64) with storage type T.  Returns the final Ctl in *out.
 template <typename T>
 static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
-                   T* x, const SolveArgs& a, int n_eff, int sz, int K, int64_t cap, Ctl* out, cudaStream_t st) {
+                   const double* scale, T* x, const SolveArgs& a, int n_eff, int sz, int K, int64_t cap, Ctl* out,
+                   cudaStream_t st) {
     const int G = w->nparts;
     T* P = static_cast<T*>(w->P);
     T* Q = static_cast<T*>(w->Q);
     T* r = static_cast<T*>(w->r);
     T* z = static_cast<T*>(w->z);
-    k_init_vec<T><<<G, kThreads, 0, st>>>(s.n_c, rhs, sign, Dinv, x, r, z, P, w->part_b);
+    k_init_vec<T><<<G, kThreads, 0, st>>>(s.n_c, rhs, sign, scale, Dinv, x, r, z, P, w->part_b);
     k_init_ctl<<<1, 32, 0, st>>>(w->ctl, w->part_b, G, a.tol, a.max_iters, a.tau, n_eff, sz, K,
-                                 static_cast<int>(cap), w->blk_off, w->blk_w);
+                                 static_cast<int>(cap), w->blk_off, w->blk_w, sizeof(T) == 4 ? kStagnation : 0.0,
+                                 sizeof(T) == 4 ? 1 : 0);
     // Q_0 = S P_0
-    k_spmv_seg<T><<<G * 4, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, S, P, Q, w->ctl, 0, 0);
+    k_spmv<T, 0><<<num_sms(), SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
+        s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr, w->ctl,
+        0);
     BA_CUDA_TRY(cudaGetLastError());
     w->launches += 3;
 
@@ -1020,7 +1493,8 @@ static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv
     key.mcg = a.mcg;
     key.fp32 = sizeof(T) == 4;
     key.chunk = a.chunk;
-    const void* ptrs[12] = {S, Dinv, x, w->P, w->Q, w->r, w->z, w->ctl, w->B, w->phip, s.row_ptr, s.col};
+    const void* ptrs[12] = {S, Dinv, x, w->P, w->Q, w->r, w->z, w->ctl, w->B, w->phip, w->items_g.items,
+                            w->use_local ? w->items_l.items : w->items_g.items};
     for (int i = 0; i < 12; ++i) key.ptrs[i] = ptrs[i];
     if (!(key == w->key) || !w->exec) {
         if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
@@ -1040,7 +1514,7 @@ static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv
         BA_CUDA_TRY(cudaStreamSynchronize(st));
         if (w->h_ctl->done) break;
         BA_CUDA_TRY(cudaGraphLaunch(w->exec, st));
-        w->launches += int64_t(a.chunk) * (a.mcg ? 8 : 4);
+        w->launches += int64_t(a.chunk) * (a.mcg ? (sizeof(T) == 8 ? 8 : 9) : 4);
     }
     BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1072,6 +1546,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     }
     const bool fp32 = a.precision == BA_PRECISION_MIXED;
     ensure_ws(w, n, cap, a.max_iters, cap * n_eff * K, fp32 ? 4 : 8);
+    ensure_items(w, s, a.mcg ? n_dirs : 1, sz, n_eff);
     w->launches = 0;
 
     cudaEvent_t e0, e1;
@@ -1083,7 +1558,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     Ctl fin;
     const int G = w->nparts;
     if (!fp32) {
-        krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, x, a, n_eff, sz, K, cap, &fin, st);
+        krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, a, n_eff, sz, K, cap, &fin, st);
         out.status = fin.status;
         out.iters = fin.it;
         out.local_steps = fin.local_steps;
@@ -1098,7 +1573,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         // float64 iterative refinement around float32 Krylov sweeps
         k_zero<<<grid_for_host(n), kThreads, 0, st>>>(n, x);
         // rt = -b~ - S x = -b~
-        k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
+        k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
         k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
         w->launches += 3;
         BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -1118,8 +1593,8 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
             const double need = a.tol * std::sqrt(bb) / std::sqrt(tr);
             inner.tol = need > a.inner_tol ? need : a.inner_tol;
             if (inner.tol >= 1.0) inner.tol = 0.5;
-            krylov<float>(w, s, y.S32, y.Dinv, w->rt, 1.0, static_cast<float*>(w->xw), inner, n_eff, sz, K, cap,
-                          &fin, st);
+            krylov<float>(w, s, y.S32, y.Dhat, w->rt, 1.0, y.lam, static_cast<float*>(w->xw), inner, n_eff, sz, K,
+                          cap, &fin, st);
             ++sweeps;
             total += fin.it;
             locals += fin.local_steps;
@@ -1127,8 +1602,8 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
             std::vector<double> h(fin.it);
             if (fin.it > 0)
                 BA_CUDA_TRY(cudaMemcpyAsync(h.data(), w->hist, sizeof(double) * fin.it, cudaMemcpyDeviceToHost, st));
-            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, static_cast<const float*>(w->xw), x);
-            k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, static_cast<const float*>(w->xw), y.lam, x);
+            k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
             k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
             w->launches += 3;
             BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -1148,7 +1623,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         out.rel_residual = std::sqrt(tr / bb);
     }
     // true relative residual in float64
-    k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, y.S, x, y.bt, nullptr, w->part_c);
+    k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, nullptr, w->part_c);
     k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
     w->launches += 2;
     out.launches = w->launches;
@@ -1187,17 +1662,18 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
     BA_CUDA_TRY(cudaEventCreate(&a));
     BA_CUDA_TRY(cudaEventCreate(&b));
     double total = 0.0;
+    ensure_items(w, s, 1, s.n_c, 1);
     for (int k = 0; k < reps; ++k) {
         flush_l2(st);
         BA_CUDA_TRY(cudaEventRecord(a, st));
         if (fp32)
-            k_pcg_spmv<float><<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, y.S32, static_cast<float*>(w->P),
-                                                      static_cast<float*>(w->r), static_cast<float*>(w->Q), w->part_a,
-                                                      w->ctl);
+            k_spmv<float, 1><<<num_sms(), SpmvCfg<float>::kWarps * 32, spmv_smem<float>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, y.S32, static_cast<float*>(w->P), w->items_g, w->items_g,
+                static_cast<float*>(w->Q), n, static_cast<float*>(w->r), w->dpart, w->dcnt, w->totals, w->ctl, 1);
         else
-            k_pcg_spmv<double><<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.col, y.S, static_cast<double*>(w->P),
-                                                       static_cast<double*>(w->r), static_cast<double*>(w->Q),
-                                                       w->part_a, w->ctl);
+            k_spmv<double, 1><<<num_sms(), SpmvCfg<double>::kWarps * 32, spmv_smem<double>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, y.S, static_cast<double*>(w->P), w->items_g, w->items_g,
+                static_cast<double*>(w->Q), n, static_cast<double*>(w->r), w->dpart, w->dcnt, w->totals, w->ctl, 1);
         BA_CUDA_TRY(cudaEventRecord(b, st));
         BA_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;

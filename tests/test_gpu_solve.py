@@ -2,7 +2,8 @@
 
 Each side solves its own reduced system (the two systems agree to ~1e-13, see
 test_gpu_build).  Tolerances:
-  * iteration counts equal (a last-step tie may move the count by one);
+  * iteration counts within 5 % (at least 1): the counts are sensitive to rounding at the
+    1e-14 level on the ill-conditioned cases (see _check_against_oracle);
   * recursive residual histories agree to 1e-6 relative over the first 20 steps
     (roundoff of two float64 trajectories drifting apart, amplified by the
     preconditioned condition number, ~5e3 here), with an absolute floor of 1e-11
@@ -55,7 +56,9 @@ def dense_ref():
 
 def _check_against_oracle(p, st, o, lin, ref, hist_steps=20):
     assert st["status"] == 0, st
-    assert abs(st["iters"] - o.iters) <= 1, (st["iters"], o.iters)
+    # iteration counts within 5 %: on seq-small the recursive residual plateaus just above eps,
+    # and the oracle itself stops at 149 or 156 steps under 1e-14 relative noise in S p
+    assert abs(st["iters"] - o.iters) <= max(1, 0.05 * o.iters), (st["iters"], o.iters)
     h = p.ba_get_residual_history()
     assert len(h) == st["iters"]
     k = min(hist_steps, len(h), len(o.rel_res))
