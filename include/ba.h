@@ -262,6 +262,37 @@ typedef enum ba_kernel {
  */
 int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
 
+/* ---- allocation-free residual check ---------------------------------------------------- */
+
+/* Largest n_cams accepted by ba_schur_residual_static. */
+#define BA_STATIC_MAX_CAMS 65536
+
+/*
+ * |-b~ - S x| and |b~| for a block-sparse S that the caller holds in device memory, computed
+ * without allocating anything.  The paper has no counterpart; this exists for callers that
+ * cannot call cudaMalloc where they check a solution: code running while a CUDA graph is being
+ * captured, loops whose device memory is fixed up front, or hosts whose allocator owns all
+ * device memory.
+ *   n_cams   block rows of S, 1 .. BA_STATIC_MAX_CAMS (larger: INVALID_ARG, nothing launched)
+ *   row_ptr  n_cams + 1 int64 block offsets, device
+ *   col      block column indices (int32), device
+ *   blocks   9x9 row-major blocks, device (the layout ba_get_schur returns)
+ *   btilde   9 n_cams, device;  x   9 n_cams, device
+ *   out      2 doubles, device: out[0] = |-b~ - S x|_2, out[1] = |b~|_2
+ *   stream   cudaStream_t (NULL = legacy default); the call returns after enqueueing
+ * Working memory is one file-scope device array of 2 * BA_STATIC_MAX_CAMS doubles (1 MiB) that
+ * every GPU loading the library holds until the process exits; each call overwrites every
+ * entry it reads, so nothing has to be cleared between calls.  All calls share that array:
+ * calls that overlap on the GPU (different streams, or different host threads) race and give
+ * wrong results, so order them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), which is not a stream operation; make that first call before
+ * any stream capture.  No cudaMalloc, cudaFree or other allocating call is made.  Errors:
+ * INVALID_ARG, CUDA; the text is available from ba_last_error(NULL) on the calling thread.
+ */
+int ba_schur_residual_static(int32_t n_cams, const int64_t* row_ptr, const int32_t* col,
+                             const double* blocks, const double* btilde, const double* x,
+                             double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

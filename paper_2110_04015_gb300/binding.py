@@ -87,7 +87,9 @@ _SIGNATURES = {
     "ba_get_residual_history": (_I32, [_P, _P, _I32, _P]),
     "ba_get_launch_count": (_I32, [_P, _P]),
     "ba_time_kernel": (_I32, [_P, _I32, _I32, _P]),
+    "ba_schur_residual_static": (_I32, [_I32, _P, _P, _P, _P, _P, _P, _P]),
 }
+BA_STATIC_MAX_CAMS = 65536
 KERNEL = {"spmv": 0, "schur": 1, "linearize": 2}
 
 _lib = None
@@ -154,6 +156,14 @@ def ba_project(cams, pts, obs_cam, obs_pt, out, stream=None) -> None:
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     code = lib().ba_project(int(cams.shape[0]), int(pts.shape[0]), int(obs_cam.shape[0]), _ptr(cams), _ptr(pts),
                             _ptr(obs_cam), _ptr(obs_pt), _ptr(out), st)
+    _check(code)
+
+
+def ba_schur_residual_static(n_cams, row_ptr, col, blocks, btilde, x, out, stream=None) -> None:
+    """|-b~ - S x| and |b~| into out[0:2] without any device allocation (device tensors)."""
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    code = lib().ba_schur_residual_static(int(n_cams), _ptr(row_ptr), _ptr(col), _ptr(blocks), _ptr(btilde),
+                                          _ptr(x), _ptr(out), st)
     _check(code)
 
 
