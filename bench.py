@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense-1936", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the float64 comparison solves")
     ap.add_argument("--n-dirs", type=int, default=16)
     ap.add_argument("--tau", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,8 +71,10 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# FP64 arithmetic peak of a GB300 (nominal 1.25 TFLOP/s dense, NVIDIA's figure for the part).
-FP64_PEAK_TFLOPS = 1.25
+# FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
+# (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
+# NVIDIA's nominal figure for the part is 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.06
 
 
 class ClockSampler:
@@ -215,6 +218,24 @@ def run_reference(a, rank: int, world: int):
 
 
 # ------------------------------------------------------------------------------------------
+# replicas: every rank solves its own problem; only the timing is combined
+
+def rank_seed(rank: int) -> int:
+    """Scene seed of a rank: independent problems, no data exchanged between ranks."""
+    return rank
+
+
+def aggregate_ms(t_local_ms: float, steps: int, world: int, dist=None, device=None) -> tuple[float, float]:
+    """(T_max over ranks, whole-job ms per step = T_max / (world * steps))."""
+    T = float(t_local_ms)
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([T], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+    return T, T / (steps * world)
+
 
 def run_ours(a, rank: int, world: int, local_rank: int):
     import torch
@@ -228,7 +249,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     gen, kw, desc = WORKLOADS[a.workload]
-    sc = synthetic.make(gen, seed=rank, **kw)
+    sc = synthetic.make(gen, seed=rank_seed(rank), **kw)
     xy = problem.device_measurements(sc, device=str(dev))
     p = problem.from_scene(sc, precision=a.precision, xy=xy)
     stream = torch.cuda.current_stream()
@@ -265,12 +286,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    T = float(sum(times))
-    if dist:
-        t = torch.tensor([T], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
-    value = T / (a.steps * world)
+    T, value = aggregate_ms(sum(times), a.steps, world, dist, dev)
 
     # breakdown of the last step
     s_pcg, s_mcg = stats[-1]
@@ -287,19 +303,19 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
     spmv_flops = 162.0 * nnzb
     if a.precision == "fp64":
-        roof = {"kernel": "k_pcg_spmv<double> (q = S p)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
+        roof = {"kernel": "k_spmv<double,1> (q = S p, Algorithm 1 line 3)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
                 "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "ms_per_launch": t_spmv,
                 "achieved_gbs": spmv_bytes / t_spmv / 1e6, "hbm_peak_gbs": peaks["hbm_gbs"],
-                "peak_source": "nominal FP64 1.25 TFLOP/s"}
+                "peak_source": "measured FP64 FMA throughput 1.06 TFLOP/s (nominal 1.25)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
-        roof = {"kernel": "k_pcg_spmv<float> (q = S p)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
+        roof = {"kernel": "k_spmv<float,1> (q = S p, Algorithm 1 line 3)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "bytes_per_launch": spmv_bytes,
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
     # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
-    roof_schur = {"kernel": "k_schur (S block build)", "ms_per_launch": t_schur}
+    roof_schur = {"kernel": "k_schur_off (off-diagonal S blocks, Eq. 13)", "ms_per_launch": t_schur}
 
     # end to end through the host-buffer API: parameters in, both solutions out
     e2e = None
@@ -317,13 +333,38 @@ def run_ours(a, rank: int, world: int, local_rank: int):
             p.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
             p.ba_get_delta(dx_h)
         torch.cuda.synchronize()
-        Te = (time.perf_counter() - t0) * 1e3
-        if dist:
-            t = torch.tensor([Te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            Te = float(t.item())
-        e2e = {"value": Te / (a.steps * world), "unit": "ms/step",
+        Te, e2e_value = aggregate_ms((time.perf_counter() - t0) * 1e3, a.steps, world, dist, dev)
+        e2e = {"value": e2e_value, "unit": "ms/step",
                "h2d_bytes_per_step": int(cams_h.nbytes + pts_h.nbytes), "d2h_bytes_per_step": int(2 * dx_h.nbytes)}
+
+    p.close()
+
+    # the same step in float64 throughout, for the FP64-vs-mixed comparison of the metric
+    fp64 = None
+    if a.precision == "mixed" and not a.no_compare:
+        q = problem.from_scene(sc, precision="fp64", xy=xy)
+        q.ba_set_stream(stream)
+
+        def step64():
+            q.ba_build_normal(LAMBDA)
+            return q.ba_solve_pcg(TOL, MAX_ITERS), q.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
+
+        step64()
+        t64 = []
+        for _ in range(2):
+            flush.zero_()
+            e0.record(stream)
+            s1, s2 = step64()
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        t_sp64 = q.ba_time_kernel("spmv", reps=5)
+        fp64 = {"step_ms": float(np.mean(t64)), "pcg": {k: s1[k] for k in ("iters", "ms", "true_rel_residual")},
+                "mcg": {k: s2[k] for k in ("iters", "local_steps", "ms", "true_rel_residual")},
+                "build_ms": float(np.mean(t64)) - s1["ms"] - s2["ms"],
+                "spmv": {"kernel": "k_spmv<double,1>", "ms_per_launch": t_sp64,
+                         "achieved_tflops": 162.0 * nnzb / t_sp64 / 1e9, "peak_tflops": FP64_PEAK_TFLOPS}}
+        q.close()
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -351,13 +392,13 @@ def run_ours(a, rank: int, world: int, local_rank: int):
             },
             "roofline": roof,
             "roofline_build": roof_schur,
+            "fp64": fp64,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    p.close()
 
 
 def main():

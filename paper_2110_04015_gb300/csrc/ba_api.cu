@@ -145,19 +145,31 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         std::vector<int64_t> fill(cam_ptr.begin(), cam_ptr.end() - 1);
         for (int64_t k = 0; k < n_o; ++k) cam_obs[fill[scam[k]]++] = int32_t(k);
     }
-    // observation pairs (a, b) of one landmark with cam(a) <= cam(b), sorted by (cam(a), cam(b))
+    // each (camera, landmark) pair at most once: the diagonal blocks of S are then sums over
+    // single observations and only pairs of different cameras feed the off-diagonal blocks
+    {
+        std::vector<int32_t> stamp(n_c, -1);
+        for (int32_t l = 0; l < n_l; ++l)
+            for (int64_t a = pt_ptr[l]; a < pt_ptr[l + 1]; ++a) {
+                if (stamp[scam[a]] == l)
+                    throw Error(BA_ERR_INVALID_ARG, "camera " + std::to_string(scam[a]) + " observes landmark " +
+                                                        std::to_string(l) + " more than once");
+                stamp[scam[a]] = l;
+            }
+    }
+    // observation pairs (a, b) of one landmark with cam(a) < cam(b), sorted by (cam(a), cam(b))
     int64_t n_pairs = 0;
     for (int32_t l = 0; l < n_l; ++l)
         for (int64_t a = pt_ptr[l]; a < pt_ptr[l + 1]; ++a)
             for (int64_t b = pt_ptr[l]; b < pt_ptr[l + 1]; ++b)
-                if (scam[a] <= scam[b]) ++n_pairs;
+                if (scam[a] < scam[b]) ++n_pairs;
     std::vector<int2> pr(n_pairs), pr2(n_pairs);
     {
         int64_t t = 0;
         for (int32_t l = 0; l < n_l; ++l)
             for (int64_t a = pt_ptr[l]; a < pt_ptr[l + 1]; ++a)
                 for (int64_t b = pt_ptr[l]; b < pt_ptr[l + 1]; ++b)
-                    if (scam[a] <= scam[b]) pr[t++] = make_int2(int32_t(a), int32_t(b));
+                    if (scam[a] < scam[b]) pr[t++] = make_int2(int32_t(a), int32_t(b));
         // LSD radix: by cam(b), then stably by cam(a)
         std::vector<int64_t> cnt(size_t(n_c) + 1);
         for (int pass = 0; pass < 2; ++pass) {
@@ -168,37 +180,29 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
             pr.swap(pr2);
         }
     }
-    // upper blocks, row by row, with the diagonal always present
+    // off-diagonal upper blocks (j < k), row by row
     std::vector<int32_t> up_j, up_k;
     std::vector<int64_t> up_pp;
     {
         int64_t q = 0;
-        for (int32_t j = 0; j < n_c; ++j) {
-            bool has_diag = q < n_pairs && scam[pr[q].x] == j && scam[pr[q].y] == j;
-            if (!has_diag) {
-                up_j.push_back(j);
-                up_k.push_back(j);
-                up_pp.push_back(q);
-            }
-            while (q < n_pairs && scam[pr[q].x] == j) {
-                int32_t k = scam[pr[q].y];
-                up_j.push_back(j);
-                up_k.push_back(k);
-                up_pp.push_back(q);
-                while (q < n_pairs && scam[pr[q].x] == j && scam[pr[q].y] == k) ++q;
-            }
+        while (q < n_pairs) {
+            const int32_t j = scam[pr[q].x], k = scam[pr[q].y];
+            up_j.push_back(j);
+            up_k.push_back(k);
+            up_pp.push_back(q);
+            while (q < n_pairs && scam[pr[q].x] == j && scam[pr[q].y] == k) ++q;
         }
         up_pp.push_back(n_pairs);
     }
     const int64_t n_up = int64_t(up_j.size());
-    // full pattern: row j = lower blocks (k < j, mirrored) then upper blocks (k >= j)
+    // full pattern: row j = lower blocks (k < j, mirrored), the diagonal, upper blocks (k > j)
     std::vector<int64_t> lower_cnt(n_c, 0), upper_cnt(n_c, 0);
     for (int64_t u = 0; u < n_up; ++u) {
         upper_cnt[up_j[u]]++;
-        if (up_k[u] != up_j[u]) lower_cnt[up_k[u]]++;
+        lower_cnt[up_k[u]]++;
     }
     std::vector<int64_t> row_ptr(size_t(n_c) + 1, 0);
-    for (int32_t j = 0; j < n_c; ++j) row_ptr[j + 1] = row_ptr[j] + lower_cnt[j] + upper_cnt[j];
+    for (int32_t j = 0; j < n_c; ++j) row_ptr[j + 1] = row_ptr[j] + lower_cnt[j] + 1 + upper_cnt[j];
     const int64_t nnzb = row_ptr[n_c];
     std::vector<int32_t> col(nnzb), diag_pos(n_c);
     std::vector<int64_t> up_pos(n_up), up_mir(n_up);
@@ -206,23 +210,21 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         std::vector<int64_t> lfill(n_c), ufill(n_c);
         for (int32_t j = 0; j < n_c; ++j) {
             lfill[j] = row_ptr[j];
-            ufill[j] = row_ptr[j] + lower_cnt[j];
+            diag_pos[j] = int32_t(row_ptr[j] + lower_cnt[j]);
+            col[diag_pos[j]] = j;
+            ufill[j] = row_ptr[j] + lower_cnt[j] + 1;
         }
         // upper blocks are sorted by (j, k): fill upper parts in order
         for (int64_t u = 0; u < n_up; ++u) {
-            int32_t j = up_j[u], k = up_k[u];
-            int64_t pos = ufill[j]++;
-            col[pos] = k;
+            int64_t pos = ufill[up_j[u]]++;
+            col[pos] = up_k[u];
             up_pos[u] = pos;
-            if (k == j) diag_pos[j] = int32_t(pos);
         }
-        // lower parts: block (k, j) for upper (j, k), j < k; iterate u in (j, k) order so that
-        // row k's lower entries come out sorted by j
+        // lower parts: block (k, j) for upper (j, k); iterating u in (j, k) order keeps row k's
+        // lower entries sorted by j
         for (int64_t u = 0; u < n_up; ++u) {
-            int32_t j = up_j[u], k = up_k[u];
-            if (j == k) { up_mir[u] = -1; continue; }
-            int64_t pos = lfill[k]++;
-            col[pos] = j;
+            int64_t pos = lfill[up_k[u]]++;
+            col[pos] = up_j[u];
             up_mir[u] = pos;
         }
     }
@@ -259,6 +261,7 @@ void alloc_system(ba_problem* p) {
     ba::Structure& s = p->s;
     ba::System& y = p->y;
     y.cams = dev_alloc<double>(p, size_t(s.n_c) * 9);
+    y.aux = dev_alloc<double>(p, size_t(s.n_c) * 24);
     y.pts = dev_alloc<double>(p, size_t(s.n_l) * 3);
     y.r = dev_alloc<double>(p, size_t(s.n_o) * 2);
     y.Jc = dev_alloc<double>(p, size_t(s.n_o) * 18);
@@ -271,12 +274,17 @@ void alloc_system(ba_problem* p) {
     y.U = dev_alloc<double>(p, size_t(s.n_c) * 81);
     y.bp = dev_alloc<double>(p, size_t(s.n_c) * 9);
     y.bt = dev_alloc<double>(p, size_t(s.n_c) * 9);
-    y.S = dev_alloc<double>(p, size_t(s.n_tiles) * ba::kTileElems);
-    BA_CUDA_TRY(cudaMemset(y.S, 0, sizeof(double) * size_t(s.n_tiles) * ba::kTileElems));   // padding blocks stay 0
+    y.Sd = dev_alloc<double>(p, size_t(s.n_c) * 81);
+    if (p->opt.precision == BA_PRECISION_FP64) {
+        y.S = dev_alloc<double>(p, size_t(s.n_tiles) * ba::kTileElems);
+        BA_CUDA_TRY(cudaMemset(y.S, 0, sizeof(double) * size_t(s.n_tiles) * ba::kTileElems));   // padding stays 0
+    }
     y.Dinv = dev_alloc<double>(p, size_t(s.n_c) * 81);
     if (p->opt.precision == BA_PRECISION_MIXED) {
         y.S32 = dev_alloc<float>(p, size_t(s.n_tiles) * ba::kTileElems);
         BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
+        y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 27);
+        y.tl = dev_alloc<double>(p, size_t(s.n_l) * 3);
         y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
         y.Dhat = dev_alloc<double>(p, size_t(s.n_c) * 81);
     }
@@ -302,16 +310,20 @@ void do_build(ba_problem* p, double lambda) {
     y.built = false;
     p->solved = false;
     BA_CUDA_TRY(cudaMemsetAsync(y.status, 0, sizeof(int), st));
+    ba::launch_cam_prep(s, y, st);
     ba::launch_linearize(s, y, st);
     ba::launch_landmarks(s, y, p->opt.damping, lambda, st);
     ba::launch_obs_G(s, y, st);
     ba::launch_cameras(s, y, p->opt.damping, lambda, st);
-    ba::launch_schur(s, y, st);
+    ba::launch_schur_diag(s, y, st);
     ba::launch_block_jacobi(s, y, st);
-    p->launches += 6;
-    if (p->opt.precision == BA_PRECISION_MIXED) {
-        ba::launch_scaled_float(s, y, st);
+    p->launches += 7;
+    if (p->opt.precision == BA_PRECISION_FP64) {
+        ba::launch_schur(s, y, st);          // off-diagonal blocks + the diagonal from Sd
         p->launches += 2;
+    } else {
+        ba::launch_schur_mixed(s, y, st);    // scaled float32 G, off-diagonal and diagonal of S^
+        p->launches += 4;
     }
     check_launch();
     int status = 0;
@@ -677,7 +689,7 @@ int ba_get_schur(const ba_problem* pc, int64_t* row_ptr, int32_t* col, double* b
         if (blocks) {
             double* tmp = nullptr;
             BA_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * 81 * size_t(p->s.nnzb)));
-            ba::launch_unslab(p->s, p->y.S, tmp, p->stream);
+            ba::launch_unslab(p->s, p->y, tmp, p->stream);
             cudaError_t e = cudaMemcpyAsync(blocks, tmp, sizeof(double) * 81 * size_t(p->s.nnzb), cudaMemcpyDefault, p->stream);
             cudaStreamSynchronize(p->stream);
             cudaFree(tmp);
@@ -743,8 +755,13 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
         for (int k = 0; k < reps; ++k) {
             ba::flush_l2(st);
             BA_CUDA_TRY(cudaEventRecord(a, st));
-            if (kernel == BA_KERNEL_SCHUR) ba::launch_schur(p->s, p->y, st);
-            else ba::launch_linearize(p->s, p->y, st);
+            if (kernel == BA_KERNEL_SCHUR) {
+                if (p->opt.precision == BA_PRECISION_FP64) ba::launch_schur(p->s, p->y, st);
+                else ba::launch_schur_mixed(p->s, p->y, st);
+            } else {
+                ba::launch_cam_prep(p->s, p->y, st);
+                ba::launch_linearize(p->s, p->y, st);
+            }
             BA_CUDA_TRY(cudaEventRecord(b, st));
             BA_CUDA_TRY(cudaEventSynchronize(b));
             check_launch();

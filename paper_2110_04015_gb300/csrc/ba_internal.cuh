@@ -8,13 +8,14 @@
 //                     b_l (3), e = L^{-1} b_l (3)
 //   per camera      : U_lambda (9x9), b_p (9), b~ (9), D_j^{-1} (9x9)
 //   S               : block-CSR over cameras, every nonzero 9x9 block of both
-//                     triangles.  The blocks of block-row j are grouped in tiles
-//                     of 32 consecutive blocks (the last tile of a row padded with
-//                     zero blocks); a tile holds its 32 x 81 values entry-major:
-//                     entry e of tile-local block l at tile[e * 32 + l].  A tile is
-//                     one contiguous run (10 KB float32, 20 KB float64) that a bulk
-//                     copy moves to shared memory, and a warp whose lanes take the
-//                     32 blocks of a tile reads consecutive words.
+//                     triangles, each block 81 contiguous values (row-major).  The
+//                     blocks of block-row j are grouped in tiles of 32 consecutive
+//                     blocks, the last tile of a row padded with zero blocks, so a
+//                     tile is one contiguous run (10 KB float32, 20 KB float64) that
+//                     a bulk copy moves to shared memory; lanes that take the 32
+//                     blocks of a tile then read shared memory at stride 81 (odd:
+//                     no bank conflicts in float32), and a warp that builds one
+//                     block writes 81 consecutive values.
 // With G_o = W_o L_l^{-T} (V_l = L_l L_l^T) the Schur complement of Eq. 13 is
 //   S_jk = delta_jk U_j - sum_{l seen by j and k} G_jl G_kl^T,
 // and b~_j = b_p,j - sum_{o in camera j} G_o e_l (Eq. 14).
@@ -36,7 +37,7 @@ constexpr int kTileElems = 81 * kTile;    // values per tile
 
 // Index of entry e (= 9 a + b) of the q-th block (row-local) of block-row j of S.
 __host__ __device__ __forceinline__ int64_t s_at(const int64_t* tile_ptr, int64_t j, int64_t q, int e) {
-    return (tile_ptr[j] + (q >> 5)) * kTileElems + int64_t(e) * kTile + (q & 31);
+    return (tile_ptr[j] * kTile + q) * 81 + e;
 }
 constexpr int kMaxDirs = 16;   // widest direction block held by the small FP64 solves
 
@@ -91,6 +92,7 @@ struct Structure {
 // The linearised system at the current parameters (rebuilt by ba_build_normal).
 struct System {
     double* cams = nullptr;   // n_c x 9 current parameters
+    double* aux = nullptr;    // n_c x 24: R, J_r, t, f, k1, k2 per camera (linearisation)
     double* pts = nullptr;    // n_l x 3
     double* r = nullptr;      // n_o x 2
     double* Jc = nullptr;     // n_o x 18
@@ -103,7 +105,8 @@ struct System {
     double* U = nullptr;      // n_c x 81
     double* bp = nullptr;     // n_c x 9
     double* bt = nullptr;     // n_c x 9
-    double* S = nullptr;      // n_tiles x 2592 (tiled layout above)
+    double* S = nullptr;      // n_tiles x 2592 (tiled layout above); float64 precision only
+    double* Sd = nullptr;     // n_c x 81: the diagonal blocks S_jj = U_j - sum_o G_o G_o^T
     double* Dinv = nullptr;   // n_c x 81
     // mixed precision: the inner solves run on the Jacobi-scaled system
     //   S^ = Lam S Lam, Lam = diag(S)^{-1/2},
@@ -111,6 +114,8 @@ struct System {
     float* S32 = nullptr;     // float(S^), tiled layout
     double* lam = nullptr;    // 9 n_c: Lam
     double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
+    float* G32 = nullptr;     // n_o x 27: float(Lam_cam G_o), the scaled observation blocks
+    double* tl = nullptr;     // n_l x 3: landmark sums of the implicit product G^T x
     int* status = nullptr;    // device error word of the build
     double lambda = 0.0;
     bool built = false;
@@ -119,14 +124,20 @@ struct System {
 // ---- launch wrappers (k_build.cu) -----------------------------------------------------
 void launch_project(int64_t n_o, const double* cams, const double* pts, const int32_t* oc,
                     const int32_t* op, double* out, cudaStream_t st);
+void launch_cam_prep(const Structure& s, System& y, cudaStream_t st);   // aux from cams (before linearize)
 void launch_linearize(const Structure& s, System& y, cudaStream_t st);
 void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
 void launch_obs_G(const Structure& s, System& y, cudaStream_t st);
 void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+void launch_schur_diag(const Structure& s, System& y, cudaStream_t st);
 void launch_schur(const Structure& s, System& y, cudaStream_t st);
+void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st);
+// out = -b~ - S x with the implicit float64 operator S x = U x - G (G^T x) (no explicit S);
+// partial[2 j], partial[2 j + 1] receive camera j's sums of out^2 and b~^2 (2 n_c values)
+void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
+                              cudaStream_t st);
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st);
 void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st);
-void launch_scaled_float(const Structure& s, System& y, cudaStream_t st);
 void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl,
                             cudaStream_t st);
 void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial,
@@ -134,7 +145,9 @@ void launch_cost(const Structure& s, const double* cams, const double* pts, doub
 void launch_add_params(const double* a, const double* da, double* out, int64_t n, cudaStream_t st);
 void launch_unpermute(const double* in, const int32_t* perm, double* out, int64_t n_o, int width,
                       cudaStream_t st);
-void launch_unslab(const Structure& s, const double* S, double* out, cudaStream_t st);
+// row-major 9x9 blocks of S (float64 precision: S itself; mixed: Lam^-1 S^ Lam^-1 off the
+// diagonal and the float64 diagonal blocks)
+void launch_unslab(const Structure& s, const System& y, double* out, cudaStream_t st);
 
 // ---- solver (k_solve.cu) -------------------------------------------------------------------
 struct SolveArgs {

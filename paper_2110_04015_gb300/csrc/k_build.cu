@@ -4,9 +4,11 @@
 //   k_landmarks     one thread per landmark: V_lambda, b_l, Cholesky V = L L^T, e = L^{-1} b_l
 //   k_obs_G         one thread per observation: G_o = (J_p^T J_l) L^{-T}
 //   k_cameras       one CTA per camera: U_lambda, b_p, b~ = b_p - sum G_o e_l
-//   k_schur         one warp per upper block (j <= k): S_jk = delta U_j - sum G_o G_o'^T,
-//                   written to (j, k) and transposed to (k, j)
+//   k_schur_diag    one CTA per camera: S_jj = U_j - sum_o G_o G_o^T (float64)
+//   k_schur_off     one warp per upper block (j < k): S_jk = - sum G_oj G_ok^T over the observation
+//                   pairs of shared landmarks, written to (j, k) and transposed to (k, j)
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
+//   k_implicit_*    the float64 product S x = U x - G (G^T x) without an explicit S
 // S is written in the tiled layout of ba_internal.cuh (s_at).
 // Every kernel uses grid-stride loops and 64-bit indices.
 #include <cuda_runtime.h>
@@ -76,51 +78,58 @@ __device__ __forceinline__ void bal_project(const double* c, const double* X, do
     out[1] = c[6] * rho * p1;
 }
 
-// Residual and Jacobian blocks of one observation.  d(R X)/d omega = -R [X]x J_r(omega),
+// Per-camera part of the linearisation, shared by all observations of the camera:
+// aux = (R[9], J_r[9], t[3], f, k1, k2), with d(R X)/d omega = -R [X]x J_r(omega) and
 // J_r = I - B [w]x + C [w]x^2 the right Jacobian of the rotation exponential.
-__device__ __forceinline__ void bal_linearize(const double* c, const double* X, const double* m,
-                                              double* r, double* Jc, double* Jl) {
-    double w[3] = {c[0], c[1], c[2]};
-    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double A, B, C, R[9];
-    rot_coeffs(th2, A, B, C);
-    rot_matrix(w, A, B, th2, R);
-    double P[3];
-    for (int a = 0; a < 3; ++a) P[a] = R[3 * a] * X[0] + R[3 * a + 1] * X[1] + R[3 * a + 2] * X[2] + c[3 + a];
+__global__ void k_cam_prep(int32_t n_c, const double* __restrict__ cams, double* __restrict__ aux) {
+    for (int64_t j = gtid(); j < n_c; j += gstride()) {
+        const double* c = cams + 9 * j;
+        double w[3] = {c[0], c[1], c[2]};
+        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        double A, B, C, R[9];
+        rot_coeffs(th2, A, B, C);
+        rot_matrix(w, A, B, th2, R);
+        double* o = aux + 24 * j;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = R[k];
+        o[9] = 1.0 + C * (w[0] * w[0] - th2);
+        o[10] = B * w[2] + C * w[0] * w[1];
+        o[11] = -B * w[1] + C * w[0] * w[2];
+        o[12] = -B * w[2] + C * w[0] * w[1];
+        o[13] = 1.0 + C * (w[1] * w[1] - th2);
+        o[14] = B * w[0] + C * w[1] * w[2];
+        o[15] = B * w[1] + C * w[0] * w[2];
+        o[16] = -B * w[0] + C * w[1] * w[2];
+        o[17] = 1.0 + C * (w[2] * w[2] - th2);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[18 + k] = c[3 + k];
+    }
+}
 
-    // J_r
-    double Jr[9];
-    Jr[0] = 1.0 + C * (w[0] * w[0] - th2);
-    Jr[1] = B * w[2] + C * w[0] * w[1];
-    Jr[2] = -B * w[1] + C * w[0] * w[2];
-    Jr[3] = -B * w[2] + C * w[0] * w[1];
-    Jr[4] = 1.0 + C * (w[1] * w[1] - th2);
-    Jr[5] = B * w[0] + C * w[1] * w[2];
-    Jr[6] = B * w[1] + C * w[0] * w[2];
-    Jr[7] = -B * w[0] + C * w[1] * w[2];
-    Jr[8] = 1.0 + C * (w[2] * w[2] - th2);
-    // M = [X]x J_r ; rows of [X]x: (0, -X2, X1), (X2, 0, -X0), (-X1, X0, 0)
+// Residual and Jacobian blocks of one observation from the camera's prepared aux block.
+__device__ __forceinline__ void bal_linearize_aux(const double* ax, const double* X, const double* m, double* r,
+                                                  double* Jc, double* Jl) {
+    const double* R = ax;
+    const double* Jr = ax + 9;
+    double P[3];
+    for (int a = 0; a < 3; ++a) P[a] = R[3 * a] * X[0] + R[3 * a + 1] * X[1] + R[3 * a + 2] * X[2] + ax[18 + a];
     double M[9];
     for (int b = 0; b < 3; ++b) {
         M[b] = -X[2] * Jr[3 + b] + X[1] * Jr[6 + b];
         M[3 + b] = X[2] * Jr[b] - X[0] * Jr[6 + b];
         M[6 + b] = -X[1] * Jr[b] + X[0] * Jr[3 + b];
     }
-    // dP/dw = -R M
     double dPdw[9];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
             dPdw[3 * a + b] = -(R[3 * a] * M[b] + R[3 * a + 1] * M[3 + b] + R[3 * a + 2] * M[6 + b]);
-
-    double iz = 1.0 / P[2];
-    double p0 = -P[0] * iz, p1 = -P[1] * iz;
-    double f = c[6], k1 = c[7], k2 = c[8];
-    double n2 = p0 * p0 + p1 * p1;
-    double rho = 1.0 + k1 * n2 + k2 * n2 * n2;
-    double drho = 2.0 * (k1 + 2.0 * k2 * n2);
-    // dpi/dp = f (rho I + drho p p^T)
-    double E00 = f * (rho + drho * p0 * p0), E01 = f * drho * p0 * p1, E11 = f * (rho + drho * p1 * p1);
-    // dp/dP = [[-iz, 0, -p0 iz], [0, -iz, -p1 iz]]  (P_x iz^2 = -p0 iz)
+    const double iz = 1.0 / P[2];
+    const double p0 = -P[0] * iz, p1 = -P[1] * iz;
+    const double f = ax[21], k1 = ax[22], k2 = ax[23];
+    const double n2 = p0 * p0 + p1 * p1;
+    const double rho = 1.0 + k1 * n2 + k2 * n2 * n2;
+    const double drho = 2.0 * (k1 + 2.0 * k2 * n2);
+    const double E00 = f * (rho + drho * p0 * p0), E01 = f * drho * p0 * p1, E11 = f * (rho + drho * p1 * p1);
     double D[6];
     D[0] = -E00 * iz;
     D[1] = -E01 * iz;
@@ -128,7 +137,6 @@ __device__ __forceinline__ void bal_linearize(const double* c, const double* X, 
     D[3] = -E01 * iz;
     D[4] = -E11 * iz;
     D[5] = -(E01 * p0 + E11 * p1) * iz;
-
     r[0] = f * rho * p0 - m[0];
     r[1] = f * rho * p1 - m[1];
     for (int a = 0; a < 2; ++a) {
@@ -169,21 +177,21 @@ __global__ void k_project(int64_t n_o, const double* __restrict__ cams, const do
     }
 }
 
-__global__ void k_linearize(int64_t n_o, const double* __restrict__ cams, const double* __restrict__ pts,
+__global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const double* __restrict__ pts,
                             const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
                             const double* __restrict__ xy, double* __restrict__ r, double* __restrict__ Jc,
                             double* __restrict__ Jl) {
     for (int64_t i = gtid(); i < n_o; i += gstride()) {
-        double c[9], X[3], m[2], rr[2], jc[18], jl[6];
-        const double* cp = cams + int64_t(oc[i]) * 9;
+        double ax[24], X[3], m[2], rr[2], jc[18], jl[6];
+        const double* cp = aux + int64_t(oc[i]) * 24;
         const double* xp = pts + int64_t(op[i]) * 3;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) c[k] = __ldg(cp + k);
+        for (int k = 0; k < 24; ++k) ax[k] = __ldg(cp + k);
 #pragma unroll
         for (int k = 0; k < 3; ++k) X[k] = __ldg(xp + k);
         m[0] = xy[2 * i];
         m[1] = xy[2 * i + 1];
-        bal_linearize(c, X, m, rr, jc, jl);
+        bal_linearize_aux(ax, X, m, rr, jc, jl);
         r[2 * i] = rr[0];
         r[2 * i + 1] = rr[1];
 #pragma unroll
@@ -249,7 +257,8 @@ __global__ void k_obs_G(int64_t n_o, const int32_t* __restrict__ op, const doubl
                         const double* __restrict__ Jl, const double* __restrict__ Lall, double* __restrict__ G) {
     for (int64_t o = gtid(); o < n_o; o += gstride()) {
         const double* L = Lall + 6 * int64_t(op[o]);
-        double l00 = L[0], l10 = L[1], l11 = L[2], l20 = L[3], l21 = L[4], l22 = L[5];
+        const double l10 = L[1], l20 = L[3], l21 = L[4];
+        const double i00 = 1.0 / L[0], i11 = 1.0 / L[2], i22 = 1.0 / L[5];
         double jl[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) jl[k] = Jl[6 * o + k];
@@ -260,9 +269,9 @@ __global__ void k_obs_G(int64_t n_o, const int32_t* __restrict__ op, const doubl
             double w0 = ca * jl[0] + cb * jl[3];
             double w1 = ca * jl[1] + cb * jl[4];
             double w2 = ca * jl[2] + cb * jl[5];
-            double g0 = w0 / l00;
-            double g1 = (w1 - l10 * g0) / l11;
-            double g2 = (w2 - l20 * g0 - l21 * g1) / l22;
+            const double g0 = w0 * i00;
+            const double g1 = (w1 - l10 * g0) * i11;
+            const double g2 = (w2 - l20 * g0 - l21 * g1) * i22;
             G[27 * o + 3 * a] = g0;
             G[27 * o + 3 * a + 1] = g1;
             G[27 * o + 3 * a + 2] = g2;
@@ -362,64 +371,217 @@ __global__ void __launch_bounds__(kCamThreads) k_cameras(
     }
 }
 
-// One warp per upper block (j, k): acc = sum over observation pairs of G_o G_o'^T.
-__global__ void k_schur(int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
-                        const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir,
-                        const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
-                        const double* __restrict__ G, const double* __restrict__ U,
-                        const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
-                        double* __restrict__ S) {
-    __shared__ double sg[kThreads / 32][2][28];
+// Diagonal blocks S_jj = U_j - sum_{o in camera j} G_o G_o^T in float64, one CTA per camera
+// (each camera sees a landmark at most once, so no pair of distinct observations adds here).
+__global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const int64_t* __restrict__ cam_ptr,
+                                                           const int32_t* __restrict__ cam_obs,
+                                                           const double* __restrict__ G, const double* __restrict__ U,
+                                                           double* __restrict__ Sd) {
+    __shared__ double red[kCamThreads / 32][48];
+    __shared__ double fin[48];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        double acc[45];
+#pragma unroll
+        for (int k = 0; k < 45; ++k) acc[k] = 0.0;
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const double* g = G + 27 * int64_t(cam_obs[q]);
+            double gv[27];
+#pragma unroll
+            for (int k = 0; k < 27; ++k) gv[k] = g[k];
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int bb = a; bb < 9; ++bb)
+                    acc[t++] += gv[3 * a] * gv[3 * bb] + gv[3 * a + 1] * gv[3 * bb + 1] + gv[3 * a + 2] * gv[3 * bb + 2];
+        }
+#pragma unroll
+        for (int k = 0; k < 45; ++k) {
+            double v = warp_sum(acc[k]);
+            if (lane == 0) red[wid][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 45) {
+            double v = 0;
+            for (int w = 0; w < kCamThreads / 32; ++w) v += red[w][threadIdx.x];
+            fin[threadIdx.x] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 81) {
+            const int a = threadIdx.x / 9, bb = threadIdx.x % 9;
+            const int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+            const int idx = lo * 9 - lo * (lo - 1) / 2 + (hi - lo);
+            Sd[81 * int64_t(j) + threadIdx.x] = U[81 * int64_t(j) + threadIdx.x] - fin[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// Off-diagonal blocks: one warp per upper block (j < k), S_jk = - sum over the observation pairs
+// (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to (k, j).  Lane
+// entries are e = lane, lane + 32, lane + 64 (< 81); G rows are read straight from global memory
+// (broadcast through L1), two pairs per step.
+template <typename T>
+__global__ void k_schur_off(int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
+                            const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir,
+                            const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
+                            const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
+                            const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
     const int64_t nw = gstride() >> 5;
-    // entries handled by this lane: e = lane, lane + 32, lane + 64 (< 81)
     const int e0 = lane, e1 = lane + 32, e2 = lane + 64;
     const int a0 = e0 / 9, b0 = e0 % 9, a1 = e1 / 9, b1 = e1 % 9;
-    const int a2 = e2 < 81 ? e2 / 9 : 0, b2 = e2 < 81 ? e2 % 9 : 0;
+    const bool has2 = e2 < 81;
+    const int a2 = has2 ? e2 / 9 : 0, b2 = has2 ? e2 % 9 : 0;
     for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
-        double s0 = 0, s1 = 0, s2 = 0;
+        T s0 = T(0), s1 = T(0), s2 = T(0);
         const int64_t pb = pair_ptr[u], pe = pair_ptr[u + 1];
-        for (int64_t q = pb; q < pe; ++q) {
-            const int2 pr = pairs[q];
-            __syncwarp();
-            if (lane < 27) {
-                sg[wid][0][lane] = G[27 * int64_t(pr.x) + lane];
-                sg[wid][1][lane] = G[27 * int64_t(pr.y) + lane];
-            }
-            __syncwarp();
-            const double* g1 = sg[wid][0];
-            const double* g2 = sg[wid][1];
-            s0 += g1[3 * a0] * g2[3 * b0] + g1[3 * a0 + 1] * g2[3 * b0 + 1] + g1[3 * a0 + 2] * g2[3 * b0 + 2];
-            s1 += g1[3 * a1] * g2[3 * b1] + g1[3 * a1 + 1] * g2[3 * b1 + 1] + g1[3 * a1 + 2] * g2[3 * b1 + 2];
-            s2 += g1[3 * a2] * g2[3 * b2] + g1[3 * a2 + 1] * g2[3 * b2 + 1] + g1[3 * a2 + 2] * g2[3 * b2 + 2];
+        int64_t q = pb;
+        for (; q + 1 < pe; q += 2) {
+            const int2 pa = pairs[q], pc = pairs[q + 1];
+            const T* g1 = G + 27 * int64_t(pa.x);
+            const T* g2 = G + 27 * int64_t(pa.y);
+            const T* h1 = G + 27 * int64_t(pc.x);
+            const T* h2 = G + 27 * int64_t(pc.y);
+            s0 += __ldg(g1 + 3 * a0) * __ldg(g2 + 3 * b0) + __ldg(g1 + 3 * a0 + 1) * __ldg(g2 + 3 * b0 + 1) +
+                  __ldg(g1 + 3 * a0 + 2) * __ldg(g2 + 3 * b0 + 2);
+            s1 += __ldg(g1 + 3 * a1) * __ldg(g2 + 3 * b1) + __ldg(g1 + 3 * a1 + 1) * __ldg(g2 + 3 * b1 + 1) +
+                  __ldg(g1 + 3 * a1 + 2) * __ldg(g2 + 3 * b1 + 2);
+            s2 += __ldg(g1 + 3 * a2) * __ldg(g2 + 3 * b2) + __ldg(g1 + 3 * a2 + 1) * __ldg(g2 + 3 * b2 + 1) +
+                  __ldg(g1 + 3 * a2 + 2) * __ldg(g2 + 3 * b2 + 2);
+            s0 += __ldg(h1 + 3 * a0) * __ldg(h2 + 3 * b0) + __ldg(h1 + 3 * a0 + 1) * __ldg(h2 + 3 * b0 + 1) +
+                  __ldg(h1 + 3 * a0 + 2) * __ldg(h2 + 3 * b0 + 2);
+            s1 += __ldg(h1 + 3 * a1) * __ldg(h2 + 3 * b1) + __ldg(h1 + 3 * a1 + 1) * __ldg(h2 + 3 * b1 + 1) +
+                  __ldg(h1 + 3 * a1 + 2) * __ldg(h2 + 3 * b1 + 2);
+            s2 += __ldg(h1 + 3 * a2) * __ldg(h2 + 3 * b2) + __ldg(h1 + 3 * a2 + 1) * __ldg(h2 + 3 * b2 + 1) +
+                  __ldg(h1 + 3 * a2 + 2) * __ldg(h2 + 3 * b2 + 2);
+        }
+        if (q < pe) {
+            const int2 pa = pairs[q];
+            const T* g1 = G + 27 * int64_t(pa.x);
+            const T* g2 = G + 27 * int64_t(pa.y);
+            s0 += __ldg(g1 + 3 * a0) * __ldg(g2 + 3 * b0) + __ldg(g1 + 3 * a0 + 1) * __ldg(g2 + 3 * b0 + 1) +
+                  __ldg(g1 + 3 * a0 + 2) * __ldg(g2 + 3 * b0 + 2);
+            s1 += __ldg(g1 + 3 * a1) * __ldg(g2 + 3 * b1) + __ldg(g1 + 3 * a1 + 1) * __ldg(g2 + 3 * b1 + 1) +
+                  __ldg(g1 + 3 * a1 + 2) * __ldg(g2 + 3 * b1 + 2);
+            s2 += __ldg(g1 + 3 * a2) * __ldg(g2 + 3 * b2) + __ldg(g1 + 3 * a2 + 1) * __ldg(g2 + 3 * b2 + 1) +
+                  __ldg(g1 + 3 * a2 + 2) * __ldg(g2 + 3 * b2 + 2);
         }
         const int j = up_j[u], k = up_k[u];
-        const int64_t pos = up_pos[u], mir = up_mir[u];
-        const int64_t qj = pos - row_ptr[j];
-        const double* Uj = U + 81 * int64_t(j);
-        const bool diag = (j == k);
-        S[s_at(tile_ptr, j, qj, e0)] = (diag ? Uj[e0] : 0.0) - s0;
-        S[s_at(tile_ptr, j, qj, e1)] = (diag ? Uj[e1] : 0.0) - s1;
-        if (e2 < 81) S[s_at(tile_ptr, j, qj, e2)] = (diag ? Uj[e2] : 0.0) - s2;
-        if (!diag) {
-            const int64_t qk = mir - row_ptr[k];
-            S[s_at(tile_ptr, k, qk, b0 * 9 + a0)] = -s0;
-            S[s_at(tile_ptr, k, qk, b1 * 9 + a1)] = -s1;
-            if (e2 < 81) S[s_at(tile_ptr, k, qk, b2 * 9 + a2)] = -s2;
+        const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
+        S[s_at(tile_ptr, j, qj, e0)] = -s0;
+        S[s_at(tile_ptr, j, qj, e1)] = -s1;
+        if (has2) S[s_at(tile_ptr, j, qj, e2)] = -s2;
+        S[s_at(tile_ptr, k, qk, b0 * 9 + a0)] = -s0;
+        S[s_at(tile_ptr, k, qk, b1 * 9 + a1)] = -s1;
+        if (has2) S[s_at(tile_ptr, k, qk, b2 * 9 + a2)] = -s2;
+    }
+}
+
+// S_jj into the tiled S: float64 copy, or (lam != nullptr) float(Lam S_jj Lam) for the scaled system.
+template <typename T>
+__global__ void k_put_diag(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
+                           const int32_t* __restrict__ diag_pos, const double* __restrict__ Sd,
+                           const double* __restrict__ lam, T* __restrict__ S) {
+    for (int64_t i = gtid(); i < int64_t(n_c) * 81; i += gstride()) {
+        const int64_t j = i / 81;
+        const int e = int(i - j * 81);
+        double v = Sd[i];
+        if (lam) v *= lam[9 * j + e / 9] * lam[9 * j + e % 9];
+        S[s_at(tile_ptr, j, diag_pos[j] - row_ptr[j], e)] = T(v);
+    }
+}
+
+// G32_o = float(Lam_cam(o) G_o): the observation blocks of the scaled system
+__global__ void k_scale_G(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
+                          const double* __restrict__ lam, float* __restrict__ G32) {
+    for (int64_t i = gtid(); i < n_o * 27; i += gstride()) {
+        const int64_t o = i / 27;
+        const int a = int(i - o * 27) / 3;
+        G32[i] = float(lam[9 * int64_t(oc[o]) + a] * G[i]);
+    }
+}
+
+// Implicit float64 product, landmark part: t_l = sum_{o in l} G_o^T x_cam(o)
+__global__ void k_implicit_t(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
+                             const double* __restrict__ G, const double* __restrict__ x, double* __restrict__ t) {
+    // one thread per (landmark, component c): t_l[c] = sum_o sum_a G_o[a][c] x_cam(o)[a]
+    for (int64_t i = gtid(); i < int64_t(n_l) * 3; i += gstride()) {
+        const int64_t l = i / 3;
+        const int c = int(i - 3 * l);
+        double acc = 0.0;
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
+            const double* g = G + 27 * o + c;
+            const double* xc = x + 9 * int64_t(oc[o]);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc += g[3 * a] * xc[a];
         }
+        t[i] = acc;
+    }
+}
+
+// Implicit float64 product, camera part, and the true residual: (S x)_j = U_j x_j - sum_{o in j} G_o t_l,
+// out_j = -b~_j - (S x)_j; CTA partial sums of |out|^2 and |b~|^2 into partial[2 b], partial[2 b + 1].
+__global__ void __launch_bounds__(kCamThreads) k_implicit_res(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const int32_t* __restrict__ op, const double* __restrict__ G, const double* __restrict__ t,
+    const double* __restrict__ U, const double* __restrict__ x, const double* __restrict__ bt,
+    double* __restrict__ out, double* __restrict__ partial) {
+    __shared__ double red[kCamThreads / 32][9];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        double tt = 0.0, bb = 0.0;
+        double acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = 0.0;
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const double* g = G + 27 * o;
+            const double* tl = t + 3 * int64_t(op[o]);
+            const double t0 = tl[0], t1 = tl[1], t2 = tl[2];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] += g[3 * a] * t0 + g[3 * a + 1] * t1 + g[3 * a + 2] * t2;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            double v = warp_sum(acc[a]);
+            if (lane == 0) red[wid][a] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            const int a = threadIdx.x;
+            double gt = 0.0;
+            for (int w = 0; w < kCamThreads / 32; ++w) gt += red[w][a];
+            double ux = 0.0;
+            for (int b = 0; b < 9; ++b) ux += U[81 * int64_t(j) + 9 * a + b] * x[9 * int64_t(j) + b];
+            const double b_ = bt[9 * int64_t(j) + a];
+            const double r = -b_ - (ux - gt);
+            if (out) out[9 * int64_t(j) + a] = r;
+            tt = r * r;
+            bb = b_ * b_;
+        }
+        // threads 0..8 hold this camera's terms; one partial pair per camera
+        if (threadIdx.x < 32) {
+            tt = warp_sum(tt);
+            bb = warp_sum(bb);
+            if (threadIdx.x == 0) {
+                partial[2 * int64_t(j)] = tt;
+                partial[2 * int64_t(j) + 1] = bb;
+            }
+        }
+        __syncthreads();
     }
 }
 
 // D_j^{-1} = (S_jj)^{-1} = L^{-T} L^{-1} from the Cholesky factor of the diagonal block.
 // With lam != nullptr the block is first scaled by its diagonal, B^ = s B s with s_a = B_aa^{-1/2};
 // Dinv then receives (B^)^{-1} and lam the scale factors.
-__global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
-                               const int32_t* __restrict__ diag_pos, const double* __restrict__ S,
-                               double* __restrict__ Dinv, double* __restrict__ lam, int* status) {
+__global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, double* __restrict__ Dinv,
+                               double* __restrict__ lam, int* status) {
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
-        const int64_t qd = diag_pos[j] - row_ptr[j];
         double L[81];
-        for (int e = 0; e < 81; ++e) L[e] = S[s_at(tile_ptr, j, qd, e)];
+        for (int e = 0; e < 81; ++e) L[e] = Sd[81 * j + e];
         if (lam) {
             double sc[9];
             for (int a = 0; a < 9; ++a) {
@@ -468,32 +630,6 @@ __global__ void k_block_jacobi(int32_t n_c, const int64_t* __restrict__ row_ptr,
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
     for (int64_t i = gtid(); i < n; i += gstride()) out[i] = static_cast<float>(in[i]);
-}
-
-// S32 = float(Lam S Lam), one warp per block-row, lanes over the row's blocks
-__global__ void k_scaled_float(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
-                               const int32_t* __restrict__ col, const double* __restrict__ S,
-                               const double* __restrict__ lam, float* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
-        const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj;
-        double lr[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) lr[a] = lam[9 * j + a];
-        for (int64_t q = lane; q < nj; q += 32) {
-            const int64_t k = col[rj + q];
-            double lc[9];
-#pragma unroll
-            for (int b = 0; b < 9; ++b) lc[b] = lam[9 * k + b];
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-#pragma unroll
-                for (int b = 0; b < 9; ++b) {
-                    const int64_t i = s_at(tile_ptr, j, q, 9 * a + b);
-                    out[i] = static_cast<float>(lr[a] * S[i] * lc[b]);
-                }
-        }
-    }
 }
 
 // dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
@@ -565,9 +701,11 @@ __global__ void k_unpermute(const double* __restrict__ in, const int32_t* __rest
     }
 }
 
-// tiled layout -> row-major 9x9 blocks
+// tiled layout -> row-major 9x9 blocks.  S64 (float64 precision) or S32 = Lam S Lam (mixed, unscaled here),
+// with the float64 diagonal blocks Sd in both cases.
 __global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
-                         const double* __restrict__ S, double* __restrict__ out) {
+                         const int32_t* __restrict__ col, const double* __restrict__ S64, const float* __restrict__ S32,
+                         const double* __restrict__ lam, const double* __restrict__ Sd, double* __restrict__ out) {
     const int64_t total = row_ptr[n_c] * 81;
     for (int64_t i = gtid(); i < total; i += gstride()) {
         const int64_t q = i / 81;
@@ -578,7 +716,15 @@ __global__ void k_unslab(int32_t n_c, const int64_t* __restrict__ row_ptr, const
             int mid = (lo + hi) >> 1;
             if (row_ptr[mid] <= q) lo = mid; else hi = mid;
         }
-        out[i] = S[s_at(tile_ptr, lo, q - row_ptr[lo], e)];
+        const int64_t k = col[q];
+        if (k == lo) {
+            out[i] = Sd[81 * int64_t(lo) + e];
+        } else if (S64) {
+            out[i] = S64[s_at(tile_ptr, lo, q - row_ptr[lo], e)];
+        } else {
+            const double v = double(S32[s_at(tile_ptr, lo, q - row_ptr[lo], e)]);
+            out[i] = v / (lam[9 * int64_t(lo) + e / 9] * lam[9 * k + e % 9]);
+        }
     }
 }
 
@@ -591,7 +737,7 @@ void launch_project(int64_t n_o, const double* cams, const double* pts, const in
 }
 
 void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
-    k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.cams, y.pts, s.obs_cam, s.obs_pt,
+    k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.aux, y.pts, s.obs_cam, s.obs_pt,
                                                                  s.obs_xy, y.r, y.Jc, y.Jl);
 }
 
@@ -610,24 +756,45 @@ void launch_cameras(const Structure& s, System& y, int damping, double lambda, c
                                          lambda, y.U, y.bp, y.bt);
 }
 
+void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
+    int g = s.n_c < num_sms() * 8 ? s.n_c : num_sms() * 8;
+    k_schur_diag<<<g, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.G, y.U, y.Sd);
+}
+
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
-    k_schur<<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir,
-                                                                   s.up_pair_ptr, s.pairs, y.G, y.U, s.row_ptr,
-                                                                   s.tile_ptr, y.S);
+    if (s.n_up > 0)
+        k_schur_off<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, s.row_ptr, s.tile_ptr, y.S);
+    k_put_diag<double><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
+        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S);
+}
+
+void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
+    k_scale_G<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, y.lam, y.G32);
+    if (s.n_up > 0)
+        k_schur_off<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, s.row_ptr, s.tile_ptr, y.S32);
+    k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
+        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32);
+}
+
+void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
+                              cudaStream_t st) {
+    k_implicit_t<<<grid_for(int64_t(s.n_l) * 3, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, x,
+                                                                             y.tl);
+    k_implicit_res<<<s.n_c, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.G, y.tl, y.U, x, y.bt, out,
+                                                  partial);
+}
+
+void launch_cam_prep(const Structure& s, System& y, cudaStream_t st) {
+    k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux);
 }
 
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
-    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.S, y.Dinv,
-                                                      nullptr, y.status);
-    if (y.S32)
-        k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.S, y.Dhat,
-                                                          y.lam, y.status);
+    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dinv, nullptr, y.status);
+    if (y.S32) k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dhat, y.lam, y.status);
 }
 
-void launch_scaled_float(const Structure& s, System& y, cudaStream_t st) {
-    k_scaled_float<<<grid_for(int64_t(s.n_c) * 32, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr,
-                                                                                   s.col, y.S, y.lam, y.S32);
-}
 
 void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st) {
     k_to_float<<<grid_for(n, kThreads), kThreads, 0, st>>>(in, out, n);
@@ -651,8 +818,9 @@ void launch_unpermute(const double* in, const int32_t* perm, double* out, int64_
     k_unpermute<<<grid_for(n_o * width, kThreads), kThreads, 0, st>>>(in, perm, out, n_o, width);
 }
 
-void launch_unslab(const Structure& s, const double* S, double* out, cudaStream_t st) {
-    k_unslab<<<grid_for(s.nnzb * 81, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, S, out);
+void launch_unslab(const Structure& s, const System& y, double* out, cudaStream_t st) {
+    k_unslab<<<grid_for(s.nnzb * 81, kThreads), kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, y.S32,
+                                                                    y.lam, y.Sd, out);
 }
 
 }  // namespace ba

@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                     T zv[9];
 #pragma unroll
                     for (int b = 0; b < 9; ++b) zv[b] = zk[b];
+                    const T* blk = tile + lane * 81;
 #pragma unroll
                     for (int a = 0; a < 9; ++a)
 #pragma unroll
-                        for (int b = 0; b < 9; ++b) acc[a] += tile[(9 * a + b) * 32 + lane] * zv[b];
+                        for (int b = 0; b < 9; ++b) acc[a] += blk[9 * a + b] * zv[b];
                 }
                 __syncwarp();
                 if (f.item < L.n) {
@@ -365,56 +366,110 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
 }
 
 // Q[:, off + c] = S P[:, off + c] for the w > 1 columns of a new local block (Algorithm 2, line 3,
-// used by the float32 sweeps, where the Eq. 18 update cancels).  Lane = 4 * qi + g: the lane takes
-// block q0 + qi (+ 8 per round) and columns 4g .. 4g + 3, so each 9x9 block is read once per warp
-// and multiplies up to 16 columns.  Items and their combination are those of k_spmv.
+// used by the float32 sweeps, where the Eq. 18 update cancels).  Tiles stream through shared memory
+// as in k_spmv; lane = 4 qi + g takes tile-local blocks qi, qi + 8, qi + 16, qi + 24 and columns
+// 4g .. 4g + 3, so each 9x9 block multiplies up to 16 columns per read from shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_spmm(const int64_t* __restrict__ row_ptr,
-                                                   const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
-                                                   const T* __restrict__ S, const T* __restrict__ P, ItemList gl,
-                                                   T* __restrict__ part, T* __restrict__ Q, int64_t n,
-                                                   const Ctl* __restrict__ ctl) {
+constexpr size_t spmm_smem() {
+    return spmv_smem<T>() + sizeof(T) * SpmvCfg<T>::kWarps * kMaxDirs * 9;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
+    const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
+    const T* __restrict__ S, const T* __restrict__ P, ItemList gl, T* __restrict__ part, T* __restrict__ Q, int64_t n,
+    Ctl* ctl) {
+    constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     if (ctl->done) return;
     const int w = ctl->w_new;
     if (w <= 1) return;
     const int off = ctl->new_off;
-    __shared__ T red[kThreads / 32][kMaxDirs * 9];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int qi = lane >> 2, g = lane & 3;
     const int nout = 9 * w;
-    for (int64_t i = gtid() >> 5; i < gl.n; i += gstride() >> 5) {
-        const SpItem it = gl.items[i];
-        const int64_t rj = row_ptr[it.row], tb = tile_ptr[it.row];
-        const int32_t* cj = col + rj;
+    T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
+    T* red = reinterpret_cast<T*>(smem_raw + spmv_smem<T>()) + wid * (kMaxDirs * 9);
+    constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
+    const ItemList L = gl;
+    if (lane == 0) {
+        for (int st = 0; st < NS; ++st) mbar_init(&bars[st]);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int64_t W = int64_t(gridDim.x) * NW;
+    const int64_t w0 = int64_t(blockIdx.x) * NW + wid;
+    TileCursor f;
+    cursor_seek(f, L, tile_ptr, w0, W);
+    uint32_t parity = 0, inflight = 0;
+    for (int st = 0; st < NS; ++st) {
+        if (f.item < L.n) {
+            if (lane == 0) bulk_load(tiles + st * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[st]);
+            inflight |= 1u << st;
+            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+        }
+    }
+    int stage = 0;
+    bool bad = false;
+    for (int64_t i = w0; i < L.n && !bad; i += W) {
+        const SpItem it = L.items[i];
+        const int64_t rj = row_ptr[it.row];
         T acc[9][4];
 #pragma unroll
         for (int a = 0; a < 9; ++a)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-        if (4 * g < w) {
-            for (int q = it.q0 + qi; q < it.q1; q += 8) {
-                const int64_t k9 = int64_t(cj[q]) * 9;
-                T pv[9][4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int cc = 4 * g + c;
-                    const T* pc = P + int64_t(off + (cc < w ? cc : 0)) * n + k9;
-#pragma unroll
-                    for (int b = 0; b < 9; ++b) pv[b][c] = cc < w ? pc[b] : T(0);
+        if (it.q1 > it.q0) {
+            const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
+            for (int t = t0; t < t1; ++t) {
+                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    bad = true;
+                    break;
                 }
-                const T* sp = S + (tb + (q >> 5)) * kTileElems + (q & 31);
+                parity ^= 1u << stage;
+                inflight &= ~(1u << stage);
+                const T* tile = tiles + stage * kTileElems;
+                if (4 * g < w) {
+#pragma unroll 1
+                    for (int r = 0; r < 4; ++r) {
+                        const int l = r * 8 + qi;
+                        const int q = t * 32 + l;
+                        if (q < it.q0 || q >= it.q1) continue;
+                        const int64_t k9 = int64_t(col[rj + q]) * 9;
+                        T pv[9][4];
 #pragma unroll
-                for (int a = 0; a < 9; ++a) {
+                        for (int c = 0; c < 4; ++c) {
+                            const int cc = 4 * g + c;
+                            const T* pc = P + int64_t(off + (cc < w ? cc : 0)) * n + k9;
 #pragma unroll
-                    for (int b = 0; b < 9; ++b) {
-                        const T sab = sp[(9 * a + b) * 32];
+                            for (int b = 0; b < 9; ++b) pv[b][c] = cc < w ? pc[b] : T(0);
+                        }
+                        const T* blk = tile + l * 81;
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[a][c] += sab * pv[b][c];
+                        for (int a = 0; a < 9; ++a)
+#pragma unroll
+                            for (int b = 0; b < 9; ++b) {
+                                const T sab = blk[9 * a + b];
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) acc[a][c] += sab * pv[b][c];
+                            }
                     }
                 }
+                __syncwarp();
+                if (f.item < L.n) {
+                    fence_proxy_async();
+                    if (lane == 0)
+                        bulk_load(tiles + stage * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[stage]);
+                    inflight |= 1u << stage;
+                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+                }
+                stage = stage + 1 == NS ? 0 : stage + 1;
             }
+            if (bad) break;
         }
-        // sum over the 8 lanes of each column group
+        // sum over the 8 lanes of each column group, then lanes 0..3 hold their columns
 #pragma unroll
         for (int a = 0; a < 9; ++a)
 #pragma unroll
@@ -432,16 +487,16 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const int64_t* __restrict__ r
                 const int cc = 4 * g + c;
                 if (cc < w)
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) red[wid][cc * 9 + a] = acc[a][c];
+                    for (int a = 0; a < 9; ++a) red[cc * 9 + a] = acc[a][c];
             }
         }
         __syncwarp();
         bool fin = true;
         if (it.ng > 1) {
-            for (int o = lane; o < nout; o += 32) part[i * (kMaxDirs * 9) + o] = red[wid][o];
+            for (int o = lane; o < nout; o += 32) part[i * (kMaxDirs * 9) + o] = red[o];
             __threadfence();
             int last = 0;
-            if (lane == 0) last = (atomicAdd(gl.cnt + it.grp, 1) == it.ng - 1);
+            if (lane == 0) last = (atomicAdd(L.cnt + it.grp, 1) == it.ng - 1);
             last = __shfl_sync(0xffffffffu, last, 0);
             fin = last != 0;
             if (fin) {
@@ -450,19 +505,27 @@ __global__ void __launch_bounds__(kThreads) k_spmm(const int64_t* __restrict__ r
                 for (int o = lane; o < nout; o += 32) {
                     T sum = T(0);
                     for (int c = 0; c < it.ng; ++c) sum += __ldcg(part + (first + c) * (kMaxDirs * 9) + o);
-                    red[wid][o] = sum;
+                    red[o] = sum;
                 }
                 __syncwarp();
-                if (lane == 0) gl.cnt[it.grp] = 0;
+                if (lane == 0) L.cnt[it.grp] = 0;
             }
         }
         if (fin) {
             for (int o = lane; o < nout; o += 32) {
                 const int cc = o / 9, a = o % 9;
-                Q[int64_t(off + cc) * n + 9 * int64_t(it.row) + a] = red[wid][o];
+                Q[int64_t(off + cc) * n + 9 * int64_t(it.row) + a] = red[o];
             }
         }
         __syncwarp();
+    }
+    if (bad) {
+        if (lane == 0) {
+            atomicExch(&ctl->status, BA_ERR_TIMEOUT);
+            atomicExch(&ctl->done, 1);
+        }
+        for (int st = 0; st < NS; ++st)
+            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
     }
 }
 
@@ -1141,11 +1204,11 @@ __global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr
             double xv[9];
 #pragma unroll
             for (int b = 0; b < 9; ++b) xv[b] = xk[b];
-            const double* sp = S + (tb + (q >> 5)) * kTileElems + (q & 31);
+            const double* sp = S + (tb * kTile + q) * 81;
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
 #pragma unroll
-                for (int b = 0; b < 9; ++b) acc[a] += sp[(9 * a + b) * 32] * xv[b];
+                for (int b = 0; b < 9; ++b) acc[a] += sp[9 * a + b] * xv[b];
             }
         }
 #pragma unroll
@@ -1181,6 +1244,32 @@ __global__ void k_accumulate(int64_t n, const float* __restrict__ d, const doubl
 
 __global__ void k_zero(int64_t n, double* __restrict__ x) {
     for (int64_t i = gtid(); i < n; i += gstride()) x[i] = 0.0;
+}
+
+// refinement start: x = 0 and rt = -b~
+__global__ void k_start_refine(int64_t n, const double* __restrict__ bt, double* __restrict__ x,
+                               double* __restrict__ rt) {
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        x[i] = 0.0;
+        rt[i] = -bt[i];
+    }
+}
+
+// ctl->true_rr = ctl->bb = |v|^2 (one CTA, fixed summation order)
+__global__ void k_norm2(int64_t n, const double* __restrict__ v, Ctl* ctl) {
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (int(threadIdx.x) < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctl->true_rr = red[0];
+        ctl->bb = red[0];
+    }
 }
 
 template <typename T>
@@ -1222,6 +1311,7 @@ struct Solver {
     double* part_a = nullptr; // nparts x kGramMax
     double* part_b = nullptr; // nparts x 2
     double* part_c = nullptr; // nparts x 2
+    double* part_cam = nullptr;  // n_c x 2 (per-camera partials of the implicit residual)
     double* dpinv = nullptr;  // (max_iters + 1) x 256
     double* B = nullptr;      // cap x 16
     double* phip = nullptr;
@@ -1331,6 +1421,8 @@ static void ensure_items(Solver* w, const Structure& s, int n_dirs, int sz, int 
         BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
         BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
         BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<float>())));
+        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<double>())));
         attrs = true;
     }
     if (!w->totals) {
@@ -1345,10 +1437,10 @@ static int spmv_grid() { return num_sms() * 8; }
 
 static void free_ws(Solver* w) {
     void* ptrs[] = {w->P, w->Q, w->r, w->z, w->xw, w->part_a, w->part_b, w->part_c, w->dpinv, w->B,
-                    w->phip, w->hist, w->blk_off, w->blk_w, w->ctl, w->rt};
+                    w->phip, w->hist, w->blk_off, w->blk_w, w->ctl, w->rt, w->part_cam};
     for (void* p : ptrs) if (p) cudaFree(p);
     w->P = w->Q = w->r = w->z = w->xw = nullptr;
-    w->part_a = w->part_b = w->part_c = w->dpinv = w->B = w->phip = w->hist = w->rt = nullptr;
+    w->part_a = w->part_b = w->part_c = w->dpinv = w->B = w->phip = w->hist = w->rt = w->part_cam = nullptr;
     w->blk_off = w->blk_w = nullptr;
     w->ctl = nullptr;
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
@@ -1412,6 +1504,7 @@ static void ensure_ws(Solver* w, int64_t n, int64_t cap, int max_iters, int64_t 
     alloc_checked<char>((void**)&w->part_a, size_t(w->nparts) * kGramMax * sizeof(double));
     alloc_checked<char>((void**)&w->part_b, size_t(w->nparts) * 2 * sizeof(double));
     alloc_checked<char>((void**)&w->part_c, size_t(w->nparts) * 2 * sizeof(double));
+    alloc_checked<char>((void**)&w->part_cam, size_t(n / 9 + 1) * 2 * sizeof(double));
     alloc_checked<char>((void**)&w->dpinv, size_t(max_iters + 1) * kMaxDirs * kMaxDirs * sizeof(double));
     alloc_checked<char>((void**)&w->B, size_t(cap) * kMaxDirs * sizeof(double));
     alloc_checked<char>((void**)&w->phip, size_t(phip_len > 0 ? phip_len : 1) * sizeof(double));
@@ -1462,8 +1555,8 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
             k_spmv<T, 2><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr,
                 w->ctl, 1);
-            k_spmm<T><<<Gs, kThreads, 0, st>>>(s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g,
-                                               static_cast<T*>(w->mm_part), Q, w->n, w->ctl);
+            k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, static_cast<T*>(w->mm_part), Q, w->n, w->ctl);
         }
     }
 }
@@ -1521,6 +1614,23 @@ static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv
     *out = *w->h_ctl;
 }
 
+// out = -b~ - S x and its norms into ctl (true_rr, bb): explicit tiled S in float64 precision,
+// the implicit float64 operator U x - G (G^T x) in mixed precision (no float64 S is built there).
+static void true_residual(Solver* w, const Structure& s, const System& y, const double* x, double* out,
+                          cudaStream_t st) {
+    const int G = w->nparts;
+    if (y.S) {
+        k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, w->part_c);
+        w->launches += 1;
+        k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
+    } else {
+        launch_implicit_residual(s, y, x, out, w->part_cam, st);
+        w->launches += 2;
+        k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_cam, s.n_c);
+    }
+    w->launches += 1;
+}
+
 static int grid_for_host(int64_t n) {
     int64_t g = (n + kThreads - 1) / kThreads;
     int cap = num_sms() * 8;
@@ -1569,17 +1679,19 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         if (fin.it > 0)
             BA_CUDA_TRY(cudaMemcpyAsync(w->host_hist.data(), w->hist, sizeof(double) * fin.it,
                                         cudaMemcpyDeviceToHost, st));
+        // true relative residual in float64
+        true_residual(w, s, y, x, nullptr, st);
     } else {
         // float64 iterative refinement around float32 Krylov sweeps
-        k_zero<<<grid_for_host(n), kThreads, 0, st>>>(n, x);
-        // rt = -b~ - S x = -b~
-        k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
-        k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
-        w->launches += 3;
+        // x = 0, so the true residual is -b~ itself: rt = -b~, |rt|^2 = |b~|^2
+        k_start_refine<<<grid_for_host(n), kThreads, 0, st>>>(n, y.bt, x, w->rt);
+        w->launches += 1;
+        k_norm2<<<1, kThreads, 0, st>>>(n, y.bt, w->ctl);
+        w->launches += 1;
         BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         BA_CUDA_TRY(cudaStreamSynchronize(st));
         const double bb = w->h_ctl->bb;
-        double tr = w->h_ctl->true_rr;
+        double tr = bb;
         SolveArgs inner = a;
         inner.tol = a.inner_tol;
         int total = 0, locals = 0;
@@ -1603,9 +1715,8 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
             if (fin.it > 0)
                 BA_CUDA_TRY(cudaMemcpyAsync(h.data(), w->hist, sizeof(double) * fin.it, cudaMemcpyDeviceToHost, st));
             k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, static_cast<const float*>(w->xw), y.lam, x);
-            k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, w->rt, w->part_c);
-            k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
-            w->launches += 3;
+            true_residual(w, s, y, x, w->rt, st);
+            w->launches += 1;
             BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             BA_CUDA_TRY(cudaStreamSynchronize(st));
             const double prev = tr;
@@ -1621,11 +1732,8 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         out.local_steps = locals;
         out.refinements = sweeps;
         out.rel_residual = std::sqrt(tr / bb);
+        // the last sweep's float64 true residual is the result's (ctl holds it)
     }
-    // true relative residual in float64
-    k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, nullptr, w->part_c);
-    k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
-    w->launches += 2;
     out.launches = w->launches;
     BA_CUDA_TRY(cudaEventRecord(e1, st));
     BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

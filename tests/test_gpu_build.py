@@ -138,3 +138,33 @@ def test_dense_full_size_sampled_blocks():
     for j in (0, 977, 1935):
         ref = osch.btilde_block(ne, j)
         assert np.abs(bt[j] - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_mixed_precision_schur_matches_oracle_to_float32():
+    """Mixed precision keeps S as float32 Lam S Lam (Lam = diag(S)^-1/2) with float64 diagonal blocks."""
+    sc = scene("seq-small")
+    m, lin, _ = oracle_system("seq-small")
+    with problem.from_scene(sc, precision="mixed") as p:
+        p.ba_build_normal(1e-4)
+        row_ptr, col, B, bt = p.ba_get_schur()
+    Sg = bsr_from_gpu(row_ptr, col, B, sc.n_cams)
+    So = lin.S
+    d = np.sqrt(np.abs(So.diagonal()))
+    # relative to the scaled entries |S_ij| / (sqrt(S_ii) sqrt(S_jj)): float32 accumulation of
+    # the pair products (~1e-7 each, tens of terms)
+    diff = (Sg - So).tocoo()
+    rel = np.abs(diff.data) / (d[diff.row] * d[diff.col])
+    assert rel.max() < 1e-5
+    assert rel_max(bt, lin.btilde) < 1e-9   # b~ stays float64
+
+
+def test_duplicate_observations_are_rejected():
+    from paper_2110_04015_gb300 import binding
+
+    sc = scene("tiny")
+    xy = problem.device_measurements(sc).cpu().numpy()
+    oc = np.concatenate([sc.obs_cam, sc.obs_cam[:1]])
+    op = np.concatenate([sc.obs_pt, sc.obs_pt[:1]])
+    with pytest.raises(binding.BAError) as e:
+        binding.Problem(sc.cams0, sc.pts0, oc, op, np.concatenate([xy, xy[:1]]))
+    assert e.value.code == binding.BA_ERR_INVALID_ARG and "more than once" in str(e.value)
