@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the float64 comparison solves")
     ap.add_argument("--n-dirs", type=int, default=16)
     ap.add_argument("--tau", type=float, default=10.0)
+    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize"],
+                    help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
+                         "400k landmarks, ~1.6M observations) and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -385,9 +388,9 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                        "l2": "256 MiB buffer written before every timed step; S and the observation arrays exceed L2"},
             "breakdown": {
                 "step_ms": [round(x, 4) for x in times],
-                "pcg": {k: s_pcg[k] for k in ("iters", "ms", "true_rel_residual", "status")},
+                "pcg": {k: s_pcg[k] for k in ("iters", "ms", "true_rel_residual", "status", "refinements")},
                 "mcg": {k: s_mcg[k] for k in ("iters", "local_steps", "ms", "true_rel_residual", "status",
-                                              "history_cols", "n_dirs_eff")},
+                                              "history_cols", "n_dirs_eff", "refinements")},
                 "build_ms": T / a.steps - s_pcg["ms"] - s_mcg["ms"],
             },
             "roofline": roof,
@@ -401,8 +404,27 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def run_kernel_case(a):
+    """A problem small enough for multi-pass ncu captures (S ~0.3 GB float32), larger than L2."""
+    import torch
+
+    from paper_2110_04015_gb300 import problem
+
+    sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
+    p = problem.from_scene(sc, precision=a.precision)
+    p.ba_build_normal(LAMBDA)
+    ms = p.ba_time_kernel(a.kernel_case, 3)
+    print(json.dumps({"kernel_case": a.kernel_case, "precision": a.precision, "nnzb": p.ba_get_schur_nnzb(),
+                      "n_obs": sc.n_obs, "ms_per_launch": ms}), flush=True)
+    p.close()
+    torch.cuda.synchronize()
+
+
 def main():
     a = parse()
+    if a.kernel_case:
+        run_kernel_case(a)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -284,7 +284,26 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
+            // the 9 entries of z this lane needs for tile t, fetched one tile ahead
+            T zn[9];
+            {
+                const int q = t0 * 32 + lane;
+                const bool in = q >= it.q0 && q < it.q1;
+                const T* zk = z + (in ? int64_t(col[rj + q]) * 9 : 0);
+#pragma unroll
+                for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
+            }
             for (int t = t0; t < t1; ++t) {
+                T zv[9];
+#pragma unroll
+                for (int b = 0; b < 9; ++b) zv[b] = zn[b];
+                if (t + 1 < t1) {
+                    const int qn = (t + 1) * 32 + lane;
+                    const bool in = qn < it.q1;
+                    const T* zk = z + (in ? int64_t(col[rj + qn]) * 9 : 0);
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
+                }
                 // every lane observes the phase (visibility of the copied bytes); the warp agrees
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -296,10 +315,6 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                 const T* tile = tiles + stage * kTileElems;
                 const int q = t * 32 + lane;
                 if (q >= it.q0 && q < it.q1) {
-                    const T* zk = z + int64_t(col[rj + q]) * 9;
-                    T zv[9];
-#pragma unroll
-                    for (int b = 0; b < 9; ++b) zv[b] = zk[b];
                     const T* blk = tile + lane * 81;
 #pragma unroll
                     for (int a = 0; a < 9; ++a)
@@ -374,10 +389,26 @@ constexpr size_t spmm_smem() {
     return spmv_smem<T>() + sizeof(T) * SpmvCfg<T>::kWarps * kMaxDirs * 9;
 }
 
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
-    const T* __restrict__ S, const T* __restrict__ P, ItemList gl, T* __restrict__ part, T* __restrict__ Q, int64_t n,
+    const T* __restrict__ S, const T* __restrict__ PT, ItemList gl, T* __restrict__ part, T* __restrict__ Q, int64_t n,
     Ctl* ctl) {
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -437,15 +468,11 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
                         const int l = r * 8 + qi;
                         const int q = t * 32 + l;
                         if (q < it.q0 || q >= it.q1) continue;
-                        const int64_t k9 = int64_t(col[rj + q]) * 9;
+                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of the row-major copy PT (n x 16)
+                        const T* pk = PT + (int64_t(col[rj + q]) * 9) * kMaxDirs + 4 * g;
                         T pv[9][4];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int cc = 4 * g + c;
-                            const T* pc = P + int64_t(off + (cc < w ? cc : 0)) * n + k9;
-#pragma unroll
-                            for (int b = 0; b < 9; ++b) pv[b][c] = cc < w ? pc[b] : T(0);
-                        }
+                        for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[b]);
                         const T* blk = tile + l * 81;
 #pragma unroll
                         for (int a = 0; a < 9; ++a)
@@ -910,14 +937,12 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np
     const int w = ctl->w_cur;
     const int it = ctl->it;
     const int ne = w * w + w;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    for (int e = wid; e < ne; e += nw) {
-        double s = sum_partials(partial, np, kGramMax, e);
-        if (lane == 0) {
-            if (e < w * w) sA[e / w][e % w] = s;
-            else sg[e - w * w] = s;
-        }
+    // one thread per entry sums the CTA partials in CTA order (independent loads, no shuffles)
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < np; ++b) s += partial[int64_t(b) * kGramMax + e];
+        if (e < w * w) sA[e / w][e % w] = s;
+        else sg[e - w * w] = s;
     }
     __syncthreads();
     // symmetrise
@@ -1119,7 +1144,7 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
 // P_new = Z - P_hist B, Q_new = (S Z) - Q_hist B, one thread per row; B tiles staged in shared memory.
 template <typename T>
 __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, const T* __restrict__ z,
-                         const double* __restrict__ B, const Ctl* __restrict__ ctl) {
+                         const double* __restrict__ B, T* __restrict__ PT, const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
     constexpr int TC = 64;
     __shared__ T sB[TC][kMaxDirs];
@@ -1180,6 +1205,8 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
                     P[int64_t(off + s) * n + row] = ap[s];
                     if (upd_q) Q[int64_t(off + s) * n + row] = aq[s];
                 }
+                // row-major copy of the new block for the multi-column product (zero past w)
+                if (!upd_q) PT[row * kMaxDirs + s] = s < w ? ap[s] : T(0);
             }
         }
     }
@@ -1308,6 +1335,7 @@ struct Solver {
     void* r = nullptr;
     void* z = nullptr;
     void* xw = nullptr;       // working x of the inner solve (mixed)
+    void* PT = nullptr;       // n x 16 row-major copy of the newest block (float32 direct-Q products)
     double* part_a = nullptr; // nparts x kGramMax
     double* part_b = nullptr; // nparts x 2
     double* part_c = nullptr; // nparts x 2
@@ -1436,10 +1464,10 @@ static void ensure_items(Solver* w, const Structure& s, int n_dirs, int sz, int 
 static int spmv_grid() { return num_sms() * 8; }
 
 static void free_ws(Solver* w) {
-    void* ptrs[] = {w->P, w->Q, w->r, w->z, w->xw, w->part_a, w->part_b, w->part_c, w->dpinv, w->B,
+    void* ptrs[] = {w->P, w->Q, w->r, w->z, w->xw, w->PT, w->part_a, w->part_b, w->part_c, w->dpinv, w->B,
                     w->phip, w->hist, w->blk_off, w->blk_w, w->ctl, w->rt, w->part_cam};
     for (void* p : ptrs) if (p) cudaFree(p);
-    w->P = w->Q = w->r = w->z = w->xw = nullptr;
+    w->P = w->Q = w->r = w->z = w->xw = w->PT = nullptr;
     w->part_a = w->part_b = w->part_c = w->dpinv = w->B = w->phip = w->hist = w->rt = w->part_cam = nullptr;
     w->blk_off = w->blk_w = nullptr;
     w->ctl = nullptr;
@@ -1501,6 +1529,7 @@ static void ensure_ws(Solver* w, int64_t n, int64_t cap, int max_iters, int64_t 
     alloc_checked<char>(&w->r, size_t(n) * elt);
     alloc_checked<char>(&w->z, size_t(n) * elt);
     alloc_checked<char>(&w->xw, size_t(n) * elt);
+    alloc_checked<char>(&w->PT, size_t(n) * kMaxDirs * elt);
     alloc_checked<char>((void**)&w->part_a, size_t(w->nparts) * kGramMax * sizeof(double));
     alloc_checked<char>((void**)&w->part_b, size_t(w->nparts) * 2 * sizeof(double));
     alloc_checked<char>((void**)&w->part_c, size_t(w->nparts) * 2 * sizeof(double));
@@ -1537,8 +1566,10 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_pcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals, w->hist);
         k_pcg_dir<T><<<G, kThreads, 0, st>>>(w->n, z, P, w->ctl);
     } else {
-        k_mcg_gram<T><<<G, kThreads, 0, st>>>(w->n, P, Q, r, w->part_a, w->ctl);
-        k_mcg_small<<<1, kThreads, 0, st>>>(w->ctl, w->part_a, G, w->dpinv);
+        // Gram partials: one CTA per 512 rows at most, so the small solve sums few partials
+        const int Gg = int(std::min<int64_t>(G, (w->n + 511) / 512));
+        k_mcg_gram<T><<<Gg, kThreads, 0, st>>>(w->n, P, Q, r, w->part_a, w->ctl);
+        k_mcg_small<<<1, kThreads, 0, st>>>(w->ctl, w->part_a, Gg, w->dpinv);
         k_mcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, dp2, w->dcnt + 2, w->totals + 8, w->ctl);
         k_mcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals + 8, w->hist, w->blk_off, w->blk_w);
         k_mcg_phi<T><<<G * 4, kThreads, 0, st>>>(n_c, Q, z, w->phip, w->ctl);
@@ -1548,15 +1579,16 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
             k_spmv<T, 0><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g, w->use_local ? w->items_l : w->items_g, Q, w->n,
                 nullptr, nullptr, nullptr, nullptr, w->ctl, 1);
-            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, w->ctl);
+            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, nullptr, w->ctl);
         } else {
             // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
-            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, w->ctl);
+            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, static_cast<T*>(w->PT), w->ctl);
             k_spmv<T, 2><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr,
                 w->ctl, 1);
             k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, static_cast<T*>(w->mm_part), Q, w->n, w->ctl);
+                s.row_ptr, s.tile_ptr, s.col, S, static_cast<const T*>(w->PT), w->items_g, static_cast<T*>(w->mm_part),
+                Q, w->n, w->ctl);
         }
     }
 }
@@ -1701,9 +1733,10 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         if (bb == 0.0) status = BA_OK;
         while (status != BA_OK && sweeps < a.max_refine && total < a.max_iters) {
             inner.max_iters = a.max_iters - total;
-            // the inner tolerance never asks for less than what is left to reach tol
+            // per sweep the inner solve reduces its residual by inner_tol; when what is left to reach
+            // tol is within ten times that, the sweep aims 3x past it so that it is the last one
             const double need = a.tol * std::sqrt(bb) / std::sqrt(tr);
-            inner.tol = need > a.inner_tol ? need : a.inner_tol;
+            inner.tol = need > 0.1 * a.inner_tol ? std::max(0.3 * need, 0.1 * a.inner_tol) : a.inner_tol;
             if (inner.tol >= 1.0) inner.tol = 0.5;
             krylov<float>(w, s, y.S32, y.Dhat, w->rt, 1.0, y.lam, static_cast<float*>(w->xw), inner, n_eff, sz, K,
                           cap, &fin, st);
