@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
                          "400k landmarks, ~1.6M observations) and exit")
+    ap.add_argument("--sweep", choices=["tau", "ndirs", "density"],
+                    help="sensitivity mode (Figs. 3-5 of the paper): MCG vs PCG time-to-1e-6 over tau, N or the "
+                         "density of S; prints one JSON line per point and exits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -73,6 +76,11 @@ def load_peaks() -> dict:
         return d
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
+
+# DRAM bytes per stored 9x9 block of one k_spmv<float,1> launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture of the 1000-camera case, 323.3 MB / 958,652 blocks;
+# traffic grows with the stored blocks): profiles/k_spmv_f32_dense-1000cams.md
+SPMV_F32_TRAFFIC_PER_BLOCK = 337.3
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
@@ -314,7 +322,9 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof = {"kernel": "k_spmv<float,1> (q = S p, Algorithm 1 line 3)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None, "bytes_per_launch": spmv_bytes,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": SPMV_F32_TRAFFIC_PER_BLOCK * nnzb,
+                "traffic_source": "ncu dram bytes of the 1000-camera case scaled by stored blocks",
+                "bytes_per_launch": spmv_bytes,
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
     # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
@@ -420,8 +430,48 @@ def run_kernel_case(a):
     torch.cuda.synchronize()
 
 
+def run_sweep(a):
+    """Solver time ratio t_MCG / t_PCG (the paper's "solver runtime ratio") against tau, N or density."""
+    import torch
+
+    from paper_2110_04015_gb300 import problem
+
+    def measure(p, reps=2):
+        p.ba_build_normal(LAMBDA)
+        pcg = [p.ba_solve_pcg(TOL, MAX_ITERS) for _ in range(reps)]
+        return min(s["ms"] for s in pcg), pcg[-1]["iters"]
+
+    def one(sc, label, points):
+        p = problem.from_scene(sc, precision=a.precision)
+        t_pcg, it_pcg = measure(p)
+        for N, tau in points:
+            runs = [p.ba_solve_mcg(TOL, MAX_ITERS, N, tau) for _ in range(2)]
+            m = min(r["ms"] for r in runs)
+            print(json.dumps({"sweep": a.sweep, **label, "n_dirs": N, "tau": tau, "precision": a.precision,
+                              "pcg_ms": t_pcg, "pcg_iters": it_pcg, "mcg_ms": m, "mcg_iters": runs[-1]["iters"],
+                              "local_steps": runs[-1]["local_steps"], "ratio": m / t_pcg,
+                              "true_rel_residual": runs[-1]["true_rel_residual"]}), flush=True)
+        p.close()
+        torch.cuda.synchronize()
+
+    gen, kw, _ = WORKLOADS[a.workload]
+    if a.sweep == "tau":
+        one(synthetic.make(gen, 0, **kw), {"workload": a.workload},
+            [(16, t) for t in (0.0, 1.0, 2.0, 3.0, 6.0, 10.0, 30.0, 1e9)])
+    elif a.sweep == "ndirs":
+        one(synthetic.make(gen, 0, **kw), {"workload": a.workload}, [(N, 10.0) for N in (1, 2, 4, 8, 16)])
+    else:
+        for pu in (0.01, 0.03, 0.1, 0.25, 0.6):
+            sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33, p_uniform=pu)
+            d = nnzb_estimate(sc) / sc.n_cams ** 2
+            one(sc, {"workload": "dense-1000x400k", "p_uniform": pu, "density": d}, [(16, 10.0)])
+
+
 def main():
     a = parse()
+    if a.sweep:
+        run_sweep(a)
+        return
     if a.kernel_case:
         run_kernel_case(a)
         return
