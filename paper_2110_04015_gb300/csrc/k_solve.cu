@@ -1566,8 +1566,8 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_pcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals, w->hist);
         k_pcg_dir<T><<<G, kThreads, 0, st>>>(w->n, z, P, w->ctl);
     } else {
-        // Gram partials: one CTA per 512 rows at most, so the small solve sums few partials
-        const int Gg = int(std::min<int64_t>(G, (w->n + 511) / 512));
+        // Gram partials: one CTA per 128 rows at most; the small solve sums them one entry per thread
+        const int Gg = int(std::min<int64_t>(G, (w->n + 127) / 128));
         k_mcg_gram<T><<<Gg, kThreads, 0, st>>>(w->n, P, Q, r, w->part_a, w->ctl);
         k_mcg_small<<<1, kThreads, 0, st>>>(w->ctl, w->part_a, Gg, w->dpinv);
         k_mcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, dp2, w->dcnt + 2, w->totals + 8, w->ctl);
