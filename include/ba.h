@@ -79,7 +79,10 @@ typedef struct ba_options {
     int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1) */
     double inner_tol;          /* MIXED: relative residual reduction of one inner solve (default 1e-3) */
     int32_t max_refine;        /* MIXED: maximum outer refinement sweeps (default 12) */
-    int32_t reserved[7];
+    int32_t item_blocks;       /* stored 9x9 blocks of S per work item of the block-sparse products:
+                                  0 (default) = a per-problem rule (about 64 items per SM, 32..256),
+                                  else a multiple of 32 in [32, 4096]; ba_autotune sets it */
+    int32_t reserved[6];
 } ba_options;
 
 /* Filled by ba_solve_pcg / ba_solve_mcg. */
@@ -132,6 +135,25 @@ void ba_default_options(ba_options* opt);
 int ba_problem_create(const ba_options* opt, int32_t n_cams, int32_t n_pts, int64_t n_obs,
                       const double* cams, const double* pts, const int32_t* obs_cam,
                       const int32_t* obs_pt, const double* obs_xy, ba_problem** out);
+
+/*
+ * Create one handle over n_problems independent problems (a batch).  Problem b owns the cameras
+ * [cam_off[b], cam_off[b + 1]) (cam_off: n_problems + 1 int32, host or device, strictly increasing,
+ * cam_off[0] = 0, cam_off[n_problems] = n_cams); every landmark must be observed only by cameras of
+ * one problem, so S is block-diagonal over the problems.  The other arguments are those of
+ * ba_problem_create over the concatenated arrays.  ba_build_normal builds every problem (one
+ * lambda), and ba_solve_pcg / ba_solve_mcg solve every problem in the same kernel launches, each
+ * problem with its own step sizes, tau-test, direction history and stop test (Algorithms 1 and 2
+ * run independently per problem; the paper solves one problem at a time).  MCG's pose subsets are
+ * formed per problem.  Their stats summarise the batch (the first failing problem's status, the
+ * largest iteration counts and residuals); ba_get_batch_stats gives each problem's.  A problem's
+ * result does not depend on the others in the batch.  ba_lm_step takes single-problem handles only.
+ * Errors: those of ba_problem_create; INVALID_ARG also for n_problems outside [1, 65535], a bad
+ * cam_off, or a landmark shared by two problems.
+ */
+int ba_batch_create(const ba_options* opt, int32_t n_problems, const int32_t* cam_off, int32_t n_cams,
+                    int32_t n_pts, int64_t n_obs, const double* cams, const double* pts,
+                    const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_xy, ba_problem** out);
 
 /* Free every device and host allocation of the handle.  NULL is ignored. */
 void ba_problem_destroy(ba_problem* p);
@@ -238,8 +260,19 @@ int ba_get_schur(const ba_problem* p, int64_t* row_ptr, int32_t* col, double* bl
 int ba_get_preconditioner(const ba_problem* p, double* Dinv);
 
 /* Recursive relative residuals |r_{i+1}| / |r_0| of the last solve, one per step; at most
- * `cap` values are written to `hist` (host or device) and the count to *n. */
+ * `cap` values are written to `hist` (host or device) and the count to *n.  MIXED: the inner
+ * sweeps' values in units of |b~|.  Batches: those of problem 0 (see ba_get_batch_history). */
 int ba_get_residual_history(const ba_problem* p, double* hist, int32_t cap, int32_t* n);
+
+/* Number of problems of the handle (1 unless made by ba_batch_create). */
+int ba_get_batch_size(const ba_problem* p, int32_t* n_problems);
+
+/* Per-problem results of the last solve: stats[b] for b < n (n must equal the batch size; ms is
+ * the whole batch's).  STATE if nothing was solved. */
+int ba_get_batch_stats(const ba_problem* p, ba_solve_stats* stats, int32_t n);
+
+/* ba_get_residual_history for problem `problem` of the batch. */
+int ba_get_batch_history(const ba_problem* p, int32_t problem, double* hist, int32_t cap, int32_t* n);
 
 /* ---- measurement ------------------------------------------------------------------------ */
 
@@ -261,6 +294,16 @@ typedef enum ba_kernel {
  * build, INVALID_ARG for an unknown kernel or reps < 1.
  */
 int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
+
+/*
+ * Choose the work-item size of the block-sparse products by measurement: the PCG product q = S p
+ * (Algorithm 1, line 3) over every problem is timed for 32, 64, 128, 256, 512 and 1024 blocks per
+ * item (`reps` launches each, L2 flushed before each), and the fastest is stored in the handle's
+ * item_blocks option for later solves.  Needs ba_build_normal.  *item_blocks and *ms (may be
+ * NULL) receive the choice and its mean time.  The paper has no counterpart (its products run on
+ * the CPU).  STATE before a build, INVALID_ARG for reps < 1.
+ */
+int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms);
 
 /* ---- allocation-free residual check ---------------------------------------------------- */
 

@@ -35,7 +35,7 @@ SOLVER = {"pcg": 0, "mcg": 1}
 class ba_options(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_iters", ctypes.c_int32),
                 ("max_history", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("item_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class ba_solve_stats(ctypes.Structure):
@@ -67,6 +67,7 @@ _I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _SIGNATURES = {
     "ba_default_options": (None, [_P]),
     "ba_problem_create": (_I32, [_P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P]),
+    "ba_batch_create": (_I32, [_P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P]),
     "ba_problem_destroy": (None, [_P]),
     "ba_last_error": (ctypes.c_char_p, [_P]),
     "ba_set_stream": (_I32, [_P, _P]),
@@ -85,6 +86,10 @@ _SIGNATURES = {
     "ba_get_schur": (_I32, [_P, _P, _P, _P, _P]),
     "ba_get_preconditioner": (_I32, [_P, _P]),
     "ba_get_residual_history": (_I32, [_P, _P, _I32, _P]),
+    "ba_get_batch_size": (_I32, [_P, _P]),
+    "ba_get_batch_stats": (_I32, [_P, _P, _I32]),
+    "ba_get_batch_history": (_I32, [_P, _I32, _P, _I32, _P]),
+    "ba_autotune": (_I32, [_P, _I32, _P, _P]),
     "ba_get_launch_count": (_I32, [_P, _P]),
     "ba_time_kernel": (_I32, [_P, _I32, _I32, _P]),
     "ba_schur_residual_static": (_I32, [_I32, _P, _P, _P, _P, _P, _P, _P]),
@@ -168,10 +173,14 @@ def ba_schur_residual_static(n_cams, row_ptr, col, blocks, btilde, x, out, strea
 
 
 class Problem:
-    """One bundle-adjustment problem held by the library (a ``ba_problem`` handle)."""
+    """One bundle-adjustment problem held by the library (a ``ba_problem`` handle).
+
+    With ``cam_off`` (n_problems + 1 camera offsets) the handle holds a batch of independent
+    problems over the concatenated arrays (``ba_batch_create``).
+    """
 
     def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, damping="marquardt", precision="fp64",
-                 chunk_iters=8, max_history=0, inner_tol=1e-3, max_refine=12):
+                 chunk_iters=8, max_history=0, inner_tol=1e-3, max_refine=12, item_blocks=0, cam_off=None):
         L = lib()
         opt = ba_options()
         L.ba_default_options(ctypes.byref(opt))
@@ -181,14 +190,23 @@ class Problem:
         opt.max_history = max_history
         opt.inner_tol = inner_tol
         opt.max_refine = max_refine
+        opt.item_blocks = item_blocks
         self._keep = [_f64(cams), _f64(pts), _i32(obs_cam), _i32(obs_pt), _f64(obs_xy)]
         cams, pts, obs_cam, obs_pt, obs_xy = self._keep
         self.n_cams = int(cams.shape[0])
         self.n_pts = int(pts.shape[0])
         self.n_obs = int(obs_cam.shape[0])
         h = ctypes.c_void_p()
-        code = L.ba_problem_create(ctypes.byref(opt), self.n_cams, self.n_pts, self.n_obs, _ptr(cams), _ptr(pts),
-                                   _ptr(obs_cam), _ptr(obs_pt), _ptr(obs_xy), ctypes.byref(h))
+        if cam_off is None:
+            self.n_problems = 1
+            code = L.ba_problem_create(ctypes.byref(opt), self.n_cams, self.n_pts, self.n_obs, _ptr(cams),
+                                       _ptr(pts), _ptr(obs_cam), _ptr(obs_pt), _ptr(obs_xy), ctypes.byref(h))
+        else:
+            off = _i32(np.asarray(cam_off))
+            self.n_problems = int(off.shape[0]) - 1
+            code = L.ba_batch_create(ctypes.byref(opt), self.n_problems, _ptr(off), self.n_cams, self.n_pts,
+                                     self.n_obs, _ptr(cams), _ptr(pts), _ptr(obs_cam), _ptr(obs_pt), _ptr(obs_xy),
+                                     ctypes.byref(h))
         self._keep = None
         if code != BA_OK:
             raise BAError(code, L.ba_last_error(None).decode())
@@ -304,6 +322,29 @@ class Problem:
         n = ctypes.c_int32()
         _check(lib().ba_get_residual_history(self.h, _ptr(h), int(cap), ctypes.byref(n)), self.h)
         return h[:min(n.value, cap)].copy()
+
+    def ba_get_batch_size(self) -> int:
+        n = ctypes.c_int32()
+        _check(lib().ba_get_batch_size(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def ba_get_batch_stats(self) -> list[dict]:
+        nb = self.ba_get_batch_size()
+        arr = (ba_solve_stats * nb)()
+        _check(lib().ba_get_batch_stats(self.h, arr, nb), self.h)
+        return [arr[b].as_dict() for b in range(nb)]
+
+    def ba_get_batch_history(self, problem: int, cap=100000):
+        h = np.empty(cap)
+        n = ctypes.c_int32()
+        _check(lib().ba_get_batch_history(self.h, int(problem), _ptr(h), int(cap), ctypes.byref(n)), self.h)
+        return h[:min(n.value, cap)].copy()
+
+    def ba_autotune(self, reps=5) -> tuple[int, float]:
+        cb = ctypes.c_int32()
+        ms = ctypes.c_double()
+        _check(lib().ba_autotune(self.h, int(reps), ctypes.byref(cb), ctypes.byref(ms)), self.h)
+        return cb.value, ms.value
 
     def ba_get_launch_count(self) -> int:
         n = ctypes.c_int64()

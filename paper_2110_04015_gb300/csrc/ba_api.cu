@@ -53,6 +53,8 @@ struct ba_problem {
     bool solved = false;
     double lm_lambda = -1.0;
     int64_t launches = 0;         // kernel executions issued so far
+    std::vector<ba::ProbOut> last;   // per-problem results of the last solve
+    double last_ms = 0.0;
     std::string err;
     std::vector<void*> owned;     // every device allocation, freed by destroy
 };
@@ -103,11 +105,12 @@ int fail(ba_problem* p, const Error& e) {
 
 // Observation sort, camera CSR, pattern of S and the observation pairs feeding each upper block.
 void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const int32_t* oc_in,
-                     const int32_t* op_in, const double* xy_in) {
+                     const int32_t* op_in, const double* xy_in, const std::vector<int32_t>& cam_off) {
     ba::Structure& s = p->s;
     s.n_c = n_c;
     s.n_l = n_l;
     s.n_o = n_o;
+    s.h_cam_off = cam_off;
     std::vector<int32_t> oc = fetch(oc_in, n_o), op = fetch(op_in, n_o);
     std::vector<double> xy = fetch(xy_in, size_t(n_o) * 2);
     for (int64_t i = 0; i < n_o; ++i) {
@@ -144,6 +147,18 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     {
         std::vector<int64_t> fill(cam_ptr.begin(), cam_ptr.end() - 1);
         for (int64_t k = 0; k < n_o; ++k) cam_obs[fill[scam[k]]++] = int32_t(k);
+    }
+    // batches: every landmark is seen by the cameras of one problem only (S is then block-diagonal)
+    if (cam_off.size() > 2) {
+        std::vector<int32_t> prob(n_c);
+        for (size_t b = 0; b + 1 < cam_off.size(); ++b)
+            for (int32_t j = cam_off[b]; j < cam_off[b + 1]; ++j) prob[j] = int32_t(b);
+        for (int32_t l = 0; l < n_l; ++l)
+            for (int64_t a = pt_ptr[l]; a + 1 < pt_ptr[l + 1]; ++a)
+                if (prob[scam[a]] != prob[scam[a + 1]])
+                    throw Error(BA_ERR_INVALID_ARG, "landmark " + std::to_string(l) + " is seen by cameras of problems " +
+                                                        std::to_string(prob[scam[a]]) + " and " +
+                                                        std::to_string(prob[scam[a + 1]]));
     }
     // each (camera, landmark) pair at most once: the diagonal blocks of S are then sums over
     // single observations and only pairs of different cameras feed the off-diagonal blocks
@@ -349,6 +364,8 @@ int do_solve(ba_problem* p, const ba::SolveArgs& a, ba_solve_stats* st) {
     }
     p->launches += out.launches;
     p->solved = true;
+    p->last = out.probs;
+    p->last_ms = out.ms;
     if (st) {
         st->status = out.status;
         st->iters = out.iters;
@@ -391,7 +408,65 @@ ba::SolveArgs make_args(const ba_problem* p, int mcg, double tol, int32_t max_it
     a.inner_tol = p->opt.inner_tol;
     a.max_refine = p->opt.max_refine;
     a.max_history = p->opt.max_history;
+    a.item_blocks = p->opt.item_blocks;
     return a;
+}
+
+void check_options(const ba_options& o) {
+    if (o.chunk_iters < 1 || o.chunk_iters > 256) throw Error(BA_ERR_INVALID_ARG, "chunk_iters must be in [1, 256]");
+    if (o.damping != BA_DAMPING_MARQUARDT && o.damping != BA_DAMPING_IDENTITY)
+        throw Error(BA_ERR_INVALID_ARG, "unknown damping");
+    if (o.precision != BA_PRECISION_FP64 && o.precision != BA_PRECISION_MIXED)
+        throw Error(BA_ERR_INVALID_ARG, "unknown precision");
+    if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) throw Error(BA_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+    if (o.max_refine < 1) throw Error(BA_ERR_INVALID_ARG, "max_refine must be >= 1");
+    if (o.item_blocks != 0 && (o.item_blocks < 32 || o.item_blocks > 4096 || o.item_blocks % 32 != 0))
+        throw Error(BA_ERR_INVALID_ARG, "item_blocks must be 0 or a multiple of 32 in [32, 4096]");
+}
+
+int create(const ba_options* opt, int32_t n_problems, const int32_t* cam_off_in, int32_t n_cams, int32_t n_pts,
+           int64_t n_obs, const double* cams, const double* pts, const int32_t* obs_cam, const int32_t* obs_pt,
+           const double* obs_xy, ba_problem** out) {
+    g_create_error.clear();
+    ba::set_thread_error("");
+    if (!out) { g_create_error = "out is NULL"; return BA_ERR_INVALID_ARG; }
+    *out = nullptr;
+    ba_problem* p = nullptr;
+    try {
+        if (n_cams < 1 || n_pts < 1 || n_obs < 1) throw Error(BA_ERR_INVALID_ARG, "n_cams, n_pts and n_obs must be >= 1");
+        if (n_obs >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "n_obs must be < 2^31");
+        if (!cams || !pts || !obs_cam || !obs_pt || !obs_xy) throw Error(BA_ERR_INVALID_ARG, "NULL input array");
+        if (n_problems < 1 || n_problems > 65535) throw Error(BA_ERR_INVALID_ARG, "n_problems must be in [1, 65535]");
+        std::vector<int32_t> cam_off{0, n_cams};
+        if (cam_off_in) {
+            cam_off = fetch(cam_off_in, size_t(n_problems) + 1);
+            if (cam_off[0] != 0 || cam_off[n_problems] != n_cams)
+                throw Error(BA_ERR_INVALID_ARG, "cam_off must start at 0 and end at n_cams");
+            for (int32_t b = 0; b < n_problems; ++b)
+                if (cam_off[b + 1] <= cam_off[b])
+                    throw Error(BA_ERR_INVALID_ARG, "problem " + std::to_string(b) + " has no camera");
+        } else if (n_problems != 1) {
+            throw Error(BA_ERR_INVALID_ARG, "cam_off is NULL");
+        }
+        p = new ba_problem();
+        ba_default_options(&p->opt);
+        if (opt) p->opt = *opt;
+        check_options(p->opt);
+        build_structure(p, n_cams, n_pts, n_obs, obs_cam, obs_pt, obs_xy, cam_off);
+        alloc_system(p);
+        BA_CUDA_TRY(cudaMemcpy(p->y.cams, cams, sizeof(double) * 9 * size_t(n_cams), cudaMemcpyDefault));
+        BA_CUDA_TRY(cudaMemcpy(p->y.pts, pts, sizeof(double) * 3 * size_t(n_pts), cudaMemcpyDefault));
+        *out = p;
+        return BA_OK;
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        if (p) ba_problem_destroy(p);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_create_error = "host allocation failed";
+        if (p) ba_problem_destroy(p);
+        return BA_ERR_OOM;
+    }
 }
 
 }  // namespace
@@ -412,40 +487,18 @@ void ba_default_options(ba_options* opt) {
 int ba_problem_create(const ba_options* opt, int32_t n_cams, int32_t n_pts, int64_t n_obs, const double* cams,
                       const double* pts, const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_xy,
                       ba_problem** out) {
-    g_create_error.clear();
-    ba::set_thread_error("");
-    if (!out) { g_create_error = "out is NULL"; return BA_ERR_INVALID_ARG; }
-    *out = nullptr;
-    ba_problem* p = nullptr;
-    try {
-        if (n_cams < 1 || n_pts < 1 || n_obs < 1) throw Error(BA_ERR_INVALID_ARG, "n_cams, n_pts and n_obs must be >= 1");
-        if (n_obs >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "n_obs must be < 2^31");
-        if (!cams || !pts || !obs_cam || !obs_pt || !obs_xy) throw Error(BA_ERR_INVALID_ARG, "NULL input array");
-        p = new ba_problem();
-        ba_default_options(&p->opt);
-        if (opt) p->opt = *opt;
-        if (p->opt.chunk_iters < 1 || p->opt.chunk_iters > 256) throw Error(BA_ERR_INVALID_ARG, "chunk_iters must be in [1, 256]");
-        if (p->opt.damping != BA_DAMPING_MARQUARDT && p->opt.damping != BA_DAMPING_IDENTITY)
-            throw Error(BA_ERR_INVALID_ARG, "unknown damping");
-        if (p->opt.precision != BA_PRECISION_FP64 && p->opt.precision != BA_PRECISION_MIXED)
-            throw Error(BA_ERR_INVALID_ARG, "unknown precision");
-        if (!(p->opt.inner_tol > 0.0 && p->opt.inner_tol < 1.0)) throw Error(BA_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
-        if (p->opt.max_refine < 1) throw Error(BA_ERR_INVALID_ARG, "max_refine must be >= 1");
-        build_structure(p, n_cams, n_pts, n_obs, obs_cam, obs_pt, obs_xy);
-        alloc_system(p);
-        BA_CUDA_TRY(cudaMemcpy(p->y.cams, cams, sizeof(double) * 9 * size_t(n_cams), cudaMemcpyDefault));
-        BA_CUDA_TRY(cudaMemcpy(p->y.pts, pts, sizeof(double) * 3 * size_t(n_pts), cudaMemcpyDefault));
-        *out = p;
-        return BA_OK;
-    } catch (const Error& e) {
-        g_create_error = e.msg;
-        if (p) ba_problem_destroy(p);
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        g_create_error = "host allocation failed";
-        if (p) ba_problem_destroy(p);
-        return BA_ERR_OOM;
+    return create(opt, 1, nullptr, n_cams, n_pts, n_obs, cams, pts, obs_cam, obs_pt, obs_xy, out);
+}
+
+int ba_batch_create(const ba_options* opt, int32_t n_problems, const int32_t* cam_off, int32_t n_cams, int32_t n_pts,
+                    int64_t n_obs, const double* cams, const double* pts, const int32_t* obs_cam,
+                    const int32_t* obs_pt, const double* obs_xy, ba_problem** out) {
+    if (!cam_off) {
+        g_create_error = "cam_off is NULL";
+        if (out) *out = nullptr;
+        return BA_ERR_INVALID_ARG;
     }
+    return create(opt, n_problems, cam_off, n_cams, n_pts, n_obs, cams, pts, obs_cam, obs_pt, obs_xy, out);
 }
 
 void ba_problem_destroy(ba_problem* p) {
@@ -556,6 +609,7 @@ int ba_lm_step(ba_problem* p, int32_t solver, double lambda0, double tol, int32_
     std::memset(&s, 0, sizeof(s));
     try {
         if (solver != BA_SOLVER_PCG && solver != BA_SOLVER_MCG) throw Error(BA_ERR_INVALID_ARG, "unknown solver");
+        if (p->s.h_cam_off.size() > 2) throw Error(BA_ERR_INVALID_ARG, "ba_lm_step takes a single-problem handle");
         if (p->lm_lambda <= 0.0) {
             if (!(lambda0 > 0.0)) throw Error(BA_ERR_INVALID_ARG, "lambda0 must be positive");
             p->lm_lambda = lambda0;
@@ -720,10 +774,78 @@ int ba_get_residual_history(const ba_problem* pc, double* hist, int32_t cap, int
     try {
         if (!p->solver || !p->solved) { *n = 0; return BA_OK; }
         const double* h = nullptr;
-        int cnt = ba::solver_history(p->solver, &h);
+        int cnt = ba::solver_history(p->solver, 0, &h);
         *n = cnt;
         int m = cnt < cap ? cnt : cap;
         if (hist && m > 0) BA_CUDA_TRY(cudaMemcpy(hist, h, sizeof(double) * m, cudaMemcpyDefault));
+        return BA_OK;
+    } catch (const Error& e) {
+        return fail(p, e);
+    }
+}
+
+int ba_get_batch_size(const ba_problem* p, int32_t* n_problems) {
+    if (!p || !n_problems) return BA_ERR_INVALID_ARG;
+    *n_problems = int32_t(p->s.h_cam_off.size()) - 1;
+    return BA_OK;
+}
+
+int ba_get_batch_stats(const ba_problem* pc, ba_solve_stats* stats, int32_t n) {
+    ba_problem* p = const_cast<ba_problem*>(pc);
+    if (!p || !stats) return BA_ERR_INVALID_ARG;
+    try {
+        const int nb = int(p->s.h_cam_off.size()) - 1;
+        if (n != nb) throw Error(BA_ERR_INVALID_ARG, "n must equal the number of problems");
+        if (!p->solved || int(p->last.size()) != nb) throw Error(BA_ERR_STATE, "no solution: call a solve first");
+        for (int b = 0; b < nb; ++b) {
+            const ba::ProbOut& o = p->last[b];
+            ba_solve_stats& st = stats[b];
+            st.status = o.status;
+            st.iters = o.iters;
+            st.local_steps = o.local_steps;
+            st.n_dirs_eff = o.n_eff;
+            st.refinements = o.refinements;
+            st.history_cols = int32_t(o.history_cols);
+            st.rel_residual = o.rel_residual;
+            st.true_rel_residual = o.true_rel_residual;
+            st.ms = p->last_ms;
+        }
+        return BA_OK;
+    } catch (const Error& e) {
+        return fail(p, e);
+    }
+}
+
+int ba_get_batch_history(const ba_problem* pc, int32_t problem, double* hist, int32_t cap, int32_t* n) {
+    ba_problem* p = const_cast<ba_problem*>(pc);
+    if (!p || !n) return BA_ERR_INVALID_ARG;
+    try {
+        const int nb = int(p->s.h_cam_off.size()) - 1;
+        if (problem < 0 || problem >= nb) throw Error(BA_ERR_INVALID_ARG, "problem out of range");
+        if (!p->solver || !p->solved) { *n = 0; return BA_OK; }
+        const double* h = nullptr;
+        int cnt = ba::solver_history(p->solver, problem, &h);
+        *n = cnt;
+        int m = cnt < cap ? cnt : cap;
+        if (hist && m > 0) BA_CUDA_TRY(cudaMemcpy(hist, h, sizeof(double) * m, cudaMemcpyDefault));
+        return BA_OK;
+    } catch (const Error& e) {
+        return fail(p, e);
+    }
+}
+
+int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms) {
+    if (!p) return BA_ERR_INVALID_ARG;
+    try {
+        if (reps < 1) throw Error(BA_ERR_INVALID_ARG, "reps must be >= 1");
+        if (!p->y.built) throw Error(BA_ERR_STATE, "nothing built");
+        if (!p->solver) p->solver = ba::solver_create();
+        double best = 0.0;
+        const int cb = ba::solver_autotune(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps, &best,
+                                           p->stream, nullptr);
+        p->opt.item_blocks = cb;
+        if (item_blocks) *item_blocks = cb;
+        if (ms) *ms = best;
         return BA_OK;
     } catch (const Error& e) {
         return fail(p, e);
@@ -744,7 +866,8 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
         cudaStream_t st = p->stream;
         if (kernel == BA_KERNEL_SPMV) {
             if (!p->solver) p->solver = ba::solver_create();
-            *ms = ba::solver_time_spmv(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps, st);
+            *ms = ba::solver_time_spmv(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps,
+                                     p->opt.item_blocks, st);
             return BA_OK;
         }
         if (kernel != BA_KERNEL_SCHUR && kernel != BA_KERNEL_LINEARIZE) throw Error(BA_ERR_INVALID_ARG, "unknown kernel");

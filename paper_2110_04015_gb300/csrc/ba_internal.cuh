@@ -25,6 +25,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ba.h"
@@ -83,6 +84,8 @@ struct Structure {
     int64_t* up_mir = nullptr;    // n_up: block index of (k, j), -1 on the diagonal
     int64_t* up_pair_ptr = nullptr;  // n_up + 1
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
+    // batch: problem b owns cameras [h_cam_off[b], h_cam_off[b + 1]); one problem: {0, n_c}
+    std::vector<int32_t> h_cam_off;
     // host copies of the pattern (work lists of the block-sparse products are built from them)
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_col;
@@ -161,6 +164,18 @@ struct SolveArgs {
     double inner_tol = 1e-3;
     int max_refine = 12;
     int64_t max_history = 0;
+    int item_blocks = 0;    // blocks per work item of the block-sparse products (0: per-problem heuristic)
+};
+
+struct ProbOut {
+    int status = BA_OK;
+    int iters = 0;
+    int local_steps = 0;
+    int n_eff = 1;
+    int refinements = 0;
+    int64_t history_cols = 0;
+    double rel_residual = 0.0;
+    double true_rel_residual = 0.0;
 };
 
 struct SolveOut {
@@ -174,17 +189,25 @@ struct SolveOut {
     double true_rel_residual = 0.0;
     double ms = 0.0;
     int64_t launches = 0;   // kernel executions issued by the solve
+    std::vector<ProbOut> probs;   // per problem of the batch (the fields above summarise them)
 };
 
 struct Solver;   // workspace, defined in k_solve.cu
 Solver* solver_create();
 void solver_destroy(Solver* w);
-// Solve S x = -b~ into x (device, 9 n_c); history of recursive residuals kept in the workspace.
+// Solve S x = -b~ into x (device, 9 n_c) for every problem of the batch; the history of recursive
+// residuals of each problem is kept in the workspace.
 void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x,
                 SolveOut& out, cudaStream_t st);
-int solver_history(const Solver* w, const double** hist);
-// Mean ms of one launch of the PCG product q = S p (float64 or float32 system), L2 flushed between launches.
-double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, cudaStream_t st);
+int solver_history(const Solver* w, int problem, const double** hist);
+// Mean ms of one launch of the PCG product q = S p over all problems (float64 or float32 system),
+// L2 flushed between launches; item_blocks as in SolveArgs.
+double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int item_blocks,
+                        cudaStream_t st);
+// Blocks per work item (32 .. 1024) that makes the PCG product fastest; *best_ms its time; trace
+// (optional) receives every (candidate, ms).
+int solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, double* best_ms,
+                    cudaStream_t st, std::vector<std::pair<int, double>>* trace);
 void flush_l2(cudaStream_t st);
 
 int num_sms();

@@ -1,19 +1,24 @@
-// Krylov solvers of the reduced camera system S dx_p = -b~ (Section 3.2).
+// Krylov solvers of the reduced camera system S dx_p = -b~ (Section 3.2), for one problem or for
+// a batch of independent problems that share every launch.
 //
-// Algorithm 1 (block-Jacobi PCG) and Algorithm 2 (MCG) run as a fixed sequence of
-// kernels per iteration.  All data-dependent control (the stop test, the tau-test
-// and the width of the next direction block, the history size) lives in a device
-// struct Ctl written only by single-CTA "decide" kernels and read by the others, so a
-// chunk of iterations is captured once as a CUDA graph and replayed; the host reads
-// back one flag per chunk.  Multi-CTA kernels return at once when Ctl::done is set.
+// Algorithm 1 (block-Jacobi PCG) and Algorithm 2 (MCG) run as a fixed sequence of kernels per
+// iteration.  All data-dependent control (the stop test, the tau-test and the width of the next
+// direction block, the history size) lives in one device struct Ctl per problem, written only by
+// the per-problem "decide" kernels and read by the others, so a chunk of iterations is captured
+// once as a CUDA graph and replayed; the host reads the Ctl array back once per chunk.  A problem
+// whose Ctl::done is set is skipped by every later launch while the others go on.
 //
-// Reductions are deterministic: each CTA writes a partial sum, and the consumer sums
-// the partials in a fixed order.
+// Batches: problem b owns the cameras [c0, c0 + nc) of the handle (S is block-diagonal over the
+// problems, since no landmark is seen by two of them).  Per-problem kernels take the problem from
+// blockIdx.y; the block-sparse products run over one work list of all problems' rows, each item
+// tagged with its problem.  Every per-problem result is summed in an order fixed by the problem
+// alone (its own cameras, rows and work items), so a problem solved inside a batch gives the
+// same bits as the same problem solved alone.  One problem is the batch of one.
 //
-// MCG data: the search blocks P_j and their images Q_j are kept as columns of two
-// column-major arrays (column c at c * n, n = 9 n_cams); block j starts at column
-// blk_off[j] and is blk_w[j] wide (1 for a global step, N_eff for a local one).  The
-// pseudo-inverse of Delta_j is kept for the full reorthogonalisation
+// MCG data: the search blocks P_j and their images Q_j are kept as columns of two column-major
+// arrays per problem (column c at hoff + c * n, n = 9 nc); block j starts at column blk_off[j]
+// and is blk_w[j] wide (1 for a global step, N_eff for a local one).  The pseudo-inverse of
+// Delta_j is kept for the full reorthogonalisation
 //     beta_{i,j} = Delta_j^+ Q_j^T Z_{i+1},  P_{i+1} = Z_{i+1} - sum_j P_j beta_{i,j},
 //     Q_{i+1}   = S Z_{i+1} - sum_j Q_j beta_{i,j}            (Eq. 18 with j = 0..i)
 // where S Z_{i+1} applies each block S_jk only to the column of the subset of pose k
@@ -35,8 +40,19 @@ namespace {
 constexpr int kGramMax = kMaxDirs * kMaxDirs + kMaxDirs;   // Delta (w x w) and gamma (w)
 constexpr int kChunkCams = 112;                             // cameras per Phi partial
 constexpr double kStagnation = 1e-4;                        // float32 sweep stop on t_i (see Ctl::stag)
+constexpr int kTotals = 16;                                 // per-problem grid totals
+
+// Where one problem of the batch lives (fixed for a solve).
+struct Layout {
+    int c0, nc;          // first camera, number of cameras
+    int64_t hoff;        // first element of its direction history (cap columns of 9 nc rows)
+    int64_t phoff;       // first Phi partial
+    int64_t boff;        // first beta row (16 values each)
+    int n_eff, sz, K, cap;
+};
 
 struct Ctl {
+    Layout lay;
     int it;            // completed steps
     int done;
     int status;
@@ -62,6 +78,20 @@ struct Ctl {
     int pad_;
 };
 
+// Float64 iterative refinement of one problem (mixed precision).
+struct Outer {
+    double bb;         // |b~|^2
+    double tr;         // |-b~ - S x|^2 of the current x
+    double tr_prev;    // the same before the last sweep (scales that sweep's residual history)
+    double tol_in;     // relative tolerance of the next inner sweep
+    int status;
+    int active;        // still refining
+    int swept;         // takes part in the sweep being run
+    int sweeps, iters, locals;
+    int max_in;        // iteration budget of the next sweep
+    int cols;          // history columns of its last sweep
+};
+
 __device__ __forceinline__ int64_t gtid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
 
@@ -76,7 +106,8 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Sum `nv` values per thread over the CTA; thread 0 writes them to out[0..nv).
+// Sum `nv` values per thread over the CTA; threads 0..NV-1 write them to out[0..NV) (global or
+// shared memory), visible to the whole CTA on return.
 template <int NV>
 __device__ __forceinline__ void cta_sum_write(double (&v)[NV], double* out) {
     __shared__ double red[kThreads / 32][NV];
@@ -95,7 +126,7 @@ __device__ __forceinline__ void cta_sum_write(double (&v)[NV], double* out) {
     __syncthreads();
 }
 
-// Sum partial[p * stride + k] over p < np in a fixed order (called by one warp; lane 0 returns).
+// Sum partial[p * stride + k] over p < np in a fixed order (called by one warp; every lane returns it).
 __device__ __forceinline__ double sum_partials(const double* partial, int np, int stride, int k) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
@@ -108,11 +139,12 @@ __device__ __forceinline__ double sum_partials(const double* partial, int np, in
 
 // Work items of the block-sparse products.  Item = a chunk [q0, q1) of the blocks of block-row
 // `row` that feed output column `seg` (the subset of the column cameras in MCG's local step, 0
-// otherwise).  The ng items of one output group (row, seg) are consecutive; each writes its 9
-// partial sums, and the warp that finishes last (atomic count, no waiting) adds the partials in
-// item order, so the result does not depend on scheduling.  Counters reset themselves.
+// otherwise) of problem `prob`.  The ng items of one output group (row, seg) are consecutive;
+// each writes its 9 partial sums, and the warp that finishes last (atomic count, no waiting)
+// adds the partials in item order, so the result does not depend on scheduling.  Counters reset
+// themselves.
 struct SpItem {
-    int row, seg, q0, q1, grp, k, ng, pad;
+    int row, seg, q0, q1, grp, k, ng, prob;
 };
 
 struct ItemList {
@@ -122,8 +154,25 @@ struct ItemList {
     void* part = nullptr;     // n x 9 partial sums (element type of the product)
 };
 
-// Sum the CTA's NV values, publish them as partial[blockIdx], and let the last CTA to finish
-// write the grid totals (in CTA order) to totals[0..NV).  Every CTA of the grid must call it.
+// Which problems a product serves: every live one, those forming a global (local) block, or those
+// whose new block is one column wide (wider).
+enum : int { kSelLive = 0, kSelGlobal = 1, kSelLocal = 2, kSelW1 = 3, kSelWide = 4 };
+
+__device__ __forceinline__ bool selected(const Ctl* ctl, int prob, int sel) {
+    const Ctl& c = ctl[prob];
+    if (c.done) return false;
+    switch (sel) {
+        case kSelGlobal: return c.local == 0;
+        case kSelLocal: return c.local != 0;
+        case kSelW1: return c.w_new == 1;
+        case kSelWide: return c.w_new > 1;
+        default: return true;
+    }
+}
+
+// Sum the CTA's NV values, publish them as partial[blockIdx.x], and let the last CTA of the grid
+// row to finish write the row's totals (in CTA order) to totals[0..NV).  Every CTA of the grid
+// row must call it.
 template <int NV>
 __device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* partial, int* cnt, double* totals) {
     __shared__ double red[kThreads / 32][NV];
@@ -207,17 +256,20 @@ constexpr size_t spmv_smem() {
            sizeof(uint64_t) * SpmvCfg<T>::kWarps * SpmvCfg<T>::kStages;
 }
 
-// Tile cursor of a warp: the tiles of items w0, w0 + W, ... in order, skipping empty items.
+
+// Tile cursor of a warp: the tiles of the selected items w0, w0 + W, ... in order, skipping empty
+// items.  The consumer loop selects items with the same predicate, which no kernel changes while
+// it runs.
 struct TileCursor {
     int64_t item;
     int t, te;
     int64_t base;
 };
-__device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, const int64_t* tile_ptr, int64_t item,
-                                            int64_t W) {
+__device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, const int64_t* tile_ptr,
+                                            const Ctl* ctl, int sel, int64_t item, int64_t W) {
     for (; item < L.n; item += W) {
         const SpItem it = L.items[item];
-        if (it.q1 > it.q0) {
+        if (it.q1 > it.q0 && selected(ctl, it.prob, sel)) {
             c.item = item;
             c.t = it.q0 >> 5;
             c.te = (it.q1 + 31) >> 5;
@@ -233,26 +285,22 @@ __device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, co
 // y(row, seg) = sum over the item's blocks of S_row,col(q) z_col(q).  Each warp streams the
 // tiles of its items through kStages shared-memory buffers with bulk copies (issued by lane 0,
 // NS tiles ahead) and multiplies them with the gathered z blocks.
-// MODE 0: write y to column (off + seg) of `out` (off and the item list from ctl when use_ctl).
-// MODE 1 (Algorithm 1, line 3-4): q = y, and the totals of Delta = q^T p and gamma = p^T r.
-// MODE 2 (Algorithm 2, line 3, width 1): z is column new_off of P, y goes to the same column of out.
-template <typename T, int MODE>
+// ZH: z is a column of the problem's direction history (column new_off in MODE 2, column 0
+//     otherwise); else z is a vector over all cameras.
+// MODE 0: y goes to column new_off + seg of the problem's Q.
+// MODE 1 (Algorithm 1, line 3): q = y (Q column 0) and, per camera, the sums of q^T p and p^T r
+//         (Delta and gamma of Algorithm 1, line 4, before the sum over cameras).
+// MODE 2 (Algorithm 2, line 3, width 1): y goes to column new_off of Q.
+template <typename T, int MODE, bool ZH>
 __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
-    const T* __restrict__ S, const T* __restrict__ z, ItemList gl, ItemList lo, T* __restrict__ out, int64_t n,
-    const T* __restrict__ rvec, double* __restrict__ dpart, int* __restrict__ dcnt, double* __restrict__ totals,
-    Ctl* ctl, int use_ctl) {
+    const T* __restrict__ S, const T* __restrict__ z, ItemList L, int sel, T* __restrict__ out,
+    const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl) {
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (use_ctl && ctl->done) return;
-    if (MODE == 2 && ctl->w_new != 1) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
-    const bool local = MODE == 0 && use_ctl && ctl->local;
-    const ItemList L = local ? lo : gl;
-    const int off = use_ctl ? ctl->new_off : 0;
-    if (MODE == 2) z += int64_t(off) * n;
     T* part = static_cast<T*>(L.part);
     constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
 
@@ -264,20 +312,26 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
     const int64_t W = int64_t(gridDim.x) * NW;
     const int64_t w0 = int64_t(blockIdx.x) * NW + wid;
     TileCursor f;
-    cursor_seek(f, L, tile_ptr, w0, W);
+    cursor_seek(f, L, tile_ptr, ctl, sel, w0, W);
     uint32_t parity = 0, inflight = 0;
     for (int st = 0; st < NS; ++st) {
         if (f.item < L.n) {
             if (lane == 0) bulk_load(tiles + st * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[st]);
             inflight |= 1u << st;
-            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, ctl, sel, f.item + W, W);
         }
     }
     int stage = 0;
     bool bad = false;
-    double v[2] = {0.0, 0.0};
+    int bad_prob = 0;
     for (int64_t i = w0; i < L.n && !bad; i += W) {
         const SpItem it = L.items[i];
+        if (!selected(ctl, it.prob, sel)) continue;
+        const Ctl& c = ctl[it.prob];
+        const int64_t n = int64_t(c.lay.nc) * 9;
+        const int64_t hb = c.lay.hoff - 9 * int64_t(c.lay.c0);   // history column 0 at global row i: hb + i
+        const int64_t zoff = ZH ? hb + int64_t(MODE == 2 ? c.new_off : 0) * n : 0;
+        const int64_t ooff = hb + int64_t(MODE == 1 ? 0 : (MODE == 2 ? c.new_off : c.new_off + it.seg)) * n;
         const int64_t rj = row_ptr[it.row];
         T acc[9];
 #pragma unroll
@@ -289,7 +343,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
             {
                 const int q = t0 * 32 + lane;
                 const bool in = q >= it.q0 && q < it.q1;
-                const T* zk = z + (in ? int64_t(col[rj + q]) * 9 : 0);
+                const T* zk = z + zoff + int64_t(in ? col[rj + q] : it.row) * 9;
 #pragma unroll
                 for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
             }
@@ -300,7 +354,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                 if (t + 1 < t1) {
                     const int qn = (t + 1) * 32 + lane;
                     const bool in = qn < it.q1;
-                    const T* zk = z + (in ? int64_t(col[rj + qn]) * 9 : 0);
+                    const T* zk = z + zoff + int64_t(in ? col[rj + qn] : it.row) * 9;
 #pragma unroll
                     for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
                 }
@@ -308,6 +362,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
                     bad = true;
+                    bad_prob = it.prob;
                     break;
                 }
                 parity ^= 1u << stage;
@@ -327,7 +382,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                     if (lane == 0)
                         bulk_load(tiles + stage * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[stage]);
                     inflight |= 1u << stage;
-                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, ctl, sel, f.item + W, W);
                 }
                 stage = stage + 1 == NS ? 0 : stage + 1;
             }
@@ -351,39 +406,44 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmv(
                 T sum = T(0);
                 const int64_t first = i - it.k;
                 if (lane < 9)
-                    for (int c = 0; c < it.ng; ++c) sum += __ldcg(part + (first + c) * 9 + lane);
+                    for (int cc = 0; cc < it.ng; ++cc) sum += __ldcg(part + (first + cc) * 9 + lane);
                 val = sum;
                 if (lane == 0) L.cnt[it.grp] = 0;
             }
         }
-        if (fin && lane < 9) {
+        if (fin) {
             const int64_t rowi = 9 * int64_t(it.row) + lane;
-            if (MODE != 1) {
-                out[int64_t(off + it.seg) * n + rowi] = val;
-            } else {
-                out[rowi] = val;
-                const double pv = double(z[rowi]);
-                v[0] += double(val) * pv;
-                v[1] += pv * double(rvec[rowi]);
+            if (lane < 9) out[ooff + rowi] = val;
+            if (MODE == 1) {
+                double dq = 0.0, dr = 0.0;
+                if (lane < 9) {
+                    const double pv = double(z[zoff + rowi]);
+                    dq = double(val) * pv;
+                    dr = pv * double(rvec[rowi]);
+                }
+                dq = warp_sum(dq);
+                dr = warp_sum(dr);
+                if (lane == 0) {
+                    camdot[2 * int64_t(it.row)] = dq;
+                    camdot[2 * int64_t(it.row) + 1] = dr;
+                }
             }
         }
     }
     if (bad) {
-        // a copy did not land in time: report, then wait (bounded) for this warp's copies in flight
-        if (lane == 0) {
-            atomicExch(&ctl->status, BA_ERR_TIMEOUT);
-            atomicExch(&ctl->done, 1);
-        }
+        // a copy did not land in time: report, then wait (bounded) for this warp's copies in flight;
+        // the problem's next decide kernel ends it with the status
+        if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
             if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
     }
-    if (MODE == 1) grid_sum_finalize<2>(v, dpart, dcnt, totals);
 }
 
-// Q[:, off + c] = S P[:, off + c] for the w > 1 columns of a new local block (Algorithm 2, line 3,
-// used by the float32 sweeps, where the Eq. 18 update cancels).  Tiles stream through shared memory
-// as in k_spmv; lane = 4 qi + g takes tile-local blocks qi, qi + 8, qi + 16, qi + 24 and columns
-// 4g .. 4g + 3, so each 9x9 block multiplies up to 16 columns per read from shared memory.
+// Q[:, new_off + c] = S P[:, new_off + c] for the w > 1 columns of a new local block (Algorithm 2,
+// line 3, used by the float32 sweeps, where the Eq. 18 update cancels).  Tiles stream through
+// shared memory as in k_spmv; lane = 4 qi + g takes tile-local blocks qi, qi + 8, qi + 16, qi + 24
+// and columns 4g .. 4g + 3, so each 9x9 block multiplies up to 16 columns per read from shared
+// memory.  PT is the row-major copy (9 n_c x 16, all problems) of the new blocks.
 template <typename T>
 constexpr size_t spmm_smem() {
     return spmv_smem<T>() + sizeof(T) * SpmvCfg<T>::kWarps * kMaxDirs * 9;
@@ -408,22 +468,17 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
 template <typename T>
 __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
-    const T* __restrict__ S, const T* __restrict__ PT, ItemList gl, T* __restrict__ part, T* __restrict__ Q, int64_t n,
+    const T* __restrict__ S, const T* __restrict__ PT, ItemList L, T* __restrict__ part, T* __restrict__ Q,
     Ctl* ctl) {
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
+    constexpr int sel = kSelWide;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (ctl->done) return;
-    const int w = ctl->w_new;
-    if (w <= 1) return;
-    const int off = ctl->new_off;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int qi = lane >> 2, g = lane & 3;
-    const int nout = 9 * w;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
     T* red = reinterpret_cast<T*>(smem_raw + spmv_smem<T>()) + wid * (kMaxDirs * 9);
     constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
-    const ItemList L = gl;
     if (lane == 0) {
         for (int st = 0; st < NS; ++st) mbar_init(&bars[st]);
         fence_mbar_init();
@@ -432,31 +487,39 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
     const int64_t W = int64_t(gridDim.x) * NW;
     const int64_t w0 = int64_t(blockIdx.x) * NW + wid;
     TileCursor f;
-    cursor_seek(f, L, tile_ptr, w0, W);
+    cursor_seek(f, L, tile_ptr, ctl, sel, w0, W);
     uint32_t parity = 0, inflight = 0;
     for (int st = 0; st < NS; ++st) {
         if (f.item < L.n) {
             if (lane == 0) bulk_load(tiles + st * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[st]);
             inflight |= 1u << st;
-            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+            if (++f.t == f.te) cursor_seek(f, L, tile_ptr, ctl, sel, f.item + W, W);
         }
     }
     int stage = 0;
     bool bad = false;
+    int bad_prob = 0;
     for (int64_t i = w0; i < L.n && !bad; i += W) {
         const SpItem it = L.items[i];
+        if (!selected(ctl, it.prob, sel)) continue;
+        const Ctl& c = ctl[it.prob];
+        const int w = c.w_new;
+        const int nout = 9 * w;
+        const int64_t n = int64_t(c.lay.nc) * 9;
+        const int64_t ooff = c.lay.hoff - 9 * int64_t(c.lay.c0) + int64_t(c.new_off) * n;
         const int64_t rj = row_ptr[it.row];
         T acc[9][4];
 #pragma unroll
         for (int a = 0; a < 9; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+            for (int cc = 0; cc < 4; ++cc) acc[a][cc] = T(0);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
             for (int t = t0; t < t1; ++t) {
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
                     bad = true;
+                    bad_prob = it.prob;
                     break;
                 }
                 parity ^= 1u << stage;
@@ -468,7 +531,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
                         const int l = r * 8 + qi;
                         const int q = t * 32 + l;
                         if (q < it.q0 || q >= it.q1) continue;
-                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of the row-major copy PT (n x 16)
+                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT
                         const T* pk = PT + (int64_t(col[rj + q]) * 9) * kMaxDirs + 4 * g;
                         T pv[9][4];
 #pragma unroll
@@ -480,7 +543,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
                             for (int b = 0; b < 9; ++b) {
                                 const T sab = blk[9 * a + b];
 #pragma unroll
-                                for (int c = 0; c < 4; ++c) acc[a][c] += sab * pv[b][c];
+                                for (int cc = 0; cc < 4; ++cc) acc[a][cc] += sab * pv[b][cc];
                             }
                     }
                 }
@@ -490,7 +553,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
                     if (lane == 0)
                         bulk_load(tiles + stage * kTileElems, S + (f.base + f.t) * kTileElems, tile_bytes, &bars[stage]);
                     inflight |= 1u << stage;
-                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, f.item + W, W);
+                    if (++f.t == f.te) cursor_seek(f, L, tile_ptr, ctl, sel, f.item + W, W);
                 }
                 stage = stage + 1 == NS ? 0 : stage + 1;
             }
@@ -500,21 +563,21 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
 #pragma unroll
         for (int a = 0; a < 9; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                T v = acc[a][c];
+            for (int cc = 0; cc < 4; ++cc) {
+                T v = acc[a][cc];
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
-                acc[a][c] = v;
+                acc[a][cc] = v;
             }
         __syncwarp();
         if (qi == 0) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int cc = 4 * g + c;
-                if (cc < w)
+            for (int cc = 0; cc < 4; ++cc) {
+                const int ci = 4 * g + cc;
+                if (ci < w)
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) red[cc * 9 + a] = acc[a][c];
+                    for (int a = 0; a < 9; ++a) red[ci * 9 + a] = acc[a][cc];
             }
         }
         __syncwarp();
@@ -531,7 +594,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
                 const int64_t first = i - it.k;
                 for (int o = lane; o < nout; o += 32) {
                     T sum = T(0);
-                    for (int c = 0; c < it.ng; ++c) sum += __ldcg(part + (first + c) * (kMaxDirs * 9) + o);
+                    for (int cc = 0; cc < it.ng; ++cc) sum += __ldcg(part + (first + cc) * (kMaxDirs * 9) + o);
                     red[o] = sum;
                 }
                 __syncwarp();
@@ -540,17 +603,14 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
         }
         if (fin) {
             for (int o = lane; o < nout; o += 32) {
-                const int cc = o / 9, a = o % 9;
-                Q[int64_t(off + cc) * n + 9 * int64_t(it.row) + a] = red[o];
+                const int ci = o / 9, a = o % 9;
+                Q[ooff + int64_t(ci) * n + 9 * int64_t(it.row) + a] = red[o];
             }
         }
         __syncwarp();
     }
     if (bad) {
-        if (lane == 0) {
-            atomicExch(&ctl->status, BA_ERR_TIMEOUT);
-            atomicExch(&ctl->done, 1);
-        }
+        if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
             if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
     }
@@ -558,13 +618,16 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32) k_spmm(
 
 // ---------------------------------------------------------------------------------------
 // initialisation shared by both algorithms: x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z
+// (grid: CTAs x problems; thread = camera of the problem)
 
 template <typename T>
-__global__ void k_init_vec(int32_t n_c, const double* __restrict__ rhs, double sign, const double* __restrict__ scale,
-                           const double* __restrict__ Dinv, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                           T* __restrict__ P0, double* __restrict__ partial) {
+__global__ void k_init_vec(const Layout* __restrict__ lay, const double* __restrict__ rhs, double sign,
+                           const double* __restrict__ scale, const double* __restrict__ Dinv, T* __restrict__ x,
+                           T* __restrict__ r, T* __restrict__ z, T* __restrict__ P, double* __restrict__ partial) {
+    const Layout L = lay[blockIdx.y];
     double v[1] = {0.0};
-    for (int64_t j = gtid(); j < n_c; j += gstride()) {
+    for (int64_t jl = gtid(); jl < L.nc; jl += gstride()) {
+        const int64_t j = L.c0 + jl;
         double rv[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
@@ -582,28 +645,40 @@ __global__ void k_init_vec(int32_t n_c, const double* __restrict__ rhs, double s
 #pragma unroll
             for (int b = 0; b < 9; ++b) s += D[9 * a + b] * rv[b];
             z[9 * j + a] = T(s);
-            P0[9 * j + a] = T(s);
+            P[L.hoff + 9 * jl + a] = T(s);
         }
     }
-    cta_sum_write<1>(v, partial + blockIdx.x);
+    cta_sum_write<1>(v, partial + int64_t(blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
-__global__ void k_init_ctl(Ctl* ctl, const double* __restrict__ partial, int np, double tol, int max_iters,
-                           double tau, int n_eff, int sz, int K, int cap, int* blk_off, int* blk_w, double stag,
-                           int direct_q) {
-    double rr0 = sum_partials(partial, np, 1, 0);
+// One warp per problem.  outer (mixed precision, may be null) supplies the sweep's tolerance and
+// iteration budget and leaves the problems that are not refined any more done from the start.
+__global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const double* __restrict__ partial, int np,
+                           double tol, int max_iters, double tau, double stag, int direct_q,
+                           const Outer* __restrict__ outer, int* blk_off, int* blk_w, int mi1) {
+    const int p = blockIdx.x;
+    const double rr0 = sum_partials(partial + int64_t(p) * np, np, 1, 0);
     if (threadIdx.x == 0) {
         Ctl c;
         memset(&c, 0, sizeof(c));
+        c.lay = lay[p];
+        double tl = tol;
+        int mi = max_iters;
+        bool act = true;
+        if (outer) {
+            act = outer[p].swept != 0;
+            tl = outer[p].tol_in;
+            mi = outer[p].max_in;
+        }
         c.rr0 = rr0;
         c.rr = rr0;
-        c.tol2 = tol * tol;
+        c.tol2 = tl * tl;
         c.tau = tau;
-        c.max_iters = max_iters;
-        c.n_eff = n_eff;
-        c.sz = sz;
-        c.K = K;
-        c.cap = cap;
+        c.max_iters = mi;
+        c.n_eff = c.lay.n_eff;
+        c.sz = c.lay.sz;
+        c.K = c.lay.K;
+        c.cap = c.lay.cap;
         c.cols = 1;
         c.w_new = 1;
         c.new_off = 0;
@@ -613,33 +688,56 @@ __global__ void k_init_ctl(Ctl* ctl, const double* __restrict__ partial, int np,
         c.stag = stag;
         c.direct_q = direct_q;
         c.status = BA_OK;
-        if (!(rr0 == rr0) || isinf(rr0)) { c.done = 1; c.status = BA_ERR_BREAKDOWN; }
-        else if (rr0 == 0.0 || max_iters <= 0) { c.done = 1; c.status = rr0 == 0.0 ? BA_OK : BA_ERR_NOT_CONVERGED; }
-        *ctl = c;
-        blk_off[0] = 0;
-        blk_w[0] = 1;
+        if (!act) { c.done = 1; }
+        else if (!(rr0 == rr0) || isinf(rr0)) { c.done = 1; c.status = BA_ERR_BREAKDOWN; }
+        else if (rr0 == 0.0 || mi <= 0) { c.done = 1; c.status = rr0 == 0.0 ? BA_OK : BA_ERR_NOT_CONVERGED; }
+        ctl[p] = c;
+        blk_off[int64_t(p) * mi1] = 0;
+        blk_w[int64_t(p) * mi1] = 1;
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// Algorithm 1
+// Algorithm 1 (grid: CTAs x problems)
 
-// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2 and q^T z.
+// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2, q^T z, r^T z.
+// Delta and gamma are the sums over the problem's cameras (camera order) of the per-camera sums
+// of the product; every CTA forms them the same way, CTA 0 stores them for the decide kernel.
 template <typename T>
-__global__ void k_pcg_update(int32_t n_c, const double* __restrict__ Dinv, const T* __restrict__ p,
-                             const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                             double* __restrict__ totals, double* __restrict__ dpart, int* __restrict__ dcnt,
-                             const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
-    const T alpha = T(totals[1] / totals[0]);
+__global__ void k_pcg_update(const double* __restrict__ Dinv, const T* __restrict__ P, const T* __restrict__ Q,
+                             T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                             const double* __restrict__ camdot, double* __restrict__ totals,
+                             double* __restrict__ dpart, int* __restrict__ dcnt, const Ctl* __restrict__ ctl) {
+    const int p = blockIdx.y;
+    const Ctl& c = ctl[p];
+    if (c.done) return;
+    const int64_t c0 = c.lay.c0;
+    const int nc = c.lay.nc;
+    __shared__ double dg[2];
+    {
+        double d[2] = {0.0, 0.0};
+        for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
+            d[0] += camdot[2 * (c0 + jl)];
+            d[1] += camdot[2 * (c0 + jl) + 1];
+        }
+        cta_sum_write<2>(d, dg);
+    }
+    double* tot = totals + int64_t(p) * kTotals;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tot[0] = dg[0];
+        tot[1] = dg[1];
+    }
+    const T alpha = T(dg[1] / dg[0]);
+    const int64_t hb = c.lay.hoff - 9 * c0;
     double v[3] = {0.0, 0.0, 0.0};
-    for (int64_t j = gtid(); j < n_c; j += gstride()) {
+    for (int64_t jl = gtid(); jl < nc; jl += gstride()) {
+        const int64_t j = c0 + jl;
         T rv[9], qv[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const int64_t i = 9 * j + a;
-            x[i] = x[i] + alpha * p[i];
-            qv[a] = q[i];
+            x[i] = x[i] + alpha * P[hb + i];
+            qv[a] = Q[hb + i];
             rv[a] = r[i] - alpha * qv[a];
             r[i] = rv[a];
             v[0] += double(rv[a]) * double(rv[a]);
@@ -656,74 +754,96 @@ __global__ void k_pcg_update(int32_t n_c, const double* __restrict__ Dinv, const
             v[2] += double(rv[a]) * double(zs);
         }
     }
-    grid_sum_finalize<3>(v, dpart, dcnt, totals + 2);
+    grid_sum_finalize<3>(v, dpart + int64_t(p) * gridDim.x * 3, dcnt + 4 * p, tot + 2);
 }
 
-// stop test and beta = Phi / Delta (one thread)
+// stop test and beta = Phi / Delta (one thread per problem); hist is iteration-major (it x nb)
 __global__ void k_pcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist) {
-    if (ctl->done || threadIdx.x != 0) return;
-    const double D = totals[0], g = totals[1], rr = totals[2], phi = totals[3];
-    const int it = ctl->it + 1;
-    ctl->it = it;
-    ctl->Delta = D;
-    ctl->gamma = g;
-    ctl->alpha = g / D;
-    ctl->rr = rr;
-    hist[it - 1] = sqrt(rr / ctl->rr0);
+    const int p = blockIdx.x;
+    Ctl* c = ctl + p;
+    if (c->done || threadIdx.x != 0) return;
+    if (c->status == BA_ERR_TIMEOUT) { c->done = 1; return; }
+    const double* tot = totals + int64_t(p) * kTotals;
+    const double D = tot[0], g = tot[1], rr = tot[2], phi = tot[3];
+    const int it = c->it + 1;
+    c->it = it;
+    c->Delta = D;
+    c->gamma = g;
+    c->alpha = g / D;
+    c->rr = rr;
+    hist[int64_t(it - 1) * gridDim.x + p] = sqrt(rr / c->rr0);
     if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
-        ctl->done = 1;
-        ctl->status = BA_ERR_BREAKDOWN;
-    } else if (rr < ctl->tol2 * ctl->rr0) {
-        ctl->done = 1;
-        ctl->status = BA_OK;
-    } else if (it >= ctl->max_iters) {
-        ctl->done = 1;
-        ctl->status = BA_ERR_NOT_CONVERGED;
-    } else if (ctl->stag > 0.0 && (g * g / D) < ctl->stag * totals[4]) {
-        ctl->done = 1;          // no measurable progress left at this precision: end the sweep
-        ctl->status = BA_OK;
+        c->done = 1;
+        c->status = BA_ERR_BREAKDOWN;
+    } else if (rr < c->tol2 * c->rr0) {
+        c->done = 1;
+        c->status = BA_OK;
+    } else if (it >= c->max_iters) {
+        c->done = 1;
+        c->status = BA_ERR_NOT_CONVERGED;
+    } else if (c->stag > 0.0 && (g * g / D) < c->stag * tot[4]) {
+        c->done = 1;          // no measurable progress left at this precision: end the sweep
+        c->status = BA_OK;
     } else {
-        ctl->beta = phi / D;
+        c->beta = phi / D;
     }
 }
 
-// p = z - beta p
+// p = z - beta p (rows of the problem)
 template <typename T>
-__global__ void k_pcg_dir(int64_t n, const T* __restrict__ z, T* __restrict__ p, const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
-    const T beta = T(ctl->beta);
-    for (int64_t i = gtid(); i < n; i += gstride()) p[i] = z[i] - beta * p[i];
+__global__ void k_pcg_dir(const T* __restrict__ z, T* __restrict__ P, const Ctl* __restrict__ ctl) {
+    const Ctl& c = ctl[blockIdx.y];
+    if (c.done) return;
+    const T beta = T(c.beta);
+    const int64_t n = int64_t(c.lay.nc) * 9, r0 = 9 * int64_t(c.lay.c0);
+    T* Pp = P + c.lay.hoff;
+    for (int64_t i = gtid(); i < n; i += gstride()) Pp[i] = z[r0 + i] - beta * Pp[i];
 }
 
 // ---------------------------------------------------------------------------------------
 // Algorithm 2
 
-// partials of Delta_i = Q_i^T P_i (w x w) and gamma_i = P_i^T r (w) for the current block
+// Gram partials of Delta_i = Q_i^T P_i (w x w) and gamma_i = P_i^T r (w) for the current block.
+// A problem of n rows uses min(gridDim.x, ceil(n / 128)) CTAs of its grid row (the rest return),
+// each a contiguous run of rows, so the partition depends on the problem alone.
+__device__ __forceinline__ int gram_ctas(int64_t n, int gx) {
+    const int64_t g = (n + 127) / 128;
+    return int(g < gx ? g : gx);
+}
+
 template <typename T>
-__global__ void k_mcg_gram(int64_t n, const T* __restrict__ P, const T* __restrict__ Q, const T* __restrict__ r,
+__global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, const T* __restrict__ r,
                            double* __restrict__ partial, const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
+    const int p = blockIdx.y;
+    const Ctl& c = ctl[p];
+    if (c.done) return;
+    const int64_t n = int64_t(c.lay.nc) * 9;
+    const int gp = gram_ctas(n, gridDim.x);
+    if (int(blockIdx.x) >= gp) return;
     constexpr int TR = 32;
     __shared__ T sP[TR][kMaxDirs + 1], sQ[TR][kMaxDirs + 1], sr[TR];
-    const int w = ctl->w_cur, off = ctl->off_cur;
+    const int w = c.w_cur, off = c.off_cur;
     const int ne = w * w + w;
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const T* Pp = P + c.lay.hoff;
+    const T* Qp = Q + c.lay.hoff;
+    const T* rp = r + 9 * int64_t(c.lay.c0);
+    const int64_t per = (n + gp - 1) / gp;
     const int64_t r0 = int64_t(blockIdx.x) * per;
     const int64_t r1 = r0 + per < n ? r0 + per : n;
     double acc[2] = {0.0, 0.0};   // entries threadIdx.x and threadIdx.x + 256
     for (int64_t base = r0; base < r1; base += TR) {
         const int rows = int(r1 - base < TR ? r1 - base : TR);
         for (int t = threadIdx.x; t < TR * kMaxDirs; t += blockDim.x) {
-            const int rr = t / kMaxDirs, c = t % kMaxDirs;
+            const int rr = t / kMaxDirs, cc = t % kMaxDirs;
             T pv = T(0), qv = T(0);
-            if (rr < rows && c < w) {
-                pv = P[int64_t(off + c) * n + base + rr];
-                qv = Q[int64_t(off + c) * n + base + rr];
+            if (rr < rows && cc < w) {
+                pv = Pp[int64_t(off + cc) * n + base + rr];
+                qv = Qp[int64_t(off + cc) * n + base + rr];
             }
-            sP[rr][c] = pv;
-            sQ[rr][c] = qv;
+            sP[rr][cc] = pv;
+            sQ[rr][cc] = qv;
         }
-        if (threadIdx.x < TR) sr[threadIdx.x] = threadIdx.x < rows ? r[base + threadIdx.x] : T(0);
+        if (threadIdx.x < TR) sr[threadIdx.x] = int(threadIdx.x) < rows ? rp[base + threadIdx.x] : T(0);
         __syncthreads();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -742,10 +862,11 @@ __global__ void k_mcg_gram(int64_t n, const T* __restrict__ P, const T* __restri
         }
         __syncthreads();
     }
+    double* out = partial + (int64_t(p) * gridDim.x + blockIdx.x) * kGramMax;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int e = threadIdx.x + h * blockDim.x;
-        if (e < ne) partial[int64_t(blockIdx.x) * kGramMax + e] = acc[h];
+        if (e < ne) out[e] = acc[h];
     }
 }
 
@@ -929,18 +1050,24 @@ __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxD
 }
 
 // Delta_i, gamma_i -> Delta_i^+ (stored for the reorthogonalisation), alpha_i, gamma^T alpha.
-__global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np, double* __restrict__ dpinv) {
-    if (ctl->done) return;
+// One CTA per problem; gx is the width of the Gram grid.
+__global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx, double* __restrict__ dpinv,
+                            int mi1) {
+    const int p = blockIdx.x;
+    Ctl* c = ctl + p;
+    if (c->done) return;
     __shared__ double sA[kMaxDirs][kMaxDirs + 1], sV[kMaxDirs][kMaxDirs + 1], sX[kMaxDirs][kMaxDirs + 1];
     __shared__ double sg[kMaxDirs];
     __shared__ double sal[kMaxDirs];
-    const int w = ctl->w_cur;
-    const int it = ctl->it;
+    const int w = c->w_cur;
+    const int it = c->it;
     const int ne = w * w + w;
+    const int np = gram_ctas(int64_t(c->lay.nc) * 9, gx);
+    const double* part = partial + int64_t(p) * gx * kGramMax;
     // one thread per entry sums the CTA partials in CTA order (independent loads, no shuffles)
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
         double s = 0.0;
-        for (int b = 0; b < np; ++b) s += partial[int64_t(b) * kGramMax + e];
+        for (int b = 0; b < np; ++b) s += part[int64_t(b) * kGramMax + e];
         if (e < w * w) sA[e / w][e % w] = s;
         else sg[e - w * w] = s;
     }
@@ -959,9 +1086,9 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np
         pinv_sym_jacobi(sA, sV, sX, w);
     }
     if (threadIdx.x < kMaxDirs * kMaxDirs) {
-        dpinv[int64_t(it) * kMaxDirs * kMaxDirs + threadIdx.x] = (i < w && j < w) ? sX[i][j] : 0.0;
+        dpinv[(int64_t(p) * mi1 + it) * kMaxDirs * kMaxDirs + threadIdx.x] = (i < w && j < w) ? sX[i][j] : 0.0;
     }
-    if (threadIdx.x < w) {
+    if (int(threadIdx.x) < w) {
         double s = 0.0;
         for (int b = 0; b < w; ++b) s += sX[threadIdx.x][b] * sg[b];
         sal[threadIdx.x] = s;
@@ -971,35 +1098,41 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int np
         double ga = 0.0;
         for (int a = 0; a < w; ++a) {
             ga += sg[a] * sal[a];
-            ctl->alpha_v[a] = sal[a];
+            c->alpha_v[a] = sal[a];
         }
-        ctl->ga = ga;
-        if (!(ga == ga)) { ctl->done = 1; ctl->status = BA_ERR_BREAKDOWN; }
+        c->ga = ga;
+        if (!(ga == ga)) { c->done = 1; c->status = BA_ERR_BREAKDOWN; }
     }
 }
 
-// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z.
+// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z (grid: CTAs x problems).
 template <typename T>
-__global__ void k_mcg_update(int32_t n_c, const double* __restrict__ Dinv, const T* __restrict__ P,
-                             const T* __restrict__ Q, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                             double* __restrict__ dpart, int* __restrict__ dcnt, double* __restrict__ totals,
-                             const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
-    const int64_t n = int64_t(n_c) * 9;
-    const int w = ctl->w_cur, off = ctl->off_cur;
+__global__ void k_mcg_update(const double* __restrict__ Dinv, const T* __restrict__ P, const T* __restrict__ Q,
+                             T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, double* __restrict__ dpart,
+                             int* __restrict__ dcnt, double* __restrict__ totals, const Ctl* __restrict__ ctl) {
+    const int p = blockIdx.y;
+    const Ctl& c = ctl[p];
+    if (c.done) return;
+    const int64_t c0 = c.lay.c0;
+    const int nc = c.lay.nc;
+    const int64_t n = int64_t(nc) * 9;
+    const int w = c.w_cur, off = c.off_cur;
+    const T* Pp = P + c.lay.hoff + int64_t(off) * n;
+    const T* Qp = Q + c.lay.hoff + int64_t(off) * n;
     __shared__ T sal[kMaxDirs];
-    if (threadIdx.x < kMaxDirs) sal[threadIdx.x] = threadIdx.x < w ? T(ctl->alpha_v[threadIdx.x]) : T(0);
+    if (threadIdx.x < kMaxDirs) sal[threadIdx.x] = int(threadIdx.x) < w ? T(c.alpha_v[threadIdx.x]) : T(0);
     __syncthreads();
     double v[2] = {0.0, 0.0};
-    for (int64_t j = gtid(); j < n_c; j += gstride()) {
+    for (int64_t jl = gtid(); jl < nc; jl += gstride()) {
+        const int64_t j = c0 + jl;
         T rv[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const int64_t i = 9 * j + a;
+            const int64_t il = 9 * jl + a, i = 9 * j + a;
             T dx = T(0), dr = T(0);
             for (int b = 0; b < w; ++b) {
-                dx += P[int64_t(off + b) * n + i] * sal[b];
-                dr += Q[int64_t(off + b) * n + i] * sal[b];
+                dx += Pp[int64_t(b) * n + il] * sal[b];
+                dr += Qp[int64_t(b) * n + il] * sal[b];
             }
             x[i] = x[i] + dx;
             rv[a] = r[i] - dr;
@@ -1017,140 +1150,160 @@ __global__ void k_mcg_update(int32_t n_c, const double* __restrict__ Dinv, const
             v[1] += double(rv[a]) * double(zs);
         }
     }
-    grid_sum_finalize<2>(v, dpart, dcnt, totals);
+    grid_sum_finalize<2>(v, dpart + int64_t(p) * gridDim.x * 2, dcnt + 4 * p + 1, totals + int64_t(p) * kTotals + 8);
 }
 
-// stop test, tau-test and the layout of the next block (one thread)
-__global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist, int* blk_off, int* blk_w) {
-    if (ctl->done) return;
-    const double rr = totals[0], rz = totals[1];
-    if (threadIdx.x == 0) {
-        const int it = ctl->it + 1;
-        ctl->it = it;
-        ctl->rr = rr;
-        ctl->rz = rz;
-        hist[it - 1] = sqrt(rr / ctl->rr0);
-        if (!(rr == rr) || isinf(rr)) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_BREAKDOWN;
-            return;
-        }
-        if (rr < ctl->tol2 * ctl->rr0) {
-            ctl->done = 1;
-            ctl->status = BA_OK;
-            return;
-        }
-        if (it >= ctl->max_iters) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_NOT_CONVERGED;
-            return;
-        }
-        if (!(rz > 0.0)) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_BREAKDOWN;
-            return;
-        }
-        const double t = ctl->ga / rz;
-        if (ctl->stag > 0.0 && t < ctl->stag) {
-            ctl->done = 1;      // no measurable progress left at this precision: end the sweep
-            ctl->status = BA_OK;
-            return;
-        }
-        const int local = (t < ctl->tau) ? 1 : 0;
-        const int w = local ? ctl->n_eff : 1;
-        if (ctl->cols + w > ctl->cap) {
-            ctl->done = 1;
-            ctl->status = BA_ERR_OOM;
-            return;
-        }
-        ctl->local = local;
-        ctl->local_steps += local;
-        ctl->w_new = w;
-        ctl->new_off = ctl->cols;
-        ctl->hist_cols = ctl->cols;
-        ctl->w_cur = w;
-        ctl->off_cur = ctl->cols;
-        blk_off[it] = ctl->cols;
-        blk_w[it] = w;
-        ctl->cols += w;
+// stop test, tau-test and the layout of the next block (one thread per problem)
+__global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist, int* blk_off, int* blk_w,
+                             int mi1) {
+    const int p = blockIdx.x;
+    Ctl* c = ctl + p;
+    if (c->done || threadIdx.x != 0) return;
+    if (c->status == BA_ERR_TIMEOUT) { c->done = 1; return; }
+    const double* tot = totals + int64_t(p) * kTotals + 8;
+    const double rr = tot[0], rz = tot[1];
+    const int it = c->it + 1;
+    c->it = it;
+    c->rr = rr;
+    c->rz = rz;
+    hist[int64_t(it - 1) * gridDim.x + p] = sqrt(rr / c->rr0);
+    if (!(rr == rr) || isinf(rr)) {
+        c->done = 1;
+        c->status = BA_ERR_BREAKDOWN;
+        return;
     }
+    if (rr < c->tol2 * c->rr0) {
+        c->done = 1;
+        c->status = BA_OK;
+        return;
+    }
+    if (it >= c->max_iters) {
+        c->done = 1;
+        c->status = BA_ERR_NOT_CONVERGED;
+        return;
+    }
+    if (!(rz > 0.0)) {
+        c->done = 1;
+        c->status = BA_ERR_BREAKDOWN;
+        return;
+    }
+    const double t = c->ga / rz;
+    if (c->stag > 0.0 && t < c->stag) {
+        c->done = 1;      // no measurable progress left at this precision: end the sweep
+        c->status = BA_OK;
+        return;
+    }
+    const int local = (t < c->tau) ? 1 : 0;
+    const int w = local ? c->n_eff : 1;
+    if (c->cols + w > c->cap) {
+        c->done = 1;
+        c->status = BA_ERR_OOM;
+        return;
+    }
+    c->local = local;
+    c->local_steps += local;
+    c->w_new = w;
+    c->new_off = c->cols;
+    c->hist_cols = c->cols;
+    c->w_cur = w;
+    c->off_cur = c->cols;
+    blk_off[int64_t(p) * mi1 + it] = c->cols;
+    blk_w[int64_t(p) * mi1 + it] = w;
+    c->cols += w;
 }
 
 // partial sums of Q[:, c]^T z over row chunks inside each subset:
-// phip[(c * n_eff + s) * K + k] for c < hist_cols
+// phip[(c * n_eff + s) * K + k] for c < hist_cols (one warp per entry; grid: CTAs x problems)
 template <typename T>
-__global__ void k_mcg_phi(int32_t n_c, const T* __restrict__ Q, const T* __restrict__ z, double* __restrict__ phip,
+__global__ void k_mcg_phi(const T* __restrict__ Q, const T* __restrict__ z, double* __restrict__ phip,
                           const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
+    const Ctl& c = ctl[blockIdx.y];
+    if (c.done) return;
     const int lane = threadIdx.x & 31;
-    const int64_t n = int64_t(n_c) * 9;
-    const int n_eff = ctl->n_eff, sz = ctl->sz, K = ctl->K;
+    const int nc = c.lay.nc;
+    const int64_t n = int64_t(nc) * 9;
+    const int n_eff = c.n_eff, sz = c.sz, K = c.K;
     const int cz = (sz + K - 1) / K;
-    const int64_t items = int64_t(ctl->hist_cols) * n_eff * K;
+    const int64_t items = int64_t(c.hist_cols) * n_eff * K;
+    const T* Qp = Q + c.lay.hoff;
+    const T* zp = z + 9 * int64_t(c.lay.c0);
+    double* ph = phip + c.lay.phoff;
     for (int64_t it = gtid() >> 5; it < items; it += gstride() >> 5) {
         const int k = int(it % K);
         const int64_t cs = it / K;
         const int s = int(cs % n_eff);
-        const int64_t c = cs / n_eff;
+        const int64_t cc = cs / n_eff;
         int j0 = s * sz + k * cz;
         int j1 = j0 + cz;
-        const int send = (s + 1) * sz < n_c ? (s + 1) * sz : n_c;
+        const int send = (s + 1) * sz < nc ? (s + 1) * sz : nc;
         if (j1 > send) j1 = send;
         double acc = 0.0;
-        const T* qc = Q + c * n;
+        const T* qc = Qp + cc * n;
         for (int64_t row = int64_t(j0) * 9 + lane; row < int64_t(j1) * 9; row += 32)
-            acc += double(qc[row]) * double(z[row]);
+            acc += double(qc[row]) * double(zp[row]);
         acc = warp_sum(acc);
-        if (lane == 0) phip[it] = acc;
+        if (lane == 0) ph[it] = acc;
     }
 }
 
-// beta_{i,j} = Delta_j^+ Phi_{i,j} for every history block j, into B[c * 16 + s]
+// beta_{i,j} = Delta_j^+ Phi_{i,j} for every history block j, into beta rows (one warp per block)
 __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __restrict__ dpinv,
-                           const int* __restrict__ blk_off, const int* __restrict__ blk_w, double* __restrict__ B,
-                           const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
+                           const int* __restrict__ blk_off, const int* __restrict__ blk_w, double* __restrict__ beta,
+                           const Ctl* __restrict__ ctl, int mi1) {
+    const int p = blockIdx.y;
+    const Ctl& c = ctl[p];
+    if (c.done) return;
     __shared__ double sphi[kThreads / 32][kMaxDirs * kMaxDirs];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nblk = ctl->it;   // blocks 0..it-1 are the history
-    const int n_eff = ctl->n_eff, K = ctl->K, w = ctl->w_new, local = ctl->local;
+    const int nblk = c.it;   // blocks 0..it-1 are the history
+    const int n_eff = c.n_eff, K = c.K, w = c.w_new, local = c.local;
+    const double* ph = phip + c.lay.phoff;
+    const int* bo = blk_off + int64_t(p) * mi1;
+    const int* bw = blk_w + int64_t(p) * mi1;
+    double* Bp = beta + c.lay.boff * kMaxDirs;
     for (int64_t jb = gtid() >> 5; jb < nblk; jb += gstride() >> 5) {
-        const int off = blk_off[jb], wj = blk_w[jb];
+        const int off = bo[jb], wj = bw[jb];
         // Phi_j (wj x w)
         for (int e = lane; e < wj * w; e += 32) {
             const int a = e / w, s = e % w;
-            const int64_t c = off + a;
+            const int64_t cc = off + a;
             double v = 0.0;
             if (local) {
-                for (int k = 0; k < K; ++k) v += phip[(c * n_eff + s) * K + k];
+                for (int k = 0; k < K; ++k) v += ph[(cc * n_eff + s) * K + k];
             } else {
                 for (int ss = 0; ss < n_eff; ++ss)
-                    for (int k = 0; k < K; ++k) v += phip[(c * n_eff + ss) * K + k];
+                    for (int k = 0; k < K; ++k) v += ph[(cc * n_eff + ss) * K + k];
             }
             sphi[wid][e] = v;
         }
         __syncwarp();
-        const double* Dp = dpinv + int64_t(jb) * kMaxDirs * kMaxDirs;
+        const double* Dp = dpinv + (int64_t(p) * mi1 + jb) * kMaxDirs * kMaxDirs;
         for (int e = lane; e < wj * w; e += 32) {
             const int a = e / w, s = e % w;
             double v = 0.0;
             for (int b = 0; b < wj; ++b) v += Dp[a * kMaxDirs + b] * sphi[wid][b * w + s];
-            B[int64_t(off + a) * kMaxDirs + s] = v;
+            Bp[int64_t(off + a) * kMaxDirs + s] = v;
         }
         __syncwarp();
     }
 }
 
-// P_new = Z - P_hist B, Q_new = (S Z) - Q_hist B, one thread per row; B tiles staged in shared memory.
+// P_new = Z - P_hist beta, Q_new = (S Z) - Q_hist beta, one thread per row; beta tiles staged in
+// shared memory (grid: CTAs x problems, each CTA a contiguous run of the problem's rows).
 template <typename T>
-__global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, const T* __restrict__ z,
-                         const double* __restrict__ B, T* __restrict__ PT, const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
+__global__ void k_mcg_pq(T* __restrict__ P, T* __restrict__ Q, const T* __restrict__ z,
+                         const double* __restrict__ beta, T* __restrict__ PT, const Ctl* __restrict__ ctl) {
+    const Ctl& c = ctl[blockIdx.y];
+    if (c.done) return;
     constexpr int TC = 64;
     __shared__ T sB[TC][kMaxDirs];
-    const int64_t n = int64_t(n_c) * 9;
-    const int w = ctl->w_new, off = ctl->new_off, hc = ctl->hist_cols, local = ctl->local, sz = ctl->sz;
-    const bool upd_q = !ctl->direct_q;
+    const int64_t n = int64_t(c.lay.nc) * 9;
+    const int64_t r0g = 9 * int64_t(c.lay.c0);
+    const int w = c.w_new, off = c.new_off, hc = c.hist_cols, local = c.local, sz = c.sz;
+    const bool upd_q = !c.direct_q;
+    T* Pp = P + c.lay.hoff;
+    T* Qp = Q + c.lay.hoff;
+    const double* Bp = beta + c.lay.boff * kMaxDirs;
     // every thread of the CTA walks all tiles, so the loop bounds are CTA-uniform
     const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
     const int64_t rbeg = int64_t(blockIdx.x) * per_cta;
@@ -1160,14 +1313,14 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
         const bool act = row < rend;
         T ap[kMaxDirs], aq[kMaxDirs];
         const int sub = act ? int(row / 9) / sz : 0;
-        const T zr = act ? z[row] : T(0);
+        const T zr = act ? z[r0g + row] : T(0);
 #pragma unroll
         for (int s = 0; s < kMaxDirs; ++s) {
             ap[s] = T(0);
             aq[s] = T(0);
             if (act && s < w) {
                 ap[s] = (local ? (s == sub) : (s == 0)) ? zr : T(0);
-                aq[s] = upd_q ? Q[int64_t(off + s) * n + row] : T(0);
+                aq[s] = upd_q ? Qp[int64_t(off + s) * n + row] : T(0);
             }
         }
         for (int c0 = 0; c0 < hc; c0 += TC) {
@@ -1175,14 +1328,14 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
             __syncthreads();
             for (int t = threadIdx.x; t < TC * kMaxDirs; t += blockDim.x) {
                 const int cc = t / kMaxDirs, s = t % kMaxDirs;
-                sB[cc][s] = (cc < tc && s < w) ? T(B[int64_t(c0 + cc) * kMaxDirs + s]) : T(0);
+                sB[cc][s] = (cc < tc && s < w) ? T(Bp[int64_t(c0 + cc) * kMaxDirs + s]) : T(0);
             }
             __syncthreads();
             if (act) {
                 if (upd_q) {
                     for (int cc = 0; cc < tc; ++cc) {
-                        const T pv = P[int64_t(c0 + cc) * n + row];
-                        const T qv = Q[int64_t(c0 + cc) * n + row];
+                        const T pv = Pp[int64_t(c0 + cc) * n + row];
+                        const T qv = Qp[int64_t(c0 + cc) * n + row];
 #pragma unroll
                         for (int s = 0; s < kMaxDirs; ++s) {
                             ap[s] -= pv * sB[cc][s];
@@ -1191,7 +1344,7 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
                     }
                 } else {
                     for (int cc = 0; cc < tc; ++cc) {
-                        const T pv = P[int64_t(c0 + cc) * n + row];
+                        const T pv = Pp[int64_t(c0 + cc) * n + row];
 #pragma unroll
                         for (int s = 0; s < kMaxDirs; ++s) ap[s] -= pv * sB[cc][s];
                     }
@@ -1202,25 +1355,25 @@ __global__ void k_mcg_pq(int32_t n_c, T* __restrict__ P, T* __restrict__ Q, cons
 #pragma unroll
             for (int s = 0; s < kMaxDirs; ++s) {
                 if (s < w) {
-                    P[int64_t(off + s) * n + row] = ap[s];
-                    if (upd_q) Q[int64_t(off + s) * n + row] = aq[s];
+                    Pp[int64_t(off + s) * n + row] = ap[s];
+                    if (upd_q) Qp[int64_t(off + s) * n + row] = aq[s];
                 }
                 // row-major copy of the new block for the multi-column product (zero past w)
-                if (!upd_q) PT[row * kMaxDirs + s] = s < w ? ap[s] : T(0);
+                if (!upd_q) PT[(r0g + row) * kMaxDirs + s] = s < w ? ap[s] : T(0);
             }
         }
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// true residual t = -b~ - S x in float64 and |t|^2, |b~|^2 partials
+// true residual t = -b~ - S x in float64; partial[2 j], partial[2 j + 1] = camera j's sums of
+// t^2 and b~^2 (one warp per camera, all problems)
 
 __global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
                                 const int32_t* __restrict__ col, const double* __restrict__ S,
                                 const double* __restrict__ x, const double* __restrict__ bt, double* __restrict__ res,
                                 double* __restrict__ partial) {
     const int lane = threadIdx.x & 31;
-    double v[2] = {0.0, 0.0};
     for (int64_t j = gtid() >> 5; j < n_c; j += gstride() >> 5) {
         const int64_t rj = row_ptr[j], nj = row_ptr[j + 1] - rj, tb = tile_ptr[j];
         double acc[9];
@@ -1240,6 +1393,7 @@ __global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = warp_sum(acc[a]);
+        double tt = 0.0, bb = 0.0;
         if (lane < 9) {
             double sx = acc[0];
 #pragma unroll
@@ -1247,19 +1401,27 @@ __global__ void k_true_residual(int32_t n_c, const int64_t* __restrict__ row_ptr
             const double b = bt[9 * j + lane];
             const double t = -b - sx;
             if (res) res[9 * j + lane] = t;
-            v[0] += t * t;
-            v[1] += b * b;
+            tt = t * t;
+            bb = b * b;
+        }
+        tt = warp_sum(tt);
+        bb = warp_sum(bb);
+        if (lane == 0) {
+            partial[2 * j] = tt;
+            partial[2 * j + 1] = bb;
         }
     }
-    cta_sum_write<2>(v, partial + 2 * blockIdx.x);
 }
 
-__global__ void k_true_reduce(Ctl* ctl, const double* __restrict__ partial, int np) {
-    double a = sum_partials(partial, np, 2, 0);
-    double b = sum_partials(partial, np, 2, 1);
+// per problem: ctl.true_rr and ctl.bb from the per-camera partials (camera order)
+__global__ void k_true_reduce(Ctl* ctl, const double* __restrict__ partial) {
+    Ctl* c = ctl + blockIdx.x;
+    const double* pp = partial + 2 * int64_t(c->lay.c0);
+    const double a = sum_partials(pp, c->lay.nc, 2, 0);
+    const double b = sum_partials(pp, c->lay.nc, 2, 1);
     if (threadIdx.x == 0) {
-        ctl->true_rr = a;
-        ctl->bb = b;
+        c->true_rr = a;
+        c->bb = b;
     }
 }
 
@@ -1267,10 +1429,6 @@ __global__ void k_true_reduce(Ctl* ctl, const double* __restrict__ partial, int 
 __global__ void k_accumulate(int64_t n, const float* __restrict__ d, const double* __restrict__ lam,
                              double* __restrict__ x) {
     for (int64_t i = gtid(); i < n; i += gstride()) x[i] += lam[i] * double(d[i]);
-}
-
-__global__ void k_zero(int64_t n, double* __restrict__ x) {
-    for (int64_t i = gtid(); i < n; i += gstride()) x[i] = 0.0;
 }
 
 // refinement start: x = 0 and rt = -b~
@@ -1282,30 +1440,72 @@ __global__ void k_start_refine(int64_t n, const double* __restrict__ bt, double*
     }
 }
 
-// ctl->true_rr = ctl->bb = |v|^2 (one CTA, fixed summation order)
-__global__ void k_norm2(int64_t n, const double* __restrict__ v, Ctl* ctl) {
-    __shared__ double red[kThreads];
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (int(threadIdx.x) < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
+// One CTA per problem: |b~|^2 (fixed order) and the refinement state at x = 0.
+__global__ void k_outer_init(const Layout* __restrict__ lay, const double* __restrict__ bt, Outer* outer) {
+    const Layout L = lay[blockIdx.x];
+    const int64_t n = int64_t(L.nc) * 9;
+    const double* b = bt + 9 * int64_t(L.c0);
+    double v[1] = {0.0};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[0] += b[i] * b[i];
+    __shared__ double s[1];
+    cta_sum_write<1>(v, s);
     if (threadIdx.x == 0) {
-        ctl->true_rr = red[0];
-        ctl->bb = red[0];
+        Outer o;
+        memset(&o, 0, sizeof(o));
+        o.bb = s[0];
+        o.tr = s[0];
+        o.tr_prev = s[0];
+        o.status = s[0] == 0.0 ? BA_OK : BA_ERR_NOT_CONVERGED;
+        o.active = s[0] == 0.0 ? 0 : 1;
+        outer[blockIdx.x] = o;
     }
 }
 
-template <typename T>
-__global__ void k_copy_out(int64_t n, const T* __restrict__ x, double* __restrict__ out) {
-    for (int64_t i = gtid(); i < n; i += gstride()) out[i] = double(x[i]);
+// Plan the next float32 sweep of every problem still refining: per sweep the inner solve reduces
+// its residual by inner_tol; when what is left to reach tol is within ten times that, the sweep
+// aims 3x past it so that it is the last one.
+__global__ void k_refine_plan(Outer* outer, double tol, double inner_tol, int max_iters, int max_refine) {
+    Outer* o = outer + blockIdx.x;
+    if (threadIdx.x != 0) return;
+    o->swept = 0;
+    if (!o->active) return;
+    if (o->sweeps >= max_refine || o->iters >= max_iters) {
+        o->active = 0;
+        return;
+    }
+    const double need = tol * sqrt(o->bb) / sqrt(o->tr);
+    double t = need > 0.1 * inner_tol ? fmax(0.3 * need, 0.1 * inner_tol) : inner_tol;
+    if (t >= 1.0) t = 0.5;
+    o->tol_in = t;
+    o->max_in = max_iters - o->iters;
+    o->swept = 1;
 }
 
-__global__ void k_to_float_vec(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
-    for (int64_t i = gtid(); i < n; i += gstride()) out[i] = float(in[i]);
+// After a sweep and the float64 true residual: account the sweep and decide whether to go on.
+__global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, double tol, int mcg) {
+    Outer* o = outer + blockIdx.x;
+    const Ctl& c = ctl[blockIdx.x];
+    if (threadIdx.x != 0 || !o->swept) return;
+    o->sweeps += 1;
+    o->iters += c.it;
+    o->locals += c.local_steps;
+    o->cols = mcg ? c.cols : 1;
+    o->tr_prev = o->tr;
+    o->tr = c.true_rr;
+    if (c.status == BA_ERR_BREAKDOWN || c.status == BA_ERR_OOM || c.status == BA_ERR_TIMEOUT) {
+        o->status = c.status;
+        o->active = 0;
+        return;
+    }
+    if (!(o->tr == o->tr)) {
+        o->status = BA_ERR_BREAKDOWN;
+        o->active = 0;
+        return;
+    }
+    if (o->tr <= tol * tol * o->bb) {
+        o->status = BA_OK;
+        o->active = 0;
+    }
 }
 
 }  // namespace
@@ -1314,100 +1514,123 @@ __global__ void k_to_float_vec(int64_t n, const double* __restrict__ in, float* 
 // host side
 
 struct GraphKey {
-    int mcg = -1, fp32 = -1, chunk = 0;
-    const void* ptrs[12] = {};
+    int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1;
+    const void* ptrs[14] = {};
     bool operator==(const GraphKey& o) const {
-        if (mcg != o.mcg || fp32 != o.fp32 || chunk != o.chunk) return false;
-        for (int i = 0; i < 12; ++i) if (ptrs[i] != o.ptrs[i]) return false;
+        if (mcg != o.mcg || fp32 != o.fp32 || chunk != o.chunk || mi1 != o.mi1 || use_l != o.use_l ||
+            epoch != o.epoch)
+            return false;
+        for (int i = 0; i < 14; ++i) if (ptrs[i] != o.ptrs[i]) return false;
         return true;
     }
 };
 
+// device buffer that only grows
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
 struct Solver {
-    int64_t n = 0;            // 9 n_c
-    int64_t cap = 0;          // history columns
-    int max_iters = 0;
-    int nparts = 0;
-    int64_t phip_len = 0;
-    int elt = 8;              // bytes per element of the vectors
-    void* P = nullptr;        // cap x n
-    void* Q = nullptr;
-    void* r = nullptr;
-    void* z = nullptr;
-    void* xw = nullptr;       // working x of the inner solve (mixed)
-    void* PT = nullptr;       // n x 16 row-major copy of the newest block (float32 direct-Q products)
-    double* part_a = nullptr; // nparts x kGramMax
-    double* part_b = nullptr; // nparts x 2
-    double* part_c = nullptr; // nparts x 2
-    double* part_cam = nullptr;  // n_c x 2 (per-camera partials of the implicit residual)
-    double* dpinv = nullptr;  // (max_iters + 1) x 256
-    double* B = nullptr;      // cap x 16
-    double* phip = nullptr;
-    double* hist = nullptr;   // max_iters (of the last sweep)
-    int* blk_off = nullptr;
-    int* blk_w = nullptr;
-    Ctl* ctl = nullptr;
-    Ctl* h_ctl = nullptr;     // pinned
-    double* rt = nullptr;     // true residual vector (float64, n)
-    std::vector<double> host_hist;
+    int nb = 0;               // problems
+    int64_t n = 0;            // 9 n_c over all problems
+    int mi1 = 0;              // per-problem stride of the per-step arrays (max_iters + 1)
+    int gx = 1;               // grid width of the per-camera kernels
+    int gg = 1;               // Gram grid width
+    int gq = 1;               // grid width of the per-row kernels
+    int gphi = 1, gb = 1;     // Phi and beta grid widths
+    std::vector<Layout> lay;  // of the current solve
+    Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, phip, hist, blk_off, blk_w, ctl, outer, rt, lay_d,
+        totals, dpart, dcnt, camdot;
+    Ctl* h_ctl = nullptr;     // pinned, nb
+    Outer* h_outer = nullptr; // pinned, nb
+    std::vector<std::vector<double>> host_hist;   // per problem, residual history of the last solve
+    std::vector<double> rows;                     // staging of the iteration-major device history
     int64_t launches = 0;     // kernel executions issued by the current solve
-    void* flush = nullptr;    // L2 flush buffer for kernel timing
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     GraphKey key;
     // work lists of the block-sparse products: whole rows, and rows split by pose subset
     ItemList items_g, items_l;
+    int items_cb = -1;         // item chunk rule the lists were built with (0 = per-problem heuristic)
     int items_l_dirs = -1;
-    bool use_local = false;    // local steps read items_l (false when there is a single subset)
+    bool use_l = false;        // the current MCG solve splits rows by pose subset (n_dirs > 1)
+    int epoch = 0;             // incremented whenever a work list is rebuilt (captured graphs hold them)
     void* mm_part = nullptr;   // k_spmm partials: items_g.n x 16 x 9
-    double* totals = nullptr;  // grid totals: [0] Delta [1] gamma [2] |r|^2 [3] Phi [4] r^T z ; [8] |r|^2 [9] r^T z
-    double* dpart = nullptr;   // 3 x (num_sms * 8) x 2 CTA partials
-    int* dcnt = nullptr;       // 4 self-resetting arrival counters
 };
 
-// Items of the block-sparse product: each (row, segment) split into chunks of at most cb blocks.
-// sz = 0: one segment per row; otherwise segment s holds the blocks whose column camera lies in
-// [s sz, (s + 1) sz), for s < n_seg (empty segments get one empty item, which writes zeros).
-static std::vector<SpItem> build_items(const Structure& s, int sz, int n_seg, int cb) {
-    std::vector<SpItem> out;
-    int grp = 0;
-    for (int32_t j = 0; j < s.n_c; ++j) {
-        const int64_t rj = s.h_row_ptr[j], nj = s.h_row_ptr[j + 1] - rj;
-        const int32_t* cj = s.h_col.data() + rj;
-        const int nseg = sz > 0 ? n_seg : 1;
-        for (int g = 0; g < nseg; ++g) {
-            int q0 = 0, q1 = int(nj);
-            if (sz > 0) {
-                q0 = int(std::lower_bound(cj, cj + nj, g * sz) - cj);
-                q1 = int(std::lower_bound(cj, cj + nj, (g + 1) * sz) - cj);
-            }
-            const int nch = q1 > q0 ? (q1 - q0 + cb - 1) / cb : 1;
-            for (int c = 0; c < nch; ++c) {
-                SpItem it;
-                it.row = j;
-                it.seg = g;
-                it.q0 = q0 + c * cb;
-                it.q1 = std::min(q1, q0 + (c + 1) * cb);
-                if (it.q1 < it.q0) it.q1 = it.q0;
-                it.grp = grp;
-                it.k = c;
-                it.ng = nch;
-                it.pad = 0;
-                out.push_back(it);
-            }
-            ++grp;
-        }
+static void grow(Buf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        throw Error(e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
-    return out;
+    b.bytes = bytes;
+}
+template <typename T>
+static T* ptr(const Buf& b) {
+    return static_cast<T*>(b.p);
 }
 
-static int item_chunk(const Structure& s) {
+// Blocks per work item when the problem holds nnzb stored blocks: about 64 items per SM over the
+// problem, a multiple of the 32-block tile, within [32, 256].
+static int item_chunk(int64_t nnzb) {
     int64_t target = int64_t(num_sms()) * 64;
-    int64_t cb = (s.nnzb + target - 1) / target;
+    int64_t cb = (nnzb + target - 1) / target;
     cb = (cb + 31) / 32 * 32;
     if (cb < 32) cb = 32;
     if (cb > 256) cb = 256;
     return int(cb);
+}
+
+// Items of the block-sparse product, problem by problem: each (row, segment) split into chunks of
+// at most cb blocks (cb = forced_cb, or the heuristic for the problem's own block count).
+// split = false: one segment per row; otherwise segment s of a row of problem b holds the blocks
+// whose column camera lies in [c0 + s sz, c0 + (s + 1) sz), for s < n_eff (empty segments get
+// one empty item, which writes zeros).
+static std::vector<SpItem> build_items(const Structure& s, const std::vector<Layout>& lay, bool split, int forced_cb) {
+    std::vector<SpItem> out;
+    int grp = 0;
+    for (size_t b = 0; b < lay.size(); ++b) {
+        const Layout& L = lay[b];
+        const int64_t nnzb_b = s.h_row_ptr[L.c0 + L.nc] - s.h_row_ptr[L.c0];
+        const int cb = forced_cb > 0 ? forced_cb : item_chunk(nnzb_b);
+        const int nseg = split ? L.n_eff : 1;
+        for (int32_t j = L.c0; j < L.c0 + L.nc; ++j) {
+            const int64_t rj = s.h_row_ptr[j], nj = s.h_row_ptr[j + 1] - rj;
+            const int32_t* cj = s.h_col.data() + rj;
+            for (int g = 0; g < nseg; ++g) {
+                int q0 = 0, q1 = int(nj);
+                if (split) {
+                    q0 = int(std::lower_bound(cj, cj + nj, L.c0 + g * L.sz) - cj);
+                    q1 = int(std::lower_bound(cj, cj + nj, L.c0 + (g + 1) * L.sz) - cj);
+                }
+                const int nch = q1 > q0 ? (q1 - q0 + cb - 1) / cb : 1;
+                for (int c = 0; c < nch; ++c) {
+                    SpItem it;
+                    it.row = j;
+                    it.seg = g;
+                    it.q0 = q0 + c * cb;
+                    it.q1 = std::min(q1, q0 + (c + 1) * cb);
+                    if (it.q1 < it.q0) it.q1 = it.q0;
+                    it.grp = grp;
+                    it.k = c;
+                    it.ng = nch;
+                    it.prob = int(b);
+                    out.push_back(it);
+                }
+                ++grp;
+            }
+        }
+    }
+    return out;
 }
 
 static void free_items(ItemList& L) {
@@ -1420,8 +1643,8 @@ static void free_items(ItemList& L) {
 static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
     free_items(L);
     SpItem* d = nullptr;
-    BA_CUDA_TRY(cudaMalloc(&d, sizeof(SpItem) * v.size()));
-    BA_CUDA_TRY(cudaMemcpy(d, v.data(), sizeof(SpItem) * v.size(), cudaMemcpyHostToDevice));
+    BA_CUDA_TRY(cudaMalloc(&d, sizeof(SpItem) * (v.empty() ? 1 : v.size())));
+    if (!v.empty()) BA_CUDA_TRY(cudaMemcpy(d, v.data(), sizeof(SpItem) * v.size(), cudaMemcpyHostToDevice));
     L.items = d;
     L.n = int64_t(v.size());
     const int ngrp = v.empty() ? 1 : v.back().grp + 1;
@@ -1430,197 +1653,253 @@ static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
     BA_CUDA_TRY(cudaMalloc(&L.part, sizeof(double) * 9 * (v.size() > 0 ? v.size() : 1)));
 }
 
-static void ensure_items(Solver* w, const Structure& s, int n_dirs, int sz, int n_eff) {
-    const int cb = item_chunk(s);
-    if (!w->items_g.items) {
-        upload_items(w->items_g, build_items(s, 0, 1, cb));
-        BA_CUDA_TRY(cudaMalloc(&w->mm_part, sizeof(double) * kMaxDirs * 9 * size_t(w->items_g.n)));
+static void set_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<float>())));
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<double>())));
+    done = true;
+}
+
+// (Re)build the work lists when the chunk rule or the subset layout changed.
+static void ensure_items(Solver* w, const Structure& s, int n_dirs, int forced_cb) {
+    const int cb = forced_cb > 0 ? forced_cb : 0;
+    if (!w->items_g.items || w->items_cb != cb) {
+        upload_items(w->items_g, build_items(s, w->lay, false, cb));
+        if (w->mm_part) cudaFree(w->mm_part);
+        w->mm_part = nullptr;
+        BA_CUDA_TRY(cudaMalloc(&w->mm_part, sizeof(double) * kMaxDirs * 9 * size_t(w->items_g.n > 0 ? w->items_g.n : 1)));
+        w->items_l_dirs = -1;
+        w->items_cb = cb;
+        ++w->epoch;
     }
-    if (n_eff > 1 && w->items_l_dirs != n_dirs) {
-        upload_items(w->items_l, build_items(s, sz, n_eff, cb));
+    if (n_dirs > 1 && w->items_l_dirs != n_dirs) {
+        upload_items(w->items_l, build_items(s, w->lay, true, cb));
         w->items_l_dirs = n_dirs;
+        ++w->epoch;
     }
-    w->use_local = n_eff > 1;
-    static bool attrs = false;
-    if (!attrs) {
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<float>())));
-        BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<double>())));
-        attrs = true;
-    }
-    if (!w->totals) {
-        BA_CUDA_TRY(cudaMalloc(&w->totals, sizeof(double) * 16));
-        BA_CUDA_TRY(cudaMalloc(&w->dpart, sizeof(double) * 3 * 2 * size_t(num_sms()) * 8));
-        BA_CUDA_TRY(cudaMalloc(&w->dcnt, sizeof(int) * 4));
-        BA_CUDA_TRY(cudaMemset(w->dcnt, 0, sizeof(int) * 4));
-    }
+    w->use_l = n_dirs > 1;
+    set_smem_attrs();
 }
 
-static int spmv_grid() { return num_sms() * 8; }
-
-static void free_ws(Solver* w) {
-    void* ptrs[] = {w->P, w->Q, w->r, w->z, w->xw, w->PT, w->part_a, w->part_b, w->part_c, w->dpinv, w->B,
-                    w->phip, w->hist, w->blk_off, w->blk_w, w->ctl, w->rt, w->part_cam};
-    for (void* p : ptrs) if (p) cudaFree(p);
-    w->P = w->Q = w->r = w->z = w->xw = w->PT = nullptr;
-    w->part_a = w->part_b = w->part_c = w->dpinv = w->B = w->phip = w->hist = w->rt = w->part_cam = nullptr;
-    w->blk_off = w->blk_w = nullptr;
-    w->ctl = nullptr;
-    if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
-    w->key = GraphKey();
-    w->n = w->cap = 0;
+static int grid_for_host(int64_t n) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    int cap = num_sms() * 8;
+    return int(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-Solver* solver_create() {
-    Solver* w = new Solver();
-    return w;
+// Per-problem layout of a solve and the grid widths; buffers grow to fit.
+static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dirs, bool fp32) {
+    const int nb = int(s.h_cam_off.size()) - 1;
+    std::vector<Layout> lay(nb);
+    int64_t hoff = 0, phoff = 0, boff = 0;
+    int nc_max = 1;
+    for (int b = 0; b < nb; ++b) {
+        Layout& L = lay[b];
+        L.c0 = s.h_cam_off[b];
+        L.nc = s.h_cam_off[b + 1] - L.c0;
+        nc_max = std::max(nc_max, L.nc);
+        const int nd = a.mcg ? n_dirs : 1;
+        L.sz = (L.nc + nd - 1) / nd;
+        L.n_eff = (L.nc + L.sz - 1) / L.sz;
+        L.K = (L.sz + kChunkCams - 1) / kChunkCams;
+        int64_t cap = 1;
+        if (a.mcg) {
+            cap = a.max_history > 0 ? a.max_history : int64_t(a.max_iters) * L.n_eff + 1;
+            if (cap < 1 + L.n_eff) cap = 1 + L.n_eff;
+            if (cap > (int64_t(1) << 30)) throw Error(BA_ERR_INVALID_ARG, "direction history too large");
+        }
+        L.cap = int(cap);
+        L.hoff = hoff;
+        L.phoff = phoff;
+        L.boff = boff;
+        hoff += cap * 9 * int64_t(L.nc);
+        phoff += cap * L.n_eff * L.K;
+        boff += cap;
+    }
+    const int64_t n = 9 * int64_t(s.n_c);
+    const size_t elt = fp32 ? 4 : 8;
+    const int G = num_sms() * 2;
+    w->nb = nb;
+    w->n = n;
+    w->mi1 = std::max(w->mi1, a.max_iters + 1);
+    w->gx = int(std::min<int64_t>(G, (nc_max + kThreads - 1) / kThreads));
+    w->gg = int(std::min<int64_t>(G, (9 * int64_t(nc_max) + 127) / 128));
+    w->gq = std::max(1, G / nb);
+    w->gphi = std::max(1, 4 * G / nb);
+    w->gb = std::max(1, G / nb);
+    if (!w->h_ctl || int(w->lay.size()) != nb) {
+        if (w->h_ctl) cudaFreeHost(w->h_ctl);
+        if (w->h_outer) cudaFreeHost(w->h_outer);
+        w->h_ctl = nullptr;
+        w->h_outer = nullptr;
+        BA_CUDA_TRY(cudaMallocHost(&w->h_ctl, sizeof(Ctl) * nb));
+        BA_CUDA_TRY(cudaMallocHost(&w->h_outer, sizeof(Outer) * nb));
+    }
+    if (!w->cap_stream) BA_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
+    grow(w->P, size_t(hoff) * elt);
+    grow(w->Q, size_t(hoff) * elt);
+    grow(w->r, size_t(n) * elt);
+    grow(w->z, size_t(n) * elt);
+    grow(w->xw, size_t(n) * elt);
+    grow(w->PT, size_t(n) * kMaxDirs * elt);
+    grow(w->part_a, size_t(nb) * w->gg * kGramMax * sizeof(double));
+    grow(w->part_b, size_t(nb) * w->gx * sizeof(double));
+    grow(w->part_cam, size_t(s.n_c) * 2 * sizeof(double));
+    grow(w->dpinv, size_t(nb) * w->mi1 * kMaxDirs * kMaxDirs * sizeof(double));
+    grow(w->beta, size_t(boff) * kMaxDirs * sizeof(double));
+    grow(w->phip, size_t(phoff) * sizeof(double));
+    grow(w->hist, size_t(nb) * w->mi1 * sizeof(double));
+    grow(w->blk_off, size_t(nb) * w->mi1 * sizeof(int));
+    grow(w->blk_w, size_t(nb) * w->mi1 * sizeof(int));
+    grow(w->ctl, size_t(nb) * sizeof(Ctl));
+    grow(w->outer, size_t(nb) * sizeof(Outer));
+    grow(w->rt, size_t(n) * sizeof(double));
+    grow(w->lay_d, size_t(nb) * sizeof(Layout));
+    grow(w->totals, size_t(nb) * kTotals * sizeof(double));
+    grow(w->dpart, size_t(nb) * w->gx * 5 * sizeof(double));
+    grow(w->camdot, size_t(s.n_c) * 2 * sizeof(double));
+    if (w->dcnt.bytes < size_t(nb) * 4 * sizeof(int)) {
+        grow(w->dcnt, size_t(nb) * 4 * sizeof(int));
+        BA_CUDA_TRY(cudaMemset(w->dcnt.p, 0, w->dcnt.bytes));
+    }
+    BA_CUDA_TRY(cudaMemcpy(w->lay_d.p, lay.data(), sizeof(Layout) * nb, cudaMemcpyHostToDevice));
+    w->lay = lay;
+    ensure_items(w, s, a.mcg ? n_dirs : 1, a.item_blocks);
 }
+
+static void free_buf(Buf& b) {
+    if (b.p) cudaFree(b.p);
+    b = Buf();
+}
+
+Solver* solver_create() { return new Solver(); }
 
 void solver_destroy(Solver* w) {
     if (!w) return;
-    free_ws(w);
+    Buf* bufs[] = {&w->P, &w->Q, &w->r, &w->z, &w->xw, &w->PT, &w->part_a, &w->part_b, &w->part_cam, &w->dpinv,
+                   &w->beta, &w->phip, &w->hist, &w->blk_off, &w->blk_w, &w->ctl, &w->outer, &w->rt, &w->lay_d,
+                   &w->totals, &w->dpart, &w->dcnt, &w->camdot};
+    for (Buf* b : bufs) free_buf(*b);
+    if (w->exec) cudaGraphExecDestroy(w->exec);
     free_items(w->items_g);
     free_items(w->items_l);
     if (w->mm_part) cudaFree(w->mm_part);
-    if (w->totals) cudaFree(w->totals);
-    if (w->dpart) cudaFree(w->dpart);
-    if (w->dcnt) cudaFree(w->dcnt);
     if (w->h_ctl) cudaFreeHost(w->h_ctl);
-    if (w->flush) cudaFree(w->flush);
+    if (w->h_outer) cudaFreeHost(w->h_outer);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
     delete w;
 }
 
-int solver_history(const Solver* w, const double** hist) {
-    *hist = w->host_hist.data();
-    return static_cast<int>(w->host_hist.size());
-}
-
-template <typename T>
-static void alloc_checked(void** p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error(e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,
-                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+int solver_history(const Solver* w, int problem, const double** hist) {
+    if (problem < 0 || problem >= int(w->host_hist.size())) {
+        *hist = nullptr;
+        return 0;
     }
+    *hist = w->host_hist[problem].data();
+    return static_cast<int>(w->host_hist[problem].size());
 }
 
-static void ensure_ws(Solver* w, int64_t n, int64_t cap, int max_iters, int64_t phip_len, int elt) {
-    if (!w->h_ctl) BA_CUDA_TRY(cudaMallocHost(&w->h_ctl, sizeof(Ctl)));
-    if (!w->cap_stream) BA_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
-    if (w->n == n && w->cap >= cap && w->max_iters >= max_iters && w->phip_len >= phip_len && w->elt == elt &&
-        w->P)
-        return;
-    free_ws(w);
-    w->n = n;
-    w->cap = cap;
-    w->max_iters = max_iters;
-    w->phip_len = phip_len;
-    w->elt = elt;
-    w->nparts = num_sms() * 2;
-    alloc_checked<char>(&w->P, size_t(cap) * n * elt);
-    alloc_checked<char>(&w->Q, size_t(cap) * n * elt);
-    alloc_checked<char>(&w->r, size_t(n) * elt);
-    alloc_checked<char>(&w->z, size_t(n) * elt);
-    alloc_checked<char>(&w->xw, size_t(n) * elt);
-    alloc_checked<char>(&w->PT, size_t(n) * kMaxDirs * elt);
-    alloc_checked<char>((void**)&w->part_a, size_t(w->nparts) * kGramMax * sizeof(double));
-    alloc_checked<char>((void**)&w->part_b, size_t(w->nparts) * 2 * sizeof(double));
-    alloc_checked<char>((void**)&w->part_c, size_t(w->nparts) * 2 * sizeof(double));
-    alloc_checked<char>((void**)&w->part_cam, size_t(n / 9 + 1) * 2 * sizeof(double));
-    alloc_checked<char>((void**)&w->dpinv, size_t(max_iters + 1) * kMaxDirs * kMaxDirs * sizeof(double));
-    alloc_checked<char>((void**)&w->B, size_t(cap) * kMaxDirs * sizeof(double));
-    alloc_checked<char>((void**)&w->phip, size_t(phip_len > 0 ? phip_len : 1) * sizeof(double));
-    alloc_checked<char>((void**)&w->hist, size_t(max_iters + 1) * sizeof(double));
-    alloc_checked<char>((void**)&w->blk_off, size_t(max_iters + 1) * sizeof(int));
-    alloc_checked<char>((void**)&w->blk_w, size_t(max_iters + 1) * sizeof(int));
-    alloc_checked<char>((void**)&w->ctl, sizeof(Ctl));
-    alloc_checked<char>((void**)&w->rt, size_t(n) * sizeof(double));
-}
-
-// Enqueue one iteration of the chosen algorithm on `st`.
+// Enqueue one iteration of the chosen algorithm for every problem on `st`.
 template <typename T>
 static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const double* Dinv, T* x, bool mcg,
                               cudaStream_t st) {
-    const int G = w->nparts;
-    T* P = static_cast<T*>(w->P);
-    T* Q = static_cast<T*>(w->Q);
-    T* r = static_cast<T*>(w->r);
-    T* z = static_cast<T*>(w->z);
-    const int n_c = s.n_c;
-    const int Gs = spmv_grid();
-    const int Gt = num_sms();   // tile-streaming product: one CTA per SM
-    double* dp0 = w->dpart;
-    double* dp1 = w->dpart + 2 * Gs;
-    double* dp2 = w->dpart + 4 * Gs;
+    const int nb = w->nb;
+    T* P = ptr<T>(w->P);
+    T* Q = ptr<T>(w->Q);
+    T* r = ptr<T>(w->r);
+    T* z = ptr<T>(w->z);
+    Ctl* ctl = ptr<Ctl>(w->ctl);
+    double* totals = ptr<double>(w->totals);
+    int* dcnt = ptr<int>(w->dcnt);
+    const int Gt = num_sms();   // tile-streaming products: one CTA per SM
+    const size_t sm = spmv_smem<T>();
     if (!mcg) {
-        k_spmv<T, 1><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
-            s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, r, dp0, w->dcnt, w->totals, w->ctl, 1);
-        k_pcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, w->totals, dp1, w->dcnt + 1, w->ctl);
-        k_pcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals, w->hist);
-        k_pcg_dir<T><<<G, kThreads, 0, st>>>(w->n, z, P, w->ctl);
+        k_spmv<T, 1, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
+            s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelLive, Q, r, ptr<double>(w->camdot), ctl);
+        k_pcg_update<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
+                                                               ptr<double>(w->dpart), dcnt, ctl);
+        k_pcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist));
+        k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
     } else {
-        // Gram partials: one CTA per 128 rows at most; the small solve sums them one entry per thread
-        const int Gg = int(std::min<int64_t>(G, (w->n + 127) / 128));
-        k_mcg_gram<T><<<Gg, kThreads, 0, st>>>(w->n, P, Q, r, w->part_a, w->ctl);
-        k_mcg_small<<<1, kThreads, 0, st>>>(w->ctl, w->part_a, Gg, w->dpinv);
-        k_mcg_update<T><<<G, kThreads, 0, st>>>(n_c, Dinv, P, Q, x, r, z, dp2, w->dcnt + 2, w->totals + 8, w->ctl);
-        k_mcg_decide<<<1, 32, 0, st>>>(w->ctl, w->totals + 8, w->hist, w->blk_off, w->blk_w);
-        k_mcg_phi<T><<<G * 4, kThreads, 0, st>>>(n_c, Q, z, w->phip, w->ctl);
-        k_mcg_beta<<<G, kThreads, 0, st>>>(w->phip, w->dpinv, w->blk_off, w->blk_w, w->B, w->ctl);
+        k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
+        k_mcg_small<<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
+        k_mcg_update<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gx,
+                                                               dcnt, totals, ctl);
+        k_mcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist), ptr<int>(w->blk_off), ptr<int>(w->blk_w),
+                                        w->mi1);
+        k_mcg_phi<T><<<dim3(w->gphi, nb), kThreads, 0, st>>>(Q, z, ptr<double>(w->phip), ctl);
+        k_mcg_beta<<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
+                                                         ptr<int>(w->blk_off), ptr<int>(w->blk_w),
+                                                         ptr<double>(w->beta), ctl, w->mi1);
         if (sizeof(T) == 8) {
-            // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}
-            k_spmv<T, 0><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g, w->use_local ? w->items_l : w->items_g, Q, w->n,
-                nullptr, nullptr, nullptr, nullptr, w->ctl, 1);
-            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, nullptr, w->ctl);
+            // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}; S Z over whole rows for the
+            // problems forming a global block, over the subset segments for the local ones
+            k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
+                s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g, w->use_l ? kSelGlobal : kSelLive, Q, nullptr,
+                nullptr, ctl);
+            if (w->use_l)
+                k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
+                    s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l, kSelLocal, Q, nullptr, nullptr, ctl);
+            k_mcg_pq<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(P, Q, z, ptr<double>(w->beta), nullptr, ctl);
         } else {
             // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
-            k_mcg_pq<T><<<G, kThreads, 0, st>>>(n_c, P, Q, z, w->B, static_cast<T*>(w->PT), w->ctl);
-            k_spmv<T, 2><<<Gt, SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr,
-                w->ctl, 1);
+            k_mcg_pq<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(P, Q, z, ptr<double>(w->beta), ptr<T>(w->PT), ctl);
+            k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
+                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
             k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, static_cast<const T*>(w->PT), w->items_g, static_cast<T*>(w->mm_part),
-                Q, w->n, w->ctl);
+                s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->PT), w->items_g, static_cast<T*>(w->mm_part), Q, ctl);
         }
     }
 }
 
-// One Krylov solve of S x = sign * rhs (rhs float64) with storage type T.  Returns the final Ctl in *out.
+static int iteration_launches(bool mcg, bool fp32, bool two_lists) {
+    if (!mcg) return 4;
+    return fp32 ? 9 : (two_lists ? 9 : 8);
+}
+
+// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0.
 template <typename T>
-static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
-                   const double* scale, T* x, const SolveArgs& a, int n_eff, int sz, int K, int64_t cap, Ctl* out,
-                   cudaStream_t st) {
-    const int G = w->nparts;
-    T* P = static_cast<T*>(w->P);
-    T* Q = static_cast<T*>(w->Q);
-    T* r = static_cast<T*>(w->r);
-    T* z = static_cast<T*>(w->z);
-    k_init_vec<T><<<G, kThreads, 0, st>>>(s.n_c, rhs, sign, scale, Dinv, x, r, z, P, w->part_b);
-    k_init_ctl<<<1, 32, 0, st>>>(w->ctl, w->part_b, G, a.tol, a.max_iters, a.tau, n_eff, sz, K,
-                                 static_cast<int>(cap), w->blk_off, w->blk_w, sizeof(T) == 4 ? kStagnation : 0.0,
-                                 sizeof(T) == 4 ? 1 : 0);
-    // Q_0 = S P_0
-    k_spmv<T, 0><<<num_sms(), SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
-        s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, w->items_g, Q, w->n, nullptr, nullptr, nullptr, nullptr, w->ctl,
-        0);
+static void krylov_init(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
+                        const double* scale, T* x, const SolveArgs& a, const Outer* outer, cudaStream_t st) {
+    const int nb = w->nb;
+    k_init_vec<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(ptr<Layout>(w->lay_d), rhs, sign, scale, Dinv, x, ptr<T>(w->r),
+                                                         ptr<T>(w->z), ptr<T>(w->P), ptr<double>(w->part_b));
+    k_init_ctl<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Layout>(w->lay_d), ptr<double>(w->part_b), w->gx, a.tol,
+                                  a.max_iters, a.tau, sizeof(T) == 4 ? kStagnation : 0.0, sizeof(T) == 4 ? 1 : 0, outer,
+                                  ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1);
+    k_spmv<T, 0, true><<<num_sms(), SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
+        s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->P), w->items_g, kSelLive, ptr<T>(w->Q), nullptr, nullptr,
+        ptr<Ctl>(w->ctl));
     BA_CUDA_TRY(cudaGetLastError());
     w->launches += 3;
+}
 
+// One Krylov solve per problem of S x = sign * rhs (rhs float64) with storage type T, all problems
+// in the same launches.  On return w->h_ctl holds every problem's final control block.
+template <typename T>
+static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
+                   const double* scale, T* x, const SolveArgs& a, const Outer* outer, cudaStream_t st) {
+    const int nb = w->nb;
+    krylov_init<T>(w, s, S, Dinv, rhs, sign, scale, x, a, outer, st);
     GraphKey key;
     key.mcg = a.mcg;
     key.fp32 = sizeof(T) == 4;
     key.chunk = a.chunk;
-    const void* ptrs[12] = {S, Dinv, x, w->P, w->Q, w->r, w->z, w->ctl, w->B, w->phip, w->items_g.items,
-                            w->use_local ? w->items_l.items : w->items_g.items};
-    for (int i = 0; i < 12; ++i) key.ptrs[i] = ptrs[i];
+    key.mi1 = w->mi1;
+    key.use_l = w->use_l;
+    key.epoch = w->epoch;
+    const void* ptrs[14] = {S, Dinv, x, w->P.p, w->Q.p, w->r.p, w->z.p, w->ctl.p, w->beta.p, w->phip.p,
+                            w->items_g.items, w->items_l.items, w->PT.p, w->dpinv.p};
+    for (int i = 0; i < 14; ++i) key.ptrs[i] = ptrs[i];
     if (!(key == w->key) || !w->exec) {
         if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
         cudaGraph_t g = nullptr;
@@ -1633,40 +1912,49 @@ static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv
         if (ce != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
         w->key = key;
     }
+    const int per_iter = iteration_launches(a.mcg != 0, sizeof(T) == 4, w->use_l);
     const int max_chunks = a.max_iters / a.chunk + 2;
     for (int c = 0; c < max_chunks; ++c) {
-        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
         BA_CUDA_TRY(cudaStreamSynchronize(st));
-        if (w->h_ctl->done) break;
+        bool all_done = true;
+        for (int b = 0; b < nb && all_done; ++b) all_done = w->h_ctl[b].done != 0;
+        if (all_done) break;
         BA_CUDA_TRY(cudaGraphLaunch(w->exec, st));
-        w->launches += int64_t(a.chunk) * (a.mcg ? (sizeof(T) == 8 ? 8 : 9) : 4);
+        w->launches += int64_t(a.chunk) * per_iter;
     }
-    BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaStreamSynchronize(st));
-    *out = *w->h_ctl;
 }
 
-// out = -b~ - S x and its norms into ctl (true_rr, bb): explicit tiled S in float64 precision,
-// the implicit float64 operator U x - G (G^T x) in mixed precision (no float64 S is built there).
+// out = -b~ - S x and, per problem, its norms into ctl (true_rr, bb): explicit tiled S in float64
+// precision, the implicit float64 operator U x - G (G^T x) in mixed precision (no float64 S).
 static void true_residual(Solver* w, const Structure& s, const System& y, const double* x, double* out,
                           cudaStream_t st) {
-    const int G = w->nparts;
     if (y.S) {
-        k_true_residual<<<G, kThreads, 0, st>>>(s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, w->part_c);
+        k_true_residual<<<grid_for_host(int64_t(s.n_c) * 32), kThreads, 0, st>>>(
+            s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, ptr<double>(w->part_cam));
         w->launches += 1;
-        k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_c, G);
     } else {
-        launch_implicit_residual(s, y, x, out, w->part_cam, st);
+        launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
         w->launches += 2;
-        k_true_reduce<<<1, 32, 0, st>>>(w->ctl, w->part_cam, s.n_c);
     }
+    k_true_reduce<<<w->nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<double>(w->part_cam));
     w->launches += 1;
 }
 
-static int grid_for_host(int64_t n) {
-    int64_t g = (n + kThreads - 1) / kThreads;
-    int cap = num_sms() * 8;
-    return int(g < 1 ? 1 : (g > cap ? cap : g));
+// Append rows [0, its) of the iteration-major device history to each problem's host history,
+// problem b's values multiplied by scale[b] (rows past a problem's own count are ignored).
+static void collect_history(Solver* w, const std::vector<int>& its, const std::vector<double>& scale, cudaStream_t st) {
+    const int nb = w->nb;
+    int rows = 0;
+    for (int v : its) rows = std::max(rows, v);
+    if (rows == 0) return;
+    w->rows.resize(size_t(rows) * nb);
+    BA_CUDA_TRY(cudaMemcpyAsync(w->rows.data(), w->hist.p, sizeof(double) * w->rows.size(), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < its[b]; ++i) w->host_hist[b].push_back(w->rows[size_t(i) * nb + b] * scale[b]);
 }
 
 void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x, SolveOut& out,
@@ -1675,109 +1963,112 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     int n_dirs = a.mcg ? a.n_dirs : 1;
     if (n_dirs < 1) n_dirs = 1;
     if (n_dirs > kMaxDirs) throw Error(BA_ERR_INVALID_ARG, "n_dirs must be in [1, 16]");
-    const int sz = (s.n_c + n_dirs - 1) / n_dirs;
-    const int n_eff = (s.n_c + sz - 1) / sz;
-    const int K = (sz + kChunkCams - 1) / kChunkCams;
-    int64_t cap = 1;
-    if (a.mcg) {
-        cap = a.max_history > 0 ? a.max_history : int64_t(a.max_iters) * n_eff + 1;
-        if (cap < 1 + n_eff) cap = 1 + n_eff;
-        if (cap > (int64_t(1) << 30)) throw Error(BA_ERR_INVALID_ARG, "direction history too large");
-    } else {
-        cap = 1;
-    }
     const bool fp32 = a.precision == BA_PRECISION_MIXED;
-    ensure_ws(w, n, cap, a.max_iters, cap * n_eff * K, fp32 ? 4 : 8);
-    ensure_items(w, s, a.mcg ? n_dirs : 1, sz, n_eff);
+    prepare(w, s, a, n_dirs, fp32);
+    const int nb = w->nb;
     w->launches = 0;
+    w->host_hist.assign(nb, std::vector<double>());
 
     cudaEvent_t e0, e1;
     BA_CUDA_TRY(cudaEventCreate(&e0));
     BA_CUDA_TRY(cudaEventCreate(&e1));
     BA_CUDA_TRY(cudaEventRecord(e0, st));
     out = SolveOut();
-    out.n_eff = n_eff;
-    Ctl fin;
-    const int G = w->nparts;
+    out.probs.assign(nb, ProbOut());
     if (!fp32) {
-        krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, a, n_eff, sz, K, cap, &fin, st);
-        out.status = fin.status;
-        out.iters = fin.it;
-        out.local_steps = fin.local_steps;
-        out.history_cols = a.mcg ? fin.cols : 1;
-        out.rel_residual = fin.rr0 > 0 ? std::sqrt(fin.rr / fin.rr0) : 0.0;
-        out.refinements = 1;
-        w->host_hist.resize(fin.it);
-        if (fin.it > 0)
-            BA_CUDA_TRY(cudaMemcpyAsync(w->host_hist.data(), w->hist, sizeof(double) * fin.it,
-                                        cudaMemcpyDeviceToHost, st));
+        krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, a, nullptr, st);
+        std::vector<int> its(nb);
+        for (int b = 0; b < nb; ++b) its[b] = w->h_ctl[b].it;
+        collect_history(w, its, std::vector<double>(nb, 1.0), st);
+        std::vector<Ctl> fin(w->h_ctl, w->h_ctl + nb);
         // true relative residual in float64
         true_residual(w, s, y, x, nullptr, st);
-    } else {
-        // float64 iterative refinement around float32 Krylov sweeps
-        // x = 0, so the true residual is -b~ itself: rt = -b~, |rt|^2 = |b~|^2
-        k_start_refine<<<grid_for_host(n), kThreads, 0, st>>>(n, y.bt, x, w->rt);
-        w->launches += 1;
-        k_norm2<<<1, kThreads, 0, st>>>(n, y.bt, w->ctl);
-        w->launches += 1;
-        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
         BA_CUDA_TRY(cudaStreamSynchronize(st));
-        const double bb = w->h_ctl->bb;
-        double tr = bb;
-        SolveArgs inner = a;
-        inner.tol = a.inner_tol;
-        int total = 0, locals = 0;
-        int status = BA_ERR_NOT_CONVERGED;
-        w->host_hist.clear();
-        int sweeps = 0;
-        if (bb == 0.0) status = BA_OK;
-        while (status != BA_OK && sweeps < a.max_refine && total < a.max_iters) {
-            inner.max_iters = a.max_iters - total;
-            // per sweep the inner solve reduces its residual by inner_tol; when what is left to reach
-            // tol is within ten times that, the sweep aims 3x past it so that it is the last one
-            const double need = a.tol * std::sqrt(bb) / std::sqrt(tr);
-            inner.tol = need > 0.1 * a.inner_tol ? std::max(0.3 * need, 0.1 * a.inner_tol) : a.inner_tol;
-            if (inner.tol >= 1.0) inner.tol = 0.5;
-            krylov<float>(w, s, y.S32, y.Dhat, w->rt, 1.0, y.lam, static_cast<float*>(w->xw), inner, n_eff, sz, K,
-                          cap, &fin, st);
-            ++sweeps;
-            total += fin.it;
-            locals += fin.local_steps;
-            out.history_cols = a.mcg ? fin.cols : 1;
-            std::vector<double> h(fin.it);
-            if (fin.it > 0)
-                BA_CUDA_TRY(cudaMemcpyAsync(h.data(), w->hist, sizeof(double) * fin.it, cudaMemcpyDeviceToHost, st));
-            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, static_cast<const float*>(w->xw), y.lam, x);
-            true_residual(w, s, y, x, w->rt, st);
-            w->launches += 1;
-            BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-            BA_CUDA_TRY(cudaStreamSynchronize(st));
-            const double prev = tr;
-            tr = w->h_ctl->true_rr;
-            // history in units of the outer |b~|: inner relative residuals scaled by the sweep's start
-            for (double v : h) w->host_hist.push_back(v * std::sqrt(prev / bb));
-            if (fin.status == BA_ERR_BREAKDOWN || fin.status == BA_ERR_OOM) { status = fin.status; break; }
-            if (tr <= a.tol * a.tol * bb) status = BA_OK;
-            if (!(tr == tr)) { status = BA_ERR_BREAKDOWN; break; }
+        for (int b = 0; b < nb; ++b) {
+            ProbOut& o = out.probs[b];
+            const Ctl& c = fin[b];
+            o.status = c.status;
+            o.iters = c.it;
+            o.local_steps = c.local_steps;
+            o.n_eff = w->lay[b].n_eff;
+            o.history_cols = a.mcg ? c.cols : 1;
+            o.rel_residual = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
+            o.refinements = 1;
+            o.true_rel_residual = w->h_ctl[b].bb > 0 ? std::sqrt(w->h_ctl[b].true_rr / w->h_ctl[b].bb) : 0.0;
         }
-        out.status = status;
-        out.iters = total;
-        out.local_steps = locals;
-        out.refinements = sweeps;
-        out.rel_residual = std::sqrt(tr / bb);
-        // the last sweep's float64 true residual is the result's (ctl holds it)
+    } else {
+        // float64 iterative refinement around float32 Krylov sweeps; x = 0, so the true residual
+        // starts as -b~ itself
+        k_start_refine<<<grid_for_host(n), kThreads, 0, st>>>(n, y.bt, x, ptr<double>(w->rt));
+        k_outer_init<<<nb, kThreads, 0, st>>>(ptr<Layout>(w->lay_d), y.bt, ptr<Outer>(w->outer));
+        w->launches += 2;
+        SolveArgs inner = a;
+        for (int sweep = 0; sweep < a.max_refine; ++sweep) {
+            k_refine_plan<<<nb, 32, 0, st>>>(ptr<Outer>(w->outer), a.tol, a.inner_tol, a.max_iters, a.max_refine);
+            BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
+            BA_CUDA_TRY(cudaStreamSynchronize(st));
+            w->launches += 1;
+            bool any = false;
+            for (int b = 0; b < nb && !any; ++b) any = w->h_outer[b].swept != 0;
+            if (!any) break;
+            // history of this sweep in units of the outer |b~|: scaled by the sweep's start residual
+            std::vector<double> scale(nb, 0.0);
+            for (int b = 0; b < nb; ++b)
+                if (w->h_outer[b].swept) scale[b] = std::sqrt(w->h_outer[b].tr / w->h_outer[b].bb);
+            int budget = 0;
+            for (int b = 0; b < nb; ++b)
+                if (w->h_outer[b].swept) budget = std::max(budget, w->h_outer[b].max_in);
+            inner.max_iters = budget;   // host loop bound; each problem stops at its own budget
+            krylov<float>(w, s, y.S32, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw), inner,
+                          ptr<Outer>(w->outer), st);
+            std::vector<int> its(nb, 0);
+            for (int b = 0; b < nb; ++b) its[b] = w->h_outer[b].swept ? w->h_ctl[b].it : 0;
+            collect_history(w, its, scale, st);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x);
+            true_residual(w, s, y, x, ptr<double>(w->rt), st);
+            k_refine_after<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), a.tol, a.mcg);
+            w->launches += 2;
+        }
+        BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
+        BA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b = 0; b < nb; ++b) {
+            ProbOut& o = out.probs[b];
+            const Outer& u = w->h_outer[b];
+            o.status = u.status;
+            o.iters = u.iters;
+            o.local_steps = u.locals;
+            o.n_eff = w->lay[b].n_eff;
+            o.history_cols = u.cols;
+            o.refinements = u.sweeps;
+            // tr is the float64 true residual of the problem's current x
+            o.rel_residual = u.bb > 0 ? std::sqrt(u.tr / u.bb) : 0.0;
+            o.true_rel_residual = o.rel_residual;
+        }
     }
     out.launches = w->launches;
     BA_CUDA_TRY(cudaEventRecord(e1, st));
-    BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    BA_CUDA_TRY(cudaStreamSynchronize(st));
+    BA_CUDA_TRY(cudaEventSynchronize(e1));
     BA_CUDA_TRY(cudaGetLastError());
-    out.true_rel_residual = w->h_ctl->bb > 0 ? std::sqrt(w->h_ctl->true_rr / w->h_ctl->bb) : 0.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     out.ms = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // the batch's summary: the first failing problem's status, the largest counts and residuals
+    out.status = BA_OK;
+    out.n_eff = 1;
+    for (int b = 0; b < nb; ++b) {
+        const ProbOut& o = out.probs[b];
+        if (out.status == BA_OK && o.status != BA_OK) out.status = o.status;
+        out.iters = std::max(out.iters, o.iters);
+        out.local_steps = std::max(out.local_steps, o.local_steps);
+        out.n_eff = std::max(out.n_eff, o.n_eff);
+        out.refinements = std::max(out.refinements, o.refinements);
+        out.history_cols = std::max(out.history_cols, o.history_cols);
+        out.rel_residual = std::max(out.rel_residual, o.rel_residual);
+        out.true_rel_residual = std::max(out.true_rel_residual, o.true_rel_residual);
+    }
 }
 
 void flush_l2(cudaStream_t st) {
@@ -1787,43 +2078,64 @@ void flush_l2(cudaStream_t st) {
     BA_CUDA_TRY(cudaMemsetAsync(buf, 0, bytes, st));
 }
 
-double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, cudaStream_t st) {
-    const int64_t n = int64_t(s.n_c) * 9;
-    ensure_ws(w, n, w->cap > 0 ? w->cap : 1, w->max_iters > 0 ? w->max_iters : 1,
-              w->phip_len > 0 ? w->phip_len : 1, fp32 ? 4 : 8);
-    BA_CUDA_TRY(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
-    const int G = w->nparts;
-    if (fp32) {
-        k_to_float_vec<<<G, kThreads, 0, st>>>(n, y.bt, static_cast<float*>(w->P));
-    } else {
-        BA_CUDA_TRY(cudaMemcpyAsync(w->P, y.bt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    }
-    BA_CUDA_TRY(cudaMemcpyAsync(w->r, w->P, size_t(n) * (fp32 ? 4 : 8), cudaMemcpyDeviceToDevice, st));
-    cudaEvent_t a, b;
-    BA_CUDA_TRY(cudaEventCreate(&a));
-    BA_CUDA_TRY(cudaEventCreate(&b));
+// The PCG product q = S p of every problem (k_spmv MODE 1, the kernel of Algorithm 1, line 3),
+// set up as at the start of a PCG solve (p = D^{-1} b~).
+double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int item_blocks,
+                        cudaStream_t st) {
+    SolveArgs a;
+    a.mcg = 0;
+    a.max_iters = 1;
+    a.item_blocks = item_blocks;
+    a.precision = fp32 ? BA_PRECISION_MIXED : BA_PRECISION_FP64;
+    prepare(w, s, a, 1, fp32);
+    if (fp32)
+        krylov_init<float>(w, s, y.S32, y.Dhat, y.bt, -1.0, y.lam, ptr<float>(w->xw), a, nullptr, st);
+    else
+        krylov_init<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, ptr<double>(w->xw), a, nullptr, st);
+    cudaEvent_t e0, e1;
+    BA_CUDA_TRY(cudaEventCreate(&e0));
+    BA_CUDA_TRY(cudaEventCreate(&e1));
     double total = 0.0;
-    ensure_items(w, s, 1, s.n_c, 1);
     for (int k = 0; k < reps; ++k) {
         flush_l2(st);
-        BA_CUDA_TRY(cudaEventRecord(a, st));
+        BA_CUDA_TRY(cudaEventRecord(e0, st));
         if (fp32)
-            k_spmv<float, 1><<<num_sms(), SpmvCfg<float>::kWarps * 32, spmv_smem<float>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, y.S32, static_cast<float*>(w->P), w->items_g, w->items_g,
-                static_cast<float*>(w->Q), n, static_cast<float*>(w->r), w->dpart, w->dcnt, w->totals, w->ctl, 1);
+            k_spmv<float, 1, true><<<num_sms(), SpmvCfg<float>::kWarps * 32, spmv_smem<float>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, y.S32, ptr<float>(w->P), w->items_g, kSelLive, ptr<float>(w->Q),
+                ptr<float>(w->r), ptr<double>(w->camdot), ptr<Ctl>(w->ctl));
         else
-            k_spmv<double, 1><<<num_sms(), SpmvCfg<double>::kWarps * 32, spmv_smem<double>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, y.S, static_cast<double*>(w->P), w->items_g, w->items_g,
-                static_cast<double*>(w->Q), n, static_cast<double*>(w->r), w->dpart, w->dcnt, w->totals, w->ctl, 1);
-        BA_CUDA_TRY(cudaEventRecord(b, st));
-        BA_CUDA_TRY(cudaEventSynchronize(b));
+            k_spmv<double, 1, true><<<num_sms(), SpmvCfg<double>::kWarps * 32, spmv_smem<double>(), st>>>(
+                s.row_ptr, s.tile_ptr, s.col, y.S, ptr<double>(w->P), w->items_g, kSelLive, ptr<double>(w->Q),
+                ptr<double>(w->r), ptr<double>(w->camdot), ptr<Ctl>(w->ctl));
+        BA_CUDA_TRY(cudaEventRecord(e1, st));
+        BA_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
-        BA_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        BA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         total += ms;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return total / reps;
+}
+
+// Item chunk chosen by timing the PCG product: candidates cb = 32 .. 1024 blocks per work item,
+// `reps` launches each; ties keep the smaller chunk.  The lists are left built for the winner.
+int solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, double* best_ms,
+                    cudaStream_t st, std::vector<std::pair<int, double>>* trace) {
+    const int cands[] = {32, 64, 128, 256, 512, 1024};
+    int best = 0;
+    double bms = 0.0;
+    for (int cb : cands) {
+        const double ms = solver_time_spmv(w, s, y, fp32, reps, cb, st);
+        if (trace) trace->push_back({cb, ms});
+        if (best == 0 || ms < bms) {
+            best = cb;
+            bms = ms;
+        }
+    }
+    solver_time_spmv(w, s, y, fp32, 1, best, st);
+    if (best_ms) *best_ms = bms;
+    return best;
 }
 
 }  // namespace ba

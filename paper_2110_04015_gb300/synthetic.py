@@ -353,6 +353,7 @@ def batched(seed: int = 0, n_problems: int = 64, cams_lo: int = 50, cams_hi: int
             scale: float = 1.0) -> list[Scene]:
     """Independent uneven problems (sphere geometry, clustered long tracks, mean 8).
 
+    Tracks are capped at half the problem's cameras so that distinct cameras can always be drawn.
     ``scale`` shrinks the landmark count for quick tests.
     """
     s = Stream(seed, "batched/sizes")
@@ -363,7 +364,7 @@ def batched(seed: int = 0, n_problems: int = 64, cams_lo: int = 50, cams_hi: int
         n_l = max(8, int(pts_per_cam * n_c * scale))
         n_cl = max(1, n_c // 30)
         sc = dense(seed=seed * 1000 + b, n_cams=n_c, n_pts=n_l, n_clusters=n_cl,
-                   track_extra_mean=track_extra_mean, p_uniform=p_uniform)
+                   track_extra_mean=track_extra_mean, track_cap=min(200, n_c // 2), p_uniform=p_uniform)
         sc.name = f"batched[{b}]"
         out.append(sc)
     return out

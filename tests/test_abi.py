@@ -49,3 +49,16 @@ def test_default_options_and_errors_without_device(libba):
     assert code == binding.BA_ERR_INVALID_ARG
     assert b"n_cams" in L.ba_last_error(None)
     assert L.ba_project(0, 1, 1, None, None, None, None, None, None) == binding.BA_ERR_INVALID_ARG
+
+
+def test_batch_create_argument_errors_without_device(libba):
+    L = binding.lib()
+    out = ctypes.c_void_p()
+    # n_problems out of range and a missing offsets array are rejected before any device work
+    code = L.ba_batch_create(None, 0, None, 4, 4, 4, None, None, None, None, None, ctypes.byref(out))
+    assert code == binding.BA_ERR_INVALID_ARG
+    code = L.ba_batch_create(None, 2, None, 4, 4, 4, None, None, None, None, None, ctypes.byref(out))
+    assert code == binding.BA_ERR_INVALID_ARG
+    assert b"cam_off" in L.ba_last_error(None)
+    for name in ["ba_get_batch_size", "ba_get_batch_stats", "ba_get_batch_history", "ba_autotune"]:
+        assert getattr(L, name)(None, *([0] * (len(binding._SIGNATURES[name][1]) - 1))) == binding.BA_ERR_INVALID_ARG
