@@ -79,9 +79,9 @@ typedef struct ba_options {
     int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1) */
     double inner_tol;          /* MIXED: relative residual reduction of one inner solve (default 1e-3) */
     int32_t max_refine;        /* MIXED: maximum outer refinement sweeps (default 12) */
-    int32_t item_blocks;       /* stored 9x9 blocks of S per work item of the block-sparse products:
-                                  0 (default) = a per-problem rule (about 64 items per SM, 32..256),
-                                  else a multiple of 32 in [32, 4096]; ba_autotune sets it */
+    int32_t item_blocks;       /* stored 9x9 blocks of S per work item of the block-sparse products
+                                  (longer rows are split): 0 (default) = 512, else a multiple of 32
+                                  in [32, 4096]; ba_autotune sets it */
     int32_t reserved[6];
 } ba_options;
 

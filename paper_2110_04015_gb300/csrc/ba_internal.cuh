@@ -164,7 +164,7 @@ struct SolveArgs {
     double inner_tol = 1e-3;
     int max_refine = 12;
     int64_t max_history = 0;
-    int item_blocks = 0;    // blocks per work item of the block-sparse products (0: per-problem heuristic)
+    int item_blocks = 0;    // blocks per work item of the block-sparse products (0: 512)
 };
 
 struct ProbOut {
