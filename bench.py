@@ -65,6 +65,11 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="batch mode: 64 uneven problems (50-600 cameras, 300 landmarks per camera, tracks mean 8) "
                          "solved by MCG in the same launches, against looping single-problem solves; one JSON line")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-grouping mode: train the grouping network on normal equations harvested from LM "
+                         "iterations of shuffled synthetic problems, then MCG with and without it on held-out seeds")
+    ap.add_argument("--learn-problems", type=int, default=100,
+                    help="training problems per family (each gives 10 normal equations)")
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="landmarks per camera x this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -568,8 +573,73 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(a):
+    """Learned pose grouping: training cost, then MCG iterations and time with and without it.
+
+    Training: one Adam step per normal equation of 10 LM iterations of each of ``--learn-problems``
+    shuffled problems per family (sequential and clustered dense, 80-240 cameras).  Evaluation on
+    held-out seeds (1000+): MCG (N = 16, tau = 10) on the problem in its given random camera order,
+    against MCG on the problem renumbered in the network's order (float32 and bfloat16 inference);
+    the time with the network includes its inference on the built system.
+    """
+    import torch
+
+    from paper_2110_04015_gb300 import binding, learn, problem
+
+    g = binding.GNN(learn.init_params(0))
+    t0 = time.perf_counter()
+    l0 = g.ba_gnn_launch_count()
+    losses = learn.harvest_train(g, seeds=range(a.learn_problems), kinds=("sequential", "dense"), lm_steps=10,
+                                 lr=3e-3, precision=a.precision)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    train_launches = g.ba_gnn_launch_count() - l0
+    evals = []
+    for kind, seed, n in [("sequential", 1000, 1000), ("sequential", 1001, 400), ("dense", 1002, 600)]:
+        if kind == "sequential":
+            sc = synthetic.sequential(seed, n_cams=n, n_pts=100 * n)
+        else:
+            sc = synthetic.dense(seed, n_cams=n, n_pts=300 * n, n_clusters=n // 30)
+        sc = synthetic.shuffled(sc, seed)
+        p = problem.from_scene(sc, precision=a.precision)
+        p.ba_build_normal(LAMBDA)
+        base = min((p.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau) for _ in range(2)), key=lambda s: s["ms"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        row = {"workload": f"{kind}-{n} shuffled", "seed": seed, "n_cams": n,
+               "without": {k: base[k] for k in ("iters", "local_steps", "ms", "true_rel_residual")}}
+        for bf16 in (False, True):
+            e0.record()
+            order, L = g.ba_gnn_order(p, bf16=bf16)
+            e1.record()
+            e1.synchronize()
+            t_inf = e0.elapsed_time(e1)
+            q = problem.from_scene(synthetic.permute_cameras(sc, order), precision=a.precision)
+            q.ba_build_normal(LAMBDA)
+            st = min((q.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau) for _ in range(2)), key=lambda s: s["ms"])
+            q.close()
+            row["bf16" if bf16 else "fp32"] = {"iters": st["iters"], "local_steps": st["local_steps"], "ms": st["ms"],
+                                               "inference_ms": t_inf, "loss": L,
+                                               "true_rel_residual": st["true_rel_residual"],
+                                               "iters_ratio": st["iters"] / base["iters"],
+                                               "time_ratio": (st["ms"] + t_inf) / base["ms"]}
+        p.close()
+        evals.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    line = {"mode": "learned", "metric": "MCG time to rel. residual 1e-6 with the learned grouping / without",
+            "value": float(np.mean([r["fp32"]["time_ratio"] for r in evals])), "unit": "ratio",
+            "higher_is_better": False, "precision": a.precision, "mcg": {"n_dirs": a.n_dirs, "tau": a.tau},
+            "training": {"normal_equations": len(losses), "seconds": t_train, "gpu_launches": int(train_launches),
+                         "loss_first_50": float(np.mean(losses[:50])), "loss_last_50": float(np.mean(losses[-50:]))},
+            "eval": evals}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.learned:
+        run_learned(a)
+        return
     if a.batched:
         run_batched(a)
         return

@@ -305,6 +305,55 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
  */
 int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms);
 
+/* ---- learned pose grouping for MCG ------------------------------------------------------
+ *
+ * Algorithm 2 splits the poses into N subsets of consecutive poses (Section 3.2; the paper
+ * notes that the best decomposition is not obvious).  A small message-passing network over the
+ * camera co-visibility graph of S scores every camera; sorting the cameras by score gives a camera
+ * order whose consecutive runs are the subsets (create the problem with its cameras in that order;
+ * any order is valid for MCG).  The paper has no learned component: the network is this library's.
+ *
+ *   graph      c_jk = |Lam_j S_jk Lam_k|_F for each stored block j != k (Lam = diag(S)^-1/2),
+ *              d_j = sum_k c_jk
+ *   features   8 per camera: its centre -R^T t standardised per axis, its viewing axis (third row
+ *              of R), log(1 + d_j) standardised, and 1
+ *   layers     3 x  H' = relu(H Ws + (D^-1 C H) Wn + b), widths 8 -> 64 -> 64 -> 64
+ *   read-out   s = H wo + bo
+ *   loss       L = u^T (D - C) u / u^T D u with u = s - (d^T s / sum d): the Rayleigh quotient of
+ *              the coupling Laplacian, small when strongly coupled cameras get close scores
+ *   training   Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on dL/dtheta
+ * Parameters (float32, in this order): for each layer Ws (in x 64, row-major), Wn (in x 64),
+ * b (64); then wo (64), bo (1); ba_gnn_param_count gives the total.  The network is trained in
+ * float32; inference may round weights and activations to bfloat16 (float32 accumulation).
+ * Every call that takes a ba_problem needs ba_build_normal, a single-problem handle and at most
+ * 65536 cameras (INVALID_ARG / STATE otherwise), and runs on the problem's stream.
+ */
+typedef struct ba_gnn ba_gnn;
+
+/* A network with zero parameters (set them with ba_gnn_set_params).  OOM, CUDA. */
+int ba_gnn_create(ba_gnn** out);
+void ba_gnn_destroy(ba_gnn* g);
+const char* ba_gnn_last_error(const ba_gnn* g);
+int ba_gnn_param_count(int64_t* n);
+/* Copy all parameters in (host or device, float32) and reset the Adam state. */
+int ba_gnn_set_params(ba_gnn* g, const float* params);
+int ba_gnn_get_params(const ba_gnn* g, float* params);
+/* The graph of p's built system: features (n_cams x 8) and coupling weights c (nnzb, in the
+ * block order of ba_get_schur, 0 on the diagonal); host or device; NULL skips. */
+int ba_gnn_graph(ba_gnn* g, ba_problem* p, float* features, float* coupling);
+/* Forward pass on p's built system: *loss (may be NULL), scores (n_cams, may be NULL) and, when
+ * grad != NULL, the backward pass: dL/dtheta (param_count floats).  Host or device pointers. */
+int ba_gnn_loss(ba_gnn* g, ba_problem* p, double* loss, float* scores, float* grad);
+/* One training step on p's built system: forward, backward and an Adam update with learning rate
+ * lr; *loss receives the loss before the update. */
+int ba_gnn_train_step(ba_gnn* g, ba_problem* p, double lr, double* loss);
+/* The grouping order: order[r] = the camera of rank r by score (ties by index), host or device,
+ * n_cams int32; bf16 != 0 runs the forward pass with bfloat16 weights and activations; *loss (may
+ * be NULL) receives the loss of the scores. */
+int ba_gnn_order(ba_gnn* g, ba_problem* p, int32_t bf16, int32_t* order, double* loss);
+/* Kernel executions issued by this network so far. */
+int ba_gnn_launch_count(const ba_gnn* g, int64_t* n);
+
 /* ---- allocation-free residual check ---------------------------------------------------- */
 
 /* Largest n_cams accepted by ba_schur_residual_static. */

@@ -93,6 +93,17 @@ _SIGNATURES = {
     "ba_get_launch_count": (_I32, [_P, _P]),
     "ba_time_kernel": (_I32, [_P, _I32, _I32, _P]),
     "ba_schur_residual_static": (_I32, [_I32, _P, _P, _P, _P, _P, _P, _P]),
+    "ba_gnn_create": (_I32, [_P]),
+    "ba_gnn_destroy": (None, [_P]),
+    "ba_gnn_last_error": (ctypes.c_char_p, [_P]),
+    "ba_gnn_param_count": (_I32, [_P]),
+    "ba_gnn_set_params": (_I32, [_P, _P]),
+    "ba_gnn_get_params": (_I32, [_P, _P]),
+    "ba_gnn_graph": (_I32, [_P, _P, _P, _P]),
+    "ba_gnn_loss": (_I32, [_P, _P, _P, _P, _P]),
+    "ba_gnn_train_step": (_I32, [_P, _P, _D, _P]),
+    "ba_gnn_order": (_I32, [_P, _P, _I32, _P, _P]),
+    "ba_gnn_launch_count": (_I32, [_P, _P]),
 }
 BA_STATIC_MAX_CAMS = 65536
 KERNEL = {"spmv": 0, "schur": 1, "linearize": 2}
@@ -363,3 +374,74 @@ class Problem:
     get_delta = ba_get_delta
     lm_step = ba_lm_step
     cost = ba_cost
+
+
+def _gcheck(code: int, g) -> None:
+    if code != BA_OK:
+        raise BAError(code, lib().ba_gnn_last_error(g).decode())
+
+
+class GNN:
+    """The pose-grouping network held by the library (a ``ba_gnn`` handle)."""
+
+    def __init__(self, params=None):
+        L = lib()
+        h = ctypes.c_void_p()
+        code = L.ba_gnn_create(ctypes.byref(h))
+        if code != BA_OK:
+            raise BAError(code, L.ba_last_error(None).decode())
+        self.h = h
+        n = ctypes.c_int64()
+        _check(L.ba_gnn_param_count(ctypes.byref(n)))
+        self.n_params = n.value
+        if params is not None:
+            self.ba_gnn_set_params(params)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_gnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ba_gnn_set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32) if isinstance(params, np.ndarray) else params
+        _gcheck(lib().ba_gnn_set_params(self.h, _ptr(params)), self.h)
+
+    def ba_gnn_get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        _gcheck(lib().ba_gnn_get_params(self.h, _ptr(out)), self.h)
+        return out
+
+    def ba_gnn_graph(self, p: "Problem"):
+        X = np.empty((p.n_cams, 8), np.float32)
+        c = np.empty(p.ba_get_schur_nnzb(), np.float32)
+        _gcheck(lib().ba_gnn_graph(self.h, p.h, _ptr(X), _ptr(c)), self.h)
+        return X, c
+
+    def ba_gnn_loss(self, p: "Problem", grad=False):
+        loss = ctypes.c_double()
+        s = np.empty(p.n_cams, np.float32)
+        g = np.empty(self.n_params, np.float32) if grad else None
+        _gcheck(lib().ba_gnn_loss(self.h, p.h, ctypes.byref(loss), _ptr(s), _ptr(g)), self.h)
+        return (loss.value, s, g) if grad else (loss.value, s)
+
+    def ba_gnn_train_step(self, p: "Problem", lr=1e-3) -> float:
+        loss = ctypes.c_double()
+        _gcheck(lib().ba_gnn_train_step(self.h, p.h, float(lr), ctypes.byref(loss)), self.h)
+        return loss.value
+
+    def ba_gnn_order(self, p: "Problem", bf16=False):
+        order = np.empty(p.n_cams, np.int32)
+        loss = ctypes.c_double()
+        _gcheck(lib().ba_gnn_order(self.h, p.h, int(bool(bf16)), _ptr(order), ctypes.byref(loss)), self.h)
+        return order, loss.value
+
+    def ba_gnn_launch_count(self) -> int:
+        n = ctypes.c_int64()
+        _gcheck(lib().ba_gnn_launch_count(self.h, ctypes.byref(n)), self.h)
+        return n.value

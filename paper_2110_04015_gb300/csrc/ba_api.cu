@@ -852,6 +852,122 @@ int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms) {
     }
 }
 
+}  // extern "C"
+
+struct ba_gnn {
+    ba::Gnn* g = nullptr;
+    std::string err;
+};
+
+namespace {
+int gnn_fail(ba_gnn* g, const Error& e) {
+    if (g) g->err = e.msg;
+    return e.code;
+}
+}  // namespace
+
+extern "C" {
+
+int ba_gnn_create(ba_gnn** out) {
+    if (!out) return BA_ERR_INVALID_ARG;
+    *out = nullptr;
+    ba_gnn* g = new ba_gnn();
+    try {
+        g->g = ba::gnn_create();
+        *out = g;
+        return BA_OK;
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        delete g;
+        return e.code;
+    }
+}
+
+void ba_gnn_destroy(ba_gnn* g) {
+    if (!g) return;
+    ba::gnn_destroy(g->g);
+    delete g;
+}
+
+const char* ba_gnn_last_error(const ba_gnn* g) { return g ? g->err.c_str() : ""; }
+
+int ba_gnn_param_count(int64_t* n) {
+    if (!n) return BA_ERR_INVALID_ARG;
+    *n = ba::gnn_param_count();
+    return BA_OK;
+}
+
+int ba_gnn_set_params(ba_gnn* g, const float* params) {
+    if (!g || !params) return BA_ERR_INVALID_ARG;
+    try {
+        ba::gnn_set_params(g->g, params, nullptr);
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_get_params(const ba_gnn* gc, float* params) {
+    ba_gnn* g = const_cast<ba_gnn*>(gc);
+    if (!g || !params) return BA_ERR_INVALID_ARG;
+    try {
+        ba::gnn_get_params(g->g, params, nullptr);
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_graph(ba_gnn* g, ba_problem* p, float* features, float* coupling) {
+    if (!g || !p) return BA_ERR_INVALID_ARG;
+    try {
+        ba::gnn_graph_out(g->g, p->s, p->y, features, coupling, p->stream);
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_loss(ba_gnn* g, ba_problem* p, double* loss, float* scores, float* grad) {
+    if (!g || !p) return BA_ERR_INVALID_ARG;
+    try {
+        const double L = ba::gnn_loss(g->g, p->s, p->y, grad != nullptr, scores, grad, p->stream);
+        if (loss) *loss = L;
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_train_step(ba_gnn* g, ba_problem* p, double lr, double* loss) {
+    if (!g || !p) return BA_ERR_INVALID_ARG;
+    try {
+        if (!(lr > 0.0) || !std::isfinite(lr)) throw Error(BA_ERR_INVALID_ARG, "lr must be positive");
+        const double L = ba::gnn_train_step(g->g, p->s, p->y, lr, p->stream);
+        if (loss) *loss = L;
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_order(ba_gnn* g, ba_problem* p, int32_t bf16, int32_t* order, double* loss) {
+    if (!g || !p || !order) return BA_ERR_INVALID_ARG;
+    try {
+        const double L = ba::gnn_order(g->g, p->s, p->y, bf16 != 0, order, p->stream);
+        if (loss) *loss = L;
+        return BA_OK;
+    } catch (const Error& e) {
+        return gnn_fail(g, e);
+    }
+}
+
+int ba_gnn_launch_count(const ba_gnn* g, int64_t* n) {
+    if (!g || !n) return BA_ERR_INVALID_ARG;
+    *n = ba::gnn_launches(g->g);
+    return BA_OK;
+}
+
 int ba_get_launch_count(const ba_problem* p, int64_t* n) {
     if (!p || !n) return BA_ERR_INVALID_ARG;
     *n = p->launches;

@@ -210,6 +210,24 @@ int solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, i
                     cudaStream_t st, std::vector<std::pair<int, double>>* trace);
 void flush_l2(cudaStream_t st);
 
+// ---- learned pose grouping (k_learn.cu) -------------------------------------------------------
+struct Gnn;
+int64_t gnn_param_count();
+Gnn* gnn_create();
+void gnn_destroy(Gnn* g);
+void gnn_set_params(Gnn* g, const float* params, cudaStream_t st);   // resets the Adam state
+void gnn_get_params(const Gnn* g, float* params, cudaStream_t st);
+int64_t gnn_launches(const Gnn* g);
+// features (n_c x 8) and coupling weights (nnzb, CSR order) of the built system
+void gnn_graph_out(Gnn* g, const Structure& s, const System& y, float* X, float* c, cudaStream_t st);
+// loss of the built system; scores (n_c) and the gradient copied out when non-null
+double gnn_loss(Gnn* g, const Structure& s, const System& y, bool with_grad, float* scores, float* grad,
+                cudaStream_t st);
+// loss, gradient and one Adam step (returns the loss before the step)
+double gnn_train_step(Gnn* g, const Structure& s, const System& y, double lr, cudaStream_t st);
+// camera order by score (ties by index); returns the loss of the scores
+double gnn_order(Gnn* g, const Structure& s, const System& y, bool bf16, int32_t* order, cudaStream_t st);
+
 int num_sms();
 // error text of handle-less calls on this thread (read back by ba_last_error(NULL))
 void set_thread_error(const std::string& msg);

@@ -370,6 +370,26 @@ def batched(seed: int = 0, n_problems: int = 64, cams_lo: int = 50, cams_hi: int
     return out
 
 
+def permute_cameras(sc: Scene, order: np.ndarray) -> Scene:
+    """The same scene with its cameras renumbered: new camera i is old camera order[i].
+
+    Observations keep their measurements and noise (the rows are only relabelled), so the problem
+    is the same one in another camera order.
+    """
+    order = np.asarray(order, dtype=np.int64)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size)
+    return Scene(sc.name, sc.seed, sc.cams_true[order], sc.pts_true, inv[sc.obs_cam].astype(np.int32),
+                 sc.obs_pt, sc.noise, sc.cams0[order], sc.pts0, dict(sc.meta, camera_order="permuted"))
+
+
+def shuffled(sc: Scene, seed: int) -> Scene:
+    """The scene with its cameras in a seeded random order (as in collections whose camera
+    numbering carries no geometry)."""
+    s = Stream(seed, "shuffle")
+    return permute_cameras(sc, np.argsort(s.uniform(sc.n_cams), kind="stable"))
+
+
 CONFIGS = {
     "tiny": tiny,
     "sequential": sequential,

@@ -62,3 +62,14 @@ def test_batch_create_argument_errors_without_device(libba):
     assert b"cam_off" in L.ba_last_error(None)
     for name in ["ba_get_batch_size", "ba_get_batch_stats", "ba_get_batch_history", "ba_autotune"]:
         assert getattr(L, name)(None, *([0] * (len(binding._SIGNATURES[name][1]) - 1))) == binding.BA_ERR_INVALID_ARG
+
+
+def test_grouping_network_parameter_layout(libba):
+    # 3 layers of (Ws, Wn, b) with widths 8 -> 64 -> 64 -> 64, then wo (64) and bo (1)
+    from paper_2110_04015_gb300 import learn
+
+    n = ctypes.c_int64()
+    assert binding.lib().ba_gnn_param_count(ctypes.byref(n)) == binding.BA_OK
+    assert n.value == 2 * 8 * 64 + 64 + 2 * (2 * 64 * 64 + 64) + 64 + 1
+    assert n.value == sum(int(__import__("numpy").prod(s)) for _, s in learn.layer_shapes())
+    assert learn.init_params(0).size == n.value
