@@ -87,10 +87,10 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# DRAM bytes per stored 9x9 block of one k_spmv<float,1> launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of the 1000-camera case, 323.3 MB / 958,652 blocks;
+# DRAM bytes per stored 9x9 block of one k_spmv<float,1,true> launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture of the 1000-camera case, 319.8 MB / 958,652 blocks;
 # traffic grows with the stored blocks): profiles/k_spmv_f32_dense-1000cams.md
-SPMV_F32_TRAFFIC_PER_BLOCK = 337.3
+SPMV_F32_TRAFFIC_PER_BLOCK = 333.6
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
@@ -587,6 +587,20 @@ def run_learned(a):
     from paper_2110_04015_gb300 import binding, learn, problem
 
     g = binding.GNN(learn.init_params(0))
+
+    def held_out_loss():
+        out = {}
+        for kind in ("sequential", "dense"):
+            ls = []
+            for seed in (5000, 5001, 5002):
+                q = problem.from_scene(learn.training_scene(kind, seed), precision=a.precision)
+                q.ba_build_normal(LAMBDA)
+                ls.append(g.ba_gnn_loss(q)[0])
+                q.close()
+            out[kind] = float(np.mean(ls))
+        return out
+
+    loss_before = held_out_loss()
     t0 = time.perf_counter()
     l0 = g.ba_gnn_launch_count()
     losses = learn.harvest_train(g, seeds=range(a.learn_problems), kinds=("sequential", "dense"), lm_steps=10,
@@ -594,6 +608,7 @@ def run_learned(a):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     train_launches = g.ba_gnn_launch_count() - l0
+    loss_after = held_out_loss()
     evals = []
     for kind, seed, n in [("sequential", 1000, 1000), ("sequential", 1001, 400), ("dense", 1002, 600)]:
         if kind == "sequential":
@@ -630,7 +645,7 @@ def run_learned(a):
             "value": float(np.mean([r["fp32"]["time_ratio"] for r in evals])), "unit": "ratio",
             "higher_is_better": False, "precision": a.precision, "mcg": {"n_dirs": a.n_dirs, "tau": a.tau},
             "training": {"normal_equations": len(losses), "seconds": t_train, "gpu_launches": int(train_launches),
-                         "loss_first_50": float(np.mean(losses[:50])), "loss_last_50": float(np.mean(losses[-50:]))},
+                         "held_out_loss_before": loss_before, "held_out_loss_after": loss_after},
             "eval": evals}
     print(json.dumps(line), flush=True)
 

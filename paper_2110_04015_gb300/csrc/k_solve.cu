@@ -456,20 +456,13 @@ __device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
     v[2] = t.z;
     v[3] = t.w;
 }
-__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    const double2 b = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
     const T* __restrict__ S, const T* __restrict__ PT, ItemList L, T* __restrict__ part, T* __restrict__ Q,
     Ctl* ctl) {
+    static_assert(sizeof(T) == 4, "the multi-column product serves the float32 sweeps");
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
     constexpr int sel = kSelWide;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -515,7 +508,28 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
             for (int cc = 0; cc < 4; ++cc) acc[a][cc] = T(0);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
+            const bool active = 4 * g < w;
+            // column cameras of this lane's blocks r * 8 + qi (r = 0..3) of tile t, -1 outside the
+            // item; fetched one tile ahead, and the P rows of each block one block ahead, so the
+            // gathers overlap the arithmetic
+            int kc[4], kn[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int q = t0 * 32 + r * 8 + qi;
+                kc[r] = (active && q >= it.q0 && q < it.q1) ? col[rj + q] : -1;
+            }
             for (int t = t0; t < t1; ++t) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int q = (t + 1) * 32 + r * 8 + qi;
+                    kn[r] = (active && t + 1 < t1 && q < it.q1) ? col[rj + q] : -1;
+                }
+                T pv[2][9][4];
+                if (kc[0] >= 0) {
+                    const T* pk = PT + (int64_t(kc[0]) * 9) * kMaxDirs + 4 * g;
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[0][b]);
+                }
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
                     bad = true;
@@ -525,28 +539,29 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
                 parity ^= 1u << stage;
                 inflight &= ~(1u << stage);
                 const T* tile = tiles + stage * kTileElems;
-                if (4 * g < w) {
-#pragma unroll 1
-                    for (int r = 0; r < 4; ++r) {
-                        const int l = r * 8 + qi;
-                        const int q = t * 32 + l;
-                        if (q < it.q0 || q >= it.q1) continue;
-                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT
-                        const T* pk = PT + (int64_t(col[rj + q]) * 9) * kMaxDirs + 4 * g;
-                        T pv[9][4];
+                if (active) {
 #pragma unroll
-                        for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[b]);
-                        const T* blk = tile + l * 81;
+                    for (int r = 0; r < 4; ++r) {
+                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT for the next block
+                        if (r < 3 && kc[r + 1] >= 0) {
+                            const T* pk = PT + (int64_t(kc[r + 1]) * 9) * kMaxDirs + 4 * g;
+#pragma unroll
+                            for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[(r + 1) & 1][b]);
+                        }
+                        if (kc[r] < 0) continue;
+                        const T* blk = tile + (r * 8 + qi) * 81;
 #pragma unroll
                         for (int a = 0; a < 9; ++a)
 #pragma unroll
                             for (int b = 0; b < 9; ++b) {
                                 const T sab = blk[9 * a + b];
 #pragma unroll
-                                for (int cc = 0; cc < 4; ++cc) acc[a][cc] += sab * pv[b][cc];
+                                for (int cc = 0; cc < 4; ++cc) acc[a][cc] += sab * pv[r & 1][b][cc];
                             }
                     }
                 }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) kc[r] = kn[r];
                 __syncwarp();
                 if (f.item < L.n) {
                     fence_proxy_async();
@@ -1652,15 +1667,12 @@ static void set_smem_attrs() {
     static bool done = false;
     if (done) return;
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<float>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<double>())));
     done = true;
 }
 
@@ -1835,7 +1847,7 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_mcg_beta<<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
                                                          ptr<int>(w->blk_off), ptr<int>(w->blk_w),
                                                          ptr<double>(w->beta), ctl, w->mi1);
-        if (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8) {
             // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}; S Z over whole rows for the
             // problems forming a global block, over the subset segments for the local ones
             k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
