@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-compare", action="store_true", help="skip the float64 comparison solves")
     ap.add_argument("--n-dirs", type=int, default=16)
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="mixed precision: relative residual reduction of one float32 sweep (library default)")
     ap.add_argument("--tau", type=float, default=10.0)
     ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
@@ -71,6 +73,7 @@ def parse():
     ap.add_argument("--learn-problems", type=int, default=100,
                     help="training problems per family (each gives 10 normal equations)")
     ap.add_argument("--batch-problems", type=int, default=64)
+    ap.add_argument("--no-loop", action="store_true", help="batch mode: skip the looped single-problem solves")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="landmarks per camera x this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -272,7 +275,8 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     gen, kw, desc = WORKLOADS[a.workload]
     sc = synthetic.make(gen, seed=rank_seed(rank), **kw)
     xy = problem.device_measurements(sc, device=str(dev))
-    p = problem.from_scene(sc, precision=a.precision, xy=xy)
+    p = problem.from_scene(sc, precision=a.precision, xy=xy,
+                           **({} if a.inner_tol is None else {"inner_tol": a.inner_tol}))
     stream = torch.cuda.current_stream()
     p.ba_set_stream(stream)
 
@@ -531,28 +535,29 @@ def run_batched(a):
     spmv_bytes = nnzb * (81 * elt + 4) + 8 * (n_cams + 1) + 3 * 9 * n_cams * elt
     pb.close()
 
-    singles = [problem.from_scene(sc, precision=a.precision) for sc in scs]
-    for q in singles:
-        q.ba_set_stream(stream)
-
-    def step_loop():
-        out = []
-        for q in singles:
-            q.ba_build_normal(LAMBDA)
-            out.append(q.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau))
-        return out
-
-    step_loop()
     tl = []
-    for _ in range(max(1, min(a.steps, 3))):
-        t, sts = timed(step_loop)
-        tl.append(t)
-    assert all(s["status"] == 0 for s in sts)
-    for q in singles:
-        q.close()
+    if not a.no_loop:
+        singles = [problem.from_scene(sc, precision=a.precision) for sc in scs]
+        for q in singles:
+            q.ba_set_stream(stream)
+
+        def step_loop():
+            out = []
+            for q in singles:
+                q.ba_build_normal(LAMBDA)
+                out.append(q.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau))
+            return out
+
+        step_loop()
+        for _ in range(max(1, min(a.steps, 3))):
+            t, sts = timed(step_loop)
+            tl.append(t)
+        assert all(s["status"] == 0 for s in sts)
+        for q in singles:
+            q.close()
     torch.cuda.synchronize()
     ms_b = float(np.mean(tb))
-    ms_l = float(np.mean(tl))
+    ms_l = float(np.mean(tl)) if tl else None
     line = {
         "mode": "batched", "metric": "time to rel. residual 1e-6, all problems of a batch (MCG)",
         "value": ms_b, "unit": "ms/batch", "higher_is_better": False, "steps": a.steps, "warmup": a.warmup,
@@ -561,7 +566,7 @@ def run_batched(a):
                    "cams": [sc.n_cams for sc in scs], "n_cams": n_cams, "n_obs": n_obs, "nnzb": nnzb,
                    "mcg": {"n_dirs": a.n_dirs, "tau": a.tau}, "precision": a.precision, "tol": TOL,
                    "l2": "256 MiB buffer written before every timed step"},
-        "looped_single_ms": ms_l, "speedup_vs_loop": ms_l / ms_b,
+        "looped_single_ms": ms_l, "speedup_vs_loop": ms_l / ms_b if ms_l else None,
         "per_problem_iters": [s["iters"] for s in per],
         "autotune": {"item_blocks": cb, "spmv_ms_tuned": t_tuned, "spmv_ms_heuristic": t_heur},
         "roofline": {"kernel": "k_spmv<T,1> over all problems", "bound": "hbm" if elt == 4 else "alu",

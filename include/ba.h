@@ -76,9 +76,12 @@ typedef struct ba_options {
     int32_t precision;         /* ba_precision */
     int32_t chunk_iters;       /* Krylov iterations per captured CUDA graph between host checks of
                                   the device stop flag (default 8, 1..256) */
-    int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1) */
-    double inner_tol;          /* MIXED: relative residual reduction of one inner solve (default 1e-3) */
-    int32_t max_refine;        /* MIXED: maximum outer refinement sweeps (default 12) */
+    int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1);
+                                  when it is full FP64 stops with OOM, while MIXED ends the float32
+                                  sweep and the refinement starts another from the true residual */
+    double inner_tol;          /* MIXED: relative residual reduction aimed at by one float32 sweep
+                                  (default 1e-6: one sweep when float32 reaches the tolerance) */
+    int32_t max_refine;        /* MIXED: maximum outer refinement sweeps (default 64) */
     int32_t item_blocks;       /* stored 9x9 blocks of S per work item of the block-sparse products
                                   (longer rows are split): 0 (default) = 512, else a multiple of 32
                                   in [32, 4096]; ba_autotune sets it */

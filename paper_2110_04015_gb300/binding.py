@@ -191,7 +191,7 @@ class Problem:
     """
 
     def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, damping="marquardt", precision="fp64",
-                 chunk_iters=8, max_history=0, inner_tol=1e-3, max_refine=12, item_blocks=0, cam_off=None):
+                 chunk_iters=8, max_history=0, inner_tol=1e-6, max_refine=64, item_blocks=0, cam_off=None):
         L = lib()
         opt = ba_options()
         L.ba_default_options(ctypes.byref(opt))

@@ -300,6 +300,7 @@ void alloc_system(ba_problem* p) {
         BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
         y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 27);
         y.tl = dev_alloc<double>(p, size_t(s.n_l) * 3);
+        y.uo = dev_alloc<double>(p, size_t(s.n_o) * 3);
         y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
         y.Dhat = dev_alloc<double>(p, size_t(s.n_c) * 81);
     }
@@ -480,8 +481,8 @@ void ba_default_options(ba_options* opt) {
     opt->precision = BA_PRECISION_FP64;
     opt->chunk_iters = 8;
     opt->max_history = 0;
-    opt->inner_tol = 1e-3;
-    opt->max_refine = 12;
+    opt->inner_tol = 1e-6;
+    opt->max_refine = 64;
 }
 
 int ba_problem_create(const ba_options* opt, int32_t n_cams, int32_t n_pts, int64_t n_obs, const double* cams,

@@ -420,15 +420,19 @@ __global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const i
 
 // Off-diagonal blocks: one warp per upper block (j < k), S_jk = - sum over the observation pairs
 // (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to (k, j).  Lane
-// entries are e = lane, lane + 32, lane + 64 (< 81); G rows are read straight from global memory
-// (broadcast through L1), two pairs per step.
+// entries are e = lane, lane + 32, lane + 64 (< 81).  The warp takes the pairs kChunk at a time:
+// lanes 0..26 load the two 27-value G blocks of every pair of the chunk (one coalesced load per
+// block, all of the chunk's loads in flight together), stage them in shared memory, and every
+// lane then accumulates its entries over the chunk's pairs in order.
 template <typename T>
-__global__ void k_schur_off(int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
-                            const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir,
-                            const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
-                            const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
-                            const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kThreads) k_schur_off(
+    int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
+    const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
+    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
+    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    constexpr int kChunk = 8;
+    __shared__ T sg[kThreads / 32][kChunk][2][28];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = gstride() >> 5;
     const int e0 = lane, e1 = lane + 32, e2 = lane + 64;
     const int a0 = e0 / 9, b0 = e0 % 9, a1 = e1 / 9, b1 = e1 % 9;
@@ -437,36 +441,38 @@ __global__ void k_schur_off(int64_t n_up, const int32_t* __restrict__ up_j, cons
     for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
         T s0 = T(0), s1 = T(0), s2 = T(0);
         const int64_t pb = pair_ptr[u], pe = pair_ptr[u + 1];
-        int64_t q = pb;
-        for (; q + 1 < pe; q += 2) {
-            const int2 pa = pairs[q], pc = pairs[q + 1];
-            const T* g1 = G + 27 * int64_t(pa.x);
-            const T* g2 = G + 27 * int64_t(pa.y);
-            const T* h1 = G + 27 * int64_t(pc.x);
-            const T* h2 = G + 27 * int64_t(pc.y);
-            s0 += __ldg(g1 + 3 * a0) * __ldg(g2 + 3 * b0) + __ldg(g1 + 3 * a0 + 1) * __ldg(g2 + 3 * b0 + 1) +
-                  __ldg(g1 + 3 * a0 + 2) * __ldg(g2 + 3 * b0 + 2);
-            s1 += __ldg(g1 + 3 * a1) * __ldg(g2 + 3 * b1) + __ldg(g1 + 3 * a1 + 1) * __ldg(g2 + 3 * b1 + 1) +
-                  __ldg(g1 + 3 * a1 + 2) * __ldg(g2 + 3 * b1 + 2);
-            s2 += __ldg(g1 + 3 * a2) * __ldg(g2 + 3 * b2) + __ldg(g1 + 3 * a2 + 1) * __ldg(g2 + 3 * b2 + 1) +
-                  __ldg(g1 + 3 * a2 + 2) * __ldg(g2 + 3 * b2 + 2);
-            s0 += __ldg(h1 + 3 * a0) * __ldg(h2 + 3 * b0) + __ldg(h1 + 3 * a0 + 1) * __ldg(h2 + 3 * b0 + 1) +
-                  __ldg(h1 + 3 * a0 + 2) * __ldg(h2 + 3 * b0 + 2);
-            s1 += __ldg(h1 + 3 * a1) * __ldg(h2 + 3 * b1) + __ldg(h1 + 3 * a1 + 1) * __ldg(h2 + 3 * b1 + 1) +
-                  __ldg(h1 + 3 * a1 + 2) * __ldg(h2 + 3 * b1 + 2);
-            s2 += __ldg(h1 + 3 * a2) * __ldg(h2 + 3 * b2) + __ldg(h1 + 3 * a2 + 1) * __ldg(h2 + 3 * b2 + 1) +
-                  __ldg(h1 + 3 * a2 + 2) * __ldg(h2 + 3 * b2 + 2);
-        }
-        if (q < pe) {
-            const int2 pa = pairs[q];
-            const T* g1 = G + 27 * int64_t(pa.x);
-            const T* g2 = G + 27 * int64_t(pa.y);
-            s0 += __ldg(g1 + 3 * a0) * __ldg(g2 + 3 * b0) + __ldg(g1 + 3 * a0 + 1) * __ldg(g2 + 3 * b0 + 1) +
-                  __ldg(g1 + 3 * a0 + 2) * __ldg(g2 + 3 * b0 + 2);
-            s1 += __ldg(g1 + 3 * a1) * __ldg(g2 + 3 * b1) + __ldg(g1 + 3 * a1 + 1) * __ldg(g2 + 3 * b1 + 1) +
-                  __ldg(g1 + 3 * a1 + 2) * __ldg(g2 + 3 * b1 + 2);
-            s2 += __ldg(g1 + 3 * a2) * __ldg(g2 + 3 * b2) + __ldg(g1 + 3 * a2 + 1) * __ldg(g2 + 3 * b2 + 1) +
-                  __ldg(g1 + 3 * a2 + 2) * __ldg(g2 + 3 * b2 + 2);
+        for (int64_t q = pb; q < pe; q += kChunk) {
+            const int np = int(pe - q < kChunk ? pe - q : kChunk);
+            int2 pr = make_int2(0, 0);
+            if (lane < np) pr = pairs[q + lane];
+            T ga[kChunk], gb[kChunk];
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) {
+                const int ox = __shfl_sync(0xffffffffu, pr.x, p);
+                const int oy = __shfl_sync(0xffffffffu, pr.y, p);
+                ga[p] = T(0);
+                gb[p] = T(0);
+                if (p < np && lane < 27) {
+                    ga[p] = __ldg(G + 27 * int64_t(ox) + lane);
+                    gb[p] = __ldg(G + 27 * int64_t(oy) + lane);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) {
+                if (lane < 27) {
+                    sg[wid][p][0][lane] = ga[p];
+                    sg[wid][p][1][lane] = gb[p];
+                }
+            }
+            __syncwarp();
+            for (int p = 0; p < np; ++p) {
+                const T* x = sg[wid][p][0];
+                const T* y = sg[wid][p][1];
+                s0 += x[3 * a0] * y[3 * b0] + x[3 * a0 + 1] * y[3 * b0 + 1] + x[3 * a0 + 2] * y[3 * b0 + 2];
+                s1 += x[3 * a1] * y[3 * b1] + x[3 * a1 + 1] * y[3 * b1 + 1] + x[3 * a1 + 2] * y[3 * b1 + 2];
+                s2 += x[3 * a2] * y[3 * b2] + x[3 * a2 + 1] * y[3 * b2 + 1] + x[3 * a2 + 2] * y[3 * b2 + 2];
+            }
         }
         const int j = up_j[u], k = up_k[u];
         const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
@@ -493,7 +499,8 @@ __global__ void k_put_diag(int32_t n_c, const int64_t* __restrict__ row_ptr, con
     }
 }
 
-// G32_o = float(Lam_cam(o) G_o): the observation blocks of the scaled system
+// G32_o = float(Lam_cam(o) G_o): the observation blocks of the scaled system (point order: the two
+// observations of a pair belong to one landmark, so their blocks lie close together)
 __global__ void k_scale_G(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
                           const double* __restrict__ lam, float* __restrict__ G32) {
     for (int64_t i = gtid(); i < n_o * 27; i += gstride()) {
@@ -503,56 +510,79 @@ __global__ void k_scale_G(int64_t n_o, const int32_t* __restrict__ oc, const dou
     }
 }
 
-// Implicit float64 product, landmark part: t_l = sum_{o in l} G_o^T x_cam(o)
-__global__ void k_implicit_t(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
-                             const double* __restrict__ G, const double* __restrict__ x, double* __restrict__ t) {
-    // one thread per (landmark, component c): t_l[c] = sum_o sum_a G_o[a][c] x_cam(o)[a]
+// Implicit float64 product, landmark part, in two passes:
+//   u_o = G_o^T x_cam(o)                           (one thread per observation, streaming G)
+//   t_l = sum_{o seen of l} u_o                    (one thread per landmark component, in slot order)
+__global__ void k_implicit_u(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
+                             const double* __restrict__ x, double* __restrict__ u) {
+    for (int64_t o = gtid(); o < n_o; o += gstride()) {
+        const double* g = G + 27 * o;
+        const double* xc = x + 9 * int64_t(oc[o]);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double xa = xc[a];
+            a0 += g[3 * a] * xa;
+            a1 += g[3 * a + 1] * xa;
+            a2 += g[3 * a + 2] * xa;
+        }
+        u[3 * o] = a0;
+        u[3 * o + 1] = a1;
+        u[3 * o + 2] = a2;
+    }
+}
+
+__global__ void k_implicit_tsum(int32_t n_l, const int64_t* __restrict__ pt_ptr, const double* __restrict__ u,
+                                double* __restrict__ t) {
     for (int64_t i = gtid(); i < int64_t(n_l) * 3; i += gstride()) {
         const int64_t l = i / 3;
         const int c = int(i - 3 * l);
         double acc = 0.0;
-        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
-            const double* g = G + 27 * o + c;
-            const double* xc = x + 9 * int64_t(oc[o]);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) acc += g[3 * a] * xc[a];
-        }
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) acc += u[3 * o + c];
         t[i] = acc;
     }
 }
 
 // Implicit float64 product, camera part, and the true residual: (S x)_j = U_j x_j - sum_{o in j} G_o t_l,
-// out_j = -b~_j - (S x)_j; CTA partial sums of |out|^2 and |b~|^2 into partial[2 b], partial[2 b + 1].
+// out_j = -b~_j - (S x)_j; camera j's sums of |out_j|^2 and |b~_j|^2 into partial[2 j], partial[2 j + 1].
 __global__ void __launch_bounds__(kCamThreads) k_implicit_res(
     int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
     const int32_t* __restrict__ op, const double* __restrict__ G, const double* __restrict__ t,
     const double* __restrict__ U, const double* __restrict__ x, const double* __restrict__ bt,
     double* __restrict__ out, double* __restrict__ partial) {
-    __shared__ double red[kCamThreads / 32][9];
+    // lane 3 a + c (lanes 0..26) of every warp accumulates sum_o G_o[a][c] t_l(o)[c] over the
+    // warp's observations; each observation's 27 values are one coalesced 216-byte load
+    __shared__ double red[kCamThreads / 32][27];
+    constexpr int kUnroll = 4;   // observations in flight per warp
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = kCamThreads / 32;
+    const int c = lane % 3;
     for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
         double tt = 0.0, bb = 0.0;
-        double acc[9];
+        double acc = 0.0;
+        const int64_t q1 = cam_ptr[j + 1];
+        for (int64_t q = cam_ptr[j] + wid; q < q1; q += kUnroll * nw) {
+            double gv[kUnroll], tv[kUnroll];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) acc[a] = 0.0;
-        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
-            const int64_t o = cam_obs[q];
-            const double* g = G + 27 * o;
-            const double* tl = t + 3 * int64_t(op[o]);
-            const double t0 = tl[0], t1 = tl[1], t2 = tl[2];
+            for (int k = 0; k < kUnroll; ++k) {
+                const int64_t qq = q + int64_t(k) * nw;
+                gv[k] = 0.0;
+                tv[k] = 0.0;
+                if (qq < q1 && lane < 27) {
+                    const int64_t o = cam_obs[qq];
+                    gv[k] = G[27 * o + lane];
+                    tv[k] = t[3 * int64_t(op[o]) + c];
+                }
+            }
 #pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] += g[3 * a] * t0 + g[3 * a + 1] * t1 + g[3 * a + 2] * t2;
+            for (int k = 0; k < kUnroll; ++k) acc += gv[k] * tv[k];
         }
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            double v = warp_sum(acc[a]);
-            if (lane == 0) red[wid][a] = v;
-        }
+        if (lane < 27) red[wid][lane] = acc;
         __syncthreads();
         if (threadIdx.x < 9) {
             const int a = threadIdx.x;
             double gt = 0.0;
-            for (int w = 0; w < kCamThreads / 32; ++w) gt += red[w][a];
+            for (int w = 0; w < nw; ++w) gt += red[w][3 * a] + red[w][3 * a + 1] + red[w][3 * a + 2];
             double ux = 0.0;
             for (int b = 0; b < 9; ++b) ux += U[81 * int64_t(j) + 9 * a + b] * x[9 * int64_t(j) + b];
             const double b_ = bt[9 * int64_t(j) + a];
@@ -780,8 +810,8 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
 
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st) {
-    k_implicit_t<<<grid_for(int64_t(s.n_l) * 3, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, x,
-                                                                             y.tl);
+    k_implicit_u<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, x, y.uo);
+    k_implicit_tsum<<<grid_for(int64_t(s.n_l) * 3, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, y.uo, y.tl);
     k_implicit_res<<<s.n_c, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.G, y.tl, y.U, x, y.bt, out,
                                                   partial);
 }

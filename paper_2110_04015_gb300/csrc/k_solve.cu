@@ -1211,8 +1211,10 @@ __global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ totals, double
     const int local = (t < c->tau) ? 1 : 0;
     const int w = local ? c->n_eff : 1;
     if (c->cols + w > c->cap) {
+        // history full: a float32 sweep ends here and the float64 refinement restarts it from the
+        // true residual; a float64 solve cannot go on
         c->done = 1;
-        c->status = BA_ERR_OOM;
+        c->status = c->stag > 0.0 ? BA_OK : BA_ERR_OOM;
         return;
     }
     c->local = local;
@@ -1303,15 +1305,23 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
     }
 }
 
-// P_new = Z - P_hist beta, Q_new = (S Z) - Q_hist beta, one thread per row; beta tiles staged in
-// shared memory (grid: CTAs x problems, each CTA a contiguous run of the problem's rows).
+// P_new = Z - P_hist beta, Q_new = (S Z) - Q_hist beta (Eq. 18; Q only when Q is updated rather than
+// recomputed).  A tall-skinny product over the history: a CTA takes 32 consecutive rows of one
+// problem, its kPqSlices warps split each 64-column tile of the history (warp k takes columns
+// k, k + kPqSlices, ...; lane = row, so every column is read as 32 consecutive values), beta
+// tiles are staged in shared memory, and the slices are added in slice order at the end.
+// A one-column block (a global step) accumulates one column only.
+constexpr int kPqSlices = 4;
 template <typename T>
-__global__ void k_mcg_pq(T* __restrict__ P, T* __restrict__ Q, const T* __restrict__ z,
-                         const double* __restrict__ beta, T* __restrict__ PT, const Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T* __restrict__ Q,
+                                                            const T* __restrict__ z, const double* __restrict__ beta,
+                                                            T* __restrict__ PT, const Ctl* __restrict__ ctl) {
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
     constexpr int TC = 64;
     __shared__ T sB[TC][kMaxDirs];
+    __shared__ T red[2][kPqSlices][32][kMaxDirs + 1];
+    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
     const int64_t n = int64_t(c.lay.nc) * 9;
     const int64_t r0g = 9 * int64_t(c.lay.c0);
     const int w = c.w_new, off = c.new_off, hc = c.hist_cols, local = c.local, sz = c.sz;
@@ -1319,24 +1329,14 @@ __global__ void k_mcg_pq(T* __restrict__ P, T* __restrict__ Q, const T* __restri
     T* Pp = P + c.lay.hoff;
     T* Qp = Q + c.lay.hoff;
     const double* Bp = beta + c.lay.boff * kMaxDirs;
-    // every thread of the CTA walks all tiles, so the loop bounds are CTA-uniform
-    const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t rbeg = int64_t(blockIdx.x) * per_cta;
-    const int64_t rend = rbeg + per_cta < n ? rbeg + per_cta : n;
-    for (int64_t base = rbeg; base < rend; base += blockDim.x) {
-        const int64_t row = base + threadIdx.x;
-        const bool act = row < rend;
+    for (int64_t base = int64_t(blockIdx.x) * 32; base < n; base += int64_t(gridDim.x) * 32) {
+        const int64_t row = base + lane;
+        const bool act = row < n;
         T ap[kMaxDirs], aq[kMaxDirs];
-        const int sub = act ? int(row / 9) / sz : 0;
-        const T zr = act ? z[r0g + row] : T(0);
 #pragma unroll
         for (int s = 0; s < kMaxDirs; ++s) {
             ap[s] = T(0);
             aq[s] = T(0);
-            if (act && s < w) {
-                ap[s] = (local ? (s == sub) : (s == 0)) ? zr : T(0);
-                aq[s] = upd_q ? Qp[int64_t(off + s) * n + row] : T(0);
-            }
         }
         for (int c0 = 0; c0 < hc; c0 += TC) {
             const int tc = hc - c0 < TC ? hc - c0 : TC;
@@ -1346,37 +1346,62 @@ __global__ void k_mcg_pq(T* __restrict__ P, T* __restrict__ Q, const T* __restri
                 sB[cc][s] = (cc < tc && s < w) ? T(Bp[int64_t(c0 + cc) * kMaxDirs + s]) : T(0);
             }
             __syncthreads();
-            if (act) {
-                if (upd_q) {
-                    for (int cc = 0; cc < tc; ++cc) {
-                        const T pv = Pp[int64_t(c0 + cc) * n + row];
-                        const T qv = Qp[int64_t(c0 + cc) * n + row];
+            if (!act) continue;
+            const T* pc = Pp + int64_t(c0) * n + row;
+            const T* qc = Qp + int64_t(c0) * n + row;
+            if (w == 1) {
+#pragma unroll 4
+                for (int cl = k; cl < tc; cl += kPqSlices) {
+                    const T b0 = sB[cl][0];
+                    ap[0] += pc[int64_t(cl) * n] * b0;
+                    if (upd_q) aq[0] += qc[int64_t(cl) * n] * b0;
+                }
+            } else if (upd_q) {
+#pragma unroll 2
+                for (int cl = k; cl < tc; cl += kPqSlices) {
+                    const T pv = pc[int64_t(cl) * n], qv = qc[int64_t(cl) * n];
 #pragma unroll
-                        for (int s = 0; s < kMaxDirs; ++s) {
-                            ap[s] -= pv * sB[cc][s];
-                            aq[s] -= qv * sB[cc][s];
-                        }
+                    for (int s = 0; s < kMaxDirs; ++s) {
+                        ap[s] += pv * sB[cl][s];
+                        aq[s] += qv * sB[cl][s];
                     }
-                } else {
-                    for (int cc = 0; cc < tc; ++cc) {
-                        const T pv = Pp[int64_t(c0 + cc) * n + row];
+                }
+            } else {
+#pragma unroll 4
+                for (int cl = k; cl < tc; cl += kPqSlices) {
+                    const T pv = pc[int64_t(cl) * n];
 #pragma unroll
-                        for (int s = 0; s < kMaxDirs; ++s) ap[s] -= pv * sB[cc][s];
-                    }
+                    for (int s = 0; s < kMaxDirs; ++s) ap[s] += pv * sB[cl][s];
                 }
             }
         }
-        if (act) {
+#pragma unroll
+        for (int s = 0; s < kMaxDirs; ++s) {
+            red[0][k][lane][s] = ap[s];
+            red[1][k][lane][s] = aq[s];
+        }
+        __syncthreads();
+        if (k == 0 && act) {
+            const int sub = int(row / 9) / sz;
+            const T zr = z[r0g + row];
 #pragma unroll
             for (int s = 0; s < kMaxDirs; ++s) {
+                T sp = T(0), sq = T(0);
+#pragma unroll
+                for (int kk = 0; kk < kPqSlices; ++kk) {
+                    sp += red[0][kk][lane][s];
+                    sq += red[1][kk][lane][s];
+                }
+                const T pn = ((local ? (s == sub) : (s == 0)) ? zr : T(0)) - sp;
                 if (s < w) {
-                    Pp[int64_t(off + s) * n + row] = ap[s];
-                    if (upd_q) Qp[int64_t(off + s) * n + row] = aq[s];
+                    Pp[int64_t(off + s) * n + row] = pn;
+                    if (upd_q) Qp[int64_t(off + s) * n + row] -= sq;
                 }
                 // row-major copy of the new block for the multi-column product (zero past w)
-                if (!upd_q) PT[(r0g + row) * kMaxDirs + s] = s < w ? ap[s] : T(0);
+                if (!upd_q) PT[(r0g + row) * kMaxDirs + s] = s < w ? pn : T(0);
             }
         }
+        __syncthreads();
     }
 }
 
@@ -1553,6 +1578,7 @@ struct Solver {
     int gx = 1;               // grid width of the per-camera kernels
     int gg = 1;               // Gram grid width
     int gq = 1;               // grid width of the per-row kernels
+    int gpq = 1;              // grid width of the reorthogonalisation (32-row blocks)
     int gphi = 1, gb = 1;     // Phi and beta grid widths
     std::vector<Layout> lay;  // of the current solve
     Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, phip, hist, blk_off, blk_w, ctl, outer, rt, lay_d,
@@ -1741,6 +1767,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     w->gx = int(std::min<int64_t>(G, (nc_max + kThreads - 1) / kThreads));
     w->gg = int(std::min<int64_t>(G, (9 * int64_t(nc_max) + 127) / 128));
     w->gq = std::max(1, G / nb);
+    w->gpq = int(std::max<int64_t>(1, std::min<int64_t>((9 * int64_t(nc_max) + 31) / 32, 4 * G / nb)));
     w->gphi = std::max(1, 4 * G / nb);
     w->gb = std::max(1, G / nb);
     if (!w->h_ctl || int(w->lay.size()) != nb) {
@@ -1856,10 +1883,10 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
             if (w->use_l)
                 k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                     s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l, kSelLocal, Q, nullptr, nullptr, ctl);
-            k_mcg_pq<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(P, Q, z, ptr<double>(w->beta), nullptr, ctl);
+            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, ptr<double>(w->beta), nullptr, ctl);
         } else {
             // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
-            k_mcg_pq<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(P, Q, z, ptr<double>(w->beta), ptr<T>(w->PT), ctl);
+            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, ptr<double>(w->beta), ptr<T>(w->PT), ctl);
             k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
             k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
@@ -1944,7 +1971,7 @@ static void true_residual(Solver* w, const Structure& s, const System& y, const 
         w->launches += 1;
     } else {
         launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
-        w->launches += 2;
+        w->launches += 3;
     }
     k_true_reduce<<<w->nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<double>(w->part_cam));
     w->launches += 1;

@@ -42,7 +42,8 @@ def test_default_options_and_errors_without_device(libba):
     L = binding.lib()
     opt = binding.ba_options()
     L.ba_default_options(ctypes.byref(opt))
-    assert opt.precision == 0 and opt.damping == 0 and opt.chunk_iters == 8 and opt.inner_tol == 1e-3
+    assert opt.precision == 0 and opt.damping == 0 and opt.chunk_iters == 8 and opt.inner_tol == 1e-6
+    assert opt.max_refine == 64 and opt.max_history == 0 and opt.item_blocks == 0
     # argument checks run before any device work
     out = ctypes.c_void_p()
     code = L.ba_problem_create(None, 0, 1, 1, None, None, None, None, None, ctypes.byref(out))

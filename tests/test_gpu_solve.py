@@ -209,3 +209,21 @@ def test_single_observation_landmark_and_unobserved_camera():
         st = p.ba_solve_pcg(1e-6, 2000)
         assert st["status"] == 0 and st["true_rel_residual"] < 1.5e-6
         assert np.all(p.ba_get_delta()[3] == 0)
+
+
+def test_full_history_restarts_a_float32_sweep_but_stops_float64():
+    sc = scene("seq-small")
+    # tau = 0: one column per step, so a 40-column history is full after 40 steps (this problem
+    # needs more)
+    p64 = problem.from_scene(sc, precision="fp64", max_history=40)
+    p64.ba_build_normal(1e-4)
+    with pytest.raises(binding.BAError) as e:
+        p64.ba_solve_mcg(1e-6, 1000, 16, 0.0)
+    assert e.value.code == binding.BA_ERR_OOM
+    p64.close()
+    p32 = problem.from_scene(sc, precision="mixed", max_history=40)
+    p32.ba_build_normal(1e-4)
+    st = p32.ba_solve_mcg(1e-6, 1000, 16, 0.0)
+    assert st["status"] == 0 and st["true_rel_residual"] <= 1e-6 and st["refinements"] > 1
+    assert st["history_cols"] <= 40
+    p32.close()
