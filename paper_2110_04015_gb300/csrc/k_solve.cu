@@ -41,6 +41,7 @@ constexpr int kGramMax = kMaxDirs * kMaxDirs + kMaxDirs;   // Delta (w x w) and 
 constexpr int kChunkCams = 112;                             // cameras per Phi partial
 constexpr double kStagnation = 1e-4;                        // float32 sweep stop on t_i (see Ctl::stag)
 constexpr int kTotals = 16;                                 // per-problem grid totals
+constexpr int kUpdCams = 28;                                // cameras per CTA of the update kernels (252 rows)
 
 // Where one problem of the batch lives (fixed for a solve).
 struct Layout {
@@ -718,17 +719,23 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
 // alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2, q^T z, r^T z.
 // Delta and gamma are the sums over the problem's cameras (camera order) of the per-camera sums
 // of the product; every CTA forms them the same way, CTA 0 stores them for the decide kernel.
+// Thread = one row (9 per camera, kUpdCams cameras per CTA); the rows of a camera meet in
+// shared memory for z = D^{-1} r.  CTA b of a problem takes its cameras [b kUpdCams, ...), so the
+// partition depends on the problem alone (the grid has a CTA for every chunk of the largest).
 template <typename T>
-__global__ void k_pcg_update(const double* __restrict__ Dinv, const T* __restrict__ P, const T* __restrict__ Q,
-                             T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                             const double* __restrict__ camdot, double* __restrict__ totals,
-                             double* __restrict__ dpart, int* __restrict__ dcnt, const Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restrict__ Dinv, const T* __restrict__ P,
+                                                         const T* __restrict__ Q, T* __restrict__ x,
+                                                         T* __restrict__ r, T* __restrict__ z,
+                                                         const double* __restrict__ camdot,
+                                                         double* __restrict__ totals, double* __restrict__ dpart,
+                                                         int* __restrict__ dcnt, const Ctl* __restrict__ ctl) {
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
     const int64_t c0 = c.lay.c0;
     const int nc = c.lay.nc;
     __shared__ double dg[2];
+    __shared__ T sr[kUpdCams * 9];
     {
         double d[2] = {0.0, 0.0};
         for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
@@ -744,30 +751,30 @@ __global__ void k_pcg_update(const double* __restrict__ Dinv, const T* __restric
     }
     const T alpha = T(dg[1] / dg[0]);
     const int64_t hb = c.lay.hoff - 9 * c0;
+    const int t = threadIdx.x, cl = t / 9, a = t - 9 * (t / 9);
+    const int64_t jl = int64_t(blockIdx.x) * kUpdCams + cl;
+    const bool act = t < kUpdCams * 9 && jl < nc;
+    const int64_t i = 9 * (c0 + jl) + a;
     double v[3] = {0.0, 0.0, 0.0};
-    for (int64_t jl = gtid(); jl < nc; jl += gstride()) {
-        const int64_t j = c0 + jl;
-        T rv[9], qv[9];
+    T rv = T(0), qv = T(0);
+    if (act) {
+        x[i] = x[i] + alpha * P[hb + i];
+        qv = Q[hb + i];
+        rv = r[i] - alpha * qv;
+        r[i] = rv;
+        v[0] = double(rv) * double(rv);
+    }
+    if (t < kUpdCams * 9) sr[t] = rv;
+    __syncthreads();
+    if (act) {
+        const double* D = Dinv + 81 * (c0 + jl) + 9 * a;
+        double s = 0.0;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            const int64_t i = 9 * j + a;
-            x[i] = x[i] + alpha * P[hb + i];
-            qv[a] = Q[hb + i];
-            rv[a] = r[i] - alpha * qv[a];
-            r[i] = rv[a];
-            v[0] += double(rv[a]) * double(rv[a]);
-        }
-        const double* D = Dinv + 81 * j;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            double s = 0.0;
-#pragma unroll
-            for (int b = 0; b < 9; ++b) s += D[9 * a + b] * double(rv[b]);
-            const T zs = T(s);
-            z[9 * j + a] = zs;
-            v[1] += double(qv[a]) * double(zs);
-            v[2] += double(rv[a]) * double(zs);
-        }
+        for (int b = 0; b < 9; ++b) s += D[b] * double(sr[9 * cl + b]);
+        const T zs = T(s);
+        z[i] = zs;
+        v[1] = double(qv) * double(zs);
+        v[2] = double(rv) * double(zs);
     }
     grid_sum_finalize<3>(v, dpart + int64_t(p) * gridDim.x * 3, dcnt + 4 * p, tot + 2);
 }
@@ -1120,11 +1127,14 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx
     }
 }
 
-// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z (grid: CTAs x problems).
+// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z (grid: CTAs x problems;
+// thread = one row, as in k_pcg_update).
 template <typename T>
-__global__ void k_mcg_update(const double* __restrict__ Dinv, const T* __restrict__ P, const T* __restrict__ Q,
-                             T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, double* __restrict__ dpart,
-                             int* __restrict__ dcnt, double* __restrict__ totals, const Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restrict__ Dinv, const T* __restrict__ P,
+                                                         const T* __restrict__ Q, T* __restrict__ x,
+                                                         T* __restrict__ r, T* __restrict__ z,
+                                                         double* __restrict__ dpart, int* __restrict__ dcnt,
+                                                         double* __restrict__ totals, const Ctl* __restrict__ ctl) {
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1135,35 +1145,36 @@ __global__ void k_mcg_update(const double* __restrict__ Dinv, const T* __restric
     const T* Pp = P + c.lay.hoff + int64_t(off) * n;
     const T* Qp = Q + c.lay.hoff + int64_t(off) * n;
     __shared__ T sal[kMaxDirs];
+    __shared__ T sr[kUpdCams * 9];
     if (threadIdx.x < kMaxDirs) sal[threadIdx.x] = int(threadIdx.x) < w ? T(c.alpha_v[threadIdx.x]) : T(0);
     __syncthreads();
+    const int t = threadIdx.x, cl = t / 9, a = t - 9 * (t / 9);
+    const int64_t jl = int64_t(blockIdx.x) * kUpdCams + cl;
+    const bool act = t < kUpdCams * 9 && jl < nc;
+    const int64_t il = 9 * jl + a, i = 9 * c0 + il;
     double v[2] = {0.0, 0.0};
-    for (int64_t jl = gtid(); jl < nc; jl += gstride()) {
-        const int64_t j = c0 + jl;
-        T rv[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            const int64_t il = 9 * jl + a, i = 9 * j + a;
-            T dx = T(0), dr = T(0);
-            for (int b = 0; b < w; ++b) {
-                dx += Pp[int64_t(b) * n + il] * sal[b];
-                dr += Qp[int64_t(b) * n + il] * sal[b];
-            }
-            x[i] = x[i] + dx;
-            rv[a] = r[i] - dr;
-            r[i] = rv[a];
-            v[0] += double(rv[a]) * double(rv[a]);
+    T rv = T(0);
+    if (act) {
+        T dx = T(0), dr = T(0);
+        for (int b = 0; b < w; ++b) {
+            dx += Pp[int64_t(b) * n + il] * sal[b];
+            dr += Qp[int64_t(b) * n + il] * sal[b];
         }
-        const double* D = Dinv + 81 * j;
+        x[i] = x[i] + dx;
+        rv = r[i] - dr;
+        r[i] = rv;
+        v[0] = double(rv) * double(rv);
+    }
+    if (t < kUpdCams * 9) sr[t] = rv;
+    __syncthreads();
+    if (act) {
+        const double* D = Dinv + 81 * (c0 + jl) + 9 * a;
+        double s = 0.0;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            double s = 0.0;
-#pragma unroll
-            for (int b = 0; b < 9; ++b) s += D[9 * a + b] * double(rv[b]);
-            const T zs = T(s);
-            z[9 * j + a] = zs;
-            v[1] += double(rv[a]) * double(zs);
-        }
+        for (int b = 0; b < 9; ++b) s += D[b] * double(sr[9 * cl + b]);
+        const T zs = T(s);
+        z[i] = zs;
+        v[1] = double(rv) * double(zs);
     }
     grid_sum_finalize<2>(v, dpart + int64_t(p) * gridDim.x * 2, dcnt + 4 * p + 1, totals + int64_t(p) * kTotals + 8);
 }
@@ -1576,6 +1587,7 @@ struct Solver {
     int64_t n = 0;            // 9 n_c over all problems
     int mi1 = 0;              // per-problem stride of the per-step arrays (max_iters + 1)
     int gx = 1;               // grid width of the per-camera kernels
+    int gu = 1;               // grid width of the update kernels (kUpdCams cameras per CTA)
     int gg = 1;               // Gram grid width
     int gq = 1;               // grid width of the per-row kernels
     int gpq = 1;              // grid width of the reorthogonalisation (32-row blocks)
@@ -1765,6 +1777,8 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     w->n = n;
     w->mi1 = std::max(w->mi1, a.max_iters + 1);
     w->gx = int(std::min<int64_t>(G, (nc_max + kThreads - 1) / kThreads));
+    if ((int64_t(nc_max) + kUpdCams - 1) / kUpdCams > 65535) throw Error(BA_ERR_INVALID_ARG, "too many cameras in one problem");
+    w->gu = (nc_max + kUpdCams - 1) / kUpdCams;
     w->gg = int(std::min<int64_t>(G, (9 * int64_t(nc_max) + 127) / 128));
     w->gq = std::max(1, G / nb);
     w->gpq = int(std::max<int64_t>(1, std::min<int64_t>((9 * int64_t(nc_max) + 31) / 32, 4 * G / nb)));
@@ -1799,7 +1813,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     grow(w->rt, size_t(n) * sizeof(double));
     grow(w->lay_d, size_t(nb) * sizeof(Layout));
     grow(w->totals, size_t(nb) * kTotals * sizeof(double));
-    grow(w->dpart, size_t(nb) * w->gx * 5 * sizeof(double));
+    grow(w->dpart, size_t(nb) * w->gu * 5 * sizeof(double));
     grow(w->camdot, size_t(s.n_c) * 2 * sizeof(double));
     if (w->dcnt.bytes < size_t(nb) * 4 * sizeof(int)) {
         grow(w->dcnt, size_t(nb) * 4 * sizeof(int));
@@ -1859,14 +1873,14 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
     if (!mcg) {
         k_spmv<T, 1, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
             s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelLive, Q, r, ptr<double>(w->camdot), ctl);
-        k_pcg_update<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
+        k_pcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
                                                                ptr<double>(w->dpart), dcnt, ctl);
         k_pcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist));
         k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
     } else {
         k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
         k_mcg_small<<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
-        k_mcg_update<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gx,
+        k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu,
                                                                dcnt, totals, ctl);
         k_mcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist), ptr<int>(w->blk_off), ptr<int>(w->blk_w),
                                         w->mi1);
