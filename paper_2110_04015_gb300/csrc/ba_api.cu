@@ -338,7 +338,7 @@ void do_build(ba_problem* p, double lambda) {
         ba::launch_schur(s, y, st);          // off-diagonal blocks + the diagonal from Sd
         p->launches += 2;
     } else {
-        ba::launch_schur_mixed(s, y, st);    // scaled float32 G, off-diagonal and diagonal of S^
+        ba::launch_schur_mixed(s, y, st);    // float32 G, off-diagonal and diagonal blocks of S^
         p->launches += 4;
     }
     check_launch();

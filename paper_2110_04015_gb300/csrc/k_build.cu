@@ -423,13 +423,14 @@ __global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const i
 // entries are e = lane, lane + 32, lane + 64 (< 81).  The warp takes the pairs kChunk at a time:
 // lanes 0..26 load the two 27-value G blocks of every pair of the chunk (one coalesced load per
 // block, all of the chunk's loads in flight together), stage them in shared memory, and every
-// lane then accumulates its entries over the chunk's pairs in order.
+// lane then accumulates its entries over the chunk's pairs in order.  With lam (the float32
+// system), the finished block is scaled to Lam_j S_jk Lam_k.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_schur_off(
     int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
     const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
-    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
-    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    const int2* __restrict__ pairs, const T* __restrict__ G, const double* __restrict__ lam,
+    const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
     constexpr int kChunk = 8;
     __shared__ T sg[kThreads / 32][kChunk][2][28];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -475,6 +476,11 @@ __global__ void __launch_bounds__(kThreads) k_schur_off(
             }
         }
         const int j = up_j[u], k = up_k[u];
+        if (lam) {
+            s0 *= T(lam[9 * int64_t(j) + a0] * lam[9 * int64_t(k) + b0]);
+            s1 *= T(lam[9 * int64_t(j) + a1] * lam[9 * int64_t(k) + b1]);
+            s2 *= T(lam[9 * int64_t(j) + a2] * lam[9 * int64_t(k) + b2]);
+        }
         const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
         S[s_at(tile_ptr, j, qj, e0)] = -s0;
         S[s_at(tile_ptr, j, qj, e1)] = -s1;
@@ -496,17 +502,6 @@ __global__ void k_put_diag(int32_t n_c, const int64_t* __restrict__ row_ptr, con
         double v = Sd[i];
         if (lam) v *= lam[9 * j + e / 9] * lam[9 * j + e % 9];
         S[s_at(tile_ptr, j, diag_pos[j] - row_ptr[j], e)] = T(v);
-    }
-}
-
-// G32_o = float(Lam_cam(o) G_o): the observation blocks of the scaled system (point order: the two
-// observations of a pair belong to one landmark, so their blocks lie close together)
-__global__ void k_scale_G(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
-                          const double* __restrict__ lam, float* __restrict__ G32) {
-    for (int64_t i = gtid(); i < n_o * 27; i += gstride()) {
-        const int64_t o = i / 27;
-        const int a = int(i - o * 27) / 3;
-        G32[i] = float(lam[9 * int64_t(oc[o]) + a] * G[i]);
     }
 }
 
@@ -794,16 +789,18 @@ void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
     if (s.n_up > 0)
         k_schur_off<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, s.row_ptr, s.tile_ptr, y.S);
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, nullptr, s.row_ptr, s.tile_ptr,
+            y.S);
     k_put_diag<double><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S);
 }
 
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
-    k_scale_G<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, y.lam, y.G32);
+    k_to_float<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(y.G, y.G32, s.n_o * 27);
     if (s.n_up > 0)
         k_schur_off<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, s.row_ptr, s.tile_ptr, y.S32);
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, y.lam, s.row_ptr, s.tile_ptr,
+            y.S32);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32);
 }

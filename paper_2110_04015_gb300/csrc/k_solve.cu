@@ -907,16 +907,20 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
     __syncthreads();
     const int m = (w + 1) & ~1;   // even player count (index w is a dummy when w is odd)
     for (int sweep = 0; sweep < 30 && w > 1; ++sweep) {
-        if (t == 0) {
+        if (t < 32) {
             double o = 0.0, a = 0.0;
-            for (int x = 0; x < w; ++x)
-                for (int y = 0; y < w; ++y) {
-                    double v = sA[x][y] * sA[x][y];
-                    a += v;
-                    if (x != y) o += v;
-                }
-            off_norm = o;
-            tot_norm = a;
+            for (int e = t; e < w * w; e += 32) {
+                const int x = e / w, y = e % w;
+                const double v = sA[x][y] * sA[x][y];
+                a += v;
+                if (x != y) o += v;
+            }
+            o = warp_sum(o);
+            a = warp_sum(a);
+            if (t == 0) {
+                off_norm = o;
+                tot_norm = a;
+            }
         }
         __syncthreads();
         if (!(off_norm > 1e-30 * tot_norm)) break;
