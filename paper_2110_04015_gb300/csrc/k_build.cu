@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const i
 // entries are e = lane, lane + 32, lane + 64 (< 81).  The warp takes the pairs kChunk at a time:
 // lanes 0..26 load the two 27-value G blocks of every pair of the chunk (one coalesced load per
 // block, all of the chunk's loads in flight together), stage them in shared memory, and every
-// lane then accumulates its entries over the chunk's pairs in order.  With lam (the float32
+// lane then accumulates its entries over the chunk's pairs in order (lane p fetches the indices of
+// pair p; 16-pair chunks measured no faster).  With lam (the float32
 // system), the finished block is scaled to Lam_j S_jk Lam_k.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_schur_off(
