@@ -107,6 +107,41 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum of products a_i b_i of float32 (or float64) values.  float64: plain float64 accumulation.
+// float32: each product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p)) and added to
+// a float pair (hi, lo) with an error-free two-sum, so the sum keeps about 48 bits without
+// float64 arithmetic, which runs at a small fraction of the float32 rate on this GPU.
+template <typename T>
+struct ExactSum;
+template <>
+struct ExactSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct ExactSum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(hi, p);
+        const float bv = __fsub_rn(t, hi);
+        const float te = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(te, pe));
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+// sum_k x[k * xs] y[k * ys] for k < n
+template <typename T>
+__device__ __forceinline__ double dot_rows(const T* x, int xs, const T* y, int ys, int n) {
+    ExactSum<T> s;
+    for (int k = 0; k < n; ++k) s.add(x[k * xs], y[k * ys]);
+    return s.value();
+}
+
 // Sum `nv` values per thread over the CTA; threads 0..NV-1 write them to out[0..NV) (global or
 // shared memory), visible to the whole CTA on return.
 template <int NV>
@@ -153,6 +188,7 @@ struct ItemList {
     int64_t n = 0;
     int* cnt = nullptr;       // one per group, zero between launches
     void* part = nullptr;     // n x 9 partial sums (element type of the product)
+    int nprob = 0;            // problems the list covers
 };
 
 // Which problems a product serves: every live one, those forming a global (local) block, or those
@@ -169,6 +205,15 @@ __device__ __forceinline__ bool selected(const Ctl* ctl, int prob, int sel) {
         case kSelWide: return c.w_new > 1;
         default: return true;
     }
+}
+
+// true when no problem of the list is selected (checked for small batches only; every warp of the
+// CTA reaches the same answer, so the whole CTA may return)
+__device__ __forceinline__ bool nothing_selected(const Ctl* ctl, const ItemList& L, int sel) {
+    if (L.nprob > 64) return false;
+    bool any = false;
+    for (int b = threadIdx.x & 31; b < L.nprob; b += 32) any = any || selected(ctl, b, sel);
+    return !__any_sync(0xffffffffu, any);
 }
 
 // Sum the CTA's NV values, publish them as partial[blockIdx.x], and let the last CTA of the grid
@@ -299,6 +344,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
     const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl) {
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    if (nothing_selected(ctl, L, sel)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
@@ -467,6 +513,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
     constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
     constexpr int sel = kSelWide;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    if (nothing_selected(ctl, L, sel)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int qi = lane >> 2, g = lane & 3;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
@@ -871,15 +918,10 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
         for (int h = 0; h < 2; ++h) {
             const int e = threadIdx.x + h * blockDim.x;
             if (e < ne) {
-                double s = 0.0;
-                if (e < w * w) {
-                    const int a = e / w, b = e % w;
-                    for (int k = 0; k < rows; ++k) s += double(sQ[k][a]) * double(sP[k][b]);
-                } else {
-                    const int a = e - w * w;
-                    for (int k = 0; k < rows; ++k) s += double(sP[k][a]) * double(sr[k]);
-                }
-                acc[h] += s;
+                const T* x = e < w * w ? &sQ[0][e / w] : &sP[0][e - w * w];
+                const T* y = e < w * w ? &sP[0][e % w] : &sr[0];
+                const int ys = e < w * w ? kMaxDirs + 1 : 1;
+                acc[h] += dot_rows(x, kMaxDirs + 1, y, ys, rows);
             }
         }
         __syncthreads();
@@ -1014,6 +1056,7 @@ __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxD
                                   double (*sX)[kMaxDirs + 1], int w) {
     __shared__ int ok;
     __shared__ double fro, tr;
+    __shared__ double rdiag[kMaxDirs];   // 1 / L_kk: one float64 division per pivot
     const int t = threadIdx.x;
     const int i = t / kMaxDirs, j = t % kMaxDirs;
     if (t < kMaxDirs * kMaxDirs) sL[i][j] = (i < w && j < w && j <= i) ? sA[i][j] : 0.0;
@@ -1031,9 +1074,10 @@ __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxD
             const double d = sL[k][k];
             if (!(d > 0.0)) ok = 0;
             sL[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+            rdiag[k] = 1.0 / sL[k][k];
         }
         __syncthreads();
-        if (t > k && t < w) sL[t][k] /= sL[k][k];
+        if (t > k && t < w) sL[t][k] *= rdiag[k];
         __syncthreads();
         if (t < kMaxDirs * kMaxDirs && i > k && j > k && j <= i && i < w) sL[i][j] -= sL[i][k] * sL[j][k];
         __syncthreads();
@@ -1045,7 +1089,7 @@ __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxD
         for (int r = 0; r < w; ++r) {
             double v = (r == c) ? 1.0 : 0.0;
             for (int k = c; k < r; ++k) v -= sL[r][k] * sX[k][c];
-            sX[r][c] = r < c ? 0.0 : v / sL[r][r];
+            sX[r][c] = r < c ? 0.0 : v * rdiag[r];
         }
     }
     __syncthreads();
@@ -1269,12 +1313,11 @@ __global__ void k_mcg_phi(const T* __restrict__ Q, const T* __restrict__ z, doub
         int j1 = j0 + cz;
         const int send = (s + 1) * sz < nc ? (s + 1) * sz : nc;
         if (j1 > send) j1 = send;
-        double acc = 0.0;
         const T* qc = Qp + cc * n;
-        for (int64_t row = int64_t(j0) * 9 + lane; row < int64_t(j1) * 9; row += 32)
-            acc += double(qc[row]) * double(zp[row]);
-        acc = warp_sum(acc);
-        if (lane == 0) ph[it] = acc;
+        ExactSum<T> acc;
+        for (int64_t row = int64_t(j0) * 9 + lane; row < int64_t(j1) * 9; row += 32) acc.add(qc[row], zp[row]);
+        const double sum = warp_sum(acc.value());
+        if (lane == 0) ph[it] = sum;
     }
 }
 
@@ -1700,6 +1743,7 @@ static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
     L.items = d;
     L.n = int64_t(v.size());
     const int ngrp = v.empty() ? 1 : v.back().grp + 1;
+    L.nprob = v.empty() ? 0 : v.back().prob + 1;
     BA_CUDA_TRY(cudaMalloc(&L.cnt, sizeof(int) * ngrp));
     BA_CUDA_TRY(cudaMemset(L.cnt, 0, sizeof(int) * ngrp));
     BA_CUDA_TRY(cudaMalloc(&L.part, sizeof(double) * 9 * (v.size() > 0 ? v.size() : 1)));
