@@ -158,6 +158,29 @@ def test_mixed_precision_schur_matches_oracle_to_float32():
     assert rel_max(bt, lin.btilde) < 1e-9   # b~ stays float64
 
 
+@pytest.mark.parametrize("case", ["tiny", "seq-small", "dense-small"])
+def test_mixed_precision_camera_sums_match_oracle(case):
+    """In mixed precision U, b_p, b~ and the diagonal blocks S_jj are summed in float pairs (about
+    48 significant bits), not float64: they must still agree with the float64 oracle far below the
+    float32 level."""
+    sc = scene(case)
+    m, lin, _ = oracle_system(case)
+    with problem.from_scene(sc, precision="mixed") as p:
+        p.ba_build_normal(1e-4)
+        U, _, bp, _ = p.ba_get_normal()
+        row_ptr, col, B, bt = p.ba_get_schur()
+    assert rel_max(U, lin.ne.U) < 1e-12
+    assert rel_max(bp, lin.ne.b_p) < 1e-12
+    assert rel_max(bt, lin.btilde) < 1e-9
+    Sb = lin.S.tobsr(blocksize=(9, 9))
+    Sb.sort_indices()
+    for j in range(sc.n_cams):
+        qd = row_ptr[j] + np.searchsorted(col[row_ptr[j]:row_ptr[j + 1]], j)
+        qo = Sb.indptr[j] + np.searchsorted(Sb.indices[Sb.indptr[j]:Sb.indptr[j + 1]], j)
+        ref = Sb.data[qo]
+        assert np.abs(B[qd] - ref).max() < 1e-9 * np.abs(ref).max(), j
+
+
 def test_duplicate_observations_are_rejected():
     from paper_2110_04015_gb300 import binding
 
