@@ -132,14 +132,33 @@ struct ExactSum<float> {
         lo = __fadd_rn(lo, __fadd_rn(te, pe));
     }
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+    // add another pair (h, l): error-free two-sum of the high parts, low parts added
+    __device__ __forceinline__ void add_pair(float h, float l) {
+        const float t = __fadd_rn(hi, h);
+        const float bv = __fsub_rn(t, hi);
+        const float te = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(h, bv));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(te, l));
+    }
 };
 
-// sum_k x[k * xs] y[k * ys] for k < n
+// s += sum_k x[k * xs] y[k * ys] for k < n
 template <typename T>
-__device__ __forceinline__ double dot_rows(const T* x, int xs, const T* y, int ys, int n) {
-    ExactSum<T> s;
+__device__ __forceinline__ void dot_rows(ExactSum<T>& s, const T* x, int xs, const T* y, int ys, int n) {
     for (int k = 0; k < n; ++k) s.add(x[k * xs], y[k * ys]);
-    return s.value();
+}
+
+// A Gram partial sum as stored between the Gram and the small-solve kernels: float64, or (for the
+// float32 sweeps) the float pair (hi, lo) in the same 8 bytes, so that adding the partials needs no
+// float64 arithmetic either.
+__device__ __forceinline__ void store_partial(double* slot, const ExactSum<double>& s) { *slot = s.value(); }
+__device__ __forceinline__ void store_partial(double* slot, const ExactSum<float>& s) {
+    *reinterpret_cast<float2*>(slot) = make_float2(s.hi, s.lo);
+}
+__device__ __forceinline__ void load_partial(ExactSum<double>& s, const double* slot) { s.s += *slot; }
+__device__ __forceinline__ void load_partial(ExactSum<float>& s, const double* slot) {
+    const float2 v = *reinterpret_cast<const float2*>(slot);
+    s.add_pair(v.x, v.y);
 }
 
 // Sum `nv` values per thread over the CTA; threads 0..NV-1 write them to out[0..NV) (global or
@@ -899,7 +918,7 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
     const int64_t per = (n + gp - 1) / gp;
     const int64_t r0 = int64_t(blockIdx.x) * per;
     const int64_t r1 = r0 + per < n ? r0 + per : n;
-    double acc[2] = {0.0, 0.0};   // entries threadIdx.x and threadIdx.x + 256
+    ExactSum<T> acc[2];   // entries threadIdx.x and threadIdx.x + 256
     for (int64_t base = r0; base < r1; base += TR) {
         const int rows = int(r1 - base < TR ? r1 - base : TR);
         for (int t = threadIdx.x; t < TR * kMaxDirs; t += blockDim.x) {
@@ -921,7 +940,7 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
                 const T* x = e < w * w ? &sQ[0][e / w] : &sP[0][e - w * w];
                 const T* y = e < w * w ? &sP[0][e % w] : &sr[0];
                 const int ys = e < w * w ? kMaxDirs + 1 : 1;
-                acc[h] += dot_rows(x, kMaxDirs + 1, y, ys, rows);
+                dot_rows(acc[h], x, kMaxDirs + 1, y, ys, rows);
             }
         }
         __syncthreads();
@@ -930,7 +949,7 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int e = threadIdx.x + h * blockDim.x;
-        if (e < ne) out[e] = acc[h];
+        if (e < ne) store_partial(out + e, acc[h]);
     }
 }
 
@@ -1121,6 +1140,7 @@ __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxD
 
 // Delta_i, gamma_i -> Delta_i^+ (stored for the reorthogonalisation), alpha_i, gamma^T alpha.
 // One CTA per problem; gx is the width of the Gram grid.
+template <typename T>
 __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx, double* __restrict__ dpinv,
                             int mi1) {
     const int p = blockIdx.x;
@@ -1136,8 +1156,9 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx
     const double* part = partial + int64_t(p) * gx * kGramMax;
     // one thread per entry sums the CTA partials in CTA order (independent loads, no shuffles)
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < np; ++b) s += part[int64_t(b) * kGramMax + e];
+        ExactSum<T> acc;
+        for (int b = 0; b < np; ++b) load_partial(acc, part + int64_t(b) * kGramMax + e);
+        const double s = acc.value();
         if (e < w * w) sA[e / w][e % w] = s;
         else sg[e - w * w] = s;
     }
@@ -1927,7 +1948,7 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
     } else {
         k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
-        k_mcg_small<<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
+        k_mcg_small<T><<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
         k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu,
                                                                dcnt, totals, ctl);
         k_mcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist), ptr<int>(w->blk_off), ptr<int>(w->blk_w),
