@@ -4,7 +4,8 @@
 // Algorithm 1 (block-Jacobi PCG) and Algorithm 2 (MCG) run as a fixed sequence of kernels per
 // iteration.  All data-dependent control (the stop test, the tau-test and the width of the next
 // direction block, the history size) lives in one device struct Ctl per problem, written only by
-// the per-problem "decide" kernels and read by the others, so a chunk of iterations is captured
+// the per-problem "decide" steps (run by the CTA that finalises an update kernel's sums, and by the
+// small solve) and read by the others, so a chunk of iterations is captured
 // once as a CUDA graph and replayed; the host reads the Ctl array back once per chunk.  A problem
 // whose Ctl::done is set is skipped by every later launch while the others go on.
 //
@@ -237,9 +238,10 @@ __device__ __forceinline__ bool nothing_selected(const Ctl* ctl, const ItemList&
 
 // Sum the CTA's NV values, publish them as partial[blockIdx.x], and let the last CTA of the grid
 // row to finish write the row's totals (in CTA order) to totals[0..NV).  Every CTA of the grid
-// row must call it.
+// row must call it.  Returns true (in every thread) in the CTA that wrote the totals, after they
+// are visible to the whole CTA.
 template <int NV>
-__device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* partial, int* cnt, double* totals) {
+__device__ __forceinline__ bool grid_sum_finalize(double (&v)[NV], double* partial, int* cnt, double* totals) {
     __shared__ double red[kThreads / 32][NV];
     __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -258,15 +260,16 @@ __device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* parti
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(cnt, 1) == int(gridDim.x) - 1);
     __syncthreads();
-    if (last) {
-        __threadfence();
-        if (threadIdx.x < NV) {
-            double s = 0.0;
-            for (int b = 0; b < int(gridDim.x); ++b) s += __ldcg(partial + int64_t(b) * NV + threadIdx.x);
-            totals[threadIdx.x] = s;
-        }
-        if (threadIdx.x == 0) *cnt = 0;
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int b = 0; b < int(gridDim.x); ++b) s += __ldcg(partial + int64_t(b) * NV + threadIdx.x);
+        totals[threadIdx.x] = s;
     }
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    return true;
 }
 
 // ---- bulk copies (cp.async.bulk + mbarrier) --------------------------------------------
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
     }
     if (bad) {
         // a copy did not land in time: report, then wait (bounded) for this warp's copies in flight;
-        // the problem's next decide kernel ends it with the status
+        // the problem's next decide step ends it with the status
         if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
             if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
@@ -782,9 +785,12 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
 // ---------------------------------------------------------------------------------------
 // Algorithm 1 (grid: CTAs x problems)
 
-// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2, q^T z, r^T z.
+__device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int nb);
+
+// alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2, q^T z, r^T z,
+// then (the CTA that finalises the totals) the stop test and beta.
 // Delta and gamma are the sums over the problem's cameras (camera order) of the per-camera sums
-// of the product; every CTA forms them the same way, CTA 0 stores them for the decide kernel.
+// of the product; every CTA forms them the same way, CTA 0 stores them for the decide step.
 // Thread = one row (9 per camera, kUpdCams cameras per CTA); the rows of a camera meet in
 // shared memory for z = D^{-1} r.  CTA b of a problem takes its cameras [b kUpdCams, ...), so the
 // partition depends on the problem alone (the grid has a CTA for every chunk of the largest).
@@ -794,7 +800,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
                                                          T* __restrict__ r, T* __restrict__ z,
                                                          const double* __restrict__ camdot,
                                                          double* __restrict__ totals, double* __restrict__ dpart,
-                                                         int* __restrict__ dcnt, const Ctl* __restrict__ ctl) {
+                                                         int* __restrict__ dcnt, double* __restrict__ hist,
+                                                         Ctl* ctl) {
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -842,16 +849,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
         v[1] = double(qv) * double(zs);
         v[2] = double(rv) * double(zs);
     }
-    grid_sum_finalize<3>(v, dpart + int64_t(p) * gridDim.x * 3, dcnt + 4 * p, tot + 2);
+    if (grid_sum_finalize<3>(v, dpart + int64_t(p) * gridDim.x * 3, dcnt + 4 * p, tot + 2) && threadIdx.x == 0)
+        pcg_decide(ctl + p, tot, hist, p, gridDim.y);
 }
 
-// stop test and beta = Phi / Delta (one thread per problem); hist is iteration-major (it x nb)
-__global__ void k_pcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist) {
-    const int p = blockIdx.x;
-    Ctl* c = ctl + p;
-    if (c->done || threadIdx.x != 0) return;
+// stop test and beta = Phi / Delta for problem p (one thread, after the update's totals are in);
+// hist is iteration-major (it x nb)
+__device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int nb) {
     if (c->status == BA_ERR_TIMEOUT) { c->done = 1; return; }
-    const double* tot = totals + int64_t(p) * kTotals;
     const double D = tot[0], g = tot[1], rr = tot[2], phi = tot[3];
     const int it = c->it + 1;
     c->it = it;
@@ -859,7 +864,7 @@ __global__ void k_pcg_decide(Ctl* ctl, const double* __restrict__ totals, double
     c->gamma = g;
     c->alpha = g / D;
     c->rr = rr;
-    hist[int64_t(it - 1) * gridDim.x + p] = sqrt(rr / c->rr0);
+    hist[int64_t(it - 1) * nb + p] = sqrt(rr / c->rr0);
     if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -1196,14 +1201,19 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx
     }
 }
 
-// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z (grid: CTAs x problems;
+__device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off, int* blk_w, int mi1, int p, int nb);
+
+// x += P_i alpha; r -= Q_i alpha; z = D^{-1} r; totals of |r|^2 and r^T z, then (last CTA) the
+// decide step (grid: CTAs x problems;
 // thread = one row, as in k_pcg_update).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restrict__ Dinv, const T* __restrict__ P,
                                                          const T* __restrict__ Q, T* __restrict__ x,
                                                          T* __restrict__ r, T* __restrict__ z,
                                                          double* __restrict__ dpart, int* __restrict__ dcnt,
-                                                         double* __restrict__ totals, const Ctl* __restrict__ ctl) {
+                                                         double* __restrict__ totals, double* __restrict__ hist,
+                                                         int* __restrict__ blk_off, int* __restrict__ blk_w, int mi1,
+                                                         Ctl* ctl) {
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1245,23 +1255,21 @@ __global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restric
         z[i] = zs;
         v[1] = double(rv) * double(zs);
     }
-    grid_sum_finalize<2>(v, dpart + int64_t(p) * gridDim.x * 2, dcnt + 4 * p + 1, totals + int64_t(p) * kTotals + 8);
+    double* tot = totals + int64_t(p) * kTotals + 8;
+    if (grid_sum_finalize<2>(v, dpart + int64_t(p) * gridDim.x * 2, dcnt + 4 * p + 1, tot) && threadIdx.x == 0)
+        mcg_decide(ctl + p, tot, hist, blk_off, blk_w, mi1, p, gridDim.y);
 }
 
-// stop test, tau-test and the layout of the next block (one thread per problem)
-__global__ void k_mcg_decide(Ctl* ctl, const double* __restrict__ totals, double* hist, int* blk_off, int* blk_w,
-                             int mi1) {
-    const int p = blockIdx.x;
-    Ctl* c = ctl + p;
-    if (c->done || threadIdx.x != 0) return;
+// stop test, tau-test and the layout of the next block for problem p (one thread, after the
+// update's totals are in)
+__device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off, int* blk_w, int mi1, int p, int nb) {
     if (c->status == BA_ERR_TIMEOUT) { c->done = 1; return; }
-    const double* tot = totals + int64_t(p) * kTotals + 8;
     const double rr = tot[0], rz = tot[1];
     const int it = c->it + 1;
     c->it = it;
     c->rr = rr;
     c->rz = rz;
-    hist[int64_t(it - 1) * gridDim.x + p] = sqrt(rr / c->rr0);
+    hist[int64_t(it - 1) * nb + p] = sqrt(rr / c->rr0);
     if (!(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -1943,16 +1951,14 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_spmv<T, 1, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
             s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelLive, Q, r, ptr<double>(w->camdot), ctl);
         k_pcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
-                                                               ptr<double>(w->dpart), dcnt, ctl);
-        k_pcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist));
+                                                               ptr<double>(w->dpart), dcnt, ptr<double>(w->hist), ctl);
         k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
     } else {
         k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
         k_mcg_small<T><<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
-        k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu,
-                                                               dcnt, totals, ctl);
-        k_mcg_decide<<<nb, 32, 0, st>>>(ctl, totals, ptr<double>(w->hist), ptr<int>(w->blk_off), ptr<int>(w->blk_w),
-                                        w->mi1);
+        k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(
+            Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu, dcnt, totals, ptr<double>(w->hist),
+            ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1, ctl);
         k_mcg_phi<T><<<dim3(w->gphi, nb), kThreads, 0, st>>>(Q, z, ptr<double>(w->phip), ctl);
         k_mcg_beta<<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
                                                          ptr<int>(w->blk_off), ptr<int>(w->blk_w),
@@ -1979,8 +1985,8 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
 }
 
 static int iteration_launches(bool mcg, bool fp32, bool two_lists) {
-    if (!mcg) return 4;
-    return fp32 ? 9 : (two_lists ? 9 : 8);
+    if (!mcg) return 3;
+    return fp32 ? 8 : (two_lists ? 8 : 7);
 }
 
 // x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0.
