@@ -302,6 +302,7 @@ void alloc_system(ba_problem* p) {
         y.tl = dev_alloc<double>(p, size_t(s.n_l) * 3);
         y.uo = dev_alloc<double>(p, size_t(s.n_o) * 3);
         y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
+        y.lam32 = dev_alloc<float>(p, size_t(s.n_c) * 9);
         y.Dhat = dev_alloc<double>(p, size_t(s.n_c) * 81);
     }
     y.status = dev_alloc<int>(p, 1);
@@ -338,7 +339,7 @@ void do_build(ba_problem* p, double lambda) {
         ba::launch_schur(s, y, st);          // off-diagonal blocks + the diagonal from Sd
         p->launches += 2;
     } else {
-        ba::launch_schur_mixed(s, y, st);    // float32 G, off-diagonal and diagonal blocks of S^
+        ba::launch_schur_mixed(s, y, st);    // float32 Lam G, off-diagonal and diagonal blocks of S^
         p->launches += 4;
     }
     check_launch();

@@ -117,7 +117,8 @@ struct System {
     float* S32 = nullptr;     // float(S^), tiled layout
     double* lam = nullptr;    // 9 n_c: Lam
     double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
-    float* G32 = nullptr;     // n_o x 27: float(G_o); the float32 Schur build scales each finished block
+    float* lam32 = nullptr;   // 9 n_c: float(Lam)
+    float* G32 = nullptr;     // n_o x 27: rows of Lam G_o in float32 (row a scaled by Lam_cam(o),a)
     double* tl = nullptr;     // n_l x 3: landmark sums of the implicit product G^T x
     double* uo = nullptr;     // n_o x 3: per-observation terms G_o^T x_cam(o) of those sums
     int* status = nullptr;    // device error word of the build

@@ -5,9 +5,12 @@
 //   k_obs_G         one thread per observation: G_o = (J_p^T J_l) L^{-T}
 //   k_cameras       one CTA per camera: U_lambda, b_p, b~ = b_p - sum G_o e_l
 //   k_schur_diag    one CTA per camera: S_jj = U_j - sum_o G_o G_o^T (float64)
-//   k_schur_off     one warp per upper block (j < k): S_jk = - sum G_oj G_ok^T over the observation
-//                   pairs of shared landmarks, written to (j, k) and transposed to (k, j)
+//   k_schur_off_*   one warp per upper block (j < k): S_jk = - sum G_oj G_ok^T over the observation
+//                   pairs of shared landmarks, written to (j, k) and transposed to (k, j); float64:
+//                   three entries per lane (_rows), float32: a 3x3 sub-block and a third of the
+//                   pairs per lane (_sub)
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
+//   k_scaled_g32    float32 rows of Lam G for the scaled float32 system
 //   k_implicit_*    the float64 product S x = U x - G (G^T x) without an explicit S
 // S is written in the tiled layout of ba_internal.cuh (s_at).
 // Every kernel uses grid-stride loops and 64-bit indices.
@@ -418,20 +421,20 @@ __global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const i
     }
 }
 
-// Off-diagonal blocks: one warp per upper block (j < k), S_jk = - sum over the observation pairs
-// (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to (k, j).  Lane
-// entries are e = lane, lane + 32, lane + 64 (< 81).  The warp takes the pairs kChunk at a time:
+// Off-diagonal blocks in float64: one warp per upper block (j < k), S_jk = - sum over the
+// observation pairs (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to
+// (k, j).  Lane entries are e = lane, lane + 32, lane + 64 (< 81), so every lane works on every
+// pair (the float64 multiply-adds bound this kernel).  The warp takes the pairs kChunk at a time:
 // lanes 0..26 load the two 27-value G blocks of every pair of the chunk (one coalesced load per
 // block, all of the chunk's loads in flight together), stage them in shared memory, and every
 // lane then accumulates its entries over the chunk's pairs in order (lane p fetches the indices of
-// pair p; 16-pair chunks measured no faster).  With lam (the float32
-// system), the finished block is scaled to Lam_j S_jk Lam_k.
+// pair p; 16-pair chunks measured no faster).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_schur_off(
+__global__ void __launch_bounds__(kThreads) k_schur_off_rows(
     int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
     const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
-    const int2* __restrict__ pairs, const T* __restrict__ G, const double* __restrict__ lam,
-    const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
+    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
     constexpr int kChunk = 8;
     __shared__ T sg[kThreads / 32][kChunk][2][28];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -477,11 +480,6 @@ __global__ void __launch_bounds__(kThreads) k_schur_off(
             }
         }
         const int j = up_j[u], k = up_k[u];
-        if (lam) {
-            s0 *= T(lam[9 * int64_t(j) + a0] * lam[9 * int64_t(k) + b0]);
-            s1 *= T(lam[9 * int64_t(j) + a1] * lam[9 * int64_t(k) + b1]);
-            s2 *= T(lam[9 * int64_t(j) + a2] * lam[9 * int64_t(k) + b2]);
-        }
         const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
         S[s_at(tile_ptr, j, qj, e0)] = -s0;
         S[s_at(tile_ptr, j, qj, e1)] = -s1;
@@ -489,6 +487,111 @@ __global__ void __launch_bounds__(kThreads) k_schur_off(
         S[s_at(tile_ptr, k, qk, b0 * 9 + a0)] = -s0;
         S[s_at(tile_ptr, k, qk, b1 * 9 + a1)] = -s1;
         if (has2) S[s_at(tile_ptr, k, qk, b2 * 9 + a2)] = -s2;
+    }
+}
+
+// Nine consecutive values from a 16-byte aligned shared-memory address.
+__device__ __forceinline__ void lds9(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    v[8] = p[8];
+}
+
+// Off-diagonal blocks in float32: one warp per upper block (j < k), S_jk = - sum over the
+// observation pairs (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to
+// (k, j).  Lane 9 g + 3 A + B (g < 3) accumulates the 3x3 sub-block at rows 3A.., columns 3B.. over the
+// pairs p = g (mod 3): it needs rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok, nine consecutive
+// values each, so one pair costs the lane two runs of vector shared loads for 27 fused
+// multiply-adds.  The warp takes the pairs kChunk at a time: lanes 0..26 load the two 27-value G
+// blocks of every pair of the chunk (one coalesced load per block, all of the chunk's loads in
+// flight together; lane p fetches the indices of pair p) and stage them in shared memory, each
+// 9-value part on a 16-byte boundary.  The three slices are added in slice order through shuffles,
+// the block is assembled in shared memory and written with coalesced stores to (j, k) and,
+// transposed, to (k, j).  For the scaled float32 system G holds the rows of Lam G (k_scaled_g32),
+// so the same sums give Lam_j S_jk Lam_k.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_schur_off_sub(
+    int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
+    const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
+    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
+    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
+    constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
+    constexpr int kPart = 12;                          // stride of a 9-value part (16-byte aligned)
+    __shared__ __align__(16) T sg[kThreads / 32][kChunk][2][3 * kPart];
+    __shared__ T sb[kThreads / 32][81];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = gstride() >> 5;
+    const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31 only load
+    const int A = sub / 3, B = sub - 3 * (sub / 3);
+    const int stage = (lane / 9) * kPart + lane % 9;   // where G entry `lane` (< 27) is staged
+    for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
+        T acc[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) acc[i] = T(0);
+        const int64_t pb = pair_ptr[u], pe = pair_ptr[u + 1];
+        for (int64_t q = pb; q < pe; q += kChunk) {
+            const int np = int(pe - q < kChunk ? pe - q : kChunk);
+            int2 pr = make_int2(0, 0);
+            if (lane < np) pr = pairs[q + lane];
+            T ga[kChunk], gb[kChunk];
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) {
+                const int ox = __shfl_sync(0xffffffffu, pr.x, p);
+                const int oy = __shfl_sync(0xffffffffu, pr.y, p);
+                ga[p] = T(0);
+                gb[p] = T(0);
+                if (p < np && lane < 27) {
+                    ga[p] = __ldg(G + 27 * int64_t(ox) + lane);
+                    gb[p] = __ldg(G + 27 * int64_t(oy) + lane);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < kChunk; ++p) {
+                if (lane < 27) {
+                    sg[wid][p][0][stage] = ga[p];
+                    sg[wid][p][1][stage] = gb[p];
+                }
+            }
+            __syncwarp();
+            if (g < 3) {
+                for (int p = g; p < np; p += 3) {
+                    T x[9], y[9];
+                    lds9(&sg[wid][p][0][A * kPart], x);
+                    lds9(&sg[wid][p][1][B * kPart], y);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            acc[3 * r + c] += x[3 * r] * y[3 * c] + x[3 * r + 1] * y[3 * c + 1] + x[3 * r + 2] * y[3 * c + 2];
+                }
+            }
+        }
+        // slices 1 and 2 (lanes 9..26) onto slice 0 (lanes 0..8)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const T v1 = __shfl_down_sync(0xffffffffu, acc[i], 9);
+            const T v2 = __shfl_down_sync(0xffffffffu, acc[i], 18);
+            acc[i] = (acc[i] + v1) + v2;
+        }
+        if (lane < 9) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) sb[wid][(3 * A + r) * 9 + 3 * B + c] = acc[3 * r + c];
+        }
+        __syncwarp();
+        const int j = up_j[u], k = up_k[u];
+        const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
+        for (int e = lane; e < 81; e += 32) S[s_at(tile_ptr, j, qj, e)] = -sb[wid][e];
+        for (int e = lane; e < 81; e += 32) {
+            const int b = e / 9, a = e - 9 * (e / 9);   // entry e = 9 b + a of (k, j) is (a, b) of (j, k)
+            S[s_at(tile_ptr, k, qk, e)] = -sb[wid][9 * a + b];
+        }
+        __syncwarp();
     }
 }
 
@@ -602,9 +705,9 @@ __global__ void __launch_bounds__(kCamThreads) k_implicit_res(
 
 // D_j^{-1} = (S_jj)^{-1} = L^{-T} L^{-1} from the Cholesky factor of the diagonal block.
 // With lam != nullptr the block is first scaled by its diagonal, B^ = s B s with s_a = B_aa^{-1/2};
-// Dinv then receives (B^)^{-1} and lam the scale factors.
+// Dinv then receives (B^)^{-1}, lam the scale factors and lam32 their float32 roundings.
 __global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, double* __restrict__ Dinv,
-                               double* __restrict__ lam, int* status) {
+                               double* __restrict__ lam, float* __restrict__ lam32, int* status) {
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
         double L[81];
         for (int e = 0; e < 81; ++e) L[e] = Sd[81 * j + e];
@@ -613,6 +716,7 @@ __global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, doubl
             for (int a = 0; a < 9; ++a) {
                 sc[a] = L[9 * a + a] > 0.0 ? 1.0 / sqrt(L[9 * a + a]) : 1.0;
                 lam[9 * j + a] = sc[a];
+                lam32[9 * j + a] = float(sc[a]);
             }
             for (int a = 0; a < 9; ++a)
                 for (int b = 0; b < 9; ++b) L[9 * a + b] *= sc[a] * sc[b];
@@ -656,6 +760,18 @@ __global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, doubl
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
     for (int64_t i = gtid(); i < n; i += gstride()) out[i] = static_cast<float>(in[i]);
+}
+
+// G32 = rows of Lam G in float32: entry (a, t) of G_o becomes float(G_o,at) float(Lam_cam(o),a).
+// Rounding G first and scaling in float32 keeps the float64 pipe to one conversion per value
+// (the product adds at most one more float32 rounding).
+__global__ void k_scaled_g32(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
+                             const float* __restrict__ lam32, float* __restrict__ G32) {
+    for (int64_t i = gtid(); i < n_o * 27; i += gstride()) {
+        const int64_t o = i / 27;
+        const int a = int(i - 27 * o) / 3;
+        G32[i] = static_cast<float>(G[i]) * lam32[9 * int64_t(oc[o]) + a];
+    }
 }
 
 // dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
@@ -789,19 +905,17 @@ void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
 
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
     if (s.n_up > 0)
-        k_schur_off<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, nullptr, s.row_ptr, s.tile_ptr,
-            y.S);
+        k_schur_off_rows<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, s.row_ptr, s.tile_ptr, y.S);
     k_put_diag<double><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S);
 }
 
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
-    k_to_float<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(y.G, y.G32, s.n_o * 27);
+    k_scaled_g32<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, y.lam32, y.G32);
     if (s.n_up > 0)
-        k_schur_off<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, y.lam, s.row_ptr, s.tile_ptr,
-            y.S32);
+        k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
+            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, s.row_ptr, s.tile_ptr, y.S32);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32);
 }
@@ -819,8 +933,8 @@ void launch_cam_prep(const Structure& s, System& y, cudaStream_t st) {
 }
 
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
-    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dinv, nullptr, y.status);
-    if (y.S32) k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dhat, y.lam, y.status);
+    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dinv, nullptr, nullptr, y.status);
+    if (y.S32) k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dhat, y.lam, y.lam32, y.status);
 }
 
 
