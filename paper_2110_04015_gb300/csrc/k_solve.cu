@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -72,7 +73,8 @@ struct Ctl {
     int w_cur;         // width of the current block (set by decide for the next gram)
     int off_cur;
     double rr0, rr, rz, ga, tol2, tau;
-    double Delta, gamma, alpha, beta;   // PCG scalars
+    double rr0_inv;    // 1 / rr0: the residual history stores rr / rr0 without a division per step
+    double Delta, gamma, beta;          // PCG scalars
     double alpha_v[kMaxDirs];
     double true_rr, bb;                 // true residual and |rhs|^2
     double stag;       // float32 sweeps: stop when t_i (energy decrease / r^T D^-1 r) falls below this
@@ -157,9 +159,26 @@ __device__ __forceinline__ void store_partial(double* slot, const ExactSum<float
     *reinterpret_cast<float2*>(slot) = make_float2(s.hi, s.lo);
 }
 __device__ __forceinline__ void load_partial(ExactSum<double>& s, const double* slot) { s.s += *slot; }
+__device__ __forceinline__ void combine(ExactSum<double>& a, const ExactSum<double>& b) { a.s += b.s; }
+__device__ __forceinline__ void combine(ExactSum<float>& a, const ExactSum<float>& b) { a.add_pair(b.hi, b.lo); }
+// a += the same sum held by lane (lane ^ o) (every lane of the warp calls this)
+__device__ __forceinline__ void combine_shfl(ExactSum<double>& a, int o) { a.s += __shfl_xor_sync(0xffffffffu, a.s, o); }
+__device__ __forceinline__ void combine_shfl(ExactSum<float>& a, int o) {
+    const float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a.add_pair(h, l);
+}
 __device__ __forceinline__ void load_partial(ExactSum<float>& s, const double* slot) {
     const float2 v = *reinterpret_cast<const float2*>(slot);
     s.add_pair(v.x, v.y);
+}
+
+// Value k of the kThreads / 32 warp sums in red (row stride nv), added as a fixed tree
+// ((w0 + w1) + (w2 + w3)) + ((w4 + w5) + (w6 + w7)): three dependent float64 additions.
+__device__ __forceinline__ double sum_warps(const double* red, int nv, int k) {
+    static_assert(kThreads == 256, "tree over eight warps");
+    const double a = red[0 * nv + k] + red[1 * nv + k], b = red[2 * nv + k] + red[3 * nv + k];
+    const double c = red[4 * nv + k] + red[5 * nv + k], d = red[6 * nv + k] + red[7 * nv + k];
+    return (a + b) + (c + d);
 }
 
 // Sum `nv` values per thread over the CTA; threads 0..NV-1 write them to out[0..NV) (global or
@@ -174,11 +193,7 @@ __device__ __forceinline__ void cta_sum_write(double (&v)[NV], double* out) {
         if (lane == 0) red[wid][k] = s;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s;
-    }
+    if (threadIdx.x < NV) out[threadIdx.x] = sum_warps(&red[0][0], NV, threadIdx.x);
     __syncthreads();
 }
 
@@ -251,21 +266,22 @@ __device__ __forceinline__ bool grid_sum_finalize(double (&v)[NV], double* parti
         if (lane == 0) red[wid][k] = s;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        partial[int64_t(blockIdx.x) * NV + threadIdx.x] = s;
-    }
+    if (threadIdx.x < NV) partial[int64_t(blockIdx.x) * NV + threadIdx.x] = sum_warps(&red[0][0], NV, threadIdx.x);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(cnt, 1) == int(gridDim.x) - 1);
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < NV) {
+    // warp k adds value k over the CTA partials: lane l takes partials l, l + 32, ... (independent
+    // loads, short float64 chains), then the fixed shuffle tree; partials of CTAs without rows are
+    // exact zeros, so the sum does not depend on the grid width
+    static_assert(NV <= kThreads / 32, "one warp per value");
+    if (wid < NV) {
         double s = 0.0;
-        for (int b = 0; b < int(gridDim.x); ++b) s += __ldcg(partial + int64_t(b) * NV + threadIdx.x);
-        totals[threadIdx.x] = s;
+        for (int b = lane; b < int(gridDim.x); b += 32) s += __ldcg(partial + int64_t(b) * NV + wid);
+        s = warp_sum(s);
+        if (lane == 0) totals[wid] = s;
     }
     if (threadIdx.x == 0) *cnt = 0;
     __syncthreads();
@@ -518,12 +534,15 @@ constexpr size_t spmm_smem() {
     return spmv_smem<T>() + sizeof(T) * SpmvCfg<T>::kWarps * kMaxDirs * 9;
 }
 
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x;
-    v[1] = t.y;
-    v[2] = t.z;
-    v[3] = t.w;
+// rows b = 0..8 of a 16-column PT block, 4 columns from p: (p[16 b], p[16 b + 1]) and
+// (p[16 b + 2], p[16 b + 3]) as float pairs (one 16-byte load per row)
+__device__ __forceinline__ void load_prow(const float* p, float2 (&v)[9][2]) {
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const float4 t = *reinterpret_cast<const float4*>(p + b * kMaxDirs);
+        v[b][0] = make_float2(t.x, t.y);
+        v[b][1] = make_float2(t.z, t.w);
+    }
 }
 
 template <typename T>
@@ -571,34 +590,31 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
         const int64_t n = int64_t(c.lay.nc) * 9;
         const int64_t ooff = c.lay.hoff - 9 * int64_t(c.lay.c0) + int64_t(c.new_off) * n;
         const int64_t rj = row_ptr[it.row];
-        T acc[9][4];
+        // columns (4g, 4g + 1) and (4g + 2, 4g + 3) of the 9 rows, as float pairs for the packed
+        // float32 multiply-add (each pair operation rounds like two scalar fused multiply-adds)
+        float2 acc[9][2];
 #pragma unroll
-        for (int a = 0; a < 9; ++a)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) acc[a][cc] = T(0);
+        for (int a = 0; a < 9; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
             const bool active = 4 * g < w;
             // column cameras of this lane's blocks r * 8 + qi (r = 0..3) of tile t, -1 outside the
-            // item; fetched one tile ahead, and the P rows of each block one block ahead, so the
-            // gathers overlap the arithmetic
+            // item; fetched one tile ahead, and the P rows of each block one block ahead (those of a
+            // tile's first block during the previous tile's last one), so the gathers overlap the
+            // arithmetic
             int kc[4], kn[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int q = t0 * 32 + r * 8 + qi;
                 kc[r] = (active && q >= it.q0 && q < it.q1) ? col[rj + q] : -1;
             }
+            float2 pv[2][9][2];
+            if (kc[0] >= 0) load_prow(PT + (int64_t(kc[0]) * 9) * kMaxDirs + 4 * g, pv[0]);
             for (int t = t0; t < t1; ++t) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int q = (t + 1) * 32 + r * 8 + qi;
                     kn[r] = (active && t + 1 < t1 && q < it.q1) ? col[rj + q] : -1;
-                }
-                T pv[2][9][4];
-                if (kc[0] >= 0) {
-                    const T* pk = PT + (int64_t(kc[0]) * 9) * kMaxDirs + 4 * g;
-#pragma unroll
-                    for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[0][b]);
                 }
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -613,20 +629,18 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT for the next block
-                        if (r < 3 && kc[r + 1] >= 0) {
-                            const T* pk = PT + (int64_t(kc[r + 1]) * 9) * kMaxDirs + 4 * g;
-#pragma unroll
-                            for (int b = 0; b < 9; ++b) load4(pk + b * kMaxDirs, pv[(r + 1) & 1][b]);
-                        }
+                        const int knext = r < 3 ? kc[r + 1] : kn[0];
+                        if (knext >= 0) load_prow(PT + (int64_t(knext) * 9) * kMaxDirs + 4 * g, pv[(r + 1) & 1]);
                         if (kc[r] < 0) continue;
                         const T* blk = tile + (r * 8 + qi) * 81;
 #pragma unroll
                         for (int a = 0; a < 9; ++a)
 #pragma unroll
                             for (int b = 0; b < 9; ++b) {
-                                const T sab = blk[9 * a + b];
-#pragma unroll
-                                for (int cc = 0; cc < 4; ++cc) acc[a][cc] += sab * pv[r & 1][b][cc];
+                                const float sab = blk[9 * a + b];
+                                const float2 s2 = make_float2(sab, sab);
+                                acc[a][0] = __ffma2_rn(s2, pv[r & 1][b][0], acc[a][0]);
+                                acc[a][1] = __ffma2_rn(s2, pv[r & 1][b][1], acc[a][1]);
                             }
                     }
                 }
@@ -645,15 +659,23 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
             if (bad) break;
         }
         // sum over the 8 lanes of each column group, then lanes 0..3 hold their columns
+        T accs[9][4];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            accs[a][0] = acc[a][0].x;
+            accs[a][1] = acc[a][0].y;
+            accs[a][2] = acc[a][1].x;
+            accs[a][3] = acc[a][1].y;
+        }
 #pragma unroll
         for (int a = 0; a < 9; ++a)
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
-                T v = acc[a][cc];
+                T v = accs[a][cc];
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
-                acc[a][cc] = v;
+                accs[a][cc] = v;
             }
         __syncwarp();
         if (qi == 0) {
@@ -662,7 +684,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
                 const int ci = 4 * g + cc;
                 if (ci < w)
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) red[ci * 9 + a] = acc[a][cc];
+                    for (int a = 0; a < 9; ++a) red[ci * 9 + a] = accs[a][cc];
             }
         }
         __syncwarp();
@@ -756,6 +778,7 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
             mi = outer[p].max_in;
         }
         c.rr0 = rr0;
+        c.rr0_inv = rr0 > 0.0 ? 1.0 / rr0 : 0.0;
         c.rr = rr0;
         c.tol2 = tl * tl;
         c.tau = tau;
@@ -785,6 +808,29 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
 // ---------------------------------------------------------------------------------------
 // Algorithm 1 (grid: CTAs x problems)
 
+// This thread's share of the per-camera sums (Delta, gamma) of cameras [0, nc): cameras
+// threadIdx.x + k blockDim.x, four at a time in interleaved sums (their loads in flight together),
+// added as (0 + 1) + (2 + 3).
+__device__ __forceinline__ void sum_camdot(const double* cd, int nc, double (&d)[2]) {
+    const int bd = blockDim.x;
+    double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = threadIdx.x;
+    for (; j + 3 * bd < nc; j += 4 * bd)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a0[u] += cd[2 * int64_t(j + u * bd)];
+            a1[u] += cd[2 * int64_t(j + u * bd) + 1];
+        }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (j + u * bd < nc) {
+            a0[u] += cd[2 * int64_t(j + u * bd)];
+            a1[u] += cd[2 * int64_t(j + u * bd) + 1];
+        }
+    d[0] = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+    d[1] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
+}
+
 __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int nb);
 
 // alpha = gamma / Delta; x += alpha p; r -= alpha q; z = D^{-1} r; totals of |r|^2, q^T z, r^T z,
@@ -809,12 +855,15 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
     const int nc = c.lay.nc;
     __shared__ double dg[2];
     __shared__ T sr[kUpdCams * 9];
+    const int t = threadIdx.x, cl = t / 9, a = t - 9 * (t / 9);
+    const int64_t jl = int64_t(blockIdx.x) * kUpdCams + cl;
+    const bool act = t < kUpdCams * 9 && jl < nc;
+    double drow[9];   // this row of the camera's D^{-1} block, requested before the CTA sum waits
     {
-        double d[2] = {0.0, 0.0};
-        for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
-            d[0] += camdot[2 * (c0 + jl)];
-            d[1] += camdot[2 * (c0 + jl) + 1];
-        }
+        double d[2];
+        sum_camdot(camdot + 2 * c0, nc, d);
+#pragma unroll
+        for (int b = 0; b < 9; ++b) drow[b] = act ? Dinv[81 * (c0 + jl) + 9 * a + b] : 0.0;
         cta_sum_write<2>(d, dg);
     }
     double* tot = totals + int64_t(p) * kTotals;
@@ -822,11 +871,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
         tot[0] = dg[0];
         tot[1] = dg[1];
     }
-    const T alpha = T(dg[1] / dg[0]);
+    // alpha = gamma / Delta; the float32 sweeps divide the rounded operands in float32 (a float64
+    // division is a long dependent chain on this GPU's narrow float64 pipe)
+    T alpha;
+    if constexpr (sizeof(T) == 4) alpha = __fdiv_rn(float(dg[1]), float(dg[0]));
+    else alpha = dg[1] / dg[0];
     const int64_t hb = c.lay.hoff - 9 * c0;
-    const int t = threadIdx.x, cl = t / 9, a = t - 9 * (t / 9);
-    const int64_t jl = int64_t(blockIdx.x) * kUpdCams + cl;
-    const bool act = t < kUpdCams * 9 && jl < nc;
     const int64_t i = 9 * (c0 + jl) + a;
     double v[3] = {0.0, 0.0, 0.0};
     T rv = T(0), qv = T(0);
@@ -840,10 +890,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
     if (t < kUpdCams * 9) sr[t] = rv;
     __syncthreads();
     if (act) {
-        const double* D = Dinv + 81 * (c0 + jl) + 9 * a;
         double s = 0.0;
 #pragma unroll
-        for (int b = 0; b < 9; ++b) s += D[b] * double(sr[9 * cl + b]);
+        for (int b = 0; b < 9; ++b) s += drow[b] * double(sr[9 * cl + b]);
         const T zs = T(s);
         z[i] = zs;
         v[1] = double(qv) * double(zs);
@@ -862,9 +911,8 @@ __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int n
     c->it = it;
     c->Delta = D;
     c->gamma = g;
-    c->alpha = g / D;
     c->rr = rr;
-    hist[int64_t(it - 1) * nb + p] = sqrt(rr / c->rr0);
+    hist[int64_t(it - 1) * nb + p] = rr * c->rr0_inv;   // squared relative residual
     if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -874,7 +922,7 @@ __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int n
     } else if (it >= c->max_iters) {
         c->done = 1;
         c->status = BA_ERR_NOT_CONVERGED;
-    } else if (c->stag > 0.0 && (g * g / D) < c->stag * tot[4]) {
+    } else if (c->stag > 0.0 && g * g < c->stag * tot[4] * D) {   // (g^2 / D) / tot[4] < stag
         c->done = 1;          // no measurable progress left at this precision: end the sweep
         c->status = BA_OK;
     } else {
@@ -913,7 +961,7 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
     const int64_t n = int64_t(c.lay.nc) * 9;
     const int gp = gram_ctas(n, gridDim.x);
     if (int(blockIdx.x) >= gp) return;
-    constexpr int TR = 32;
+    constexpr int TR = 128;   // rows staged at once: a problem's share of rows is usually one tile
     __shared__ T sP[TR][kMaxDirs + 1], sQ[TR][kMaxDirs + 1], sr[TR];
     const int w = c.w_cur, off = c.off_cur;
     const int ne = w * w + w;
@@ -927,7 +975,7 @@ __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, con
     for (int64_t base = r0; base < r1; base += TR) {
         const int rows = int(r1 - base < TR ? r1 - base : TR);
         for (int t = threadIdx.x; t < TR * kMaxDirs; t += blockDim.x) {
-            const int rr = t / kMaxDirs, cc = t % kMaxDirs;
+            const int rr = t % TR, cc = t / TR;   // a warp reads 32 consecutive rows of one column
             T pv = T(0), qv = T(0);
             if (rr < rows && cc < w) {
                 pv = Pp[int64_t(off + cc) * n + base + rr];
@@ -1071,82 +1119,90 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
     __syncthreads();
 }
 
-// Cholesky inverse of the symmetric w x w matrix in sA, accepted only when it equals the pseudo-
-// inverse: with A = L L^T, lambda_min(A) >= 1 / |L^{-1}|_F^2 and lambda_max(A) <= trace(A), so when
-// 1 / |L^{-1}|_F^2 exceeds 1e3 times the threshold w 2^-52 trace(A) no eigenvalue is dropped and
-// A^+ = A^{-1}.  sA is left intact; sL (lower factor, then L^{-1}) is scratch; sX receives A^{-1}.
-// Returns false (sX undefined) when the certificate fails or a pivot is not positive.
+// 1 / p in float64 without the long division chain: a float32 estimate refined by two Newton
+// steps r <- r + r (1 - p r) (each doubles the correct bits: ~23 -> ~46 -> full precision);
+// pivots outside the float32 range divide.
+__device__ __forceinline__ double fast_rcp(double p) {
+    const double ap = fabs(p);
+    if (!(ap > 1e-30 && ap < 1e30)) return 1.0 / p;
+    double r = double(__frcp_rn(float(p)));
+    r = fma(r, fma(-p, r, 1.0), r);
+    r = fma(r, fma(-p, r, 1.0), r);
+    return r;
+}
+
+// Inverse of the symmetric w x w matrix in sA by Gauss-Jordan sweeps on the diagonal (no
+// pivoting), accepted only when it equals the pseudo-inverse: every sweep pivot must be positive
+// (A positive definite), and with lambda_min(A) >= 1 / trace(A^{-1}) and lambda_max(A) <=
+// trace(A), 1 / trace(A^{-1}) exceeding 1e3 times the threshold w 2^-52 trace(A) means no
+// eigenvalue is dropped, so A^+ = A^{-1}.  Thread 16 i + j (of the first 256) owns entry (i, j);
+// a sweep updates every entry once, and the owner of the next pivot forms its reciprocal right
+// after its own update, so the dependent float64 chain is 16 reciprocals long and no other thread
+// spends the narrow float64 pipe on it.  sA is left intact; sX receives A^{-1} (symmetrised); sL
+// is unused.  Returns false (sX undefined) when the certificate fails.
 __device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxDirs + 1],
                                   double (*sX)[kMaxDirs + 1], int w) {
+    (void)sL;
     __shared__ int ok;
-    __shared__ double fro, tr;
-    __shared__ double rdiag[kMaxDirs];   // 1 / L_kk: one float64 division per pivot
+    __shared__ double tr, trinv;
+    __shared__ double rk[kMaxDirs];   // 1 / pivot k
     const int t = threadIdx.x;
     const int i = t / kMaxDirs, j = t % kMaxDirs;
-    if (t < kMaxDirs * kMaxDirs) sL[i][j] = (i < w && j < w && j <= i) ? sA[i][j] : 0.0;
-    if (t == 0) {
-        ok = 1;
-        fro = 0.0;
-        double s = 0.0;
-        for (int k = 0; k < w; ++k) s += sA[k][k];
-        tr = s;
-    }
-    __syncthreads();
-    // right-looking Cholesky on the lower triangle
-    for (int k = 0; k < w; ++k) {
+    const bool in = t < kMaxDirs * kMaxDirs && i < w && j < w;
+    if (t < kMaxDirs * kMaxDirs) sX[i][j] = in ? sA[i][j] : 0.0;
+    if (t < 32) {
+        double d = t < w ? sA[t][t] : 0.0;
+        d = warp_sum(d);
         if (t == 0) {
-            const double d = sL[k][k];
-            if (!(d > 0.0)) ok = 0;
-            sL[k][k] = d > 0.0 ? sqrt(d) : 1.0;
-            rdiag[k] = 1.0 / sL[k][k];
-        }
-        __syncthreads();
-        if (t > k && t < w) sL[t][k] *= rdiag[k];
-        __syncthreads();
-        if (t < kMaxDirs * kMaxDirs && i > k && j > k && j <= i && i < w) sL[i][j] -= sL[i][k] * sL[j][k];
-        __syncthreads();
-    }
-    if (!ok) return false;
-    // L^{-1} column by column (thread c solves column c), kept in sX temporarily
-    if (t < w) {
-        const int c = t;
-        for (int r = 0; r < w; ++r) {
-            double v = (r == c) ? 1.0 : 0.0;
-            for (int k = c; k < r; ++k) v -= sL[r][k] * sX[k][c];
-            sX[r][c] = r < c ? 0.0 : v * rdiag[r];
+            tr = d;
+            const double p0 = sA[0][0];
+            ok = p0 > 0.0;
+            rk[0] = fast_rcp(p0);
         }
     }
     __syncthreads();
-    if (t < kMaxDirs * kMaxDirs) sL[i][j] = (i < w && j < w) ? sX[i][j] : 0.0;   // sL <- L^{-1}
+    for (int k = 0; k < w; ++k) {
+        double v = 0.0;
+        if (in) {
+            const double r = rk[k];
+            if (i == k && j == k) v = r;
+            else if (i == k) v = sX[k][j] * r;
+            else if (j == k) v = -sX[i][k] * r;
+            else v = fma(-sX[i][k] * r, sX[k][j], sX[i][j]);
+        }
+        __syncthreads();
+        if (in) {
+            sX[i][j] = v;
+            if (i == k + 1 && j == k + 1) {   // the next pivot
+                if (!(v > 0.0)) ok = 0;
+                rk[k + 1] = fast_rcp(v);
+            }
+        }
+        __syncthreads();
+    }
+    double sym = 0.0;
+    if (in) sym = 0.5 * (sX[i][j] + sX[j][i]);
+    __syncthreads();
+    if (in) sX[i][j] = sym;
     __syncthreads();
     if (t < 32) {
-        double f = 0.0;
-        for (int e = t; e < w * w; e += 32) {
-            const double v = sL[e / w][e % w];
-            f += v * v;
-        }
-        f = warp_sum(f);
-        if (t == 0) fro = f;
+        double d = t < w ? sX[t][t] : 0.0;
+        d = warp_sum(d);
+        if (t == 0) trinv = d;
     }
     __syncthreads();
-    const double lam_min_bound = 1.0 / fro;
+    if (!ok) return false;
+    // 1 / trace(A^{-1}) > 1e3 thr, i.e. 1e3 thr trace(A^{-1}) < 1 (false for a NaN)
     const double thr = w * 2.220446049250313e-16 * tr;
-    if (!(lam_min_bound > 1e3 * thr)) return false;
-    // A^{-1} = L^{-T} L^{-1}
-    if (t < kMaxDirs * kMaxDirs && i < w && j < w) {
-        double v = 0.0;
-        const int k0 = i > j ? i : j;
-        for (int k = k0; k < w; ++k) v += sL[k][i] * sL[k][j];
-        sX[i][j] = v;
-    }
-    __syncthreads();
-    return true;
+    return 1e3 * thr * trinv < 1.0;
 }
 
 // Delta_i, gamma_i -> Delta_i^+ (stored for the reorthogonalisation), alpha_i, gamma^T alpha.
-// One CTA per problem; gx is the width of the Gram grid.
+// One CTA of kSmallThreads per problem (the matrix work uses the first 256); gx is the width of
+// the Gram grid.
+constexpr int kSmallThreads = 1024;
 template <typename T>
-__global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx, double* __restrict__ dpinv,
+__global__ void __launch_bounds__(kSmallThreads) k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx, double* __restrict__ dpinv,
                             int mi1) {
     const int p = blockIdx.x;
     Ctl* c = ctl + p;
@@ -1159,13 +1215,41 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx
     const int ne = w * w + w;
     const int np = gram_ctas(int64_t(c->lay.nc) * 9, gx);
     const double* part = partial + int64_t(p) * gx * kGramMax;
-    // one thread per entry sums the CTA partials in CTA order (independent loads, no shuffles)
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        ExactSum<T> acc;
-        for (int b = 0; b < np; ++b) load_partial(acc, part + int64_t(b) * kGramMax + e);
-        const double s = acc.value();
-        if (e < w * w) sA[e / w][e % w] = s;
-        else sg[e - w * w] = s;
+    // Sum of the CTA partials of every entry.  The partials sit in L2, written by the Gram CTAs, so
+    // the sum is bound by load latency: G lanes share an entry (G a power of two, as many as the
+    // block allows, at most a warp); lane g of the group takes the partials b = g, g + G, ... into
+    // eight interleaved sums (eight loads in flight), which are added in a fixed tree, and the
+    // group's sums meet in a fixed shuffle tree.  The order depends on (w, np) alone.
+    {
+        int G = 1;
+        while (G < 32 && 2 * G * ne <= int(blockDim.x)) G *= 2;
+        const int per_round = int(blockDim.x) / G;
+        for (int e0 = 0; e0 < ne; e0 += per_round) {
+            const int e = e0 + int(threadIdx.x) / G, g = int(threadIdx.x) % G;
+            // warps holding no entry of this round skip the arithmetic (and their shuffles) whole
+            if (e0 + int(threadIdx.x & ~31u) / G >= ne) continue;
+            ExactSum<T> acc[8];
+            if (e < ne) {
+                int b = g;
+                for (; b + 7 * G < np; b += 8 * G)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) load_partial(acc[k], part + int64_t(b + k * G) * kGramMax + e);
+#pragma unroll
+                for (int k = 0; k < 7; ++k)
+                    if (b + k * G < np) load_partial(acc[k], part + int64_t(b + k * G) * kGramMax + e);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) combine(acc[k], acc[k + 4]);
+            combine(acc[0], acc[2]);
+            combine(acc[1], acc[3]);
+            combine(acc[0], acc[1]);
+            for (int o = G / 2; o > 0; o >>= 1) combine_shfl(acc[0], o);
+            if (e < ne && g == 0) {
+                const double s = acc[0].value();
+                if (e < w * w) sA[e / w][e % w] = s;
+                else sg[e - w * w] = s;
+            }
+        }
     }
     __syncthreads();
     // symmetrise
@@ -1184,20 +1268,25 @@ __global__ void k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx
     if (threadIdx.x < kMaxDirs * kMaxDirs) {
         dpinv[(int64_t(p) * mi1 + it) * kMaxDirs * kMaxDirs + threadIdx.x] = (i < w && j < w) ? sX[i][j] : 0.0;
     }
-    if (int(threadIdx.x) < w) {
-        double s = 0.0;
-        for (int b = 0; b < w; ++b) s += sX[threadIdx.x][b] * sg[b];
-        sal[threadIdx.x] = s;
+    // alpha = Delta^+ gamma and gamma^T alpha: thread (a, b) = 16 a + b forms one product, the
+    // 16 lanes of row a add theirs in a fixed shuffle tree (short float64 chains)
+    if (threadIdx.x < kMaxDirs * kMaxDirs) {
+        double s = (i < w && j < w) ? sX[i][j] * sg[j] : 0.0;
+#pragma unroll
+        for (int o = kMaxDirs / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (j == 0 && i < w) {
+            sal[i] = s;
+            c->alpha_v[i] = s;
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ga = 0.0;
-        for (int a = 0; a < w; ++a) {
-            ga += sg[a] * sal[a];
-            c->alpha_v[a] = sal[a];
+    if (threadIdx.x < 32) {
+        double s = int(threadIdx.x) < w ? sg[threadIdx.x] * sal[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+            c->ga = s;
+            if (!(s == s)) { c->done = 1; c->status = BA_ERR_BREAKDOWN; }
         }
-        c->ga = ga;
-        if (!(ga == ga)) { c->done = 1; c->status = BA_ERR_BREAKDOWN; }
     }
 }
 
@@ -1225,11 +1314,14 @@ __global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restric
     const T* Qp = Q + c.lay.hoff + int64_t(off) * n;
     __shared__ T sal[kMaxDirs];
     __shared__ T sr[kUpdCams * 9];
-    if (threadIdx.x < kMaxDirs) sal[threadIdx.x] = int(threadIdx.x) < w ? T(c.alpha_v[threadIdx.x]) : T(0);
-    __syncthreads();
     const int t = threadIdx.x, cl = t / 9, a = t - 9 * (t / 9);
     const int64_t jl = int64_t(blockIdx.x) * kUpdCams + cl;
     const bool act = t < kUpdCams * 9 && jl < nc;
+    double drow[9];   // this row of the camera's D^{-1} block, requested early
+#pragma unroll
+    for (int b = 0; b < 9; ++b) drow[b] = act ? Dinv[81 * (c0 + jl) + 9 * a + b] : 0.0;
+    if (threadIdx.x < kMaxDirs) sal[threadIdx.x] = int(threadIdx.x) < w ? T(c.alpha_v[threadIdx.x]) : T(0);
+    __syncthreads();
     const int64_t il = 9 * jl + a, i = 9 * c0 + il;
     double v[2] = {0.0, 0.0};
     T rv = T(0);
@@ -1247,10 +1339,9 @@ __global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restric
     if (t < kUpdCams * 9) sr[t] = rv;
     __syncthreads();
     if (act) {
-        const double* D = Dinv + 81 * (c0 + jl) + 9 * a;
         double s = 0.0;
 #pragma unroll
-        for (int b = 0; b < 9; ++b) s += D[b] * double(sr[9 * cl + b]);
+        for (int b = 0; b < 9; ++b) s += drow[b] * double(sr[9 * cl + b]);
         const T zs = T(s);
         z[i] = zs;
         v[1] = double(rv) * double(zs);
@@ -1269,7 +1360,7 @@ __device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off
     c->it = it;
     c->rr = rr;
     c->rz = rz;
-    hist[int64_t(it - 1) * nb + p] = sqrt(rr / c->rr0);
+    hist[int64_t(it - 1) * nb + p] = rr * c->rr0_inv;   // squared relative residual
     if (!(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -1290,13 +1381,14 @@ __device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off
         c->status = BA_ERR_BREAKDOWN;
         return;
     }
-    const double t = c->ga / rz;
-    if (c->stag > 0.0 && t < c->stag) {
+    // t_i = gamma^T alpha / r^T z (rz > 0), compared without the division
+    const double ga = c->ga;
+    if (c->stag > 0.0 && ga < c->stag * rz) {
         c->done = 1;      // no measurable progress left at this precision: end the sweep
         c->status = BA_OK;
         return;
     }
-    const int local = (t < c->tau) ? 1 : 0;
+    const int local = (ga < c->tau * rz) ? 1 : 0;
     const int w = local ? c->n_eff : 1;
     if (c->cols + w > c->cap) {
         // history full: a float32 sweep ends here and the float64 refinement restarts it from the
@@ -1350,10 +1442,16 @@ __global__ void k_mcg_phi(const T* __restrict__ Q, const T* __restrict__ z, doub
     }
 }
 
-// beta_{i,j} = Delta_j^+ Phi_{i,j} for every history block j, into beta rows (one warp per block)
+// beta_{i,j} = Delta_j^+ Phi_{i,j} for every history block j, into beta rows (one warp per block);
+// betat receives the same rows in the Krylov storage type (float32 sweeps), so the
+// reorthogonalisation reads them without conversions.  Float64 additions form long dependent
+// chains on this GPU, so the sums are interleaved: with 32 or more entries a lane carries up to 8
+// entries side by side; with fewer, G lanes share an entry's partials (lane g of the group takes
+// k = g, g + G, ... into 4 interleaved sums) and add them in a fixed shuffle tree.
+template <typename T>
 __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __restrict__ dpinv,
                            const int* __restrict__ blk_off, const int* __restrict__ blk_w, double* __restrict__ beta,
-                           const Ctl* __restrict__ ctl, int mi1) {
+                           T* __restrict__ betat, const Ctl* __restrict__ ctl, int mi1) {
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1361,32 +1459,75 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nblk = c.it;   // blocks 0..it-1 are the history
     const int n_eff = c.n_eff, K = c.K, w = c.w_new, local = c.local;
+    const int m = local ? K : n_eff * K;   // partials per Phi entry
     const double* ph = phip + c.lay.phoff;
     const int* bo = blk_off + int64_t(p) * mi1;
     const int* bw = blk_w + int64_t(p) * mi1;
     double* Bp = beta + c.lay.boff * kMaxDirs;
+    T* Bt = betat + c.lay.boff * kMaxDirs;
     for (int64_t jb = gtid() >> 5; jb < nblk; jb += gstride() >> 5) {
         const int off = bo[jb], wj = bw[jb];
-        // Phi_j (wj x w)
-        for (int e = lane; e < wj * w; e += 32) {
-            const int a = e / w, s = e % w;
-            const int64_t cc = off + a;
-            double v = 0.0;
-            if (local) {
-                for (int k = 0; k < K; ++k) v += ph[(cc * n_eff + s) * K + k];
-            } else {
-                for (int ss = 0; ss < n_eff; ++ss)
-                    for (int k = 0; k < K; ++k) v += ph[(cc * n_eff + ss) * K + k];
+        const int ne = wj * w;
+        // Phi_j (wj x w): entry (a, s) adds the partials of history column off + a over subset s
+        // (local block) or over every subset (global block); they are contiguous
+        auto src = [&](int e) -> const double* {
+            const int64_t cc = off + e / w;
+            return local ? ph + (cc * n_eff + e % w) * K : ph + cc * n_eff * K;
+        };
+        if (ne >= 32) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = 0.0;
+            for (int k = 0; k < m; ++k)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = lane + 32 * u;
+                    if (e < ne) v[u] += src(e)[k];
+                }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (lane + 32 * u < ne) sphi[wid][lane + 32 * u] = v[u];
+        } else {
+            int G = 1;
+            while (2 * G * ne <= 32) G *= 2;
+            const int e = lane / G, g = lane % G;
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            if (e < ne) {
+                const double* sp = src(e);
+                int k = g;
+                for (; k + 3 * G < m; k += 4 * G) {
+                    v0 += sp[k];
+                    v1 += sp[k + G];
+                    v2 += sp[k + 2 * G];
+                    v3 += sp[k + 3 * G];
+                }
+                if (k < m) v0 += sp[k];
+                if (k + G < m) v1 += sp[k + G];
+                if (k + 2 * G < m) v2 += sp[k + 2 * G];
             }
-            sphi[wid][e] = v;
+            double v = (v0 + v1) + (v2 + v3);
+            for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (e < ne && g == 0) sphi[wid][e] = v;
         }
         __syncwarp();
         const double* Dp = dpinv + (int64_t(p) * mi1 + jb) * kMaxDirs * kMaxDirs;
-        for (int e = lane; e < wj * w; e += 32) {
-            const int a = e / w, s = e % w;
-            double v = 0.0;
-            for (int b = 0; b < wj; ++b) v += Dp[a * kMaxDirs + b] * sphi[wid][b * w + s];
-            Bp[int64_t(off + a) * kMaxDirs + s] = v;
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = 0.0;
+        for (int b2 = 0; b2 < wj; ++b2)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = lane + 32 * u;
+                if (e < ne) v[u] += Dp[(e / w) * kMaxDirs + b2] * sphi[wid][b2 * w + e % w];
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = lane + 32 * u;
+            if (e < ne) {
+                const int64_t o = int64_t(off + e / w) * kMaxDirs + e % w;
+                Bp[o] = v[u];
+                Bt[o] = T(v[u]);
+            }
         }
         __syncwarp();
     }
@@ -1401,7 +1542,7 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
 constexpr int kPqSlices = 4;
 template <typename T>
 __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T* __restrict__ Q,
-                                                            const T* __restrict__ z, const double* __restrict__ beta,
+                                                            const T* __restrict__ z, const T* __restrict__ beta,
                                                             T* __restrict__ PT, const Ctl* __restrict__ ctl) {
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
@@ -1415,7 +1556,7 @@ __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T*
     const bool upd_q = !c.direct_q;
     T* Pp = P + c.lay.hoff;
     T* Qp = Q + c.lay.hoff;
-    const double* Bp = beta + c.lay.boff * kMaxDirs;
+    const T* Bp = beta + c.lay.boff * kMaxDirs;
     for (int64_t base = int64_t(blockIdx.x) * 32; base < n; base += int64_t(gridDim.x) * 32) {
         const int64_t row = base + lane;
         const bool act = row < n;
@@ -1430,7 +1571,7 @@ __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T*
             __syncthreads();
             for (int t = threadIdx.x; t < TC * kMaxDirs; t += blockDim.x) {
                 const int cc = t / kMaxDirs, s = t % kMaxDirs;
-                sB[cc][s] = (cc < tc && s < w) ? T(Bp[int64_t(c0 + cc) * kMaxDirs + s]) : T(0);
+                sB[cc][s] = (cc < tc && s < w) ? Bp[int64_t(c0 + cc) * kMaxDirs + s] : T(0);
             }
             __syncthreads();
             if (!act) continue;
@@ -1642,10 +1783,11 @@ __global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, double
 
 struct GraphKey {
     int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1;
+    uint64_t allocs = ~uint64_t(0);   // buffer generation (any reallocation invalidates the graph)
     const void* ptrs[14] = {};
     bool operator==(const GraphKey& o) const {
         if (mcg != o.mcg || fp32 != o.fp32 || chunk != o.chunk || mi1 != o.mi1 || use_l != o.use_l ||
-            epoch != o.epoch)
+            epoch != o.epoch || allocs != o.allocs)
             return false;
         for (int i = 0; i < 14; ++i) if (ptrs[i] != o.ptrs[i]) return false;
         return true;
@@ -1669,8 +1811,8 @@ struct Solver {
     int gpq = 1;              // grid width of the reorthogonalisation (32-row blocks)
     int gphi = 1, gb = 1;     // Phi and beta grid widths
     std::vector<Layout> lay;  // of the current solve
-    Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, phip, hist, blk_off, blk_w, ctl, outer, rt, lay_d,
-        totals, dpart, dcnt, camdot;
+    Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, betaf, phip, hist, blk_off, blk_w, ctl, outer, rt,
+        lay_d, totals, dpart, dcnt, camdot;
     Ctl* h_ctl = nullptr;     // pinned, nb
     Outer* h_outer = nullptr; // pinned, nb
     std::vector<std::vector<double>> host_hist;   // per problem, residual history of the last solve
@@ -1688,9 +1830,14 @@ struct Solver {
     void* mm_part = nullptr;   // k_spmm partials: items_g.n x 16 x 9
 };
 
+// Reallocations so far: captured graphs hold buffer addresses, so any reallocation forces a new
+// capture (the graph key records this count).
+static std::atomic<uint64_t> g_allocs{0};
+
 static void grow(Buf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return;
+    ++g_allocs;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -1881,6 +2028,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     grow(w->part_cam, size_t(s.n_c) * 2 * sizeof(double));
     grow(w->dpinv, size_t(nb) * w->mi1 * kMaxDirs * kMaxDirs * sizeof(double));
     grow(w->beta, size_t(boff) * kMaxDirs * sizeof(double));
+    grow(w->betaf, size_t(boff) * kMaxDirs * sizeof(float));
     grow(w->phip, size_t(phoff) * sizeof(double));
     grow(w->hist, size_t(nb) * w->mi1 * sizeof(double));
     grow(w->blk_off, size_t(nb) * w->mi1 * sizeof(int));
@@ -1911,8 +2059,8 @@ Solver* solver_create() { return new Solver(); }
 void solver_destroy(Solver* w) {
     if (!w) return;
     Buf* bufs[] = {&w->P, &w->Q, &w->r, &w->z, &w->xw, &w->PT, &w->part_a, &w->part_b, &w->part_cam, &w->dpinv,
-                   &w->beta, &w->phip, &w->hist, &w->blk_off, &w->blk_w, &w->ctl, &w->outer, &w->rt, &w->lay_d,
-                   &w->totals, &w->dpart, &w->dcnt, &w->camdot};
+                   &w->beta, &w->betaf, &w->phip, &w->hist, &w->blk_off, &w->blk_w, &w->ctl, &w->outer, &w->rt,
+                   &w->lay_d, &w->totals, &w->dpart, &w->dcnt, &w->camdot};
     for (Buf* b : bufs) free_buf(*b);
     if (w->exec) cudaGraphExecDestroy(w->exec);
     free_items(w->items_g);
@@ -1955,14 +2103,16 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
     } else {
         k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
-        k_mcg_small<T><<<nb, kThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv), w->mi1);
+        k_mcg_small<T><<<nb, kSmallThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv),
+                                                     w->mi1);
         k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(
             Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu, dcnt, totals, ptr<double>(w->hist),
             ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1, ctl);
         k_mcg_phi<T><<<dim3(w->gphi, nb), kThreads, 0, st>>>(Q, z, ptr<double>(w->phip), ctl);
-        k_mcg_beta<<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
-                                                         ptr<int>(w->blk_off), ptr<int>(w->blk_w),
-                                                         ptr<double>(w->beta), ctl, w->mi1);
+        T* betat = sizeof(T) == 8 ? ptr<T>(w->beta) : ptr<T>(w->betaf);
+        k_mcg_beta<T><<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
+                                                            ptr<int>(w->blk_off), ptr<int>(w->blk_w),
+                                                            ptr<double>(w->beta), betat, ctl, w->mi1);
         if constexpr (sizeof(T) == 8) {
             // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}; S Z over whole rows for the
             // problems forming a global block, over the subset segments for the local ones
@@ -1972,10 +2122,10 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
             if (w->use_l)
                 k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                     s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l, kSelLocal, Q, nullptr, nullptr, ctl);
-            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, ptr<double>(w->beta), nullptr, ctl);
+            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, nullptr, ctl);
         } else {
             // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
-            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, ptr<double>(w->beta), ptr<T>(w->PT), ctl);
+            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, ptr<T>(w->PT), ctl);
             k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
             k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
@@ -2020,6 +2170,7 @@ static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv
     key.mi1 = w->mi1;
     key.use_l = w->use_l;
     key.epoch = w->epoch;
+    key.allocs = g_allocs.load();
     const void* ptrs[14] = {S, Dinv, x, w->P.p, w->Q.p, w->r.p, w->z.p, w->ctl.p, w->beta.p, w->phip.p,
                             w->items_g.items, w->items_l.items, w->PT.p, w->dpinv.p};
     for (int i = 0; i < 14; ++i) key.ptrs[i] = ptrs[i];
@@ -2066,8 +2217,9 @@ static void true_residual(Solver* w, const Structure& s, const System& y, const 
     w->launches += 1;
 }
 
-// Append rows [0, its) of the iteration-major device history to each problem's host history,
-// problem b's values multiplied by scale[b] (rows past a problem's own count are ignored).
+// Append rows [0, its) of the iteration-major device history (squared relative residuals) to each
+// problem's host history as relative residuals, problem b's values multiplied by scale[b] (rows
+// past a problem's own count are ignored).
 static void collect_history(Solver* w, const std::vector<int>& its, const std::vector<double>& scale, cudaStream_t st) {
     const int nb = w->nb;
     int rows = 0;
@@ -2077,7 +2229,7 @@ static void collect_history(Solver* w, const std::vector<int>& its, const std::v
     BA_CUDA_TRY(cudaMemcpyAsync(w->rows.data(), w->hist.p, sizeof(double) * w->rows.size(), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaStreamSynchronize(st));
     for (int b = 0; b < nb; ++b)
-        for (int i = 0; i < its[b]; ++i) w->host_hist[b].push_back(w->rows[size_t(i) * nb + b] * scale[b]);
+        for (int i = 0; i < its[b]; ++i) w->host_hist[b].push_back(std::sqrt(w->rows[size_t(i) * nb + b]) * scale[b]);
 }
 
 void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x, SolveOut& out,
