@@ -1119,16 +1119,14 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
     __syncthreads();
 }
 
-// 1 / p in float64 without the long division chain: a float32 estimate refined by two Newton
-// steps r <- r + r (1 - p r) (each doubles the correct bits: ~23 -> ~46 -> full precision);
-// pivots outside the float32 range divide.
+// 1 / p in float64 without the long division chain: a float32 estimate (relative error below
+// 2^-23) refined by one Newton step r <- r + r (1 - p r), which squares the error (below 2^-46,
+// about 1e-14); pivots outside the float32 range divide.
 __device__ __forceinline__ double fast_rcp(double p) {
     const double ap = fabs(p);
     if (!(ap > 1e-30 && ap < 1e30)) return 1.0 / p;
-    double r = double(__frcp_rn(float(p)));
-    r = fma(r, fma(-p, r, 1.0), r);
-    r = fma(r, fma(-p, r, 1.0), r);
-    return r;
+    const double r = double(__frcp_rn(float(p)));
+    return fma(r, fma(-p, r, 1.0), r);
 }
 
 // Inverse of the symmetric w x w matrix in sA by Gauss-Jordan sweeps on the diagonal (no
@@ -1465,25 +1463,37 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
     const int* bw = blk_w + int64_t(p) * mi1;
     double* Bp = beta + c.lay.boff * kMaxDirs;
     T* Bt = betat + c.lay.boff * kMaxDirs;
-    for (int64_t jb = gtid() >> 5; jb < nblk; jb += gstride() >> 5) {
+    // block jb goes to warp (jb / gridDim.x) of CTA (jb mod gridDim.x): consecutive blocks on
+    // different SMs, so their float64 products share no SM's float64 pipe
+    for (int64_t jb = blockIdx.x + int64_t(gridDim.x) * wid; jb < nblk; jb += int64_t(gridDim.x) * (blockDim.x >> 5)) {
         const int off = bo[jb], wj = bw[jb];
         const int ne = wj * w;
+        // entries e = lane + 32 u of this lane: (a, s) = (e / w, e mod w)
+        int ea[8], es[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = lane + 32 * u;
+            ea[u] = e / w;
+            es[u] = e - w * ea[u];
+        }
         // Phi_j (wj x w): entry (a, s) adds the partials of history column off + a over subset s
         // (local block) or over every subset (global block); they are contiguous
-        auto src = [&](int e) -> const double* {
-            const int64_t cc = off + e / w;
-            return local ? ph + (cc * n_eff + e % w) * K : ph + cc * n_eff * K;
+        auto src = [&](int a, int s2) -> const double* {
+            const int64_t cc = off + a;
+            return local ? ph + (cc * n_eff + s2) * K : ph + cc * n_eff * K;
         };
         if (ne >= 32) {
             double v[8];
+            const double* sp[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = 0.0;
+            for (int u = 0; u < 8; ++u) {
+                v[u] = 0.0;
+                sp[u] = src(ea[u], es[u]);
+            }
             for (int k = 0; k < m; ++k)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = lane + 32 * u;
-                    if (e < ne) v[u] += src(e)[k];
-                }
+                for (int u = 0; u < 8; ++u)
+                    if (lane + 32 * u < ne) v[u] += sp[u][k];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (lane + 32 * u < ne) sphi[wid][lane + 32 * u] = v[u];
@@ -1493,7 +1503,7 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
             const int e = lane / G, g = lane % G;
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             if (e < ne) {
-                const double* sp = src(e);
+                const double* sp = src(e / w, e % w);
                 int k = g;
                 for (; k + 3 * G < m; k += 4 * G) {
                     v0 += sp[k];
@@ -1516,15 +1526,12 @@ __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __rest
         for (int u = 0; u < 8; ++u) v[u] = 0.0;
         for (int b2 = 0; b2 < wj; ++b2)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = lane + 32 * u;
-                if (e < ne) v[u] += Dp[(e / w) * kMaxDirs + b2] * sphi[wid][b2 * w + e % w];
-            }
+            for (int u = 0; u < 8; ++u)
+                if (lane + 32 * u < ne) v[u] += Dp[ea[u] * kMaxDirs + b2] * sphi[wid][b2 * w + es[u]];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = lane + 32 * u;
-            if (e < ne) {
-                const int64_t o = int64_t(off + e / w) * kMaxDirs + e % w;
+            if (lane + 32 * u < ne) {
+                const int64_t o = int64_t(off + ea[u]) * kMaxDirs + es[u];
                 Bp[o] = v[u];
                 Bt[o] = T(v[u]);
             }
@@ -1547,7 +1554,8 @@ __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T*
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
     constexpr int TC = 64;
-    __shared__ T sB[TC][kMaxDirs];
+    constexpr int kBPer = TC * kMaxDirs / (kPqSlices * 32);   // beta values a thread stages per tile
+    __shared__ __align__(16) T sB[TC][kMaxDirs];
     __shared__ T red[2][kPqSlices][32][kMaxDirs + 1];
     const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
     const int64_t n = int64_t(c.lay.nc) * 9;
@@ -1566,14 +1574,27 @@ __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T*
             ap[s] = T(0);
             aq[s] = T(0);
         }
+        // beta tile c0 + TC is read into registers while tile c0 is used (its loads in flight)
+        T bnext[kBPer];
+        auto load_b = [&](int c0n) {
+#pragma unroll
+            for (int u = 0; u < kBPer; ++u) {
+                const int t = threadIdx.x + u * blockDim.x;
+                const int cc = t / kMaxDirs, s = t % kMaxDirs;
+                bnext[u] = (c0n + cc < hc && s < w) ? Bp[int64_t(c0n + cc) * kMaxDirs + s] : T(0);
+            }
+        };
+        load_b(0);
         for (int c0 = 0; c0 < hc; c0 += TC) {
             const int tc = hc - c0 < TC ? hc - c0 : TC;
             __syncthreads();
-            for (int t = threadIdx.x; t < TC * kMaxDirs; t += blockDim.x) {
-                const int cc = t / kMaxDirs, s = t % kMaxDirs;
-                sB[cc][s] = (cc < tc && s < w) ? Bp[int64_t(c0 + cc) * kMaxDirs + s] : T(0);
+#pragma unroll
+            for (int u = 0; u < kBPer; ++u) {
+                const int t = threadIdx.x + u * blockDim.x;
+                sB[t / kMaxDirs][t % kMaxDirs] = bnext[u];
             }
             __syncthreads();
+            if (c0 + TC < hc) load_b(c0 + TC);
             if (!act) continue;
             const T* pc = Pp + int64_t(c0) * n + row;
             const T* qc = Qp + int64_t(c0) * n + row;
