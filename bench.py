@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: relative residual reduction of one float32 sweep (library default)")
     ap.add_argument("--tau", type=float, default=10.0)
-    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize"],
+    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
-                         "400k landmarks, ~1.6M observations) and exit")
+                         "400k landmarks, ~1.6M observations) and exit; 'mcg' runs one MCG solve (N = 16) "
+                         "with every step local, so each iteration launches the 16-column kernels")
     ap.add_argument("--sweep", choices=["tau", "ndirs", "density"],
                     help="sensitivity mode (Figs. 3-5 of the paper): MCG vs PCG time-to-1e-6 over tau, N or the "
                          "density of S; prints one JSON line per point and exits")
@@ -342,7 +343,8 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
     # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
-    roof_schur = {"kernel": "k_schur_off (off-diagonal S blocks, Eq. 13)", "ms_per_launch": t_schur}
+    roof_schur = {"kernel": "float32 Schur blocks: k_scaled_g32 + k_schur_off_sub + k_put_diag (Eq. 13)",
+                  "ms_per_launch": t_schur}
 
     # end to end through the host-buffer API: parameters in, both solutions out
     e2e = None
@@ -437,6 +439,15 @@ def run_kernel_case(a):
     sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
     p = problem.from_scene(sc, precision=a.precision)
     p.ba_build_normal(LAMBDA)
+    if a.kernel_case == "mcg":
+        for rep in range(2):
+            st = p.ba_solve_mcg(TOL, MAX_ITERS, 16, 1e9)
+            print(json.dumps({"kernel_case": "mcg", "precision": a.precision, "rep": rep, "ms": st["ms"],
+                              "iters": st["iters"], "local_steps": st["local_steps"],
+                              "true_rel_residual": st["true_rel_residual"]}), flush=True)
+        p.close()
+        torch.cuda.synchronize()
+        return
     ms = p.ba_time_kernel(a.kernel_case, 3)
     print(json.dumps({"kernel_case": a.kernel_case, "precision": a.precision, "nnzb": p.ba_get_schur_nnzb(),
                       "n_obs": sc.n_obs, "ms_per_launch": ms}), flush=True)

@@ -805,6 +805,21 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
     }
 }
 
+// 1 / p in float64 without the long division chain (an exact float64 division is a dependent
+// sequence of about ten operations on this GPU's narrow float64 pipe): a float32 estimate
+// (relative error below 2^-23) refined by Newton steps r <- r + r (1 - p r), each of which
+// squares the error: one step leaves it below 2^-46 (about 1e-14), two reach float64 rounding.
+// Values outside the float32 range divide.
+template <int kSteps = 1>
+__device__ __forceinline__ double fast_rcp(double p) {
+    const double ap = fabs(p);
+    if (!(ap > 1e-30 && ap < 1e30)) return 1.0 / p;
+    double r = double(__frcp_rn(float(p)));
+#pragma unroll
+    for (int k = 0; k < kSteps; ++k) r = fma(r, fma(-p, r, 1.0), r);
+    return r;
+}
+
 // ---------------------------------------------------------------------------------------
 // Algorithm 1 (grid: CTAs x problems)
 
@@ -875,7 +890,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
     // division is a long dependent chain on this GPU's narrow float64 pipe)
     T alpha;
     if constexpr (sizeof(T) == 4) alpha = __fdiv_rn(float(dg[1]), float(dg[0]));
-    else alpha = dg[1] / dg[0];
+    else alpha = dg[1] * fast_rcp<2>(dg[0]);
     const int64_t hb = c.lay.hoff - 9 * c0;
     const int64_t i = 9 * (c0 + jl) + a;
     double v[3] = {0.0, 0.0, 0.0};
@@ -926,7 +941,7 @@ __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int n
         c->done = 1;          // no measurable progress left at this precision: end the sweep
         c->status = BA_OK;
     } else {
-        c->beta = phi / D;
+        c->beta = phi * fast_rcp<2>(D);
     }
 }
 
@@ -1119,15 +1134,6 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
     __syncthreads();
 }
 
-// 1 / p in float64 without the long division chain: a float32 estimate (relative error below
-// 2^-23) refined by one Newton step r <- r + r (1 - p r), which squares the error (below 2^-46,
-// about 1e-14); pivots outside the float32 range divide.
-__device__ __forceinline__ double fast_rcp(double p) {
-    const double ap = fabs(p);
-    if (!(ap > 1e-30 && ap < 1e30)) return 1.0 / p;
-    const double r = double(__frcp_rn(float(p)));
-    return fma(r, fma(-p, r, 1.0), r);
-}
 
 // Inverse of the symmetric w x w matrix in sA by Gauss-Jordan sweeps on the diagonal (no
 // pivoting), accepted only when it equals the pseudo-inverse: every sweep pivot must be positive
