@@ -264,10 +264,17 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     s.diag_pos = upload(p, diag_pos);
     s.n_up = n_up;
     s.n_pairs = n_pairs;
-    s.up_j = upload(p, up_j);
-    s.up_k = upload(p, up_k);
-    s.up_pos = upload(p, up_pos);
-    s.up_mir = upload(p, up_mir);
+    {
+        // element offsets in the tiled layout, so the Schur kernels write without index lookups
+        std::vector<int64_t> dst(n_up), mdst(n_up);
+        for (int64_t u = 0; u < n_up; ++u) {
+            const int32_t j = up_j[u], k = up_k[u];
+            dst[u] = (tile_ptr[j] * ba::kTile + (up_pos[u] - row_ptr[j])) * 81;
+            mdst[u] = (tile_ptr[k] * ba::kTile + (up_mir[u] - row_ptr[k])) * 81;
+        }
+        s.up_dst = upload(p, dst);
+        s.up_mdst = upload(p, mdst);
+    }
     s.up_pair_ptr = upload(p, up_pp);
     s.pairs = upload(p, pr);
 }

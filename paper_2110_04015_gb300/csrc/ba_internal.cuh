@@ -78,10 +78,8 @@ struct Structure {
     // upper blocks (j <= k) with the observation pairs that feed them
     int64_t n_up = 0;
     int64_t n_pairs = 0;
-    int32_t* up_j = nullptr;      // n_up
-    int32_t* up_k = nullptr;      // n_up
-    int64_t* up_pos = nullptr;    // n_up: block index of (j, k)
-    int64_t* up_mir = nullptr;    // n_up: block index of (k, j), -1 on the diagonal
+    int64_t* up_dst = nullptr;    // n_up: element offset of block (j, k) in the tiled S (s_at(.., 0))
+    int64_t* up_mdst = nullptr;   // n_up: element offset of its mirror (k, j)
     int64_t* up_pair_ptr = nullptr;  // n_up + 1
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
     // batch: problem b owns cameras [h_cam_off[b], h_cam_off[b + 1]); one problem: {0, n_c}

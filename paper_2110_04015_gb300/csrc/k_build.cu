@@ -431,10 +431,9 @@ __global__ void __launch_bounds__(kCamThreads) k_schur_diag(int32_t n_c, const i
 // pair p; 16-pair chunks measured no faster).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_schur_off_rows(
-    int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
-    const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
-    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
-    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+    int64_t n_up, const int64_t* __restrict__ up_dst, const int64_t* __restrict__ up_mdst,
+    const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs, const T* __restrict__ G,
+    T* __restrict__ S) {
     constexpr int kChunk = 8;
     __shared__ T sg[kThreads / 32][kChunk][2][28];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -479,16 +478,24 @@ __global__ void __launch_bounds__(kThreads) k_schur_off_rows(
                 s2 += x[3 * a2] * y[3 * b2] + x[3 * a2 + 1] * y[3 * b2 + 1] + x[3 * a2 + 2] * y[3 * b2 + 2];
             }
         }
-        const int j = up_j[u], k = up_k[u];
-        const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
-        S[s_at(tile_ptr, j, qj, e0)] = -s0;
-        S[s_at(tile_ptr, j, qj, e1)] = -s1;
-        if (has2) S[s_at(tile_ptr, j, qj, e2)] = -s2;
-        S[s_at(tile_ptr, k, qk, b0 * 9 + a0)] = -s0;
-        S[s_at(tile_ptr, k, qk, b1 * 9 + a1)] = -s1;
-        if (has2) S[s_at(tile_ptr, k, qk, b2 * 9 + a2)] = -s2;
+        T* Sj = S + up_dst[u];
+        T* Sk = S + up_mdst[u];
+        Sj[e0] = -s0;
+        Sj[e1] = -s1;
+        if (has2) Sj[e2] = -s2;
+        Sk[b0 * 9 + a0] = -s0;
+        Sk[b1 * 9 + a1] = -s1;
+        if (has2) Sk[b2 * 9 + a2] = -s2;
     }
 }
+
+// 4-byte asynchronous copy global -> shared (cp.async, completion awaited by cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Nine consecutive values from a 16-byte aligned shared-memory address.
 __device__ __forceinline__ void lds9(const float* p, float* v) {
@@ -504,19 +511,18 @@ __device__ __forceinline__ void lds9(const float* p, float* v) {
 // (k, j).  Lane 9 g + 3 A + B (g < 3) accumulates the 3x3 sub-block at rows 3A.., columns 3B.. over the
 // pairs p = g (mod 3): it needs rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok, nine consecutive
 // values each, so one pair costs the lane two runs of vector shared loads for 27 fused
-// multiply-adds.  The warp takes the pairs kChunk at a time: lanes 0..26 load the two 27-value G
-// blocks of every pair of the chunk (one coalesced load per block, all of the chunk's loads in
-// flight together; lane p fetches the indices of pair p) and stage them in shared memory, each
-// 9-value part on a 16-byte boundary.  The three slices are added in slice order through shuffles,
+// multiply-adds.  The warp takes the pairs kChunk at a time: lanes 0..26 copy the two 27-value G
+// blocks of every pair of the chunk into shared memory with 4-byte asynchronous copies (all in
+// flight together, no staging registers; lane p fetches the indices of pair p), each 9-value
+// part on a 16-byte boundary.  48 registers let five CTAs share an SM.  The three slices are added in slice order through shuffles,
 // the block is assembled in shared memory and written with coalesced stores to (j, k) and,
 // transposed, to (k, j).  For the scaled float32 system G holds the rows of Lam G (k_scaled_g32),
 // so the same sums give Lam_j S_jk Lam_k.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_schur_off_sub(
-    int64_t n_up, const int32_t* __restrict__ up_j, const int32_t* __restrict__ up_k,
-    const int64_t* __restrict__ up_pos, const int64_t* __restrict__ up_mir, const int64_t* __restrict__ pair_ptr,
-    const int2* __restrict__ pairs, const T* __restrict__ G, const int64_t* __restrict__ row_ptr,
-    const int64_t* __restrict__ tile_ptr, T* __restrict__ S) {
+__global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
+    int64_t n_up, const int64_t* __restrict__ up_dst, const int64_t* __restrict__ up_mdst,
+    const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs, const T* __restrict__ G,
+    T* __restrict__ S) {
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
     constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
     constexpr int kPart = 12;                          // stride of a 9-value part (16-byte aligned)
@@ -536,26 +542,19 @@ __global__ void __launch_bounds__(kThreads) k_schur_off_sub(
             const int np = int(pe - q < kChunk ? pe - q : kChunk);
             int2 pr = make_int2(0, 0);
             if (lane < np) pr = pairs[q + lane];
-            T ga[kChunk], gb[kChunk];
+            __syncwarp();   // every lane is done with the previous chunk's staging area
+            // the chunk's G rows go straight to shared memory as 4-byte asynchronous copies (no
+            // staging registers, all copies in flight together); pairs past np are not read
 #pragma unroll
             for (int p = 0; p < kChunk; ++p) {
                 const int ox = __shfl_sync(0xffffffffu, pr.x, p);
                 const int oy = __shfl_sync(0xffffffffu, pr.y, p);
-                ga[p] = T(0);
-                gb[p] = T(0);
                 if (p < np && lane < 27) {
-                    ga[p] = __ldg(G + 27 * int64_t(ox) + lane);
-                    gb[p] = __ldg(G + 27 * int64_t(oy) + lane);
+                    cp_async4(&sg[wid][p][0][stage], G + 27 * int64_t(ox) + lane);
+                    cp_async4(&sg[wid][p][1][stage], G + 27 * int64_t(oy) + lane);
                 }
             }
-            __syncwarp();
-#pragma unroll
-            for (int p = 0; p < kChunk; ++p) {
-                if (lane < 27) {
-                    sg[wid][p][0][stage] = ga[p];
-                    sg[wid][p][1][stage] = gb[p];
-                }
-            }
+            cp_async_wait_all();
             __syncwarp();
             if (g < 3) {
                 for (int p = g; p < np; p += 3) {
@@ -584,12 +583,11 @@ __global__ void __launch_bounds__(kThreads) k_schur_off_sub(
                 for (int c = 0; c < 3; ++c) sb[wid][(3 * A + r) * 9 + 3 * B + c] = acc[3 * r + c];
         }
         __syncwarp();
-        const int j = up_j[u], k = up_k[u];
-        const int64_t qj = up_pos[u] - row_ptr[j], qk = up_mir[u] - row_ptr[k];
-        for (int e = lane; e < 81; e += 32) S[s_at(tile_ptr, j, qj, e)] = -sb[wid][e];
+        const int64_t dj = up_dst[u], dk = up_mdst[u];
+        for (int e = lane; e < 81; e += 32) S[dj + e] = -sb[wid][e];
         for (int e = lane; e < 81; e += 32) {
             const int b = e / 9, a = e - 9 * (e / 9);   // entry e = 9 b + a of (k, j) is (a, b) of (j, k)
-            S[s_at(tile_ptr, k, qk, e)] = -sb[wid][9 * a + b];
+            S[dk + e] = -sb[wid][9 * a + b];
         }
         __syncwarp();
     }
@@ -906,7 +904,7 @@ void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
     if (s.n_up > 0)
         k_schur_off_rows<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G, s.row_ptr, s.tile_ptr, y.S);
+            s.n_up, s.up_dst, s.up_mdst, s.up_pair_ptr, s.pairs, y.G, y.S);
     k_put_diag<double><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S);
 }
@@ -915,7 +913,7 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
     k_scaled_g32<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, y.lam32, y.G32);
     if (s.n_up > 0)
         k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_j, s.up_k, s.up_pos, s.up_mir, s.up_pair_ptr, s.pairs, y.G32, s.row_ptr, s.tile_ptr, y.S32);
+            s.n_up, s.up_dst, s.up_mdst, s.up_pair_ptr, s.pairs, y.G32, y.S32);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32);
 }
