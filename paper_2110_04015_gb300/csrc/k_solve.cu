@@ -529,9 +529,20 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
 // shared memory as in k_spmv; lane = 4 qi + g takes tile-local blocks qi, qi + 8, qi + 16, qi + 24
 // and columns 4g .. 4g + 3, so each 9x9 block multiplies up to 16 columns per read from shared
 // memory.  PT is the row-major copy (9 n_c x 16, all problems) of the new blocks.
+// The multi-column product waits on L2 gathers of PT more than on its tiles, so it runs twice
+// the warps of k_spmv with one tile stage each (the other warps' copies and arithmetic cover a
+// warp's wait for its next tile); at most 128 registers a thread.
+struct SpmmCfg {
+    static constexpr int kWarps = 16, kStages = 1;
+};
+template <typename T>
+constexpr size_t spmm_tiles_smem() {
+    return sizeof(T) * SpmmCfg::kWarps * SpmmCfg::kStages * kTileElems +
+           sizeof(uint64_t) * SpmmCfg::kWarps * SpmmCfg::kStages;
+}
 template <typename T>
 constexpr size_t spmm_smem() {
-    return spmv_smem<T>() + sizeof(T) * SpmvCfg<T>::kWarps * kMaxDirs * 9;
+    return spmm_tiles_smem<T>() + sizeof(T) * SpmmCfg::kWarps * kMaxDirs * 9;
 }
 
 // rows b = 0..8 of a 16-column PT block, 4 columns from p: (p[16 b], p[16 b + 1]) and
@@ -546,12 +557,12 @@ __device__ __forceinline__ void load_prow(const float* p, float2 (&v)[9][2]) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
+__global__ void __launch_bounds__(SpmmCfg::kWarps * 32, 1) k_spmm(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
     const T* __restrict__ S, const T* __restrict__ PT, ItemList L, T* __restrict__ part, T* __restrict__ Q,
     Ctl* ctl) {
     static_assert(sizeof(T) == 4, "the multi-column product serves the float32 sweeps");
-    constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
+    constexpr int NW = SpmmCfg::kWarps, NS = SpmmCfg::kStages;
     constexpr int sel = kSelWide;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (nothing_selected(ctl, L, sel)) return;
@@ -559,7 +570,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
     const int qi = lane >> 2, g = lane & 3;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
-    T* red = reinterpret_cast<T*>(smem_raw + spmv_smem<T>()) + wid * (kMaxDirs * 9);
+    T* red = reinterpret_cast<T*>(smem_raw + spmm_tiles_smem<T>()) + wid * (kMaxDirs * 9);
     constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
     if (lane == 0) {
         for (int st = 0; st < NS; ++st) mbar_init(&bars[st]);
@@ -599,17 +610,15 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
             const bool active = 4 * g < w;
             // column cameras of this lane's blocks r * 8 + qi (r = 0..3) of tile t, -1 outside the
-            // item; fetched one tile ahead, and the P rows of each block one block ahead (those of a
-            // tile's first block during the previous tile's last one), so the gathers overlap the
-            // arithmetic
+            // item; fetched one tile ahead.  The P rows of a block are gathered right before its
+            // arithmetic: the other warps of the SM cover the wait
             int kc[4], kn[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int q = t0 * 32 + r * 8 + qi;
                 kc[r] = (active && q >= it.q0 && q < it.q1) ? col[rj + q] : -1;
             }
-            float2 pv[2][9][2];
-            if (kc[0] >= 0) load_prow(PT + (int64_t(kc[0]) * 9) * kMaxDirs + 4 * g, pv[0]);
+            float2 pv[9][2];
             for (int t = t0; t < t1; ++t) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -628,10 +637,9 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
                 if (active) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT for the next block
-                        const int knext = r < 3 ? kc[r + 1] : kn[0];
-                        if (knext >= 0) load_prow(PT + (int64_t(knext) * 9) * kMaxDirs + 4 * g, pv[(r + 1) & 1]);
                         if (kc[r] < 0) continue;
+                        // rows 9k .. 9k + 8, columns 4g .. 4g + 3 of PT for this block
+                        load_prow(PT + (int64_t(kc[r]) * 9) * kMaxDirs + 4 * g, pv);
                         const T* blk = tile + (r * 8 + qi) * 81;
 #pragma unroll
                         for (int a = 0; a < 9; ++a)
@@ -639,8 +647,8 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmm(
                             for (int b = 0; b < 9; ++b) {
                                 const float sab = blk[9 * a + b];
                                 const float2 s2 = make_float2(sab, sab);
-                                acc[a][0] = __ffma2_rn(s2, pv[r & 1][b][0], acc[a][0]);
-                                acc[a][1] = __ffma2_rn(s2, pv[r & 1][b][1], acc[a][1]);
+                                acc[a][0] = __ffma2_rn(s2, pv[b][0], acc[a][0]);
+                                acc[a][1] = __ffma2_rn(s2, pv[b][1], acc[a][1]);
                             }
                     }
                 }
@@ -2155,7 +2163,7 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
             k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, ptr<T>(w->PT), ctl);
             k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
-            k_spmm<T><<<Gt, SpmvCfg<T>::kWarps * 32, spmm_smem<T>(), st>>>(
+            k_spmm<T><<<Gt, SpmmCfg::kWarps * 32, spmm_smem<T>(), st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->PT), w->items_g, static_cast<T*>(w->mm_part), Q, ctl);
         }
     }
