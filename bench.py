@@ -42,6 +42,7 @@ WORKLOADS = {
 LAMBDA = 1e-4
 TOL = 1e-6
 MAX_ITERS = 1000
+LM_MAX_STEPS, LM_FTOL = 25, 1e-6   # Section 4.1: at most 25 LM iterations, relative cost tolerance
 METRIC = "time to rel. residual 1e-6 per LM solve (MCG vs PCG, FP64 vs mixed); HBM GB/s"
 
 
@@ -65,6 +66,10 @@ def parse():
     ap.add_argument("--sweep", choices=["tau", "ndirs", "density"],
                     help="sensitivity mode (Figs. 3-5 of the paper): MCG vs PCG time-to-1e-6 over tau, N or the "
                          "density of S; prints one JSON line per point and exits")
+    ap.add_argument("--lm-run", action="store_true",
+                    help="whole-run mode: Levenberg-Marquardt (ba_lm_step, at most 25 iterations, lambda0 1e-4, "
+                         "stop at a relative cost decrease below 1e-6) once with PCG and once with MCG from the same "
+                         "start; the paper's solver runtime ratio over the whole run; one JSON line")
     ap.add_argument("--batched", action="store_true",
                     help="batch mode: 64 uneven problems (50-600 cameras, 300 landmarks per camera, tracks mean 8) "
                          "solved by MCG in the same launches, against looping single-problem solves; one JSON line")
@@ -505,6 +510,50 @@ def run_sweep(a):
             one(sc, {"workload": "dense-1000x400k", "p_uniform": pu, "density": d}, [(16, 10.0)])
 
 
+def run_lm(a):
+    """The paper's solver runtime ratio over a whole bundle-adjustment run (Section 5): the LM loop
+    with each solver from the same start, summing the solve times of its normal equations."""
+    import torch
+
+    from paper_2110_04015_gb300 import problem
+
+    gen, kw, desc = WORKLOADS[a.workload]
+    sc = synthetic.make(gen, 0, **kw)
+    xy = problem.device_measurements(sc)
+    runs = {}
+    for solver in ("pcg", "mcg"):
+        for rep in range(2):   # the first run pays for graph capture and buffer growth
+            p = problem.from_scene(sc, precision=a.precision, xy=xy)
+            cost0 = p.ba_cost()
+            steps = []
+            for _ in range(LM_MAX_STEPS):
+                st = p.ba_lm_step(solver, lambda0=LAMBDA, tol=TOL, max_iters=MAX_ITERS, n_dirs=a.n_dirs, tau=a.tau,
+                                  ftol=LM_FTOL)
+                steps.append(st)
+                if st["converged"]:
+                    break
+            cost_end = p.ba_cost()
+            p.close()
+            torch.cuda.synchronize()
+        runs[solver] = {
+            "lm_iterations": len(steps), "accepted": sum(s["accepted"] for s in steps),
+            "converged": bool(steps[-1]["converged"]), "cost_start": cost0,
+            "cost_end": cost_end,
+            "solver_iters": sum(s["solver_iters"] for s in steps),
+            "solve_ms": sum(s["solve_ms"] for s in steps), "total_ms": sum(s["ms"] for s in steps),
+        }
+    r_solve = runs["mcg"]["solve_ms"] / runs["pcg"]["solve_ms"]
+    print(json.dumps({
+        "mode": "lm-run", "metric": "solver runtime ratio t_MCG / t_PCG over a whole LM run (Section 5)",
+        "value": r_solve, "unit": "ratio", "higher_is_better": False, "precision": a.precision,
+        "config": {"workload": a.workload, "description": desc, "n_cams": sc.n_cams, "n_obs": sc.n_obs,
+                   "lambda0": LAMBDA, "tol": TOL, "lm_max_steps": LM_MAX_STEPS, "lm_ftol": LM_FTOL,
+                   "mcg": {"n_dirs": a.n_dirs, "tau": a.tau}},
+        "pcg": runs["pcg"], "mcg": runs["mcg"],
+        "total_ratio": runs["mcg"]["total_ms"] / runs["pcg"]["total_ms"],
+    }), flush=True)
+
+
 def run_batched(a):
     """Batched uneven problems: one handle (ba_batch_create) against a loop over single-problem handles.
 
@@ -692,6 +741,9 @@ def main():
         return
     if a.kernel_case:
         run_kernel_case(a)
+        return
+    if a.lm_run:
+        run_lm(a)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

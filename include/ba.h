@@ -111,7 +111,8 @@ typedef struct ba_lm_stats {
     double cost_after;         /* F(x + dx) of the trial step */
     double lambda_used;
     double lambda_next;
-    double ms;
+    double ms;                 /* the whole step: cost, build, solve, back-substitution, trial cost */
+    double solve_ms;           /* the solve alone (Algorithm 1 or 2), as ba_solve_stats.ms */
 } ba_lm_stats;
 
 typedef struct ba_problem ba_problem;

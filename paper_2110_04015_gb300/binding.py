@@ -50,7 +50,8 @@ class ba_solve_stats(ctypes.Structure):
 class ba_lm_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("accepted", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("solver_iters", ctypes.c_int32), ("cost_before", ctypes.c_double), ("cost_after", ctypes.c_double),
-                ("lambda_used", ctypes.c_double), ("lambda_next", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("lambda_used", ctypes.c_double), ("lambda_next", ctypes.c_double), ("ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -642,6 +642,7 @@ int ba_lm_step(ba_problem* p, int32_t solver, double lambda0, double tol, int32_
             ba_solve_stats ss;
             code = do_solve(p, make_args(p, solver == BA_SOLVER_MCG, tol, max_iters, n_dirs, tau), &ss);
             s.solver_iters = ss.iters;
+            s.solve_ms = ss.ms;
             if (code != BA_OK && code != BA_ERR_NOT_CONVERGED) have_step = false;
         }
         if (have_step) {

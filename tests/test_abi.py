@@ -35,7 +35,7 @@ def test_struct_layouts_match_header():
     # sizes implied by include/ba.h (int32 fields, then doubles, natural alignment)
     assert ctypes.sizeof(binding.ba_options) == 4 * 4 + 8 + 4 * 8
     assert ctypes.sizeof(binding.ba_solve_stats) == 6 * 4 + 3 * 8
-    assert ctypes.sizeof(binding.ba_lm_stats) == 4 * 4 + 5 * 8
+    assert ctypes.sizeof(binding.ba_lm_stats) == 4 * 4 + 6 * 8
 
 
 def test_default_options_and_errors_without_device(libba):
