@@ -1152,11 +1152,9 @@ __device__ void pinv_sym_jacobi(double (*sA)[kMaxDirs + 1], double (*sV)[kMaxDir
 // eigenvalue is dropped, so A^+ = A^{-1}.  Thread 16 i + j (of the first 256) owns entry (i, j);
 // a sweep updates every entry once, and the owner of the next pivot forms its reciprocal right
 // after its own update, so the dependent float64 chain is 16 reciprocals long and no other thread
-// spends the narrow float64 pipe on it.  sA is left intact; sX receives A^{-1} (symmetrised); sL
-// is unused.  Returns false (sX undefined) when the certificate fails.
-__device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sL)[kMaxDirs + 1],
-                                  double (*sX)[kMaxDirs + 1], int w) {
-    (void)sL;
+// spends the narrow float64 pipe on it.  sA is left intact; sX receives A^{-1} (symmetrised).
+// Returns false (sX undefined) when the certificate fails.
+__device__ bool inverse_certified(double (*sA)[kMaxDirs + 1], double (*sX)[kMaxDirs + 1], int w) {
     __shared__ int ok;
     __shared__ double tr, trinv;
     __shared__ double rk[kMaxDirs];   // 1 / pivot k
@@ -1276,7 +1274,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mcg_small(Ctl* ctl, const dou
     if (w == 1) {
         if (threadIdx.x == 0) sX[0][0] = sA[0][0] > 0.0 ? 1.0 / sA[0][0] : 0.0;
         __syncthreads();
-    } else if (!inverse_certified(sA, sV, sX, w)) {
+    } else if (!inverse_certified(sA, sX, w)) {
         pinv_sym_jacobi(sA, sV, sX, w);
     }
     if (threadIdx.x < kMaxDirs * kMaxDirs) {
