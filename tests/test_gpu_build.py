@@ -9,6 +9,8 @@ Tolerances (float64 on both sides, different summation orders):
     so the error is set by the size of U, not of the result;
   * D(S)^{-1}: S_jj D_j = I to 1e-8 relative to kappa(S_jj) * 1e-16.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -48,6 +50,22 @@ def test_projection_matches_oracle(case):
     xy = problem.device_measurements(sc).cpu().numpy()
     m = olm.measurements(sc)
     assert rel_max(xy, m) < 1e-11
+
+
+def test_projection_matches_hand_worked_example():
+    import torch
+
+    from paper_2110_04015_gb300 import binding
+
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "bal_projection_worked_example.txt"))
+    dev = "cuda"
+    cams = torch.from_numpy(np.ascontiguousarray(rows[:, :9])).to(dev)
+    pts = torch.from_numpy(np.ascontiguousarray(rows[:, 9:12])).to(dev)
+    idx = torch.arange(rows.shape[0], dtype=torch.int32, device=dev)
+    out = torch.empty((rows.shape[0], 2), dtype=torch.float64, device=dev)
+    binding.ba_project(cams, pts, idx, idx, out)
+    torch.cuda.synchronize()
+    assert np.allclose(out.cpu().numpy(), rows[:, 12:14], rtol=1e-13, atol=1e-11)
 
 
 @pytest.mark.parametrize("case", BUILD_CASES)

@@ -1,4 +1,6 @@
 """Pins of the oracle's camera model (Section 3.1, Eqs. 1-4; BAL model reading)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -128,3 +130,14 @@ def test_planted_sign_error_is_caught():
         return Jp, Jl
 
     assert jacobian_fd_error(broken) > 1e-3
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "bal_projection_worked_example.txt")
+
+
+def test_projection_matches_hand_worked_example():
+    # rows: camera (9), point (3), projection worked out by hand in the file's header
+    rows = np.loadtxt(GOLDEN)
+    for r in rows:
+        pi = camera.project(r[None, :9], r[None, 9:12], np.array([0]), np.array([0]))[0]
+        assert np.allclose(pi, r[12:14], rtol=1e-14, atol=1e-12), (pi, r[12:14])
