@@ -99,9 +99,10 @@ def load_peaks() -> dict:
 
 
 # DRAM bytes per stored 9x9 block of one k_spmv<float,1,true> launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of the 1000-camera case, 319.8 MB / 958,652 blocks;
-# traffic grows with the stored blocks): profiles/k_spmv_f32_dense-1000cams.md
-SPMV_F32_TRAFFIC_PER_BLOCK = 333.6
+# dram__bytes_write.sum from an ncu capture of the 1000-camera case with 16 warps per SM,
+# 319.9 MB / 958,652 blocks; traffic grows with the stored blocks):
+# profiles/k_spmv_f32_dense-1000cams.md
+SPMV_F32_TRAFFIC_PER_BLOCK = 333.7
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
