@@ -1238,7 +1238,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mcg_small(Ctl* ctl, const dou
         const int per_round = int(blockDim.x) / G;
         for (int e0 = 0; e0 < ne; e0 += per_round) {
             const int e = e0 + int(threadIdx.x) / G, g = int(threadIdx.x) % G;
-            // warps holding no entry of this round skip the arithmetic (and their shuffles) whole
+            // warps holding no entry of this pass skip the arithmetic (and their shuffles) whole
             if (e0 + int(threadIdx.x & ~31u) / G >= ne) continue;
             ExactSum<T> acc[8];
             if (e < ne) {
