@@ -23,7 +23,7 @@
 //     beta_{i,j} = Delta_j^+ Q_j^T Z_{i+1},  P_{i+1} = Z_{i+1} - sum_j P_j beta_{i,j},
 //     Q_{i+1}   = S Z_{i+1} - sum_j Q_j beta_{i,j}            (Eq. 18 with j = 0..i)
 // where S Z_{i+1} applies each block S_jk only to the column of the subset of pose k
-// (Section 3.2, "Optimized implementation").
+// (the product trick of Section 3.2).
 #include <cuda_runtime.h>
 
 #include <algorithm>

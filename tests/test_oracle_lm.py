@@ -16,7 +16,7 @@ def test_lm_decreases_cost_to_noise_level():
 
 
 def test_pcg_and_mcg_give_the_same_cost_each_iteration():
-    """Section 4.4: "MCG and PCG give the same error at each BA iteration"."""
+    """Section 4.4: MCG and PCG reach the same error at every BA iteration."""
     sc = scene("tiny")
     m = lm.measurements(sc)
     a = lm.lm(sc.cams0, sc.pts0, sc.obs_cam, sc.obs_pt, m, solver="pcg", max_iters=8)
@@ -25,3 +25,23 @@ def test_pcg_and_mcg_give_the_same_cost_each_iteration():
     assert n >= 4
     rel = np.abs(np.array(a.costs[:n]) - np.array(b.costs[:n])) / np.array(a.costs[:n])
     assert rel.max() < 1e-6
+
+
+def test_lambda_schedule_on_rejected_and_accepted_steps():
+    """The LM lambda rule read for Section 4.1: accept when F decreases and divide lambda by 10,
+    otherwise keep the state and multiply lambda by 10 (clamped to [1e-12, 1e16])."""
+    sc = scene("tiny")
+    m = lm.measurements(sc)
+    rng = np.random.default_rng(3)
+    # a 20 % perturbation with no damping to start from: the first Gauss-Newton steps overshoot
+    cams0 = sc.cams0 + 0.2 * np.abs(sc.cams0) * rng.standard_normal(sc.cams0.shape)
+    tr = lm.lm(cams0, sc.pts0, sc.obs_cam, sc.obs_pt, m, solver="pcg", lam0=1e-12, max_iters=10)
+    assert not all(tr.accepted) and any(tr.accepted)
+    for i, ok in enumerate(tr.accepted):
+        if i + 1 < len(tr.lambdas):
+            want = max(tr.lambdas[i] / 10, 1e-12) if ok else min(tr.lambdas[i] * 10, 1e16)
+            assert tr.lambdas[i + 1] == want, (i, tr.lambdas)
+        if ok:
+            assert tr.costs[i + 1] < tr.costs[i]
+        else:
+            assert tr.costs[i + 1] == tr.costs[i]
