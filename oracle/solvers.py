@@ -3,7 +3,7 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 Both solve S dx_p = -b~ (Eq. 12/16) from x0 = 0 (the paper leaves x0 open;
-zero is the reading used).  The stop test "r_{i+1} < eps * r0" is read as the
+zero is the reading used).  The stop test, r_{i+1} against eps * r0, is read as the
 Euclidean norm of the recursive (unpreconditioned) residual, eps = 1e-6 and
 imax = 1000 by default (Section 4.1).
 
@@ -17,8 +17,9 @@ Readings of points the paper leaves open:
   w * 2^-52 * lambda_max of the w x w symmetric Delta; for a full-rank Delta it
   is the inverse and for w = 1 a division.
 * The poses are split into subsets of s = ceil(n_p / N) consecutive poses,
-  the last holding the remainder ("N - 1 subsets of same size", end of
-  Section 3.2); ceil(n_p / s) <= N of them are non-empty.
+  the last holding the remainder (the paper makes N - 1 equal subsets and puts
+  the leftover poses in the last, end of Section 3.2); ceil(n_p / s) <= N of
+  them are non-empty.
 * The tau-test is strict: t_i < tau takes the N local directions, otherwise a
   single global direction (a PCG step).
 * Eq. 18 prints Q_i = S Z_i - sum_{j<i} Q_j beta_{i,j}; applying S to the P
