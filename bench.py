@@ -99,9 +99,8 @@ def load_peaks() -> dict:
 
 
 # DRAM bytes per stored 9x9 block of one k_spmv<float,1,true> launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of the 1000-camera case with 16 warps per SM,
-# 319.9 MB / 958,652 blocks; traffic grows with the stored blocks):
-# profiles/k_spmv_f32_dense-1000cams.md
+# dram__bytes_write.sum from an ncu capture of the 1000-camera dense case with 16 warps per SM,
+# 319.9 MB / 958,652 blocks; traffic grows with the stored blocks)
 SPMV_F32_TRAFFIC_PER_BLOCK = 333.7
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
@@ -344,14 +343,14 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
     spmv_flops = 162.0 * nnzb
     if a.precision == "fp64":
-        roof = {"kernel": "k_spmv<double,1,true> (q = S p, Algorithm 1 line 3)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
+        roof = {"kernel": "k_spmv<double,1,true> (q = S p, Algorithm 1)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
                 "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "ms_per_launch": t_spmv,
                 "achieved_gbs": spmv_bytes / t_spmv / 1e6, "hbm_peak_gbs": peaks["hbm_gbs"],
                 "peak_source": "measured FP64 FMA throughput 1.06 TFLOP/s (nominal 1.25)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
-        roof = {"kernel": "k_spmv<float,1,true> (q = S p, Algorithm 1 line 3)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
+        roof = {"kernel": "k_spmv<float,1,true> (q = S p, Algorithm 1)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": SPMV_F32_TRAFFIC_PER_BLOCK * nnzb,
                 "traffic_source": "ncu dram bytes of the 1000-camera case scaled by stored blocks",
                 "bytes_per_launch": spmv_bytes,

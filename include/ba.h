@@ -285,7 +285,7 @@ int ba_get_batch_history(const ba_problem* p, int32_t problem, double* hist, int
 int ba_get_launch_count(const ba_problem* p, int64_t* n);
 
 typedef enum ba_kernel {
-    BA_KERNEL_SPMV = 0,        /* q = S p of Algorithm 1 line 3, at the handle's precision */
+    BA_KERNEL_SPMV = 0,        /* q = S p of Algorithm 1, at the handle's precision */
     BA_KERNEL_SCHUR = 1,       /* the S_jk = delta U_j - sum G G^T block build (Eq. 13) */
     BA_KERNEL_LINEARIZE = 2    /* residuals and Jacobians of every observation (Eqs. 2-4) */
 } ba_kernel;
@@ -301,7 +301,7 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
 
 /*
  * Choose the work-item size of the block-sparse products by measurement: the PCG product q = S p
- * (Algorithm 1, line 3) over every problem is timed for 32, 64, 128, 256, 512 and 1024 blocks per
+ * (Algorithm 1) over every problem is timed for 32, 64, 128, 256, 512 and 1024 blocks per
  * item (`reps` launches each, L2 flushed before each), and the fastest is stored in the handle's
  * item_blocks option for later solves.  Needs ba_build_normal.  *item_blocks and *ms (may be
  * NULL) receive the choice and its mean time.  The paper has no counterpart (its products run on
@@ -380,10 +380,14 @@ int ba_gnn_launch_count(const ba_gnn* g, int64_t* n);
  * every GPU loading the library holds until the process exits; each call overwrites every
  * entry it reads, so nothing has to be cleared between calls.  All calls share that array:
  * calls that overlap on the GPU (different streams, or different host threads) race and give
- * wrong results, so order them.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), which is not a stream operation; make that first call before
- * any stream capture.  No cudaMalloc, cudaFree or other allocating call is made.  Errors:
- * INVALID_ARG, CUDA; the text is available from ba_last_error(NULL) on the calling thread.
+ * wrong results, so order them.  A call made outside a stream capture looks up the array's
+ * device address on the current device (cudaGetSymbolAddress, not a stream operation), so the
+ * address stays right after cudaDeviceReset; a call whose stream is capturing uses the address
+ * found by the last call outside capture on that device.  Make the first call on a device before
+ * any stream capture (otherwise STATE).  No cudaMalloc, cudaFree or other allocating call is
+ * made.  The library cannot check the lengths or the device of the arrays (it gets pointers
+ * only): the caller keeps them as stated above.  Errors: INVALID_ARG, STATE, CUDA; the text is
+ * available from ba_last_error(NULL) on the calling thread.
  */
 int ba_schur_residual_static(int32_t n_cams, const int64_t* row_ptr, const int32_t* col,
                              const double* blocks, const double* btilde, const double* x,

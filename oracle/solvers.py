@@ -28,7 +28,9 @@ Readings of points the paper leaves open:
   Algorithm 2 states it.
 
 Pins: the solutions against a dense Cholesky solve of S; MCG with N = 1 or
-tau = 0 against PCG iterate by iterate; non-increasing S-energy error;
+tau = 0 against PCG iterate by iterate; non-increasing S-energy error; t_i of the
+tau-test against the energy decrease of each step over the preconditioned norm of the
+new residual, both formed independently, and a hand-worked two-camera value;
 S-conjugacy of the search blocks; finite termination of PCG; the
 pseudo-inverse against the Moore-Penrose identities and an SVD pseudo-inverse.
 """
@@ -84,6 +86,16 @@ def subsets(n_cams: int, n_dirs: int) -> tuple[np.ndarray, int]:
     return sub, int(-(-n_cams // s))
 
 
+def tau_ratio(gamma: np.ndarray, alpha: np.ndarray, r_next: np.ndarray, z_next: np.ndarray) -> float:
+    """The adaptive tau-test quantity of Algorithm 2 (Section 3.2):
+
+        t_i = gamma_i^T alpha_i / (r_{i+1}^T D(S)^{-1} r_{i+1}),
+
+    the decrease of the S-energy error made by step i over the preconditioned norm of the new
+    residual (z_next = D(S)^{-1} r_next)."""
+    return float(gamma @ alpha) / float(r_next @ z_next)
+
+
 @dataclass
 class SolveResult:
     x: np.ndarray
@@ -93,6 +105,7 @@ class SolveResult:
     local_steps: int = 0
     xs: list = field(default_factory=list)          # iterates x_{i+1} when recorded
     P: list = field(default_factory=list)           # search blocks when recorded
+    t: list = field(default_factory=list)           # MCG: t_i of every step that reached the tau-test
     converged: bool = False
 
 
@@ -176,7 +189,8 @@ def mcg(S, btilde, Dinv, n_dirs, tau, eps=1e-6, imax=1000, q_trick=True, record=
             res.converged = True
             break
         z = apply_block_diag(Dinv, r)
-        t = float(gamma @ alpha) / float(r @ z)
+        t = tau_ratio(gamma, alpha, r, z)
+        res.t.append(t)
         if t < tau:
             Z = np.zeros((n, n_eff))
             Z[np.arange(n), row_sub] = z

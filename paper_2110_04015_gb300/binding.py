@@ -176,8 +176,51 @@ def ba_project(cams, pts, obs_cam, obs_pt, out, stream=None) -> None:
     _check(code)
 
 
+def _static_args_check(n_cams, row_ptr, col, blocks, btilde, x, out) -> None:
+    """Reject what the library cannot check itself: it receives raw device pointers and no lengths,
+    so a wrong dtype, a short array or a host array would be read out of bounds on the device."""
+    import torch
+
+    named = {"row_ptr": row_ptr, "col": col, "blocks": blocks, "btilde": btilde, "x": x, "out": out}
+    for name, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor on the current CUDA device, got {type(t).__name__}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    want = {"row_ptr": torch.int64, "col": torch.int32, "blocks": torch.float64, "btilde": torch.float64,
+            "x": torch.float64, "out": torch.float64}
+    for name, dt in want.items():
+        if named[name].dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {named[name].dtype}")
+    n = int(n_cams)
+    if 1 <= n <= BA_STATIC_MAX_CAMS:
+        if row_ptr.numel() != n + 1:
+            raise ValueError(f"row_ptr must hold n_cams + 1 = {n + 1} offsets, got {row_ptr.numel()}")
+        if btilde.numel() != 9 * n or x.numel() != 9 * n:
+            raise ValueError(f"btilde and x must hold 9 n_cams = {9 * n} values")
+        if out.numel() < 2:
+            raise ValueError("out must hold 2 values")
+    for name, t in named.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, t in named.items():
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    if 1 <= n <= BA_STATIC_MAX_CAMS and (blocks.numel() % 81 != 0 or blocks.numel() // 81 != col.numel()):
+        raise ValueError(f"blocks must hold 81 values per entry of col ({col.numel()}), got {blocks.numel()}")
+
+
 def ba_schur_residual_static(n_cams, row_ptr, col, blocks, btilde, x, out, stream=None) -> None:
-    """|-b~ - S x| and |b~| into out[0:2] without any device allocation (device tensors)."""
+    """|-b~ - S x| and |b~| into out[0:2] without any device allocation.
+
+    Every array is a contiguous torch tensor on the current CUDA device: row_ptr int64 (n_cams + 1),
+    col int32, blocks float64 (81 per entry of col), btilde and x float64 (9 n_cams), out float64
+    (>= 2).  Anything else is rejected here from the tensors' metadata alone, before the library is
+    called; the contents of row_ptr and col (offsets within col, columns within [0, n_cams)) are the
+    caller's to keep valid, since checking them would mean reading device memory back.
+    """
+    _static_args_check(n_cams, row_ptr, col, blocks, btilde, x, out)
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     code = lib().ba_schur_residual_static(int(n_cams), _ptr(row_ptr), _ptr(col), _ptr(blocks), _ptr(btilde),
                                           _ptr(x), _ptr(out), st)

@@ -8,8 +8,10 @@
 //
 // The array is part of the loaded library image, so every GPU that loads the library holds it
 // (1 MiB) until the process exits.  Host code cannot use the array's name as a device address;
-// the address is looked up once per device with cudaGetSymbolAddress the first time the entry
-// point runs on that device.
+// the address comes from cudaGetSymbolAddress with the device current.  Outside a stream capture
+// it is looked up again on every call, so a call after cudaDeviceReset (which reloads the module)
+// or from another context of the device gets the current address; while the call's stream is
+// capturing, the address from the last call made outside capture on that device is used.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -99,8 +101,9 @@ __global__ void k_static_total(int32_t n_c, const double* __restrict__ scratch, 
     }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-int scratch_address(double** addr, std::string& err) {
+// Device address of the scratch array on the current device (see the file comment for when it is
+// looked up).  A call on a capturing stream with nothing cached yet is refused with STATE.
+int scratch_address(cudaStream_t st, double** addr, std::string& err) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -111,8 +114,14 @@ int scratch_address(double** addr, std::string& err) {
         err = "device index out of range";
         return BA_ERR_INVALID_ARG;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // e.g. the legacy stream queried while another stream captures
+        cs = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_residual_scratch);
         if (e != cudaSuccess || !p) {
@@ -120,6 +129,9 @@ int scratch_address(double** addr, std::string& err) {
             return BA_ERR_CUDA;
         }
         g_scratch_addr[dev] = static_cast<double*>(p);
+    } else if (!g_scratch_addr[dev]) {
+        err = "the first call on a device must be made outside a stream capture";
+        return BA_ERR_STATE;
     }
     *addr = g_scratch_addr[dev];
     return BA_OK;
@@ -143,7 +155,7 @@ extern "C" int ba_schur_residual_static(int32_t n_cams, const int64_t* row_ptr, 
         return BA_ERR_INVALID_ARG;
     }
     double* scratch = nullptr;
-    int code = ba::scratch_address(&scratch, err);
+    int code = ba::scratch_address(static_cast<cudaStream_t>(stream), &scratch, err);
     if (code != BA_OK) {
         ba::set_thread_error("ba_schur_residual_static: " + err);
         return code;

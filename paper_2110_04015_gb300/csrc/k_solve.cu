@@ -78,7 +78,7 @@ struct Ctl {
     double alpha_v[kMaxDirs];
     double true_rr, bb;                 // true residual and |rhs|^2
     double stag;       // float32 sweeps: stop when t_i (energy decrease / r^T D^-1 r) falls below this
-    int direct_q;      // 1: Q_{i+1} = S P_{i+1} (Algorithm 2, line 3); 0: the Q update of Eq. 18
+    int direct_q;      // 1: Q_{i+1} = S P_{i+1} (Algorithm 2); 0: the Q update of Eq. 18
     int pad_;
 };
 
@@ -374,9 +374,9 @@ __device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, co
 // ZH: z is a column of the problem's direction history (column new_off in MODE 2, column 0
 //     otherwise); else z is a vector over all cameras.
 // MODE 0: y goes to column new_off + seg of the problem's Q.
-// MODE 1 (Algorithm 1, line 3): q = y (Q column 0) and, per camera, the sums of q^T p and p^T r
-//         (Delta and gamma of Algorithm 1, line 4, before the sum over cameras).
-// MODE 2 (Algorithm 2, line 3, width 1): y goes to column new_off of Q.
+// MODE 1 (Algorithm 1): q = y (Q column 0) and, per camera, the sums of q^T p and p^T r
+//         (Delta and gamma of Algorithm 1, before the sum over cameras).
+// MODE 2 (Algorithm 2, width 1): y goes to column new_off of Q.
 template <typename T, int MODE, bool ZH>
 __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
 }
 
 // Q[:, new_off + c] = S P[:, new_off + c] for the w > 1 columns of a new local block (Algorithm 2,
-// line 3, used by the float32 sweeps, where the Eq. 18 update cancels).  Tiles stream through
+// used by the float32 sweeps, where the Eq. 18 update cancels).  Tiles stream through
 // shared memory as in k_spmv; lane = 4 qi + g takes tile-local blocks qi, qi + 8, qi + 16, qi + 24
 // and columns 4g .. 4g + 3, so each 9x9 block multiplies up to 16 columns per read from shared
 // memory.  PT is the row-major copy (9 n_c x 16, all problems) of the new blocks.
@@ -2159,7 +2159,7 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
                     s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l, kSelLocal, Q, nullptr, nullptr, ctl);
             k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, nullptr, ctl);
         } else {
-            // Algorithm 2, line 3: Q_{i+1} = S P_{i+1}
+            // Algorithm 2: Q_{i+1} = S P_{i+1}
             k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, ptr<T>(w->PT), ctl);
             k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
@@ -2388,7 +2388,7 @@ void flush_l2(cudaStream_t st) {
     BA_CUDA_TRY(cudaMemsetAsync(buf, 0, bytes, st));
 }
 
-// The PCG product q = S p of every problem (k_spmv MODE 1, the kernel of Algorithm 1, line 3),
+// The PCG product q = S p of every problem (k_spmv MODE 1, the kernel of Algorithm 1),
 // set up as at the start of a PCG solve (p = D^{-1} b~).
 double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int item_blocks,
                         cudaStream_t st) {

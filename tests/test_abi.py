@@ -74,3 +74,38 @@ def test_grouping_network_parameter_layout(libba):
     assert n.value == 2 * 8 * 64 + 64 + 2 * (2 * 64 * 64 + 64) + 64 + 1
     assert n.value == sum(int(__import__("numpy").prod(s)) for _, s in learn.layer_shapes())
     assert learn.init_params(0).size == n.value
+
+
+def test_static_residual_binding_rejects_bad_arrays():
+    """ba_schur_residual_static receives raw device pointers and no lengths, so the binding rejects
+    host arrays, wrong dtypes and wrong sizes before the library is called (checked here on CPU
+    tensors: every other property right, the device check comes last)."""
+    import numpy as np
+    import torch
+
+    n = 3
+    good = {"row_ptr": torch.zeros(n + 1, dtype=torch.int64), "col": torch.zeros(2, dtype=torch.int32),
+            "blocks": torch.zeros(2 * 81, dtype=torch.float64), "btilde": torch.zeros(9 * n, dtype=torch.float64),
+            "x": torch.zeros(9 * n, dtype=torch.float64), "out": torch.zeros(2, dtype=torch.float64)}
+
+    def call(**over):
+        a = dict(good, **over)
+        binding.ba_schur_residual_static(n, a["row_ptr"], a["col"], a["blocks"], a["btilde"], a["x"], a["out"])
+
+    with pytest.raises(TypeError, match="row_ptr"):
+        call(row_ptr=np.zeros(n + 1, np.int64))
+    for name, bad in [("row_ptr", torch.zeros(n + 1, dtype=torch.int32)), ("col", torch.zeros(2, dtype=torch.int64)),
+                      ("blocks", torch.zeros(2 * 81, dtype=torch.float32)),
+                      ("btilde", torch.zeros(9 * n, dtype=torch.float32)), ("x", torch.zeros(9 * n, dtype=torch.int64)),
+                      ("out", torch.zeros(2, dtype=torch.float32))]:
+        with pytest.raises(TypeError, match=name):
+            call(**{name: bad})
+    for name, bad in [("row_ptr", torch.zeros(n, dtype=torch.int64)), ("btilde", torch.zeros(9 * n - 1, dtype=torch.float64)),
+                      ("x", torch.zeros(9 * n + 9, dtype=torch.float64)), ("out", torch.zeros(1, dtype=torch.float64)),
+                      ("blocks", torch.zeros(81, dtype=torch.float64))]:
+        with pytest.raises(ValueError):
+            call(**{name: bad})
+    with pytest.raises(ValueError, match="contiguous"):
+        call(blocks=torch.zeros(2 * 81 * 2, dtype=torch.float64)[::2])
+    with pytest.raises(ValueError, match="CUDA"):
+        call()

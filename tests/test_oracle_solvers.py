@@ -210,3 +210,80 @@ def test_planted_missing_reorthogonalisation_is_caught(monkeypatch):
 
     x, conv = mcg_short(S, bt, Dinv, 8, 1e9, 1e-10, res_ok.iters)
     assert (not conv) or _rel(x, xs) > 1e-6
+
+
+# --- the tau-test ratio t_i (Algorithm 2, adaptive tau-test of Section 3.2) ---------------------
+
+def _tau_identity_errors(S, bt, res, n_cams):
+    """For each recorded t_i: |t_i d_i - (E_i^2 - E_{i+1}^2)| / (E_i^2 - E_{i+1}^2), with E_i the
+    S-energy distance of x_i to the dense Cholesky solution and d_i = r_{i+1}^T D(S)^{-1} r_{i+1}
+    built from the true residual -b~ - S x_{i+1} and dense solves with the 9x9 diagonal blocks of S.
+    A block step minimises the S-energy error over its span, so gamma_i^T alpha_i is exactly that
+    decrease; nothing here shares arithmetic with the solver's own gamma, alpha, r or z."""
+    xs = solvers.dense_solve(S, bt)
+    Sd = S.toarray()
+    xi = [np.zeros_like(xs)] + res.xs
+    E2 = [(x - xs) @ (S @ (x - xs)) for x in xi]
+    errs = []
+    for i, t in enumerate(res.t):
+        r1 = -bt - S @ xi[i + 1]
+        d = sum(r1[9 * j:9 * j + 9] @ np.linalg.solve(Sd[9 * j:9 * j + 9, 9 * j:9 * j + 9], r1[9 * j:9 * j + 9])
+                for j in range(n_cams))
+        drop = E2[i] - E2[i + 1]
+        errs.append(abs(t * d - drop) / drop)
+    return errs
+
+
+@pytest.mark.parametrize("N,tau", [(8, 3.0), (16, 10.0), (4, 1e9), (8, 0.0)])
+def test_tau_ratio_is_energy_decrease_over_preconditioned_residual(N, tau):
+    sc, S, bt, Dinv = system("tiny")
+    res = solvers.mcg(S, bt, Dinv, N, tau, eps=1e-6, record=True)
+    assert res.converged and len(res.t) == res.iters - 1
+    errs = _tau_identity_errors(S, bt, res, sc.n_cams)
+    # measured <= 6e-8 (roundoff of the energy differences near convergence)
+    assert max(errs) < 1e-6, max(errs)
+
+
+def _two_camera_system():
+    """A hand-worked 2-camera reduced system: S = [[A, b I], [b I, A]] with A = diag(d), d_1 = 3,
+    b = 1, and b~ = -(e_1, 0).  From x_0 = 0: r_0 = (e_1, 0), z_0 = (e_1 / 3, 0), Q_0 = (e_1, e_1 / 3),
+    Delta_0 = gamma_0 = 1/3, alpha_0 = 1, r_1 = (0, -e_1 / 3), z_1 = (0, -e_1 / 9), so
+    t_0 = (1/3) / (1/27) = 9 and the S-energy error drops by gamma_0 alpha_0 = 1/3."""
+    import scipy.sparse as sps
+
+    d = np.array([3.0, 2.0, 4.0, 5.0, 2.5, 6.0, 7.0, 3.5, 8.0])
+    A = np.diag(d)
+    S = np.block([[A, np.eye(9)], [np.eye(9), A]])
+    bt = np.zeros(18)
+    bt[0] = -1.0
+    return sps.csr_matrix(S), bt
+
+
+def test_tau_ratio_hand_worked_two_cameras():
+    S, bt = _two_camera_system()
+    Dinv = solvers.block_jacobi_inverse(S, 2)
+    res = solvers.mcg(S, bt, Dinv, 2, 10.0, eps=1e-12, imax=50, record=True)
+    assert abs(res.t[0] - 9.0) < 1e-13
+    assert res.widths[:2] == [1, 2]            # t_0 = 9 < 10: the second step is local
+    assert np.abs(res.xs[0] - np.r_[1.0 / 3.0, np.zeros(17)]).max() < 1e-15
+    xs = solvers.dense_solve(S, bt)
+    e0 = xs @ (S @ xs)
+    e1 = (res.xs[0] - xs) @ (S @ (res.xs[0] - xs))
+    assert abs((e0 - e1) - 1.0 / 3.0) < 1e-14
+    assert res.converged and np.abs(res.x - xs).max() < 1e-12
+
+
+@pytest.mark.parametrize("plant", ["r^T r denominator", "gamma^T gamma numerator", "alpha^T alpha numerator"])
+def test_planted_tau_ratio_mistakes_are_caught(plant, monkeypatch):
+    """A wrong numerator or denominator of t_i must fail one of the two pins above."""
+    wrong = {"r^T r denominator": lambda g, a, r, z: float(g @ a) / float(r @ r),
+             "gamma^T gamma numerator": lambda g, a, r, z: float(g @ g) / float(r @ z),
+             "alpha^T alpha numerator": lambda g, a, r, z: float(a @ a) / float(r @ z)}[plant]
+    monkeypatch.setattr(solvers, "tau_ratio", wrong)
+    S, bt = _two_camera_system()
+    hand = solvers.mcg(S, bt, solvers.block_jacobi_inverse(S, 2), 2, 10.0, eps=1e-12, imax=50, record=True)
+    hand_ok = abs(hand.t[0] - 9.0) < 1e-13
+    sc, S, bt, Dinv = system("tiny")
+    res = solvers.mcg(S, bt, Dinv, 8, 3.0, eps=1e-6, record=True)
+    energy_ok = max(_tau_identity_errors(S, bt, res, sc.n_cams)) < 1e-6
+    assert not (hand_ok and energy_ok)
