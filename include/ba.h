@@ -50,7 +50,7 @@ typedef enum ba_status {
     BA_ERR_SINGULAR = -4,      /* a damped 3x3 V_lambda or a 9x9 block of S is not positive definite */
     BA_ERR_BREAKDOWN = -5,     /* NaN/Inf or a non-positive curvature in the Krylov solve */
     BA_ERR_NOT_CONVERGED = -6, /* max_iters reached; the iterate is still returned */
-    BA_ERR_TIMEOUT = -7,       /* reserved for bounded device-side waits */
+    BA_ERR_TIMEOUT = -7,       /* a bounded device-side wait gave up (see ba_options.wait_polls) */
     BA_ERR_STATE = -8          /* call out of order, e.g. a solve before ba_build_normal */
 } ba_status;
 
@@ -74,8 +74,9 @@ typedef enum ba_solver {
 typedef struct ba_options {
     int32_t damping;           /* ba_damping; the paper's D_p, D_l of Eq. 5 are unspecified */
     int32_t precision;         /* ba_precision */
-    int32_t chunk_iters;       /* Krylov iterations per captured CUDA graph between host checks of
-                                  the device stop flag (default 8, 1..256) */
+    int32_t chunk_iters;       /* Krylov iterations per pass of the solve graph's device-side loop
+                                  between checks of the stop flags (default 8, 1..256); a solve is
+                                  one graph launch and the host waits once, at its end */
     int32_t max_history;       /* MCG: maximum stored direction columns (default 0 = max_iters * n_dirs + 1);
                                   when it is full FP64 stops with OOM, while MIXED ends the float32
                                   sweep and the refinement starts another from the true residual */
@@ -85,7 +86,12 @@ typedef struct ba_options {
     int32_t item_blocks;       /* stored 9x9 blocks of S per work item of the block-sparse products
                                   (longer rows are split): 0 (default) = 512, else a multiple of 32
                                   in [32, 4096]; ba_autotune sets it */
-    int32_t reserved[6];
+    int32_t wait_polls;        /* bounded device waits: polls of a tile copy's barrier before the
+                                  solve gives up with BA_ERR_TIMEOUT (the kernel then waits for its
+                                  own copies still in flight, with the default bound, and returns).
+                                  0 (default) = 2^20; 1 .. 2^30; -1 = no poll at all, so every such
+                                  wait gives up at once (tests the timeout path) */
+    int32_t reserved[5];
 } ba_options;
 
 /* Filled by ba_solve_pcg / ba_solve_mcg. */
@@ -96,9 +102,14 @@ typedef struct ba_solve_stats {
     int32_t n_dirs_eff;        /* MCG: non-empty pose subsets actually used */
     int32_t refinements;       /* MIXED: outer sweeps; 1 for FP64 */
     int32_t history_cols;      /* MCG: direction columns stored at exit */
+    int32_t pinv_steps;        /* MCG: steps whose Delta_i needed the eigen-decomposition pseudo-inverse
+                                  (a rank-deficient or badly conditioned direction block) */
+    int32_t host_waits;        /* times the host waited for the device during the solve (1: only for
+                                  the results at its end; the iteration loop runs on the device) */
     double rel_residual;       /* recursive |r_i| / |r_0| at exit (of the last sweep for MIXED) */
     double true_rel_residual;  /* |-b~ - S x| / |b~| recomputed in float64 at exit */
-    double ms;                 /* device time of the solve, CUDA events on the handle's stream */
+    double ms;                 /* device time of the solve, CUDA events on the handle's stream
+                                  (from the upload of its arguments to the copy-back of its results) */
 } ba_solve_stats;
 
 /* Filled by ba_lm_step. */

@@ -35,12 +35,13 @@ SOLVER = {"pcg": 0, "mcg": 1}
 class ba_options(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_iters", ctypes.c_int32),
                 ("max_history", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("item_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("item_blocks", ctypes.c_int32), ("wait_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ba_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("local_steps", ctypes.c_int32),
                 ("n_dirs_eff", ctypes.c_int32), ("refinements", ctypes.c_int32), ("history_cols", ctypes.c_int32),
+                ("pinv_steps", ctypes.c_int32), ("host_waits", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double), ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
@@ -235,7 +236,8 @@ class Problem:
     """
 
     def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, damping="marquardt", precision="fp64",
-                 chunk_iters=8, max_history=0, inner_tol=1e-6, max_refine=64, item_blocks=0, cam_off=None):
+                 chunk_iters=8, max_history=0, inner_tol=1e-6, max_refine=64, item_blocks=0, wait_polls=0,
+                 cam_off=None):
         L = lib()
         opt = ba_options()
         L.ba_default_options(ctypes.byref(opt))
@@ -246,6 +248,7 @@ class Problem:
         opt.inner_tol = inner_tol
         opt.max_refine = max_refine
         opt.item_blocks = item_blocks
+        opt.wait_polls = wait_polls
         self._keep = [_f64(cams), _f64(pts), _i32(obs_cam), _i32(obs_pt), _f64(obs_xy)]
         cams, pts, obs_cam, obs_pt, obs_xy = self._keep
         self.n_cams = int(cams.shape[0])

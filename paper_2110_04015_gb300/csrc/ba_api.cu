@@ -291,7 +291,7 @@ void alloc_system(ba_problem* p) {
     y.r = dev_alloc<double>(p, size_t(s.n_o) * 2);
     y.Jc = dev_alloc<double>(p, size_t(s.n_o) * 18);
     y.Jl = dev_alloc<double>(p, size_t(s.n_o) * 6);
-    y.G = dev_alloc<double>(p, size_t(s.n_o) * 27);
+    if (p->opt.precision == BA_PRECISION_FP64) y.G = dev_alloc<double>(p, size_t(s.n_o) * 27);
     y.V = dev_alloc<double>(p, size_t(s.n_l) * 9);
     y.L = dev_alloc<double>(p, size_t(s.n_l) * 6);
     y.bl = dev_alloc<double>(p, size_t(s.n_l) * 3);
@@ -309,8 +309,12 @@ void alloc_system(ba_problem* p) {
         y.S32 = dev_alloc<float>(p, size_t(s.n_tiles) * ba::kTileElems);
         BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
         y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 27);
-        y.tl = dev_alloc<double>(p, size_t(s.n_l) * 3);
-        y.uo = dev_alloc<double>(p, size_t(s.n_o) * 3);
+        y.aux32 = dev_alloc<float>(p, size_t(s.n_c) * 24);
+        y.PY32 = dev_alloc<float>(p, size_t(s.n_o) * 6);
+        y.L32 = dev_alloc<float>(p, size_t(s.n_l) * 6);
+        y.yl = dev_alloc<double>(p, size_t(s.n_l) * 3);
+        y.dadd = dev_alloc<double>(p, size_t(s.n_c) * 9);
+        y.uv = dev_alloc<double>(p, size_t(s.n_o) * 2);
         y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
         y.lam32 = dev_alloc<float>(p, size_t(s.n_c) * 9);
         y.Dhat = dev_alloc<double>(p, size_t(s.n_c) * 81);
@@ -340,17 +344,20 @@ void do_build(ba_problem* p, double lambda) {
     ba::launch_cam_prep(s, y, st);
     ba::launch_linearize(s, y, st);
     ba::launch_landmarks(s, y, p->opt.damping, lambda, st);
-    ba::launch_obs_G(s, y, st);
-    ba::launch_cameras(s, y, p->opt.damping, lambda, st);
-    ba::launch_schur_diag(s, y, st);
-    ba::launch_block_jacobi(s, y, st);
-    p->launches += 7;
     if (p->opt.precision == BA_PRECISION_FP64) {
+        ba::launch_obs_G(s, y, st);
+        ba::launch_cameras(s, y, p->opt.damping, lambda, st);
+        ba::launch_schur_diag(s, y, st);
+        ba::launch_block_jacobi(s, y, st);
         ba::launch_schur(s, y, st);          // off-diagonal blocks + the diagonal from Sd
-        p->launches += 2;
+        p->launches += 9;
     } else {
+        // float64: b~ and the damping; float32 Jacobians: diagonal blocks, Lam G rows, S^
+        ba::launch_cam_rhs(s, y, p->opt.damping, lambda, st);
+        ba::launch_schur_diag32(s, y, st);
+        ba::launch_block_jacobi(s, y, st);
         ba::launch_schur_mixed(s, y, st);    // float32 Lam G, off-diagonal and diagonal blocks of S^
-        p->launches += 4;
+        p->launches += 10;
     }
     check_launch();
     int status = 0;
@@ -385,6 +392,8 @@ int do_solve(ba_problem* p, const ba::SolveArgs& a, ba_solve_stats* st) {
         st->n_dirs_eff = out.n_eff;
         st->refinements = out.refinements;
         st->history_cols = int32_t(out.history_cols);
+        st->pinv_steps = out.pinv_steps;
+        st->host_waits = out.host_waits;
         st->rel_residual = out.rel_residual;
         st->true_rel_residual = out.true_rel_residual;
         st->ms = out.ms;
@@ -392,7 +401,8 @@ int do_solve(ba_problem* p, const ba::SolveArgs& a, ba_solve_stats* st) {
     if (out.status != BA_OK) {
         p->err = out.status == BA_ERR_NOT_CONVERGED ? "max_iters reached before the tolerance"
                : out.status == BA_ERR_OOM ? "direction history capacity exceeded"
-                                          : "Krylov breakdown (non-positive curvature or NaN)";
+               : out.status == BA_ERR_TIMEOUT ? "a bounded device wait for a tile copy gave up (wait_polls)"
+                                              : "Krylov breakdown (non-positive curvature or NaN)";
     }
     return out.status;
 }
@@ -421,6 +431,7 @@ ba::SolveArgs make_args(const ba_problem* p, int mcg, double tol, int32_t max_it
     a.max_refine = p->opt.max_refine;
     a.max_history = p->opt.max_history;
     a.item_blocks = p->opt.item_blocks;
+    a.wait_polls = p->opt.wait_polls == 0 ? ba::kDefaultWaitPolls : (p->opt.wait_polls < 0 ? 0 : p->opt.wait_polls);
     return a;
 }
 
@@ -434,6 +445,7 @@ void check_options(const ba_options& o) {
     if (o.max_refine < 1) throw Error(BA_ERR_INVALID_ARG, "max_refine must be >= 1");
     if (o.item_blocks != 0 && (o.item_blocks < 32 || o.item_blocks > 4096 || o.item_blocks % 32 != 0))
         throw Error(BA_ERR_INVALID_ARG, "item_blocks must be 0 or a multiple of 32 in [32, 4096]");
+    if (o.wait_polls < -1 || o.wait_polls > (1 << 30)) throw Error(BA_ERR_INVALID_ARG, "wait_polls must be in [-1, 2^30]");
 }
 
 int create(const ba_options* opt, int32_t n_problems, const int32_t* cam_off_in, int32_t n_cams, int32_t n_pts,
@@ -728,6 +740,12 @@ int ba_get_normal(const ba_problem* pc, double* U, double* V, double* b_p, doubl
     if (!p) return BA_ERR_INVALID_ARG;
     try {
         if (!p->y.built) throw Error(BA_ERR_STATE, "nothing built");
+        if (p->opt.precision == BA_PRECISION_MIXED && (U || b_p)) {
+            // the mixed build needs neither U nor b_p: form them from the stored Jacobians on request
+            ba::launch_cameras_U(p->s, p->y, p->opt.damping, p->y.lambda, p->stream);
+            check_launch();
+            p->launches += 1;
+        }
         copy_out(U, p->y.U, sizeof(double) * 81 * size_t(p->s.n_c), p->stream);
         copy_out(V, p->y.V, sizeof(double) * 9 * size_t(p->s.n_l), p->stream);
         copy_out(b_p, p->y.bp, sizeof(double) * 9 * size_t(p->s.n_c), p->stream);

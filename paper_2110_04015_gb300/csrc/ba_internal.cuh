@@ -3,9 +3,9 @@
 // Data layout in device memory (one problem):
 //   observations are kept sorted by landmark ("point order"); perm maps a
 //   point-order slot back to the caller's observation index.
-//   per observation : r (2), Jc (2x9), Jl (2x3), G = W_o L_l^{-T} (9x3)
-//   per landmark    : V_lambda (3x3), its Cholesky factor L (6 packed),
-//                     b_l (3), e = L^{-1} b_l (3)
+//   per observation : r (2), Jc (2x9), Jl (2x3), G = W_o L_l^{-T} (9x3, float64 precision only)
+//   per landmark    : V_lambda (3x3), its Cholesky factor L (6 packed, with the reciprocals of
+//                     its diagonal: 1/l00, l10, 1/l11, l20, l21, 1/l22), b_l (3), e = L^{-1} b_l (3)
 //   per camera      : U_lambda (9x9), b_p (9), b~ (9), D_j^{-1} (9x9)
 //   S               : block-CSR over cameras, every nonzero 9x9 block of both
 //                     triangles, each block 81 contiguous values (row-major).  The
@@ -41,6 +41,7 @@ __host__ __device__ __forceinline__ int64_t s_at(const int64_t* tile_ptr, int64_
     return (tile_ptr[j] * kTile + q) * 81 + e;
 }
 constexpr int kMaxDirs = 16;   // widest direction block held by the small FP64 solves
+constexpr int kDefaultWaitPolls = 1 << 20;   // polls of a tile copy's barrier before a wait gives up
 
 #define BA_CUDA_TRY(expr)                                                                   \
     do {                                                                                    \
@@ -93,17 +94,17 @@ struct Structure {
 // The linearised system at the current parameters (rebuilt by ba_build_normal).
 struct System {
     double* cams = nullptr;   // n_c x 9 current parameters
-    double* aux = nullptr;    // n_c x 24: R, J_r, t, f, k1, k2 per camera (linearisation)
+    double* aux = nullptr;    // n_c x 24: R, R J_r, t, f, k1, k2 per camera (linearisation)
     double* pts = nullptr;    // n_l x 3
     double* r = nullptr;      // n_o x 2
     double* Jc = nullptr;     // n_o x 18
     double* Jl = nullptr;     // n_o x 6
-    double* G = nullptr;      // n_o x 27
+    double* G = nullptr;      // n_o x 27 (float64 precision only)
     double* V = nullptr;      // n_l x 9
-    double* L = nullptr;      // n_l x 6
+    double* L = nullptr;      // n_l x 6 (reciprocal diagonal, see above)
     double* bl = nullptr;     // n_l x 3
     double* e = nullptr;      // n_l x 3
-    double* U = nullptr;      // n_c x 81
+    double* U = nullptr;      // n_c x 81 (mixed precision: formed only when ba_get_normal asks)
     double* bp = nullptr;     // n_c x 9
     double* bt = nullptr;     // n_c x 9
     double* S = nullptr;      // n_tiles x 2592 (tiled layout above); float64 precision only
@@ -117,8 +118,12 @@ struct System {
     double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
     float* lam32 = nullptr;   // 9 n_c: float(Lam)
     float* G32 = nullptr;     // n_o x 27: rows of Lam G_o in float32 (row a scaled by Lam_cam(o),a)
-    double* tl = nullptr;     // n_l x 3: landmark sums of the implicit product G^T x
-    double* uo = nullptr;     // n_o x 3: per-observation terms G_o^T x_cam(o) of those sums
+    float* aux32 = nullptr;   // n_c x 24: the camera's aux block in float32
+    float* PY32 = nullptr;    // n_o x 6: P = R X + t and Y = R X in float32 (formed in float64)
+    float* L32 = nullptr;     // n_l x 6: L (packed as above) in float32
+    double* yl = nullptr;     // n_l x 3: V_l^{-1} b_l
+    double* dadd = nullptr;   // n_c x 9: the damping lambda D_p^T D_p added to the diagonal of U_j
+    double* uv = nullptr;     // n_o x 2: per-observation terms of the float64 true residual
     int* status = nullptr;    // device error word of the build
     double lambda = 0.0;
     bool built = false;
@@ -133,9 +138,15 @@ void launch_landmarks(const Structure& s, System& y, int damping, double lambda,
 void launch_obs_G(const Structure& s, System& y, cudaStream_t st);
 void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
 void launch_schur_diag(const Structure& s, System& y, cudaStream_t st);
+// U_lambda and b_p only (mixed precision forms them on request)
+void launch_cameras_U(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+// mixed precision: b~ and lambda D_p in float64, then the float32 diagonal blocks into Sd
+void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st);
 void launch_schur(const Structure& s, System& y, cudaStream_t st);
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st);
-// out = -b~ - S x with the implicit float64 operator S x = U x - G (G^T x) (no explicit S);
+// out = -b~ - S x with the implicit float64 operator (mixed precision, no explicit S)
+// S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x;
 // partial[2 j], partial[2 j + 1] receive camera j's sums of out^2 and b~^2 (2 n_c values)
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st);
@@ -165,12 +176,14 @@ struct SolveArgs {
     int max_refine = 12;
     int64_t max_history = 0;
     int item_blocks = 0;    // blocks per work item of the block-sparse products (0: 512)
+    int wait_polls = kDefaultWaitPolls;   // tile-copy waits: polls before giving up (0: give up at once)
 };
 
 struct ProbOut {
     int status = BA_OK;
     int iters = 0;
     int local_steps = 0;
+    int pinv_steps = 0;
     int n_eff = 1;
     int refinements = 0;
     int64_t history_cols = 0;
@@ -182,6 +195,7 @@ struct SolveOut {
     int status = BA_OK;
     int iters = 0;
     int local_steps = 0;
+    int pinv_steps = 0;
     int n_eff = 1;
     int refinements = 0;
     int64_t history_cols = 0;
@@ -189,6 +203,7 @@ struct SolveOut {
     double true_rel_residual = 0.0;
     double ms = 0.0;
     int64_t launches = 0;   // kernel executions issued by the solve
+    int host_waits = 0;     // host waits on the device during the solve
     std::vector<ProbOut> probs;   // per problem of the batch (the fields above summarise them)
 };
 

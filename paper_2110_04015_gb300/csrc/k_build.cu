@@ -2,6 +2,7 @@
 //
 //   k_linearize     one thread per observation: r, J_p (2x9), J_l (2x3)
 //   k_landmarks     one thread per landmark: V_lambda, b_l, Cholesky V = L L^T, e = L^{-1} b_l
+//                   (L packed with the reciprocals of its diagonal)
 //   k_obs_G         one thread per observation: G_o = (J_p^T J_l) L^{-T}
 //   k_cameras       one CTA per camera: U_lambda, b_p, b~ = b_p - sum G_o e_l
 //   k_schur_diag    one CTA per camera: S_jj = U_j - sum_o G_o G_o^T (float64)
@@ -12,6 +13,14 @@
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
 //   k_scaled_g32    float32 rows of Lam G for the scaled float32 system
 //   k_implicit_*    the float64 product S x = U x - G (G^T x) without an explicit S
+// Mixed precision builds no float64 U, G or S_jj: float64 keeps r, J_p, J_l (for b~ and the true
+// residual S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x, k_jres_*), and the
+// float32 system comes from float32 Jacobians recomputed from float32 parameters:
+//   k_cam_rhs       one CTA per camera (float64): b~ = sum_o J_p^T (r - J_l V^-1 b_l), lambda D_p
+//   k_schur_diag32  one CTA per camera (float32): S_jj = sum_o J_p^T (I - A A^T) J_p + lambda D_p,
+//                   A = J_l L^{-T} (each term is positive semi-definite: no cancellation)
+//   k_obs_G32       one thread per observation (float32): rows of Lam J_p^T A, the G of the
+//                   off-diagonal blocks
 // S is written in the tiled layout of ba_internal.cuh (s_at).
 // Every kernel uses grid-stride loops and 64-bit indices.
 #include <cuda_runtime.h>
@@ -82,71 +91,107 @@ __device__ __forceinline__ void bal_project(const double* c, const double* X, do
 }
 
 // Per-camera part of the linearisation, shared by all observations of the camera:
-// aux = (R[9], J_r[9], t[3], f, k1, k2), with d(R X)/d omega = -R [X]x J_r(omega) and
-// J_r = I - B [w]x + C [w]x^2 the right Jacobian of the rotation exponential.
-__global__ void k_cam_prep(int32_t n_c, const double* __restrict__ cams, double* __restrict__ aux) {
+// aux = (R[9], RJ[9], t[3], f, k1, k2), RJ = R J_r(omega) with J_r = I - B [w]x + C [w]x^2 the
+// right Jacobian of the rotation exponential, so that d(R X)/d omega = -R [X]x J_r = -[R X]x RJ
+// (R [X]x = [R X]x R for a rotation).  aux32 (may be null) receives the same values in float32.
+__global__ void k_cam_prep(int32_t n_c, const double* __restrict__ cams, double* __restrict__ aux,
+                           float* __restrict__ aux32) {
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
         const double* c = cams + 9 * j;
         double w[3] = {c[0], c[1], c[2]};
         const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        double A, B, C, R[9];
+        double A, B, C, R[9], Jr[9];
         rot_coeffs(th2, A, B, C);
         rot_matrix(w, A, B, th2, R);
-        double* o = aux + 24 * j;
+        Jr[0] = 1.0 + C * (w[0] * w[0] - th2);
+        Jr[1] = B * w[2] + C * w[0] * w[1];
+        Jr[2] = -B * w[1] + C * w[0] * w[2];
+        Jr[3] = -B * w[2] + C * w[0] * w[1];
+        Jr[4] = 1.0 + C * (w[1] * w[1] - th2);
+        Jr[5] = B * w[0] + C * w[1] * w[2];
+        Jr[6] = B * w[1] + C * w[0] * w[2];
+        Jr[7] = -B * w[0] + C * w[1] * w[2];
+        Jr[8] = 1.0 + C * (w[2] * w[2] - th2);
+        double o[24];
 #pragma unroll
         for (int k = 0; k < 9; ++k) o[k] = R[k];
-        o[9] = 1.0 + C * (w[0] * w[0] - th2);
-        o[10] = B * w[2] + C * w[0] * w[1];
-        o[11] = -B * w[1] + C * w[0] * w[2];
-        o[12] = -B * w[2] + C * w[0] * w[1];
-        o[13] = 1.0 + C * (w[1] * w[1] - th2);
-        o[14] = B * w[0] + C * w[1] * w[2];
-        o[15] = B * w[1] + C * w[0] * w[2];
-        o[16] = -B * w[0] + C * w[1] * w[2];
-        o[17] = 1.0 + C * (w[2] * w[2] - th2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                o[9 + 3 * a + b] = R[3 * a] * Jr[b] + R[3 * a + 1] * Jr[3 + b] + R[3 * a + 2] * Jr[6 + b];
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[18 + k] = c[3 + k];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) aux[24 * j + k] = o[k];
+        if (aux32) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) aux32[24 * j + k] = float(o[k]);
+        }
     }
 }
 
-// Residual and Jacobian blocks of one observation from the camera's prepared aux block.
-__device__ __forceinline__ void bal_linearize_aux(const double* ax, const double* X, const double* m, double* r,
-                                                  double* Jc, double* Jl) {
-    const double* R = ax;
-    const double* Jr = ax + 9;
-    double P[3];
-    for (int a = 0; a < 3; ++a) P[a] = R[3 * a] * X[0] + R[3 * a + 1] * X[1] + R[3 * a + 2] * X[2] + ax[18 + a];
-    double M[9];
-    for (int b = 0; b < 3; ++b) {
-        M[b] = -X[2] * Jr[3 + b] + X[1] * Jr[6 + b];
-        M[3 + b] = X[2] * Jr[b] - X[0] * Jr[6 + b];
-        M[6 + b] = -X[1] * Jr[b] + X[0] * Jr[3 + b];
-    }
-    double dPdw[9];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            dPdw[3 * a + b] = -(R[3 * a] * M[b] + R[3 * a + 1] * M[3 + b] + R[3 * a + 2] * M[6 + b]);
-    const double iz = 1.0 / P[2];
-    const double p0 = -P[0] * iz, p1 = -P[1] * iz;
-    const double f = ax[21], k1 = ax[22], k2 = ax[23];
-    const double n2 = p0 * p0 + p1 * p1;
-    const double rho = 1.0 + k1 * n2 + k2 * n2 * n2;
-    const double drho = 2.0 * (k1 + 2.0 * k2 * n2);
-    const double E00 = f * (rho + drho * p0 * p0), E01 = f * drho * p0 * p1, E11 = f * (rho + drho * p1 * p1);
-    double D[6];
+// 1 / p: float64 from a float32 estimate and two Newton steps (each squares the relative error:
+// 2^-23 -> 2^-46 -> rounding level), which keeps the long float64 division off this GPU's narrow
+// float64 pipe; float32 divides.  Values outside the float32 range divide in float64.
+__device__ __forceinline__ double rcp_fast(double p) {
+    const double ap = fabs(p);
+    if (!(ap > 1e-30 && ap < 1e30)) return 1.0 / p;
+    double r = double(__frcp_rn(float(p)));
+    r = fma(r, fma(-p, r, 1.0), r);
+    return fma(r, fma(-p, r, 1.0), r);
+}
+__device__ __forceinline__ float rcp_fast(float p) { return __frcp_rn(p); }
+
+// 1 / sqrt(x) for x > 0 in float64 by the same scheme (Newton steps y <- y (3 - x y^2) / 2);
+// returns 0 for x <= 0 or NaN, which the caller reports as not positive definite.
+__device__ __forceinline__ double rsqrt_fast(double x) {
+    if (!(x > 0.0)) return 0.0;
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = double(rsqrtf(float(x)));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    return y * fma(-hx * y, y, 1.5);
+}
+
+// Jacobian blocks of one observation from the camera's aux block, the rotated point Y = R X and the
+// point in the camera frame P = Y + t, and the residual when r != nullptr (pi = f rho(|p|^2) p with
+// p = -P_xy / P_z: the BAL model).  With D_a = d pi_a / dP, row a of J_p has the rotation part
+// -(D_a x Y)^T RJ (D^T [Y]x = (D x Y)^T), the translation part D_a, and the intrinsics; row a of J_l
+// is D_a^T R.  (Y and P are both passed: either can be much smaller than t, so neither is formed
+// from the other in float32.)
+template <typename T>
+__device__ __forceinline__ void bal_jacobian_P(const T* ax, const T* Y, const T* P, const T* m, T* r, T* Jc,
+                                               T* Jl) {
+    const T* R = ax;
+    const T* RJ = ax + 9;
+    const T iz = rcp_fast(P[2]);
+    const T p0 = -P[0] * iz, p1 = -P[1] * iz;
+    const T f = ax[21], k1 = ax[22], k2 = ax[23];
+    const T n2 = p0 * p0 + p1 * p1;
+    const T rho = T(1) + k1 * n2 + k2 * n2 * n2;
+    const T drho = T(2) * (k1 + T(2) * k2 * n2);
+    const T E00 = f * (rho + drho * p0 * p0), E01 = f * drho * p0 * p1, E11 = f * (rho + drho * p1 * p1);
+    T D[6];
     D[0] = -E00 * iz;
     D[1] = -E01 * iz;
     D[2] = -(E00 * p0 + E01 * p1) * iz;
     D[3] = -E01 * iz;
     D[4] = -E11 * iz;
     D[5] = -(E01 * p0 + E11 * p1) * iz;
-    r[0] = f * rho * p0 - m[0];
-    r[1] = f * rho * p1 - m[1];
+    if (r) {
+        r[0] = f * rho * p0 - m[0];
+        r[1] = f * rho * p1 - m[1];
+    }
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
+        const T* d = D + 3 * a;
+        const T w0 = d[1] * Y[2] - d[2] * Y[1], w1 = d[2] * Y[0] - d[0] * Y[2], w2 = d[0] * Y[1] - d[1] * Y[0];
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
-            Jc[9 * a + b] = D[3 * a] * dPdw[b] + D[3 * a + 1] * dPdw[3 + b] + D[3 * a + 2] * dPdw[6 + b];
-            Jc[9 * a + 3 + b] = D[3 * a + b];
-            Jl[3 * a + b] = D[3 * a] * R[b] + D[3 * a + 1] * R[3 + b] + D[3 * a + 2] * R[6 + b];
+            Jc[9 * a + b] = -(w0 * RJ[b] + w1 * RJ[3 + b] + w2 * RJ[6 + b]);
+            Jc[9 * a + 3 + b] = d[b];
+            Jl[3 * a + b] = d[0] * R[b] + d[1] * R[3 + b] + d[2] * R[6 + b];
         }
     }
     Jc[6] = rho * p0;
@@ -155,6 +200,15 @@ __device__ __forceinline__ void bal_linearize_aux(const double* ax, const double
     Jc[16] = f * n2 * p1;
     Jc[8] = f * n2 * n2 * p0;
     Jc[17] = f * n2 * n2 * p1;
+}
+
+// Y = R X and P = Y + t from the camera's aux block.
+__device__ __forceinline__ void cam_point(const double* ax, const double* X, double* Y, double* P) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Y[a] = ax[3 * a] * X[0] + ax[3 * a + 1] * X[1] + ax[3 * a + 2] * X[2];
+        P[a] = Y[a] + ax[18 + a];
+    }
 }
 
 __device__ __forceinline__ double damp(double d, int damping, double lambda) {
@@ -180,12 +234,15 @@ __global__ void k_project(int64_t n_o, const double* __restrict__ cams, const do
     }
 }
 
+// Float64 residuals and Jacobians per observation; mixed precision (PY32 != null) also keeps P and
+// Y = R X in float32 (6 per observation), from which the float32 Jacobians are formed (forming P = Y + t
+// in float32 would lose digits when |Y|, |t| >> |P|, and Y = P - t when |P|, |t| >> |Y|).
 __global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const double* __restrict__ pts,
                             const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
                             const double* __restrict__ xy, double* __restrict__ r, double* __restrict__ Jc,
-                            double* __restrict__ Jl) {
+                            double* __restrict__ Jl, float* __restrict__ PY32) {
     for (int64_t i = gtid(); i < n_o; i += gstride()) {
-        double ax[24], X[3], m[2], rr[2], jc[18], jl[6];
+        double ax[24], X[3], Y[3], P[3], m[2], rr[2], jc[18], jl[6];
         const double* cp = aux + int64_t(oc[i]) * 24;
         const double* xp = pts + int64_t(op[i]) * 3;
 #pragma unroll
@@ -194,21 +251,32 @@ __global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const d
         for (int k = 0; k < 3; ++k) X[k] = __ldg(xp + k);
         m[0] = xy[2 * i];
         m[1] = xy[2 * i + 1];
-        bal_linearize_aux(ax, X, m, rr, jc, jl);
+        cam_point(ax, X, Y, P);
+        bal_jacobian_P<double>(ax, Y, P, m, rr, jc, jl);
         r[2 * i] = rr[0];
         r[2 * i + 1] = rr[1];
 #pragma unroll
         for (int k = 0; k < 18; ++k) Jc[18 * i + k] = jc[k];
 #pragma unroll
         for (int k = 0; k < 6; ++k) Jl[6 * i + k] = jl[k];
+        if (PY32) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                PY32[6 * i + k] = float(P[k]);
+                PY32[6 * i + 3 + k] = float(Y[k]);
+            }
+        }
     }
 }
 
-// V_lambda = sum J_l^T J_l + damping, b_l = sum J_l^T r, V = L L^T, e = L^{-1} b_l.
+// V_lambda = sum J_l^T J_l + damping, b_l = sum J_l^T r, V = L L^T, e = L^{-1} b_l.  L is packed as
+// (1 / l00, l10, 1 / l11, l20, l21, 1 / l22): every later use multiplies by the reciprocal diagonal.
+// Mixed precision (L32 != null) also writes L in float32 (same packing) and y_l = V^{-1} b_l =
+// L^{-T} e in float64 (for b~ in the form sum J_p^T (r - J_l y_l)).
 __global__ void k_landmarks(int32_t n_l, const int64_t* __restrict__ pt_ptr, const double* __restrict__ r,
                             const double* __restrict__ Jl, int damping, double lambda, double* __restrict__ Vout,
                             double* __restrict__ Lout, double* __restrict__ blout, double* __restrict__ eout,
-                            int* status) {
+                            float* __restrict__ L32, double* __restrict__ yout, int* status) {
     for (int64_t l = gtid(); l < n_l; l += gstride()) {
         double v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, b0 = 0, b1 = 0, b2 = 0;
         for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
@@ -232,26 +300,34 @@ __global__ void k_landmarks(int32_t n_l, const int64_t* __restrict__ pt_ptr, con
         V[0] = v00; V[1] = v01; V[2] = v02;
         V[3] = v01; V[4] = v11; V[5] = v12;
         V[6] = v02; V[7] = v12; V[8] = v22;
-        // Cholesky
-        double l00 = v00 > 0 ? sqrt(v00) : 0.0;
-        double l10 = v01 / l00, l20 = v02 / l00;
-        double d11 = v11 - l10 * l10;
-        double l11 = d11 > 0 ? sqrt(d11) : 0.0;
-        double l21 = (v12 - l20 * l10) / l11;
-        double d22 = v22 - l20 * l20 - l21 * l21;
-        double l22 = d22 > 0 ? sqrt(d22) : 0.0;
-        if (!(l00 > 0 && l11 > 0 && l22 > 0)) atomicExch(status, BA_ERR_SINGULAR);
+        // Cholesky with reciprocal square roots (a zero marks a pivot that is not positive)
+        const double i00 = rsqrt_fast(v00);
+        const double l10 = v01 * i00, l20 = v02 * i00;
+        const double i11 = rsqrt_fast(v11 - l10 * l10);
+        const double l21 = (v12 - l20 * l10) * i11;
+        const double i22 = rsqrt_fast(v22 - l20 * l20 - l21 * l21);
+        if (!(i00 > 0 && i11 > 0 && i22 > 0)) atomicExch(status, BA_ERR_SINGULAR);
         double* L = Lout + 6 * l;
-        L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = l22;
+        L[0] = i00; L[1] = l10; L[2] = i11; L[3] = l20; L[4] = l21; L[5] = i22;
         blout[3 * l] = b0;
         blout[3 * l + 1] = b1;
         blout[3 * l + 2] = b2;
-        double e0 = b0 / l00;
-        double e1 = (b1 - l10 * e0) / l11;
-        double e2 = (b2 - l20 * e0 - l21 * e1) / l22;
+        const double e0 = b0 * i00;
+        const double e1 = (b1 - l10 * e0) * i11;
+        const double e2 = (b2 - l20 * e0 - l21 * e1) * i22;
         eout[3 * l] = e0;
         eout[3 * l + 1] = e1;
         eout[3 * l + 2] = e2;
+        if (L32) {
+            const double y2 = e2 * i22;
+            const double y1 = (e1 - l21 * y2) * i11;
+            const double y0 = (e0 - l10 * y1 - l20 * y2) * i00;
+            yout[3 * l] = y0;
+            yout[3 * l + 1] = y1;
+            yout[3 * l + 2] = y2;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) L32[6 * l + k] = float(L[k]);
+        }
     }
 }
 
@@ -260,8 +336,7 @@ __global__ void k_obs_G(int64_t n_o, const int32_t* __restrict__ op, const doubl
                         const double* __restrict__ Jl, const double* __restrict__ Lall, double* __restrict__ G) {
     for (int64_t o = gtid(); o < n_o; o += gstride()) {
         const double* L = Lall + 6 * int64_t(op[o]);
-        const double l10 = L[1], l20 = L[3], l21 = L[4];
-        const double i00 = 1.0 / L[0], i11 = 1.0 / L[2], i22 = 1.0 / L[5];
+        const double i00 = L[0], l10 = L[1], i11 = L[2], l20 = L[3], l21 = L[4], i22 = L[5];
         double jl[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) jl[k] = Jl[6 * o + k];
@@ -345,6 +420,11 @@ __global__ void __launch_bounds__(kCamThreads) k_cameras(
             Uout[81 * int64_t(j) + threadIdx.x] = v;
         }
         __syncthreads();
+        if (!G) {   // U and b_p only (mixed precision builds b~ in k_cam_rhs)
+            if (threadIdx.x < 9) bpout[9 * int64_t(j) + threadIdx.x] = fin[45 + threadIdx.x];
+            __syncthreads();
+            continue;
+        }
         // b~ = b_p - sum_o G_o e_l
         double t9[9];
 #pragma unroll
@@ -607,88 +687,243 @@ __global__ void k_put_diag(int32_t n_c, const int64_t* __restrict__ row_ptr, con
     }
 }
 
-// Implicit float64 product, landmark part, in two passes:
-//   u_o = G_o^T x_cam(o)                           (one thread per observation, streaming G)
-//   t_l = sum_{o seen of l} u_o                    (one thread per landmark component, in slot order)
-__global__ void k_implicit_u(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
-                             const double* __restrict__ x, double* __restrict__ u) {
+// The damping added to the diagonal of U (Eq. 5): lambda D^T D with D^T D = diag(J^T J) clamped
+// to [1e-6, 1e32] (Marquardt) or the identity.
+__device__ __forceinline__ double damp_add(double d, int damping, double lambda) {
+    return damping == BA_DAMPING_IDENTITY ? lambda : lambda * fmin(fmax(d, 1e-6), 1e32);
+}
+
+// Mixed precision, one CTA per camera, float64: b~_j = sum_{o in j} J_p^T (r_o - J_l y_l) (Eq. 14, with
+// W V^-1 b_l = sum_o J_p^T J_l y_l and y_l = V_l^-1 b_l), and dadd_j = the damping lambda D_p^T D_p
+// added to the diagonal of U_j.
+__global__ void __launch_bounds__(kCamThreads) k_cam_rhs(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const int32_t* __restrict__ op, const double* __restrict__ r, const double* __restrict__ Jc,
+    const double* __restrict__ Jl, const double* __restrict__ yl, int damping, double lambda,
+    double* __restrict__ btout, double* __restrict__ dadd) {
+    __shared__ double red[kCamThreads / 32][18];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        double bt[9], dg[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) bt[a] = dg[a] = 0.0;
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const double* y = yl + 3 * int64_t(op[o]);
+            const double* jl = Jl + 6 * o;
+            const double y0 = y[0], y1 = y[1], y2 = y[2];
+            const double s0 = r[2 * o] - (jl[0] * y0 + jl[1] * y1 + jl[2] * y2);
+            const double s1 = r[2 * o + 1] - (jl[3] * y0 + jl[4] * y1 + jl[5] * y2);
+            const double* jc = Jc + 18 * o;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const double c0 = jc[a], c1 = jc[9 + a];
+                bt[a] += c0 * s0 + c1 * s1;
+                dg[a] += c0 * c0 + c1 * c1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const double v = warp_sum(k < 9 ? bt[k] : dg[k - 9]);
+            if (lane == 0) red[wid][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 18) {
+            const int k = threadIdx.x;
+            const double v = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
+            if (k < 9) btout[9 * int64_t(j) + k] = v;
+            else dadd[9 * int64_t(j) + k - 9] = damp_add(v, damping, lambda);
+        }
+        __syncthreads();
+    }
+}
+
+// Row a of A_o = J_l L^{-T} (2x3) from L packed with its reciprocal diagonal (float32).
+__device__ __forceinline__ void rows_A(const float* jl, const float* Lp, float (&A)[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        A[a][0] = jl[3 * a] * Lp[0];
+        A[a][1] = (jl[3 * a + 1] - Lp[1] * A[a][0]) * Lp[2];
+        A[a][2] = (jl[3 * a + 2] - Lp[3] * A[a][0] - Lp[4] * A[a][1]) * Lp[5];
+    }
+}
+
+constexpr int kDiagThreads = 256;
+
+// Mixed precision, one CTA per camera: S_jj = sum_{o in j} J_p^T (I - A A^T) J_p + lambda D_p (Eq. 13 on
+// the diagonal: U_j - sum_o G_o G_o^T with G_o = J_p^T A_o), from float32 Jacobians formed in float32
+// from the camera and the float32 point in the camera frame.  I - A A^T = I - J_l V^-1 J_l^T is positive semi-definite, so the terms
+// add without cancellation; each thread sums its observations in float32, the threads' sums are
+// added in float64 (fixed order), and the float64 damping is added last.  Sd receives float64.
+__global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const int32_t* __restrict__ op, const float* __restrict__ aux32, const float* __restrict__ PY32,
+    const float* __restrict__ L32, const double* __restrict__ dadd, double* __restrict__ Sd) {
+    constexpr int NW = kDiagThreads / 32;
+    __shared__ double red[NW][45];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        float ax[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) ax[k] = __ldg(aux32 + 24 * int64_t(j) + k);
+        float acc[45];
+#pragma unroll
+        for (int k = 0; k < 45; ++k) acc[k] = 0.f;
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const int64_t l = op[o];
+            float PY[6], Lp[6], jc[18], jl[6], A[2][3];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * o + k);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
+            bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
+            rows_A(jl, Lp, A);
+            const float m00 = 1.f - (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
+            const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
+            const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
+            float B0[9], B1[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                B0[a] = m00 * jc[a] + m01 * jc[9 + a];
+                B1[a] = m01 * jc[a] + m11 * jc[9 + a];
+            }
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
+        }
+#pragma unroll
+        for (int k = 0; k < 45; ++k) {
+            const double v = warp_sum(double(acc[k]));
+            if (lane == 0) red[wid][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 81) {
+            const int a = threadIdx.x / 9, b = threadIdx.x % 9;
+            const int lo = a < b ? a : b, hi = a < b ? b : a;
+            const int idx = lo * 9 - lo * (lo - 1) / 2 + (hi - lo);
+            double v = ((red[0][idx] + red[1][idx]) + (red[2][idx] + red[3][idx])) +
+                       ((red[4][idx] + red[5][idx]) + (red[6][idx] + red[7][idx]));
+            if (a == b) v += dadd[9 * int64_t(j) + a];
+            Sd[81 * int64_t(j) + threadIdx.x] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Mixed precision, one thread per observation: the rows of Lam_j G_o in float32, G_o = J_p^T A_o =
+// W_o L^{-T} (9x3), from float32 Jacobians formed in float32 from the camera and the float32 point in
+// the camera frame; the off-diagonal sums over these rows give Lam_j S_jk Lam_k directly.
+__global__ void k_obs_G32(int64_t n_o, const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
+                          const float* __restrict__ aux32, const float* __restrict__ PY32,
+                          const float* __restrict__ L32, const float* __restrict__ lam32, float* __restrict__ G32) {
     for (int64_t o = gtid(); o < n_o; o += gstride()) {
-        const double* g = G + 27 * o;
-        const double* xc = x + 9 * int64_t(oc[o]);
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        const int64_t j = oc[o], l = op[o];
+        float ax[24], PY[6], Lp[6], jc[18], jl[6], A[2][3];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) ax[k] = __ldg(aux32 + 24 * j + k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * o + k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
+        bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
+        rows_A(jl, Lp, A);
+        float* g = G32 + 27 * o;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const double xa = xc[a];
-            a0 += g[3 * a] * xa;
-            a1 += g[3 * a + 1] * xa;
-            a2 += g[3 * a + 2] * xa;
-        }
-        u[3 * o] = a0;
-        u[3 * o + 1] = a1;
-        u[3 * o + 2] = a2;
-    }
-}
-
-__global__ void k_implicit_tsum(int32_t n_l, const int64_t* __restrict__ pt_ptr, const double* __restrict__ u,
-                                double* __restrict__ t) {
-    for (int64_t i = gtid(); i < int64_t(n_l) * 3; i += gstride()) {
-        const int64_t l = i / 3;
-        const int c = int(i - 3 * l);
-        double acc = 0.0;
-        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) acc += u[3 * o + c];
-        t[i] = acc;
-    }
-}
-
-// Implicit float64 product, camera part, and the true residual: (S x)_j = U_j x_j - sum_{o in j} G_o t_l,
-// out_j = -b~_j - (S x)_j; camera j's sums of |out_j|^2 and |b~_j|^2 into partial[2 j], partial[2 j + 1].
-__global__ void __launch_bounds__(kCamThreads) k_implicit_res(
-    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
-    const int32_t* __restrict__ op, const double* __restrict__ G, const double* __restrict__ t,
-    const double* __restrict__ U, const double* __restrict__ x, const double* __restrict__ bt,
-    double* __restrict__ out, double* __restrict__ partial) {
-    // lane 3 a + c (lanes 0..26) of every warp accumulates sum_o G_o[a][c] t_l(o)[c] over the
-    // warp's observations; each observation's 27 values are one coalesced 216-byte load
-    __shared__ double red[kCamThreads / 32][27];
-    constexpr int kUnroll = 4;   // observations in flight per warp
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = kCamThreads / 32;
-    const int c = lane % 3;
-    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
-        double tt = 0.0, bb = 0.0;
-        double acc = 0.0;
-        const int64_t q1 = cam_ptr[j + 1];
-        for (int64_t q = cam_ptr[j] + wid; q < q1; q += kUnroll * nw) {
-            double gv[kUnroll], tv[kUnroll];
+            const float la = __ldg(lam32 + 9 * j + a);
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                const int64_t qq = q + int64_t(k) * nw;
-                gv[k] = 0.0;
-                tv[k] = 0.0;
-                if (qq < q1 && lane < 27) {
-                    const int64_t o = cam_obs[qq];
-                    gv[k] = G[27 * o + lane];
-                    tv[k] = t[3 * int64_t(op[o]) + c];
-                }
+            for (int c = 0; c < 3; ++c) g[3 * a + c] = la * (jc[a] * A[0][c] + jc[9 + a] * A[1][c]);
+        }
+    }
+}
+
+// V_l^{-1} s from L packed with its reciprocal diagonal: L z = s, then L^T y = z.
+__device__ __forceinline__ void solve_V(const double* L, double s0, double s1, double s2, double& y0, double& y1,
+                                        double& y2) {
+    const double z0 = s0 * L[0];
+    const double z1 = (s1 - L[1] * z0) * L[2];
+    const double z2 = (s2 - L[3] * z0 - L[4] * z1) * L[5];
+    y2 = z2 * L[5];
+    y1 = (z1 - L[4] * y2) * L[2];
+    y0 = (z0 - L[1] * y1 - L[3] * y2) * L[0];
+}
+
+// Mixed precision true residual, float64, landmark pass (one thread per landmark, its observations
+// are contiguous): u_o = J_p x_cam(o), y_l = V_l^-1 sum_o J_l^T u_o, and v_o = u_o - J_l y_l into uv.
+// Then (S x)_j = sum_{o in j} J_p^T v_o + lambda D_p x_j = U_j x_j - (W V^-1 W^T x)_j (Eq. 13).
+__global__ void k_jres_land(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
+                            const double* __restrict__ Jc, const double* __restrict__ Jl,
+                            const double* __restrict__ Lall, const double* __restrict__ x, double* __restrict__ uv) {
+    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        const int64_t o0 = pt_ptr[l], o1 = pt_ptr[l + 1];
+        for (int64_t o = o0; o < o1; ++o) {
+            const double* xc = x + 9 * int64_t(oc[o]);
+            const double* jc = Jc + 18 * o;
+            double u0 = 0.0, u1 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const double xa = xc[a];
+                u0 += jc[a] * xa;
+                u1 += jc[9 + a] * xa;
             }
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) acc += gv[k] * tv[k];
+            uv[2 * o] = u0;
+            uv[2 * o + 1] = u1;
+            const double* jl = Jl + 6 * o;
+            s0 += jl[0] * u0 + jl[3] * u1;
+            s1 += jl[1] * u0 + jl[4] * u1;
+            s2 += jl[2] * u0 + jl[5] * u1;
         }
-        if (lane < 27) red[wid][lane] = acc;
+        double y0, y1, y2;
+        solve_V(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
+        for (int64_t o = o0; o < o1; ++o) {
+            const double* jl = Jl + 6 * o;
+            uv[2 * o] -= jl[0] * y0 + jl[1] * y1 + jl[2] * y2;
+            uv[2 * o + 1] -= jl[3] * y0 + jl[4] * y1 + jl[5] * y2;
+        }
+    }
+}
+
+// Camera pass of the true residual: out_j = -b~_j - (S x)_j; camera j's sums of |out_j|^2 and |b~_j|^2
+// into partial[2 j], partial[2 j + 1] (one CTA per camera).
+__global__ void __launch_bounds__(kCamThreads) k_jres_cam(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const double* __restrict__ Jc, const double* __restrict__ uv, const double* __restrict__ dadd,
+    const double* __restrict__ x, const double* __restrict__ bt, double* __restrict__ out,
+    double* __restrict__ partial) {
+    __shared__ double red[kCamThreads / 32][9];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        double acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = 0.0;
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const double v0 = uv[2 * o], v1 = uv[2 * o + 1];
+            const double* jc = Jc + 18 * o;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] += jc[a] * v0 + jc[9 + a] * v1;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double v = warp_sum(acc[a]);
+            if (lane == 0) red[wid][a] = v;
+        }
         __syncthreads();
+        double tt = 0.0, bb = 0.0;
         if (threadIdx.x < 9) {
             const int a = threadIdx.x;
-            double gt = 0.0;
-            for (int w = 0; w < nw; ++w) gt += red[w][3 * a] + red[w][3 * a + 1] + red[w][3 * a + 2];
-            double ux = 0.0;
-            for (int b = 0; b < 9; ++b) ux += U[81 * int64_t(j) + 9 * a + b] * x[9 * int64_t(j) + b];
-            const double b_ = bt[9 * int64_t(j) + a];
-            const double r = -b_ - (ux - gt);
-            if (out) out[9 * int64_t(j) + a] = r;
-            tt = r * r;
+            const int64_t i = 9 * int64_t(j) + a;
+            const double sx = ((red[0][a] + red[1][a]) + (red[2][a] + red[3][a])) + dadd[i] * x[i];
+            const double b_ = bt[i];
+            const double rv = -b_ - sx;
+            if (out) out[i] = rv;
+            tt = rv * rv;
             bb = b_ * b_;
         }
-        // threads 0..8 hold this camera's terms; one partial pair per camera
         if (threadIdx.x < 32) {
             tt = warp_sum(tt);
             bb = warp_sum(bb);
@@ -698,6 +933,36 @@ __global__ void __launch_bounds__(kCamThreads) k_implicit_res(
             }
         }
         __syncthreads();
+    }
+}
+
+// Back-substitution without G (mixed precision): dx_l = -V_l^{-1} (b_l + sum_o J_l^T J_p dx_p,cam(o))
+// (Eq. 15 with the sign that follows from Eq. 6).
+__global__ void k_back_sub_J(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
+                             const double* __restrict__ Jc, const double* __restrict__ Jl,
+                             const double* __restrict__ Lall, const double* __restrict__ bl,
+                             const double* __restrict__ dxp, double* __restrict__ dxl) {
+    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+        double s0 = bl[3 * l], s1 = bl[3 * l + 1], s2 = bl[3 * l + 2];
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
+            const double* xc = dxp + 9 * int64_t(oc[o]);
+            const double* jc = Jc + 18 * o;
+            double u0 = 0.0, u1 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                u0 += jc[a] * xc[a];
+                u1 += jc[9 + a] * xc[a];
+            }
+            const double* jl = Jl + 6 * o;
+            s0 += jl[0] * u0 + jl[3] * u1;
+            s1 += jl[1] * u0 + jl[4] * u1;
+            s2 += jl[2] * u0 + jl[5] * u1;
+        }
+        double y0, y1, y2;
+        solve_V(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
+        dxl[3 * l] = -y0;
+        dxl[3 * l + 1] = -y1;
+        dxl[3 * l + 2] = -y2;
     }
 }
 
@@ -760,18 +1025,6 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     for (int64_t i = gtid(); i < n; i += gstride()) out[i] = static_cast<float>(in[i]);
 }
 
-// G32 = rows of Lam G in float32: entry (a, t) of G_o becomes float(G_o,at) float(Lam_cam(o),a).
-// Rounding G first and scaling in float32 keeps the float64 pipe to one conversion per value
-// (the product adds at most one more float32 rounding).
-__global__ void k_scaled_g32(int64_t n_o, const int32_t* __restrict__ oc, const double* __restrict__ G,
-                             const float* __restrict__ lam32, float* __restrict__ G32) {
-    for (int64_t i = gtid(); i < n_o * 27; i += gstride()) {
-        const int64_t o = i / 27;
-        const int a = int(i - 27 * o) / 3;
-        G32[i] = static_cast<float>(G[i]) * lam32[9 * int64_t(oc[o]) + a];
-    }
-}
-
 // dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
 __global__ void k_back_substitute(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
                                   const double* __restrict__ G, const double* __restrict__ Lall,
@@ -790,10 +1043,10 @@ __global__ void k_back_substitute(int32_t n_l, const int64_t* __restrict__ pt_pt
                 a2 += g[3 * a + 2] * xa;
             }
         }
-        const double* L = Lall + 6 * l;
-        double y2 = a2 / L[5];
-        double y1 = (a1 - L[4] * y2) / L[2];
-        double y0 = (a0 - L[1] * y1 - L[3] * y2) / L[0];
+        const double* L = Lall + 6 * l;   // reciprocal diagonal at 0, 2, 5
+        double y2 = a2 * L[5];
+        double y1 = (a1 - L[4] * y2) * L[2];
+        double y0 = (a0 - L[1] * y1 - L[3] * y2) * L[0];
         dxl[3 * l] = -y0;
         dxl[3 * l + 1] = -y1;
         dxl[3 * l + 2] = -y2;
@@ -878,27 +1131,42 @@ void launch_project(int64_t n_o, const double* cams, const double* pts, const in
 
 void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
     k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.aux, y.pts, s.obs_cam, s.obs_pt,
-                                                                 s.obs_xy, y.r, y.Jc, y.Jl);
+                                                                 s.obs_xy, y.r, y.Jc, y.Jl, y.PY32);
 }
 
 void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
     k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, y.r, y.Jl, damping, lambda, y.V,
-                                                                 y.L, y.bl, y.e, y.status);
+                                                                 y.L, y.bl, y.e, y.L32, y.yl, y.status);
 }
 
 void launch_obs_G(const Structure& s, System& y, cudaStream_t st) {
     k_obs_G<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_pt, y.Jc, y.Jl, y.L, y.G);
 }
 
+static int cam_grid(const Structure& s) { return s.n_c < num_sms() * 8 ? s.n_c : num_sms() * 8; }
+
 void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
-    int g = s.n_c < num_sms() * 8 ? s.n_c : num_sms() * 8;
-    k_cameras<<<g, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, y.G, y.e, damping,
-                                         lambda, y.U, y.bp, y.bt);
+    k_cameras<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, y.G, y.e, damping,
+                                                   lambda, y.U, y.bp, y.bt);
+}
+
+void launch_cameras_U(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
+    k_cameras<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, nullptr, y.e,
+                                                   damping, lambda, y.U, y.bp, nullptr);
 }
 
 void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
-    int g = s.n_c < num_sms() * 8 ? s.n_c : num_sms() * 8;
-    k_schur_diag<<<g, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.G, y.U, y.Sd);
+    k_schur_diag<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.G, y.U, y.Sd);
+}
+
+void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
+    k_cam_rhs<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, y.Jl, y.yl,
+                                                   damping, lambda, y.bt, y.dadd);
+}
+
+void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st) {
+    k_schur_diag32<<<cam_grid(s), kDiagThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.aux32, y.PY32,
+                                                         y.L32, y.dadd, y.Sd);
 }
 
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
@@ -910,7 +1178,8 @@ void launch_schur(const Structure& s, System& y, cudaStream_t st) {
 }
 
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
-    k_scaled_g32<<<grid_for(s.n_o * 27, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, y.lam32, y.G32);
+    k_obs_G32<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, s.obs_pt, y.aux32, y.PY32, y.L32,
+                                                               y.lam32, y.G32);
     if (s.n_up > 0)
         k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
             s.n_up, s.up_dst, s.up_mdst, s.up_pair_ptr, s.pairs, y.G32, y.S32);
@@ -920,14 +1189,13 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
 
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st) {
-    k_implicit_u<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, y.G, x, y.uo);
-    k_implicit_tsum<<<grid_for(int64_t(s.n_l) * 3, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, y.uo, y.tl);
-    k_implicit_res<<<s.n_c, kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.G, y.tl, y.U, x, y.bt, out,
-                                                  partial);
+    k_jres_land<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.Jc, y.Jl, y.L, x, y.uv);
+    k_jres_cam<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.Jc, y.uv, y.dadd, x, y.bt, out,
+                                                    partial);
 }
 
 void launch_cam_prep(const Structure& s, System& y, cudaStream_t st) {
-    k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux);
+    k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux, y.aux32);
 }
 
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
@@ -941,8 +1209,12 @@ void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st) {
 }
 
 void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl, cudaStream_t st) {
-    k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, y.L, y.e,
-                                                                       dxp, dxl);
+    if (y.G)
+        k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, y.L, y.e,
+                                                                           dxp, dxl);
+    else
+        k_back_sub_J<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.Jc, y.Jl, y.L, y.bl,
+                                                                      dxp, dxl);
 }
 
 void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial, int nparts,

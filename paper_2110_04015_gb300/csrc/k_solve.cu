@@ -5,9 +5,11 @@
 // iteration.  All data-dependent control (the stop test, the tau-test and the width of the next
 // direction block, the history size) lives in one device struct Ctl per problem, written only by
 // the per-problem "decide" steps (run by the CTA that finalises an update kernel's sums, and by the
-// small solve) and read by the others, so a chunk of iterations is captured
-// once as a CUDA graph and replayed; the host reads the Ctl array back once per chunk.  A problem
-// whose Ctl::done is set is skipped by every later launch while the others go on.
+// small solve) and read by the others.  A whole solve is one CUDA graph: a conditional WHILE node
+// repeats a body of `chunk` iterations while k_loop_cond finds a problem that is not done (the
+// float64 iterative refinement of mixed precision is an outer WHILE node around it), so the host
+// launches the graph once and reads the results once; nothing inside a solve waits on the host.
+// A problem whose Ctl::done is set is skipped by every later launch while the others go on.
 //
 // Batches: problem b owns the cameras [c0, c0 + nc) of the handle (S is block-diagonal over the
 // problems, since no landmark is seen by two of them).  Per-problem kernels take the problem from
@@ -79,7 +81,23 @@ struct Ctl {
     double true_rr, bb;                 // true residual and |rhs|^2
     double stag;       // float32 sweeps: stop when t_i (energy decrease / r^T D^-1 r) falls below this
     int direct_q;      // 1: Q_{i+1} = S P_{i+1} (Algorithm 2); 0: the Q update of Eq. 18
-    int pad_;
+    int pinv_steps;    // steps whose Delta_i took the eigen-decomposition pseudo-inverse
+    int hist_off;      // residual history: this sweep's first row (earlier sweeps' steps)
+    double hist_scale; // and the factor that puts its values in units of the outer |b~|^2
+};
+
+// Per-solve arguments read by the kernels (one copy in device memory, written before each launch of
+// the solve graph, so one captured graph serves every tolerance, tau and iteration budget).
+struct Params {
+    double tol, tau, inner_tol;
+    int max_iters, max_refine, mcg, pad;
+};
+
+// Loop counters of a solve (zeroed before each launch): body passes of the Krylov loop (all sweeps),
+// passes of the refinement loop, passes of the current sweep, and whether the safety bound ended a
+// loop with a problem still running.
+struct Loops {
+    int inner, outer, cur, capped;
 };
 
 // Float64 iterative refinement of one problem (mixed precision).
@@ -91,7 +109,7 @@ struct Outer {
     int status;
     int active;        // still refining
     int swept;         // takes part in the sweep being run
-    int sweeps, iters, locals;
+    int sweeps, iters, locals, pinvs;
     int max_in;        // iteration budget of the next sweep
     int cols;          // history columns of its last sweep
 };
@@ -224,6 +242,8 @@ struct ItemList {
     int* cnt = nullptr;       // one per group, zero between launches
     void* part = nullptr;     // n x 9 partial sums (element type of the product)
     int nprob = 0;            // problems the list covers
+    int polls = kDefaultWaitPolls;   // polls of a tile barrier before a wait gives up (0: at once)
+    int ngrp = 0;             // groups (counters)
 };
 
 // Which problems a product serves: every live one, those forming a global (local) block, or those
@@ -290,7 +310,8 @@ __device__ __forceinline__ bool grid_sum_finalize(double (&v)[NV], double* parti
 
 // ---- bulk copies (cp.async.bulk + mbarrier) --------------------------------------------
 
-constexpr int kMaxSpin = 1 << 20;   // bounded mbarrier waits: a copy that never lands ends the kernel
+// Bounded mbarrier waits: after `polls` unsuccessful polls a wait gives up (polls = 0: at once); the
+// kernel then records BA_ERR_TIMEOUT and drains its own copies in flight with the default bound.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -309,8 +330,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < kMaxSpin; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls) {
+    for (int i = 0; i < polls; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -446,7 +467,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
                     for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
                 }
                 // every lane observes the phase (visibility of the copied bytes); the warp agrees
-                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u, L.polls);
                 if (!__all_sync(0xffffffffu, ok)) {
                     bad = true;
                     bad_prob = it.prob;
@@ -522,7 +543,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
         // the problem's next decide step ends it with the status
         if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
-            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
+            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u, kDefaultWaitPolls);
     }
 }
 
@@ -627,7 +648,7 @@ __global__ void __launch_bounds__(SpmmCfg::kWarps * 32, 1) k_spmm(
                     const int q = (t + 1) * 32 + r * 8 + qi;
                     kn[r] = (active && t + 1 < t1 && q < it.q1) ? col[rj + q] : -1;
                 }
-                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+                const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u, L.polls);
                 if (!__all_sync(0xffffffffu, ok)) {
                     bad = true;
                     bad_prob = it.prob;
@@ -729,7 +750,7 @@ __global__ void __launch_bounds__(SpmmCfg::kWarps * 32, 1) k_spmm(
     if (bad) {
         if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
-            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u);
+            if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u, kDefaultWaitPolls);
     }
 }
 
@@ -771,7 +792,7 @@ __global__ void k_init_vec(const Layout* __restrict__ lay, const double* __restr
 // One warp per problem.  outer (mixed precision, may be null) supplies the sweep's tolerance and
 // iteration budget and leaves the problems that are not refined any more done from the start.
 __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const double* __restrict__ partial, int np,
-                           double tol, int max_iters, double tau, double stag, int direct_q,
+                           const Params* __restrict__ prm, double stag, int direct_q,
                            const Outer* __restrict__ outer, int* blk_off, int* blk_w, int mi1) {
     const int p = blockIdx.x;
     const double rr0 = sum_partials(partial + int64_t(p) * np, np, 1, 0);
@@ -779,13 +800,19 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
         Ctl c;
         memset(&c, 0, sizeof(c));
         c.lay = lay[p];
-        double tl = tol;
-        int mi = max_iters;
+        double tl = prm->tol;
+        const double tau = prm->tau;
+        int mi = prm->max_iters;
         bool act = true;
+        c.hist_off = 0;
+        c.hist_scale = 1.0;
         if (outer) {
-            act = outer[p].swept != 0;
-            tl = outer[p].tol_in;
-            mi = outer[p].max_in;
+            const Outer& o = outer[p];
+            act = o.swept != 0;
+            tl = o.tol_in;
+            mi = o.max_in;
+            c.hist_off = o.iters;
+            c.hist_scale = o.bb > 0.0 ? o.tr / o.bb : 0.0;
         }
         c.rr0 = rr0;
         c.rr0_inv = rr0 > 0.0 ? 1.0 / rr0 : 0.0;
@@ -812,6 +839,35 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
         ctl[p] = c;
         blk_off[int64_t(p) * mi1] = 0;
         blk_w[int64_t(p) * mi1] = 1;
+    }
+}
+
+// Condition of the Krylov WHILE loop: continue while a problem is not done.  first = 1 (before the
+// loop) starts the sweep's pass count; otherwise one body pass has ended.  `bound` passes (every
+// problem stops by its iteration budget well before) end the loop in any case.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Ctl* __restrict__ ctl, int nb, Loops* lp, int first,
+                            int chunk, const Params* __restrict__ prm) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) mine |= ctl[b].done == 0;
+    if (mine) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int go = any;
+        if (first) {
+            lp->cur = 0;
+        } else {
+            lp->cur += 1;
+            lp->inner += 1;
+        }
+        const int bound = (prm->max_iters + chunk - 1) / chunk + 2;
+        if (lp->cur >= bound) {
+            if (go) lp->capped = 1;
+            go = 0;
+        }
+        cudaGraphSetConditional(h, go ? 1u : 0u);
     }
 }
 
@@ -937,7 +993,7 @@ __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int n
     c->Delta = D;
     c->gamma = g;
     c->rr = rr;
-    hist[int64_t(it - 1) * nb + p] = rr * c->rr0_inv;   // squared relative residual
+    hist[int64_t(c->hist_off + it - 1) * nb + p] = rr * c->rr0_inv * c->hist_scale;   // squared relative residual
     if (!(D > 0.0) || !(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -1276,6 +1332,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mcg_small(Ctl* ctl, const dou
         __syncthreads();
     } else if (!inverse_certified(sA, sX, w)) {
         pinv_sym_jacobi(sA, sV, sX, w);
+        if (threadIdx.x == 0) c->pinv_steps += 1;
     }
     if (threadIdx.x < kMaxDirs * kMaxDirs) {
         dpinv[(int64_t(p) * mi1 + it) * kMaxDirs * kMaxDirs + threadIdx.x] = (i < w && j < w) ? sX[i][j] : 0.0;
@@ -1372,7 +1429,7 @@ __device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off
     c->it = it;
     c->rr = rr;
     c->rz = rz;
-    hist[int64_t(it - 1) * nb + p] = rr * c->rr0_inv;   // squared relative residual
+    hist[int64_t(c->hist_off + it - 1) * nb + p] = rr * c->rr0_inv * c->hist_scale;   // squared relative residual
     if (!(rr == rr) || isinf(rr)) {
         c->done = 1;
         c->status = BA_ERR_BREAKDOWN;
@@ -1766,32 +1823,50 @@ __global__ void k_outer_init(const Layout* __restrict__ lay, const double* __res
 
 // Plan the next float32 sweep of every problem still refining: per sweep the inner solve reduces
 // its residual by inner_tol; when what is left to reach tol is within ten times that, the sweep
-// aims 3x past it so that it is the last one.
-__global__ void k_refine_plan(Outer* outer, double tol, double inner_tol, int max_iters, int max_refine) {
-    Outer* o = outer + blockIdx.x;
-    if (threadIdx.x != 0) return;
-    o->swept = 0;
-    if (!o->active) return;
-    if (o->sweeps >= max_refine || o->iters >= max_iters) {
-        o->active = 0;
-        return;
+// aims 3x past it so that it is the last one.  One CTA over all problems; sets the refinement
+// loop's condition: another sweep when any problem takes part (count = 1: a loop pass has ended).
+__global__ void k_refine_plan(Outer* outer, int nb, const Params* __restrict__ prm, cudaGraphConditionalHandle h,
+                              Loops* lp, int count) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const double tol = prm->tol, inner_tol = prm->inner_tol;
+    int mine = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        Outer* o = outer + b;
+        o->swept = 0;
+        if (!o->active) continue;
+        if (o->sweeps >= prm->max_refine || o->iters >= prm->max_iters) {
+            o->active = 0;
+            continue;
+        }
+        const double need = tol * sqrt(o->bb) / sqrt(o->tr);
+        double t = need > 0.1 * inner_tol ? fmax(0.3 * need, 0.1 * inner_tol) : inner_tol;
+        if (t >= 1.0) t = 0.5;
+        o->tol_in = t;
+        o->max_in = prm->max_iters - o->iters;
+        o->swept = 1;
+        mine = 1;
     }
-    const double need = tol * sqrt(o->bb) / sqrt(o->tr);
-    double t = need > 0.1 * inner_tol ? fmax(0.3 * need, 0.1 * inner_tol) : inner_tol;
-    if (t >= 1.0) t = 0.5;
-    o->tol_in = t;
-    o->max_in = max_iters - o->iters;
-    o->swept = 1;
+    if (mine) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (count) lp->outer += 1;
+        cudaGraphSetConditional(h, any ? 1u : 0u);
+    }
 }
 
 // After a sweep and the float64 true residual: account the sweep and decide whether to go on.
-__global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, double tol, int mcg) {
+__global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, const Params* __restrict__ prm) {
     Outer* o = outer + blockIdx.x;
     const Ctl& c = ctl[blockIdx.x];
     if (threadIdx.x != 0 || !o->swept) return;
+    const double tol = prm->tol;
+    const int mcg = prm->mcg;
     o->sweeps += 1;
     o->iters += c.it;
     o->locals += c.local_steps;
+    o->pinvs += c.pinv_steps;
     o->cols = mcg ? c.cols : 1;
     o->tr_prev = o->tr;
     o->tr = c.true_rr;
@@ -1816,17 +1891,30 @@ __global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, double
 // ---------------------------------------------------------------------------------------
 // host side
 
+// What a captured solve graph depends on besides the per-solve Params: the algorithm, precision,
+// loop body, work lists, wait bound and every buffer address (a reallocation bumps `allocs`).
 struct GraphKey {
-    int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1;
+    int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1, polls = -1, nb = -1;
     uint64_t allocs = ~uint64_t(0);   // buffer generation (any reallocation invalidates the graph)
-    const void* ptrs[14] = {};
+    const void* ptrs[4] = {};
     bool operator==(const GraphKey& o) const {
         if (mcg != o.mcg || fp32 != o.fp32 || chunk != o.chunk || mi1 != o.mi1 || use_l != o.use_l ||
-            epoch != o.epoch || allocs != o.allocs)
+            epoch != o.epoch || polls != o.polls || nb != o.nb || allocs != o.allocs)
             return false;
-        for (int i = 0; i < 14; ++i) if (ptrs[i] != o.ptrs[i]) return false;
+        for (int i = 0; i < 4; ++i) if (ptrs[i] != o.ptrs[i]) return false;
         return true;
     }
+};
+
+// Kernel launches of a solve graph before, per pass of and after its loops.
+struct GraphCounts {
+    int pre = 0, sweep = 0, body = 0, post = 0;
+};
+
+struct SolveExec {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    GraphCounts gc;
 };
 
 // device buffer that only grows
@@ -1847,15 +1935,17 @@ struct Solver {
     int gphi = 1, gb = 1;     // Phi and beta grid widths
     std::vector<Layout> lay;  // of the current solve
     Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, betaf, phip, hist, blk_off, blk_w, ctl, outer, rt,
-        lay_d, totals, dpart, dcnt, camdot;
+        lay_d, totals, dpart, dcnt, camdot, params, loops;
     Ctl* h_ctl = nullptr;     // pinned, nb
     Outer* h_outer = nullptr; // pinned, nb
+    Params* h_params = nullptr;   // pinned staging of the per-solve arguments
+    Loops* h_loops = nullptr;     // pinned
+    double* h_hist = nullptr;     // pinned, nb x mi1 (iteration-major device history)
+    size_t h_hist_n = 0;
     std::vector<std::vector<double>> host_hist;   // per problem, residual history of the last solve
-    std::vector<double> rows;                     // staging of the iteration-major device history
     int64_t launches = 0;     // kernel executions issued by the current solve
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    GraphKey key;
+    cudaStream_t cap_stream = nullptr, cap2 = nullptr, cap3 = nullptr;   // capture streams (nested loops)
+    std::vector<SolveExec*> execs;   // instantiated solve graphs
     // work lists of the block-sparse products: whole rows, and rows split by pose subset
     ItemList items_g, items_l;
     int items_cb = -1;         // item chunk rule the lists were built with (0 = the default)
@@ -1954,6 +2044,7 @@ static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
     L.items = d;
     L.n = int64_t(v.size());
     const int ngrp = v.empty() ? 1 : v.back().grp + 1;
+    L.ngrp = ngrp;
     L.nprob = v.empty() ? 0 : v.back().prob + 1;
     BA_CUDA_TRY(cudaMalloc(&L.cnt, sizeof(int) * ngrp));
     BA_CUDA_TRY(cudaMemset(L.cnt, 0, sizeof(int) * ngrp));
@@ -2052,6 +2143,10 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
         BA_CUDA_TRY(cudaMallocHost(&w->h_outer, sizeof(Outer) * nb));
     }
     if (!w->cap_stream) BA_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
+    if (!w->cap2) BA_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap2, cudaStreamNonBlocking));
+    if (!w->cap3) BA_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap3, cudaStreamNonBlocking));
+    if (!w->h_params) BA_CUDA_TRY(cudaMallocHost(&w->h_params, sizeof(Params)));
+    if (!w->h_loops) BA_CUDA_TRY(cudaMallocHost(&w->h_loops, sizeof(Loops)));
     grow(w->P, size_t(hoff) * elt);
     grow(w->Q, size_t(hoff) * elt);
     grow(w->r, size_t(n) * elt);
@@ -2075,6 +2170,15 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     grow(w->totals, size_t(nb) * kTotals * sizeof(double));
     grow(w->dpart, size_t(nb) * w->gu * 5 * sizeof(double));
     grow(w->camdot, size_t(s.n_c) * 2 * sizeof(double));
+    grow(w->params, sizeof(Params));
+    grow(w->loops, sizeof(Loops));
+    if (w->h_hist_n < size_t(nb) * w->mi1) {
+        if (w->h_hist) cudaFreeHost(w->h_hist);
+        w->h_hist = nullptr;
+        w->h_hist_n = 0;
+        BA_CUDA_TRY(cudaMallocHost(&w->h_hist, sizeof(double) * size_t(nb) * w->mi1));
+        w->h_hist_n = size_t(nb) * w->mi1;
+    }
     if (w->dcnt.bytes < size_t(nb) * 4 * sizeof(int)) {
         grow(w->dcnt, size_t(nb) * 4 * sizeof(int));
         BA_CUDA_TRY(cudaMemset(w->dcnt.p, 0, w->dcnt.bytes));
@@ -2082,6 +2186,8 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     BA_CUDA_TRY(cudaMemcpy(w->lay_d.p, lay.data(), sizeof(Layout) * nb, cudaMemcpyHostToDevice));
     w->lay = lay;
     ensure_items(w, s, a.mcg ? n_dirs : 1, a.item_blocks);
+    w->items_g.polls = a.wait_polls;
+    w->items_l.polls = a.wait_polls;
 }
 
 static void free_buf(Buf& b) {
@@ -2095,15 +2201,23 @@ void solver_destroy(Solver* w) {
     if (!w) return;
     Buf* bufs[] = {&w->P, &w->Q, &w->r, &w->z, &w->xw, &w->PT, &w->part_a, &w->part_b, &w->part_cam, &w->dpinv,
                    &w->beta, &w->betaf, &w->phip, &w->hist, &w->blk_off, &w->blk_w, &w->ctl, &w->outer, &w->rt,
-                   &w->lay_d, &w->totals, &w->dpart, &w->dcnt, &w->camdot};
+                   &w->lay_d, &w->totals, &w->dpart, &w->dcnt, &w->camdot, &w->params, &w->loops};
     for (Buf* b : bufs) free_buf(*b);
-    if (w->exec) cudaGraphExecDestroy(w->exec);
+    for (SolveExec* e : w->execs) {
+        cudaGraphExecDestroy(e->exec);
+        delete e;
+    }
     free_items(w->items_g);
     free_items(w->items_l);
     if (w->mm_part) cudaFree(w->mm_part);
     if (w->h_ctl) cudaFreeHost(w->h_ctl);
     if (w->h_outer) cudaFreeHost(w->h_outer);
+    if (w->h_params) cudaFreeHost(w->h_params);
+    if (w->h_loops) cudaFreeHost(w->h_loops);
+    if (w->h_hist) cudaFreeHost(w->h_hist);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    if (w->cap2) cudaStreamDestroy(w->cap2);
+    if (w->cap3) cudaStreamDestroy(w->cap3);
     delete w;
 }
 
@@ -2174,102 +2288,199 @@ static int iteration_launches(bool mcg, bool fp32, bool two_lists) {
     return fp32 ? 8 : (two_lists ? 8 : 7);
 }
 
-// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0.
+// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0 (3 launches).
 template <typename T>
 static void krylov_init(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
-                        const double* scale, T* x, const SolveArgs& a, const Outer* outer, cudaStream_t st) {
+                        const double* scale, T* x, const Outer* outer, cudaStream_t st) {
     const int nb = w->nb;
     k_init_vec<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(ptr<Layout>(w->lay_d), rhs, sign, scale, Dinv, x, ptr<T>(w->r),
                                                          ptr<T>(w->z), ptr<T>(w->P), ptr<double>(w->part_b));
-    k_init_ctl<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Layout>(w->lay_d), ptr<double>(w->part_b), w->gx, a.tol,
-                                  a.max_iters, a.tau, sizeof(T) == 4 ? kStagnation : 0.0, sizeof(T) == 4 ? 1 : 0, outer,
-                                  ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1);
+    k_init_ctl<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Layout>(w->lay_d), ptr<double>(w->part_b), w->gx,
+                                  ptr<Params>(w->params), sizeof(T) == 4 ? kStagnation : 0.0, sizeof(T) == 4 ? 1 : 0,
+                                  outer, ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1);
     k_spmv<T, 0, true><<<num_sms(), SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
         s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->P), w->items_g, kSelLive, ptr<T>(w->Q), nullptr, nullptr,
         ptr<Ctl>(w->ctl));
-    BA_CUDA_TRY(cudaGetLastError());
-    w->launches += 3;
 }
 
-// One Krylov solve per problem of S x = sign * rhs (rhs float64) with storage type T, all problems
-// in the same launches.  On return w->h_ctl holds every problem's final control block.
+// true residual t = -b~ - S x into out (may be null) and, per problem, its norms into ctl (true_rr,
+// bb): explicit tiled S in float64 precision, the implicit float64 operator in mixed precision.
+static int true_residual(Solver* w, const Structure& s, const System& y, const double* x, double* out,
+                         cudaStream_t st) {
+    int n = 0;
+    if (y.S) {
+        k_true_residual<<<grid_for_host(int64_t(s.n_c) * 32), kThreads, 0, st>>>(
+            s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, ptr<double>(w->part_cam));
+        n = 1;
+    } else {
+        launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
+        n = 2;
+    }
+    k_true_reduce<<<w->nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<double>(w->part_cam));
+    return n + 1;
+}
+
+// ---- the solve graph: conditional WHILE nodes inserted into a stream capture ------------------
+
+// A WHILE node on handle h after the current capture frontier of stream cs; the capture goes on after
+// it.  Returns the (empty) body graph.
+static cudaGraph_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus stat;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    BA_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &stat, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    BA_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    BA_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return np.conditional.phGraph_out[0];
+}
+
+// A conditional handle of the graph being captured on cs (no default: set before the node runs).
+static cudaGraphConditionalHandle capture_handle(cudaStream_t cs) {
+    cudaStreamCaptureStatus stat;
+    cudaGraph_t g = nullptr;
+    BA_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &stat, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h;
+    BA_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    return h;
+}
+
+// The Krylov loop of one sweep, captured on cs: the sweep's start, then WHILE(any problem running) {
+// chunk iterations; loop condition } on the body stream cb.
 template <typename T>
-static void krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
-                   const double* scale, T* x, const SolveArgs& a, const Outer* outer, cudaStream_t st) {
+static void capture_krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs,
+                           double sign, const double* scale, T* x, const Outer* outer, bool mcg, int chunk,
+                           cudaStream_t cs, cudaStream_t cb) {
+    const cudaGraphConditionalHandle h = capture_handle(cs);
+    krylov_init<T>(w, s, S, Dinv, rhs, sign, scale, x, outer, cs);
+    k_loop_cond<<<1, kThreads, 0, cs>>>(h, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 1, chunk,
+                                        ptr<Params>(w->params));
+    cudaGraph_t body = capture_while(cs, h);
+    BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < chunk; ++k) enqueue_iteration<T>(w, s, S, Dinv, x, mcg, cb);
+    k_loop_cond<<<1, kThreads, 0, cb>>>(h, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 0, chunk,
+                                        ptr<Params>(w->params));
+    cudaGraph_t done = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cb, &done);
+    if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
+}
+
+
+
+// Capture and instantiate the whole solve: float64 (Krylov loop and the true residual) or mixed
+// precision (WHILE(a problem refines) { float32 Krylov loop; float64 true residual; plan the next
+// sweep }).
+static cudaGraphExec_t build_solve_graph(Solver* w, const Structure& s, const System& y, const SolveArgs& a,
+                                         double* x, GraphCounts& gc) {
+    const bool fp32 = a.precision == BA_PRECISION_MIXED;
+    const bool mcg = a.mcg != 0;
     const int nb = w->nb;
-    krylov_init<T>(w, s, S, Dinv, rhs, sign, scale, x, a, outer, st);
+    const int64_t n = int64_t(s.n_c) * 9;
+    cudaStream_t cs = w->cap_stream;
+    gc = GraphCounts();
+    gc.body = a.chunk * iteration_launches(mcg, fp32, w->use_l) + 1;
+    BA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        if (!fp32) {
+            capture_krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, mcg, a.chunk, cs, w->cap2);
+            gc.pre = 4;
+            gc.post = true_residual(w, s, y, x, nullptr, cs);
+        } else {
+            k_start_refine<<<grid_for_host(n), kThreads, 0, cs>>>(n, y.bt, x, ptr<double>(w->rt));
+            k_outer_init<<<nb, kThreads, 0, cs>>>(ptr<Layout>(w->lay_d), y.bt, ptr<Outer>(w->outer));
+            const cudaGraphConditionalHandle ho = capture_handle(cs);
+            k_refine_plan<<<1, kThreads, 0, cs>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho,
+                                                  ptr<Loops>(w->loops), 0);
+            gc.pre = 3;
+            cudaGraph_t body = capture_while(cs, ho);
+            cudaStream_t c2 = w->cap2;
+            BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(c2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            capture_krylov<float>(w, s, y.S32, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw),
+                                  ptr<Outer>(w->outer), mcg, a.chunk, c2, w->cap3);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, c2>>>(n, ptr<float>(w->xw), y.lam, x);
+            const int tr = true_residual(w, s, y, x, ptr<double>(w->rt), c2);
+            k_refine_after<<<nb, 32, 0, c2>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), ptr<Params>(w->params));
+            k_refine_plan<<<1, kThreads, 0, c2>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho,
+                                                  ptr<Loops>(w->loops), 1);
+            gc.sweep = 4 + 1 + tr + 2;
+            cudaGraph_t done = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c2, &done);
+            if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("refinement body capture: ") + cudaGetErrorString(e));
+        }
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        cudaGetLastError();
+        throw;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("solve graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("solve graph instantiate: ") + cudaGetErrorString(e));
+    return exec;
+}
+
+// The instantiated graph for this solve (kept for the next solve of the same kind; a few kinds are
+// kept, e.g. PCG and MCG in turn, and graphs that hold freed buffers are dropped).
+static cudaGraphExec_t solve_graph(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x,
+                                   GraphCounts& gc) {
+    const bool fp32 = a.precision == BA_PRECISION_MIXED;
     GraphKey key;
     key.mcg = a.mcg;
-    key.fp32 = sizeof(T) == 4;
+    key.fp32 = fp32;
     key.chunk = a.chunk;
     key.mi1 = w->mi1;
     key.use_l = w->use_l;
     key.epoch = w->epoch;
+    key.polls = a.wait_polls;
+    key.nb = w->nb;
     key.allocs = g_allocs.load();
-    const void* ptrs[14] = {S, Dinv, x, w->P.p, w->Q.p, w->r.p, w->z.p, w->ctl.p, w->beta.p, w->phip.p,
-                            w->items_g.items, w->items_l.items, w->PT.p, w->dpinv.p};
-    for (int i = 0; i < 14; ++i) key.ptrs[i] = ptrs[i];
-    if (!(key == w->key) || !w->exec) {
-        if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
-        cudaGraph_t g = nullptr;
-        BA_CUDA_TRY(cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < a.chunk; ++k) enqueue_iteration<T>(w, s, S, Dinv, x, a.mcg != 0, w->cap_stream);
-        cudaError_t ce = cudaStreamEndCapture(w->cap_stream, &g);
-        if (ce != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-        ce = cudaGraphInstantiate(&w->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
-        w->key = key;
+    const void* ptrs[4] = {x, fp32 ? (const void*)y.S32 : (const void*)y.S, w->items_g.items, w->items_l.items};
+    for (int i = 0; i < 4; ++i) key.ptrs[i] = ptrs[i];
+    for (size_t i = 0; i < w->execs.size();) {
+        if (w->execs[i]->key.allocs != key.allocs) {
+            cudaGraphExecDestroy(w->execs[i]->exec);
+            delete w->execs[i];
+            w->execs.erase(w->execs.begin() + i);
+        } else {
+            ++i;
+        }
     }
-    const int per_iter = iteration_launches(a.mcg != 0, sizeof(T) == 4, w->use_l);
-    const int max_chunks = a.max_iters / a.chunk + 2;
-    for (int c = 0; c < max_chunks; ++c) {
-        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
-        BA_CUDA_TRY(cudaStreamSynchronize(st));
-        bool all_done = true;
-        for (int b = 0; b < nb && all_done; ++b) all_done = w->h_ctl[b].done != 0;
-        if (all_done) break;
-        BA_CUDA_TRY(cudaGraphLaunch(w->exec, st));
-        w->launches += int64_t(a.chunk) * per_iter;
+    for (SolveExec* e : w->execs)
+        if (e->key == key) {
+            gc = e->gc;
+            return e->exec;
+        }
+    SolveExec* e = new SolveExec();
+    e->key = key;
+    try {
+        e->exec = build_solve_graph(w, s, y, a, x, e->gc);
+    } catch (...) {
+        delete e;
+        throw;
     }
-    BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
-    BA_CUDA_TRY(cudaStreamSynchronize(st));
-}
-
-// out = -b~ - S x and, per problem, its norms into ctl (true_rr, bb): explicit tiled S in float64
-// precision, the implicit float64 operator U x - G (G^T x) in mixed precision (no float64 S).
-static void true_residual(Solver* w, const Structure& s, const System& y, const double* x, double* out,
-                          cudaStream_t st) {
-    if (y.S) {
-        k_true_residual<<<grid_for_host(int64_t(s.n_c) * 32), kThreads, 0, st>>>(
-            s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, ptr<double>(w->part_cam));
-        w->launches += 1;
-    } else {
-        launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
-        w->launches += 3;
+    if (w->execs.size() >= 6) {
+        cudaGraphExecDestroy(w->execs.front()->exec);
+        delete w->execs.front();
+        w->execs.erase(w->execs.begin());
     }
-    k_true_reduce<<<w->nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<double>(w->part_cam));
-    w->launches += 1;
-}
-
-// Append rows [0, its) of the iteration-major device history (squared relative residuals) to each
-// problem's host history as relative residuals, problem b's values multiplied by scale[b] (rows
-// past a problem's own count are ignored).
-static void collect_history(Solver* w, const std::vector<int>& its, const std::vector<double>& scale, cudaStream_t st) {
-    const int nb = w->nb;
-    int rows = 0;
-    for (int v : its) rows = std::max(rows, v);
-    if (rows == 0) return;
-    w->rows.resize(size_t(rows) * nb);
-    BA_CUDA_TRY(cudaMemcpyAsync(w->rows.data(), w->hist.p, sizeof(double) * w->rows.size(), cudaMemcpyDeviceToHost, st));
-    BA_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int b = 0; b < nb; ++b)
-        for (int i = 0; i < its[b]; ++i) w->host_hist[b].push_back(std::sqrt(w->rows[size_t(i) * nb + b]) * scale[b]);
+    w->execs.push_back(e);
+    gc = e->gc;
+    return e->exec;
 }
 
 void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x, SolveOut& out,
                 cudaStream_t st) {
-    const int64_t n = int64_t(s.n_c) * 9;
     int n_dirs = a.mcg ? a.n_dirs : 1;
     if (n_dirs < 1) n_dirs = 1;
     if (n_dirs > kMaxDirs) throw Error(BA_ERR_INVALID_ARG, "n_dirs must be in [1, 16]");
@@ -2278,93 +2489,87 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     const int nb = w->nb;
     w->launches = 0;
     w->host_hist.assign(nb, std::vector<double>());
+    GraphCounts gc;
+    cudaGraphExec_t exec = solve_graph(w, s, y, a, x, gc);
 
     cudaEvent_t e0, e1;
     BA_CUDA_TRY(cudaEventCreate(&e0));
     BA_CUDA_TRY(cudaEventCreate(&e1));
     BA_CUDA_TRY(cudaEventRecord(e0, st));
+    // the solve: its arguments in, one graph launch, the results out, one wait
+    Params* hp = w->h_params;
+    hp->tol = a.tol;
+    hp->tau = a.tau;
+    hp->inner_tol = a.inner_tol;
+    hp->max_iters = a.max_iters;
+    hp->max_refine = a.max_refine;
+    hp->mcg = a.mcg;
+    hp->pad = 0;
+    BA_CUDA_TRY(cudaMemcpyAsync(w->params.p, hp, sizeof(Params), cudaMemcpyHostToDevice, st));
+    BA_CUDA_TRY(cudaMemsetAsync(w->loops.p, 0, sizeof(Loops), st));
+    BA_CUDA_TRY(cudaGraphLaunch(exec, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
+    if (fp32) BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(w->h_loops, w->loops.p, sizeof(Loops), cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaMemcpyAsync(w->h_hist, w->hist.p, sizeof(double) * size_t(nb) * w->mi1, cudaMemcpyDeviceToHost, st));
+    BA_CUDA_TRY(cudaEventRecord(e1, st));
+    BA_CUDA_TRY(cudaEventSynchronize(e1));
+    int host_waits = 1;
+    BA_CUDA_TRY(cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+
+    const Loops lp = *w->h_loops;
+    w->launches = gc.pre + int64_t(lp.outer) * gc.sweep + int64_t(lp.inner) * gc.body + gc.post;
     out = SolveOut();
     out.probs.assign(nb, ProbOut());
-    if (!fp32) {
-        krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, a, nullptr, st);
-        std::vector<int> its(nb);
-        for (int b = 0; b < nb; ++b) its[b] = w->h_ctl[b].it;
-        collect_history(w, its, std::vector<double>(nb, 1.0), st);
-        std::vector<Ctl> fin(w->h_ctl, w->h_ctl + nb);
-        // true relative residual in float64
-        true_residual(w, s, y, x, nullptr, st);
-        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
-        BA_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int b = 0; b < nb; ++b) {
-            ProbOut& o = out.probs[b];
-            const Ctl& c = fin[b];
-            o.status = c.status;
+    bool timed_out = false;
+    for (int b = 0; b < nb; ++b) {
+        ProbOut& o = out.probs[b];
+        const Ctl& c = w->h_ctl[b];
+        int steps = 0;
+        if (!fp32) {
+            o.status = c.done ? c.status : BA_ERR_NOT_CONVERGED;
             o.iters = c.it;
             o.local_steps = c.local_steps;
-            o.n_eff = w->lay[b].n_eff;
+            o.pinv_steps = c.pinv_steps;
             o.history_cols = a.mcg ? c.cols : 1;
             o.rel_residual = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
             o.refinements = 1;
-            o.true_rel_residual = w->h_ctl[b].bb > 0 ? std::sqrt(w->h_ctl[b].true_rr / w->h_ctl[b].bb) : 0.0;
-        }
-    } else {
-        // float64 iterative refinement around float32 Krylov sweeps; x = 0, so the true residual
-        // starts as -b~ itself
-        k_start_refine<<<grid_for_host(n), kThreads, 0, st>>>(n, y.bt, x, ptr<double>(w->rt));
-        k_outer_init<<<nb, kThreads, 0, st>>>(ptr<Layout>(w->lay_d), y.bt, ptr<Outer>(w->outer));
-        w->launches += 2;
-        SolveArgs inner = a;
-        for (int sweep = 0; sweep < a.max_refine; ++sweep) {
-            k_refine_plan<<<nb, 32, 0, st>>>(ptr<Outer>(w->outer), a.tol, a.inner_tol, a.max_iters, a.max_refine);
-            BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
-            BA_CUDA_TRY(cudaStreamSynchronize(st));
-            w->launches += 1;
-            bool any = false;
-            for (int b = 0; b < nb && !any; ++b) any = w->h_outer[b].swept != 0;
-            if (!any) break;
-            // history of this sweep in units of the outer |b~|: scaled by the sweep's start residual
-            std::vector<double> scale(nb, 0.0);
-            for (int b = 0; b < nb; ++b)
-                if (w->h_outer[b].swept) scale[b] = std::sqrt(w->h_outer[b].tr / w->h_outer[b].bb);
-            int budget = 0;
-            for (int b = 0; b < nb; ++b)
-                if (w->h_outer[b].swept) budget = std::max(budget, w->h_outer[b].max_in);
-            inner.max_iters = budget;   // host loop bound; each problem stops at its own budget
-            krylov<float>(w, s, y.S32, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw), inner,
-                          ptr<Outer>(w->outer), st);
-            std::vector<int> its(nb, 0);
-            for (int b = 0; b < nb; ++b) its[b] = w->h_outer[b].swept ? w->h_ctl[b].it : 0;
-            collect_history(w, its, scale, st);
-            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x);
-            true_residual(w, s, y, x, ptr<double>(w->rt), st);
-            k_refine_after<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), a.tol, a.mcg);
-            w->launches += 2;
-        }
-        BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
-        BA_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int b = 0; b < nb; ++b) {
-            ProbOut& o = out.probs[b];
+            o.true_rel_residual = c.bb > 0 ? std::sqrt(c.true_rr / c.bb) : 0.0;
+            steps = c.it;
+        } else {
             const Outer& u = w->h_outer[b];
             o.status = u.status;
             o.iters = u.iters;
             o.local_steps = u.locals;
-            o.n_eff = w->lay[b].n_eff;
+            o.pinv_steps = u.pinvs;
             o.history_cols = u.cols;
             o.refinements = u.sweeps;
             // tr is the float64 true residual of the problem's current x
             o.rel_residual = u.bb > 0 ? std::sqrt(u.tr / u.bb) : 0.0;
             o.true_rel_residual = o.rel_residual;
+            steps = u.iters;
         }
+        o.n_eff = w->lay[b].n_eff;
+        timed_out = timed_out || o.status == BA_ERR_TIMEOUT;
+        std::vector<double>& h = w->host_hist[b];
+        h.resize(size_t(std::min(steps, w->mi1)));
+        for (size_t i = 0; i < h.size(); ++i) h[i] = std::sqrt(w->h_hist[i * nb + b]);
+    }
+    if (timed_out) {
+        // a warp whose tile wait gave up left its work item uncounted, so its group's arrival counter
+        // did not return to zero: clear the counters for the next product
+        if (w->items_g.cnt) BA_CUDA_TRY(cudaMemsetAsync(w->items_g.cnt, 0, sizeof(int) * w->items_g.ngrp, st));
+        if (w->items_l.cnt) BA_CUDA_TRY(cudaMemsetAsync(w->items_l.cnt, 0, sizeof(int) * w->items_l.ngrp, st));
+        BA_CUDA_TRY(cudaStreamSynchronize(st));
+        ++host_waits;
     }
     out.launches = w->launches;
-    BA_CUDA_TRY(cudaEventRecord(e1, st));
-    BA_CUDA_TRY(cudaEventSynchronize(e1));
-    BA_CUDA_TRY(cudaGetLastError());
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    out.host_waits = host_waits;
     out.ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     // the batch's summary: the first failing problem's status, the largest counts and residuals
     out.status = BA_OK;
     out.n_eff = 1;
@@ -2373,6 +2578,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
         if (out.status == BA_OK && o.status != BA_OK) out.status = o.status;
         out.iters = std::max(out.iters, o.iters);
         out.local_steps = std::max(out.local_steps, o.local_steps);
+        out.pinv_steps = std::max(out.pinv_steps, o.pinv_steps);
         out.n_eff = std::max(out.n_eff, o.n_eff);
         out.refinements = std::max(out.refinements, o.refinements);
         out.history_cols = std::max(out.history_cols, o.history_cols);
@@ -2398,10 +2604,16 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
     a.item_blocks = item_blocks;
     a.precision = fp32 ? BA_PRECISION_MIXED : BA_PRECISION_FP64;
     prepare(w, s, a, 1, fp32);
+    Params* hp = w->h_params;
+    *hp = Params();
+    hp->tol = 1e-6;
+    hp->max_iters = 1;
+    BA_CUDA_TRY(cudaMemcpyAsync(w->params.p, hp, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (fp32)
-        krylov_init<float>(w, s, y.S32, y.Dhat, y.bt, -1.0, y.lam, ptr<float>(w->xw), a, nullptr, st);
+        krylov_init<float>(w, s, y.S32, y.Dhat, y.bt, -1.0, y.lam, ptr<float>(w->xw), nullptr, st);
     else
-        krylov_init<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, ptr<double>(w->xw), a, nullptr, st);
+        krylov_init<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, ptr<double>(w->xw), nullptr, st);
+    BA_CUDA_TRY(cudaGetLastError());
     cudaEvent_t e0, e1;
     BA_CUDA_TRY(cudaEventCreate(&e0));
     BA_CUDA_TRY(cudaEventCreate(&e1));

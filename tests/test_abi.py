@@ -34,7 +34,7 @@ def test_binding_covers_every_declared_call():
 def test_struct_layouts_match_header():
     # sizes implied by include/ba.h (int32 fields, then doubles, natural alignment)
     assert ctypes.sizeof(binding.ba_options) == 4 * 4 + 8 + 4 * 8
-    assert ctypes.sizeof(binding.ba_solve_stats) == 6 * 4 + 3 * 8
+    assert ctypes.sizeof(binding.ba_solve_stats) == 8 * 4 + 3 * 8
     assert ctypes.sizeof(binding.ba_lm_stats) == 4 * 4 + 6 * 8
 
 
@@ -43,7 +43,7 @@ def test_default_options_and_errors_without_device(libba):
     opt = binding.ba_options()
     L.ba_default_options(ctypes.byref(opt))
     assert opt.precision == 0 and opt.damping == 0 and opt.chunk_iters == 8 and opt.inner_tol == 1e-6
-    assert opt.max_refine == 64 and opt.max_history == 0 and opt.item_blocks == 0
+    assert opt.max_refine == 64 and opt.max_history == 0 and opt.item_blocks == 0 and opt.wait_polls == 0
     # argument checks run before any device work
     out = ctypes.c_void_p()
     code = L.ba_problem_create(None, 0, 1, 1, None, None, None, None, None, ctypes.byref(out))

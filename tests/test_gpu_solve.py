@@ -227,3 +227,110 @@ def test_full_history_restarts_a_float32_sweep_but_stops_float64():
     assert st["status"] == 0 and st["true_rel_residual"] <= 1e-6 and st["refinements"] > 1
     assert st["history_cols"] <= 40
     p32.close()
+
+
+# --- paths the full-size run takes: rows split over work items, the pseudo-inverse fallback -------
+
+@pytest.mark.parametrize("case", ["dense-small", "sequential"])
+def test_rows_split_over_work_items_match_oracle(case, dense_ref):
+    """32 blocks per work item: rows longer than 32 stored blocks are split over several items, whose
+    partial sums the last item of the row adds (the shape the full-size problems run in)."""
+    m, lin, Dinv = oracle_system(case)
+    sc = scene(case)
+    with problem.from_scene(sc, item_blocks=32) as p:
+        p.ba_build_normal(1e-4)
+        row_ptr, _, _, _ = p.ba_get_schur()
+        # rows span two (sequential: up to 45 blocks) or more (dense-small: up to 150) items
+        assert np.diff(row_ptr).max() > (2 * 32 if case == "dense-small" else 32)
+        ref = dense_ref(case) if case != "sequential" else None
+        o = osol.pcg(lin.S, lin.btilde, Dinv)
+        _check_against_oracle(p, p.ba_solve_pcg(1e-6, 1000), o, lin, ref)
+        for N, tau in [(16, 10.0), (4, 1e9)]:
+            o = osol.mcg(lin.S, lin.btilde, Dinv, N, tau)
+            st = p.ba_solve_mcg(1e-6, 1000, N, tau)
+            _check_against_oracle(p, st, o, lin, ref)
+            assert abs(st["local_steps"] - o.local_steps) <= 1
+
+
+def _unobserved_camera_case(cam=3):
+    """The tiny scene with every observation of one camera removed: its rows of b~ and of every
+    direction are zero, so with one pose per subset its local column is zero and Delta_i is
+    singular at every local step (Algorithm 2's pseudo-inverse, Section 3.2)."""
+    from oracle import lm as olm
+
+    sc = scene("tiny")
+    keep = sc.obs_cam != cam
+    m = olm.measurements(sc)[keep]
+    oc, op = sc.obs_cam[keep], sc.obs_pt[keep]
+    lin = olm.linearise(sc.cams0, sc.pts0, oc, op, m, 1e-4)
+    Dinv = osol.block_jacobi_inverse(lin.S, sc.n_cams)
+    return sc, oc, op, m, lin, Dinv
+
+
+def test_pseudo_inverse_fallback_matches_oracle():
+    sc, oc, op, m, lin, Dinv = _unobserved_camera_case()
+    ref = osol.dense_solve(lin.S, lin.btilde)
+    o = osol.mcg(lin.S, lin.btilde, Dinv, 16, 10.0)
+    assert o.converged and o.local_steps > 0
+    with binding.Problem(sc.cams0, sc.pts0, oc, op, m) as p:
+        p.ba_build_normal(1e-4)
+        st = p.ba_solve_mcg(1e-6, 1000, 16, 10.0)
+        # every local step met the zero column; global steps (width 1) need no matrix inverse
+        assert st["pinv_steps"] == st["local_steps"] > 0, st
+        _check_against_oracle(p, st, o, lin, ref)
+        assert abs(st["local_steps"] - o.local_steps) <= 1
+        assert np.all(p.ba_get_delta()[3] == 0)
+    # and in mixed precision (float32 sweeps, float64 small solves and refinement)
+    with binding.Problem(sc.cams0, sc.pts0, oc, op, m, precision="mixed") as p:
+        p.ba_build_normal(1e-4)
+        st = p.ba_solve_mcg(1e-6, 1000, 16, 10.0)
+        assert st["status"] == 0 and st["pinv_steps"] > 0 and st["true_rel_residual"] <= 1e-6, st
+        assert energy_err(lin.S, p.ba_get_delta().ravel(), ref) < 1e-4
+
+
+@pytest.mark.parametrize("case", ["tiny", "tiny-s3", "dense-small", "seq-small"])
+def test_tight_tolerance_solution_matches_dense_solve_elementwise(case, dense_ref):
+    """At tol 1e-12 the solution equals the dense Cholesky solution entry by entry: each of the 9
+    parameters of every camera within 1e-8 of that parameter's largest magnitude over the cameras
+    (the parameters differ in scale by ~1e6).  The library gets the oracle's measurements, so both
+    sides solve the same system (it then agrees to ~1e-13); the oracle's own PCG and MCG reach
+    2e-12 .. 1e-9 on these cases."""
+    from oracle import lm as olm
+
+    sc = scene(case)
+    m, lin, Dinv = oracle_system(case)
+    ref = dense_ref(case).reshape(sc.n_cams, 9)
+    scale = np.abs(ref).max(axis=0)
+    with binding.Problem(sc.cams0, sc.pts0, sc.obs_cam, sc.obs_pt, olm.measurements(sc)) as p:
+        p.ba_build_normal(1e-4)
+        for kind in ("pcg", "mcg"):
+            st = p.ba_solve_pcg(1e-12, 5000) if kind == "pcg" else p.ba_solve_mcg(1e-12, 5000, 16, 10.0)
+            assert st["status"] == 0, (kind, st)
+            dx = p.ba_get_delta()
+            err = float((np.abs(dx - ref) / scale).max())
+            assert err < 1e-8, (kind, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("chunk", [1, 4])
+def test_a_solve_is_one_graph_launch_with_one_host_wait(precision, chunk):
+    """The iteration loop (and the float64 refinement loop of mixed precision) runs on the device:
+    a solve waits on the host once, for its results, and launches exactly the kernels of the passes
+    its device-side loop made: 4 before the loop, chunk iterations plus the loop condition per pass,
+    and the 2 of the float64 true residual after it (float64); in mixed precision 3 before the
+    refinement loop and 10 around each sweep's Krylov loop."""
+    import math
+
+    sc = scene("seq-small")
+    with problem.from_scene(sc, precision=precision, chunk_iters=chunk) as p:
+        p.ba_build_normal(1e-4)
+        for kind, per in (("pcg", 3), ("mcg", 8)):
+            l0 = p.ba_get_launch_count()
+            st = p.ba_solve_pcg(1e-6, 1000) if kind == "pcg" else p.ba_solve_mcg(1e-6, 1000, 16, 10.0)
+            launched = p.ba_get_launch_count() - l0
+            assert st["status"] == 0 and st["host_waits"] == 1, st
+            body = chunk * per + 1
+            if precision == "fp64":
+                assert launched == 4 + math.ceil(st["iters"] / chunk) * body + 2, (kind, launched, st)
+            elif st["refinements"] == 1:
+                assert launched == 3 + 10 + math.ceil(st["iters"] / chunk) * body, (kind, launched, st)
