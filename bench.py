@@ -59,10 +59,11 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: relative residual reduction of one float32 sweep (library default)")
     ap.add_argument("--tau", type=float, default=10.0)
-    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg"],
+    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg", "build", "pcg"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
                          "400k landmarks, ~1.6M observations) and exit; 'mcg' runs one MCG solve (N = 16) "
-                         "with every step local, so each iteration launches the 16-column kernels")
+                         "with every step local, so each iteration launches the 16-column kernels; 'build' "
+                         "runs three whole builds; 'pcg' two PCG solves")
     ap.add_argument("--sweep", choices=["tau", "ndirs", "density"],
                     help="sensitivity mode (Figs. 3-5 of the paper): MCG vs PCG time-to-1e-6 over tau, N or the "
                          "density of S; prints one JSON line per point and exits")
@@ -82,10 +83,15 @@ def parse():
     ap.add_argument("--no-loop", action="store_true", help="batch mode: skip the looped single-problem solves")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="landmarks per camera x this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample", action="store_true",
                     help="CPU baseline from the 1/32 landmark sample, scaled (seconds) instead of one measured "
                          "oracle step on the whole workload (about two minutes)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the solve loops from the host (ba_options.host_loop), so that a profiler sees "
+                         "the iteration kernels; the default device-side loops run in graphs with conditional "
+                         "nodes, whose kernels ncu does not profile")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default work-item size instead of ba_autotune's choice")
     return ap.parse_args()
@@ -101,10 +107,11 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# DRAM bytes per stored 9x9 block of one k_spmv<float,1,true> launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of the 1000-camera dense case with 16 warps per SM,
-# 319.9 MB / 958,652 blocks; traffic grows with the stored blocks)
-SPMV_F32_TRAFFIC_PER_BLOCK = 333.7
+# DRAM bytes per stored upper 9x9 block of one float32 symmetric product (k_spmv<float,1,true,true> and
+# k_spmv_col together: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the
+# 1000-camera dense case; traffic grows with the stored blocks).  None until that capture is taken
+# of the current kernels.
+SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = None
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
@@ -238,21 +245,35 @@ def full_text(f: dict, sc) -> str:
             f"({f['mcg_iters']} it, {f['mcg_local']} local); numpy/scipy float64, the sparse products on one thread")
 
 
-def thread_scaling(sc, counts=(1, 4, None)) -> dict:
-    """The oracle step on the 1/32 landmark sample with 1, 4 and all BLAS threads (the dense parts
-    of the oracle use them; scipy's sparse products are single-threaded)."""
-    try:
-        import threadpoolctl
-    except ImportError:
-        return {"unavailable": "threadpoolctl missing"}
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def thread_scaling(workload: str, counts=(1, 4, None)) -> dict:
+    """The oracle step on the 1/32 landmark sample with 1, 4 and all BLAS/OpenMP threads, each in a
+    fresh child process (the thread count of numpy's BLAS is fixed when it loads).  The dense parts
+    of the oracle use these threads; scipy's sparse products run on one."""
     out = {}
     for n in counts:
-        key = str(n if n else os.cpu_count())
-        with threadpoolctl.threadpool_limits(limits=n):
-            s = oracle_sample_step(sc)
-        out[key] = round(s["t_build"] + s["t_pcg"] + s["t_mcg"], 3)
-    return {"sample": "landmarks with index % 32 == 0, build + PCG + MCG, seconds by BLAS thread count",
-            "seconds": out}
+        k = n if n else (os.cpu_count() or 1)
+        env = dict(os.environ)
+        for v in THREAD_VARS:
+            env[v] = str(k)
+        try:
+            res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", workload],
+                                 env=env, capture_output=True, text=True, timeout=600)
+            out[str(k)] = json.loads(res.stdout.strip().splitlines()[-1])["seconds"]
+        except (subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+            out[str(k)] = f"failed: {type(e).__name__}"
+    return {"sample": "landmarks with index % 32 == 0: build + PCG + MCG N=16 tau=10, seconds by thread count "
+                      "(OMP/BLAS thread variables of a child process)", "seconds": out}
+
+
+def run_oracle_sample(a):
+    """Child process of thread_scaling: one oracle step on the 1/32 sample, printed as JSON."""
+    gen, kw, _ = WORKLOADS[a.workload]
+    sc = synthetic.make(gen, 0, **kw)
+    s = oracle_sample_step(sc)
+    print(json.dumps({"seconds": round(s["t_build"] + s["t_pcg"] + s["t_mcg"], 3)}), flush=True)
 
 
 def sample_text(s: dict, nnzb_full) -> str:
@@ -360,7 +381,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     xy = problem.device_measurements(sc, device=str(dev))
     torch.cuda.synchronize()
     t_create = time.perf_counter()
-    p = problem.from_scene(sc, precision=a.precision, xy=xy,
+    p = problem.from_scene(sc, precision=a.precision, xy=xy, host_loop=int(a.host_loop),
                            **({} if a.inner_tol is None else {"inner_tol": a.inner_tol}))
     create_ms = (time.perf_counter() - t_create) * 1e3
     stream = torch.cuda.current_stream()
@@ -377,8 +398,8 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     tuned = None
     if not a.no_autotune:
         p.ba_build_normal(LAMBDA)
-        cb, t_cb = p.ba_autotune(reps=5)
-        tuned = {"item_blocks": cb, "spmv_ms": t_cb}
+        cb, t_cb, cfg = p.ba_autotune(reps=5)
+        tuned = {"item_blocks": cb, "spmv_config": cfg, "spmv_ms": t_cb}
     for _ in range(a.warmup):
         step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -413,13 +434,20 @@ def run_ours(a, rank: int, world: int, local_rank: int):
 
     # roofline of the dominant kernel: the product q = S p of the Krylov solves
     nnzb = p.ba_get_schur_nnzb()
+    nnzb_u = (nnzb + sc.n_cams) // 2       # upper triangle with the diagonal
     n = 9 * sc.n_cams
     t_spmv = p.ba_time_kernel("spmv", reps=10)
     t_schur = p.ba_time_kernel("schur", reps=3)
     peaks = load_peaks()
     elt = 8 if a.precision == "fp64" else 4
-    spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
     spmv_flops = 162.0 * nnzb
+    if a.precision == "fp64":
+        spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
+    else:
+        # the symmetric product streams the upper triangle once (each block serves S_jk p_k and
+        # S_jk^T p_j); the 9 transposed terms per strict upper block it writes and reads back
+        # (72 B) are not counted as algorithmic
+        spmv_bytes = nnzb_u * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
     if a.precision == "fp64":
         roof = {"kernel": "k_spmv<double,1,true> (q = S p, Algorithm 1)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
@@ -428,10 +456,13 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                 "peak_source": "measured FP64 FMA throughput 1.06 TFLOP/s (nominal 1.25)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
-        roof = {"kernel": "k_spmv<float,1,true> (q = S p, Algorithm 1)", "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": SPMV_F32_TRAFFIC_PER_BLOCK * nnzb,
-                "traffic_source": "ncu dram bytes of the 1000-camera case scaled by stored blocks",
-                "bytes_per_launch": spmv_bytes,
+        traffic = None if SPMV_F32_TRAFFIC_PER_UPPER_BLOCK is None else SPMV_F32_TRAFFIC_PER_UPPER_BLOCK * nnzb_u
+        roof = {"kernel": "k_spmv<float,1,true,true> + k_spmv_col (q = S p from the upper triangle of S, Algorithm 1)",
+                "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": traffic,
+                "traffic_source": "ncu dram bytes of the 1000-camera case scaled by stored upper blocks",
+                "bytes_per_launch": spmv_bytes, "upper_blocks": nnzb_u,
+                "bytes_moved_model": spmv_bytes + 72 * (nnzb_u - sc.n_cams),
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
     # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
@@ -471,7 +502,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     # the same step in float64 throughout, for the FP64-vs-mixed comparison of the metric
     fp64 = None
     if a.precision == "mixed" and not a.no_compare:
-        q = problem.from_scene(sc, precision="fp64", xy=xy)
+        q = problem.from_scene(sc, precision="fp64", xy=xy, host_loop=int(a.host_loop))
         q.ba_set_stream(stream)
         if not a.no_autotune:
             q.ba_build_normal(LAMBDA)
@@ -523,7 +554,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         else:
             f = oracle_full_step(sc)
             cpu = {"value": f["ms"], "unit": "ms/step", "cores": cpu_threads(), "kind": "oracle",
-                   "sample": full_text(f, sc), **cpu_info(), "thread_scaling": thread_scaling(sc)}
+                   "sample": full_text(f, sc), **cpu_info(), "thread_scaling": thread_scaling(a.workload)}
 
     if rank == 0:
         line = {
@@ -562,8 +593,28 @@ def run_kernel_case(a):
     from paper_2110_04015_gb300 import problem
 
     sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
-    p = problem.from_scene(sc, precision=a.precision)
+    p = problem.from_scene(sc, precision=a.precision, host_loop=int(a.host_loop))
     p.ba_build_normal(LAMBDA)
+    if a.kernel_case == "build":
+        import torch as _t
+
+        e0, e1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+        for rep in range(3):
+            e0.record()
+            p.ba_build_normal(LAMBDA)
+            e1.record()
+            e1.synchronize()
+            print(json.dumps({"kernel_case": "build", "precision": a.precision, "rep": rep,
+                              "ms": e0.elapsed_time(e1)}), flush=True)
+        p.close()
+        return
+    if a.kernel_case == "pcg":
+        for rep in range(2):
+            st = p.ba_solve_pcg(TOL, MAX_ITERS)
+            print(json.dumps({"kernel_case": "pcg", "precision": a.precision, "rep": rep, "ms": st["ms"],
+                              "iters": st["iters"], "true_rel_residual": st["true_rel_residual"]}), flush=True)
+        p.close()
+        return
     if a.kernel_case == "mcg":
         for rep in range(2):
             st = p.ba_solve_mcg(TOL, MAX_ITERS, 16, 1e9)
@@ -679,7 +730,7 @@ def run_batched(a):
     pb.ba_set_stream(stream)
     pb.ba_build_normal(LAMBDA)
     t_heur = pb.ba_time_kernel("spmv", reps=5)
-    cb, t_tuned = pb.ba_autotune(reps=5)
+    cb, t_tuned, cfg = pb.ba_autotune(reps=5)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -748,7 +799,7 @@ def run_batched(a):
                    "l2": "256 MiB buffer written before every timed step"},
         "looped_single_ms": ms_l, "speedup_vs_loop": ms_l / ms_b if ms_l else None,
         "per_problem_iters": [s["iters"] for s in per],
-        "autotune": {"item_blocks": cb, "spmv_ms_tuned": t_tuned, "spmv_ms_heuristic": t_heur},
+        "autotune": {"item_blocks": cb, "spmv_config": cfg, "spmv_ms_tuned": t_tuned, "spmv_ms_heuristic": t_heur},
         "roofline": {"kernel": "k_spmv<T,1> over all problems", "bound": "hbm" if elt == 4 else "alu",
                      "achieved_gbs": spmv_bytes / t_tuned / 1e6, "peak_gbs": peaks["hbm_gbs"],
                      "frac": spmv_bytes / t_tuned / 1e6 / peaks["hbm_gbs"]},
@@ -837,6 +888,9 @@ def run_learned(a):
 
 def main():
     a = parse()
+    if a.oracle_sample:
+        run_oracle_sample(a)
+        return
     if a.learned:
         run_learned(a)
         return

@@ -91,7 +91,15 @@ typedef struct ba_options {
                                   own copies still in flight, with the default bound, and returns).
                                   0 (default) = 2^20; 1 .. 2^30; -1 = no poll at all, so every such
                                   wait gives up at once (tests the timeout path) */
-    int32_t reserved[5];
+    int32_t spmv_config;       /* warps x copy stages per CTA of the tile-streaming one-column product:
+                                  0 (default) = float32 16 x 1, float64 4 x 2; 1 = 8 x 2 / 8 x 1;
+                                  2 = 20 x 1 / 2 x 4; ba_autotune sets it */
+    int32_t host_loop;         /* 1: drive the iteration and refinement loops from the host (a plain
+                                  graph of chunk_iters iterations per launch, the stop flags read back
+                                  after each) instead of the solve graph's device-side loops; the same
+                                  kernels run.  For profilers that cannot see kernels inside graphs
+                                  with conditional nodes.  Default 0. */
+    int32_t reserved[3];
 } ba_options;
 
 /* Filled by ba_solve_pcg / ba_solve_mcg. */
@@ -297,7 +305,9 @@ int ba_get_launch_count(const ba_problem* p, int64_t* n);
 
 typedef enum ba_kernel {
     BA_KERNEL_SPMV = 0,        /* q = S p of Algorithm 1, at the handle's precision */
-    BA_KERNEL_SCHUR = 1,       /* the S_jk = delta U_j - sum G G^T block build (Eq. 13) */
+    BA_KERNEL_SCHUR = 1,       /* the S_jk = delta U_j - sum G G^T block build (Eq. 13); mixed precision:
+                                  the float32 diagonal blocks and G rows, the preconditioner and the
+                                  scaled off-diagonal blocks */
     BA_KERNEL_LINEARIZE = 2    /* residuals and Jacobians of every observation (Eqs. 2-4) */
 } ba_kernel;
 
@@ -311,14 +321,17 @@ typedef enum ba_kernel {
 int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms);
 
 /*
- * Choose the work-item size of the block-sparse products by measurement: the PCG product q = S p
- * (Algorithm 1) over every problem is timed for 32, 64, 128, 256, 512 and 1024 blocks per
- * item (`reps` launches each, L2 flushed before each), and the fastest is stored in the handle's
- * item_blocks option for later solves.  Needs ba_build_normal.  *item_blocks and *ms (may be
- * NULL) receive the choice and its mean time.  The paper has no counterpart (its products run on
- * the CPU).  STATE before a build, INVALID_ARG for reps < 1.
+ * Choose the shape of the block-sparse products by measurement: the PCG product q = S p (Algorithm 1)
+ * over every problem is timed for each warps x stages shape (spmv_config 0, 1, 2) and each work-item
+ * size of 32, 64, 128, 256, 512 and 1024 blocks (`reps` launches each, L2 flushed before each), and
+ * the fastest pair is stored in the handle's spmv_config and item_blocks options for later solves.
+ * The choice is kept for the process, keyed by the precision and the size of the problem (cameras,
+ * stored blocks, problems): a handle of the same key takes it without timing (*ms then holds the
+ * time measured when it was chosen).  Needs ba_build_normal.  *item_blocks, *spmv_config and *ms
+ * (each may be NULL) receive the choice and its mean time.  The paper has no counterpart (its products
+ * run on the CPU).  STATE before a build, INVALID_ARG for reps < 1.
  */
-int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms);
+int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, int32_t* spmv_config, double* ms);
 
 /* ---- learned pose grouping for MCG ------------------------------------------------------
  *

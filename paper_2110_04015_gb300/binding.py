@@ -35,7 +35,8 @@ SOLVER = {"pcg": 0, "mcg": 1}
 class ba_options(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_iters", ctypes.c_int32),
                 ("max_history", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("item_blocks", ctypes.c_int32), ("wait_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("item_blocks", ctypes.c_int32), ("wait_polls", ctypes.c_int32), ("spmv_config", ctypes.c_int32),
+                ("host_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class ba_solve_stats(ctypes.Structure):
@@ -91,7 +92,7 @@ _SIGNATURES = {
     "ba_get_batch_size": (_I32, [_P, _P]),
     "ba_get_batch_stats": (_I32, [_P, _P, _I32]),
     "ba_get_batch_history": (_I32, [_P, _I32, _P, _I32, _P]),
-    "ba_autotune": (_I32, [_P, _I32, _P, _P]),
+    "ba_autotune": (_I32, [_P, _I32, _P, _P, _P]),
     "ba_get_launch_count": (_I32, [_P, _P]),
     "ba_time_kernel": (_I32, [_P, _I32, _I32, _P]),
     "ba_schur_residual_static": (_I32, [_I32, _P, _P, _P, _P, _P, _P, _P]),
@@ -237,7 +238,7 @@ class Problem:
 
     def __init__(self, cams, pts, obs_cam, obs_pt, obs_xy, damping="marquardt", precision="fp64",
                  chunk_iters=8, max_history=0, inner_tol=1e-6, max_refine=64, item_blocks=0, wait_polls=0,
-                 cam_off=None):
+                 host_loop=0, spmv_config=0, cam_off=None):
         L = lib()
         opt = ba_options()
         L.ba_default_options(ctypes.byref(opt))
@@ -249,6 +250,8 @@ class Problem:
         opt.max_refine = max_refine
         opt.item_blocks = item_blocks
         opt.wait_polls = wait_polls
+        opt.host_loop = host_loop
+        opt.spmv_config = spmv_config
         self._keep = [_f64(cams), _f64(pts), _i32(obs_cam), _i32(obs_pt), _f64(obs_xy)]
         cams, pts, obs_cam, obs_pt, obs_xy = self._keep
         self.n_cams = int(cams.shape[0])
@@ -398,11 +401,13 @@ class Problem:
         _check(lib().ba_get_batch_history(self.h, int(problem), _ptr(h), int(cap), ctypes.byref(n)), self.h)
         return h[:min(n.value, cap)].copy()
 
-    def ba_autotune(self, reps=5) -> tuple[int, float]:
+    def ba_autotune(self, reps=5) -> tuple[int, float, int]:
+        """(blocks per work item, mean ms of the tuned product, warps x stages shape)."""
         cb = ctypes.c_int32()
+        cfg = ctypes.c_int32()
         ms = ctypes.c_double()
-        _check(lib().ba_autotune(self.h, int(reps), ctypes.byref(cb), ctypes.byref(ms)), self.h)
-        return cb.value, ms.value
+        _check(lib().ba_autotune(self.h, int(reps), ctypes.byref(cb), ctypes.byref(cfg), ctypes.byref(ms)), self.h)
+        return cb.value, ms.value, cfg.value
 
     def ba_get_launch_count(self) -> int:
         n = ctypes.c_int64()

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -280,6 +283,51 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     }
     s.up_pair_ptr = upload(p, up_pp);
     s.pairs = upload(p, pr);
+    if (p->opt.precision == BA_PRECISION_MIXED) {
+        // upper pattern: the diagonal block first, then the upper blocks in (j, k) order
+        std::vector<int64_t> row_u(size_t(n_c) + 1, 0);
+        for (int32_t j = 0; j < n_c; ++j) row_u[j + 1] = row_u[j] + 1 + upper_cnt[j];
+        const int64_t nnzb_u = row_u[n_c];
+        std::vector<int32_t> col_u(nnzb_u);
+        std::vector<int64_t> tile_u(size_t(n_c) + 1, 0);
+        for (int32_t j = 0; j < n_c; ++j) {
+            col_u[row_u[j]] = j;
+            tile_u[j + 1] = tile_u[j] + (row_u[j + 1] - row_u[j] + ba::kTile - 1) / ba::kTile;
+        }
+        std::vector<int64_t> udst(n_up), qpos(n_up);
+        {
+            std::vector<int64_t> ufill(n_c);
+            for (int32_t j = 0; j < n_c; ++j) ufill[j] = row_u[j] + 1;
+            for (int64_t u = 0; u < n_up; ++u) {
+                const int32_t j = up_j[u];
+                const int64_t pos = ufill[j]++;
+                col_u[pos] = up_k[u];
+                qpos[u] = pos;
+                udst[u] = (tile_u[j] * ba::kTile + (pos - row_u[j])) * 81;
+            }
+        }
+        // per column k the upper blocks (j, k), j < k, in j order (u runs in (j, k) order)
+        std::vector<int64_t> qptr(size_t(n_c) + 1, 0);
+        for (int64_t u = 0; u < n_up; ++u) qptr[up_k[u] + 1]++;
+        for (int32_t k = 0; k < n_c; ++k) qptr[k + 1] += qptr[k];
+        std::vector<int32_t> qlist(n_up > 0 ? n_up : 1);
+        {
+            std::vector<int64_t> fill(qptr.begin(), qptr.end() - 1);
+            for (int64_t u = 0; u < n_up; ++u) qlist[fill[up_k[u]]++] = int32_t(qpos[u]);
+        }
+        if (nnzb_u >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
+        s.nnzb_u = nnzb_u;
+        s.row_ptr_u = upload(p, row_u);
+        s.col_u = upload(p, col_u);
+        s.tile_ptr_u = upload(p, tile_u);
+        s.n_tiles_u = tile_u[n_c];
+        s.up_udst = upload(p, udst);
+        s.qptr = upload(p, qptr);
+        s.qlist = upload(p, qlist);
+        s.h_row_ptr_u = row_u;
+        s.h_col_u = col_u;
+        s.h_tile_ptr_u = tile_u;
+    }
 }
 
 void alloc_system(ba_problem* p) {
@@ -308,6 +356,8 @@ void alloc_system(ba_problem* p) {
     if (p->opt.precision == BA_PRECISION_MIXED) {
         y.S32 = dev_alloc<float>(p, size_t(s.n_tiles) * ba::kTileElems);
         BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
+        y.S32u = dev_alloc<float>(p, size_t(s.n_tiles_u) * ba::kTileElems);
+        BA_CUDA_TRY(cudaMemset(y.S32u, 0, sizeof(float) * size_t(s.n_tiles_u) * ba::kTileElems));
         y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 27);
         y.aux32 = dev_alloc<float>(p, size_t(s.n_c) * 24);
         y.PY32 = dev_alloc<float>(p, size_t(s.n_o) * 6);
@@ -356,8 +406,8 @@ void do_build(ba_problem* p, double lambda) {
         ba::launch_cam_rhs(s, y, p->opt.damping, lambda, st);
         ba::launch_schur_diag32(s, y, st);
         ba::launch_block_jacobi(s, y, st);
-        ba::launch_schur_mixed(s, y, st);    // float32 Lam G, off-diagonal and diagonal blocks of S^
-        p->launches += 10;
+        ba::launch_schur_mixed(s, y, st);    // off-diagonal and diagonal blocks of S^ (float32)
+        p->launches += 9;
     }
     check_launch();
     int status = 0;
@@ -431,6 +481,8 @@ ba::SolveArgs make_args(const ba_problem* p, int mcg, double tol, int32_t max_it
     a.max_refine = p->opt.max_refine;
     a.max_history = p->opt.max_history;
     a.item_blocks = p->opt.item_blocks;
+    a.host_loop = p->opt.host_loop;
+    a.spmv_cfg = p->opt.spmv_config;
     a.wait_polls = p->opt.wait_polls == 0 ? ba::kDefaultWaitPolls : (p->opt.wait_polls < 0 ? 0 : p->opt.wait_polls);
     return a;
 }
@@ -446,6 +498,8 @@ void check_options(const ba_options& o) {
     if (o.item_blocks != 0 && (o.item_blocks < 32 || o.item_blocks > 4096 || o.item_blocks % 32 != 0))
         throw Error(BA_ERR_INVALID_ARG, "item_blocks must be 0 or a multiple of 32 in [32, 4096]");
     if (o.wait_polls < -1 || o.wait_polls > (1 << 30)) throw Error(BA_ERR_INVALID_ARG, "wait_polls must be in [-1, 2^30]");
+    if (o.host_loop != 0 && o.host_loop != 1) throw Error(BA_ERR_INVALID_ARG, "host_loop must be 0 or 1");
+    if (o.spmv_config < 0 || o.spmv_config > 2) throw Error(BA_ERR_INVALID_ARG, "spmv_config must be in [0, 2]");
 }
 
 int create(const ba_options* opt, int32_t n_problems, const int32_t* cam_off_in, int32_t n_cams, int32_t n_pts,
@@ -865,18 +919,42 @@ int ba_get_batch_history(const ba_problem* pc, int32_t problem, double* hist, in
     }
 }
 
-int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, double* ms) {
+int ba_autotune(ba_problem* p, int32_t reps, int32_t* item_blocks, int32_t* spmv_config, double* ms) {
     if (!p) return BA_ERR_INVALID_ARG;
     try {
         if (reps < 1) throw Error(BA_ERR_INVALID_ARG, "reps must be >= 1");
         if (!p->y.built) throw Error(BA_ERR_STATE, "nothing built");
         if (!p->solver) p->solver = ba::solver_create();
-        double best = 0.0;
-        const int cb = ba::solver_autotune(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps, &best,
-                                           p->stream, nullptr);
-        p->opt.item_blocks = cb;
-        if (item_blocks) *item_blocks = cb;
-        if (ms) *ms = best;
+        // choices kept for the process, keyed by precision and problem size
+        struct Tuned {
+            int cfg, cb;
+            double ms;
+        };
+        static std::mutex mu;
+        static std::map<std::tuple<int, int64_t, int64_t, int64_t>, Tuned> cache;
+        const auto key = std::make_tuple(p->opt.precision, int64_t(p->s.n_c), p->s.nnzb,
+                                         int64_t(p->s.h_cam_off.size()) - 1);
+        Tuned t{0, 0, 0.0};
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                t = it->second;
+                hit = true;
+            }
+        }
+        if (!hit) {
+            ba::solver_autotune(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps, &t.cfg, &t.cb,
+                                &t.ms, p->stream);
+            std::lock_guard<std::mutex> lock(mu);
+            cache[key] = t;
+        }
+        p->opt.item_blocks = t.cb;
+        p->opt.spmv_config = t.cfg;
+        if (item_blocks) *item_blocks = t.cb;
+        if (spmv_config) *spmv_config = t.cfg;
+        if (ms) *ms = t.ms;
         return BA_OK;
     } catch (const Error& e) {
         return fail(p, e);
@@ -1014,7 +1092,7 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
         if (kernel == BA_KERNEL_SPMV) {
             if (!p->solver) p->solver = ba::solver_create();
             *ms = ba::solver_time_spmv(p->solver, p->s, p->y, p->opt.precision == BA_PRECISION_MIXED, reps,
-                                     p->opt.item_blocks, st);
+                                     p->opt.item_blocks, p->opt.spmv_config, st);
             return BA_OK;
         }
         if (kernel != BA_KERNEL_SCHUR && kernel != BA_KERNEL_LINEARIZE) throw Error(BA_ERR_INVALID_ARG, "unknown kernel");
@@ -1027,7 +1105,13 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
             BA_CUDA_TRY(cudaEventRecord(a, st));
             if (kernel == BA_KERNEL_SCHUR) {
                 if (p->opt.precision == BA_PRECISION_FP64) ba::launch_schur(p->s, p->y, st);
-                else ba::launch_schur_mixed(p->s, p->y, st);
+                else {
+                    // the float32 Schur complement from the float32 Jacobians: diagonal blocks and G
+                    // rows, Lam and the preconditioner, off-diagonal blocks
+                    ba::launch_schur_diag32(p->s, p->y, st);
+                    ba::launch_block_jacobi(p->s, p->y, st);
+                    ba::launch_schur_mixed(p->s, p->y, st);
+                }
             } else {
                 ba::launch_cam_prep(p->s, p->y, st);
                 ba::launch_linearize(p->s, p->y, st);

@@ -83,12 +83,24 @@ struct Structure {
     int64_t* up_mdst = nullptr;   // n_up: element offset of its mirror (k, j)
     int64_t* up_pair_ptr = nullptr;  // n_up + 1
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
+    // upper triangle of S (mixed precision's one-column products): row j holds S_jj, then S_jk, k > j,
+    // tiled like the full pattern; qptr/qlist list, per camera k, the stored blocks (j, k), j < k
+    int64_t nnzb_u = 0, n_tiles_u = 0;
+    int64_t* row_ptr_u = nullptr;    // n_c + 1
+    int32_t* col_u = nullptr;        // nnzb_u
+    int64_t* tile_ptr_u = nullptr;   // n_c + 1
+    int64_t* up_udst = nullptr;      // n_up: element offset of block (j, k) in the tiled upper S
+    int64_t* qptr = nullptr;         // n_c + 1
+    int32_t* qlist = nullptr;        // nnzb_u - n_c: upper-pattern indices of the blocks (j, k), j < k, by k
     // batch: problem b owns cameras [h_cam_off[b], h_cam_off[b + 1]); one problem: {0, n_c}
     std::vector<int32_t> h_cam_off;
     // host copies of the pattern (work lists of the block-sparse products are built from them)
     std::vector<int64_t> h_row_ptr;
     std::vector<int32_t> h_col;
     std::vector<int64_t> h_tile_ptr;
+    std::vector<int64_t> h_row_ptr_u;
+    std::vector<int32_t> h_col_u;
+    std::vector<int64_t> h_tile_ptr_u;
 };
 
 // The linearised system at the current parameters (rebuilt by ba_build_normal).
@@ -114,10 +126,11 @@ struct System {
     //   S^ = Lam S Lam, Lam = diag(S)^{-1/2},
     // which removes the parameter-scale ill-conditioning of the 9x9 blocks before float32 rounding
     float* S32 = nullptr;     // float(S^), tiled layout
+    float* S32u = nullptr;    // its upper triangle (diagonal blocks included), tiled upper pattern
     double* lam = nullptr;    // 9 n_c: Lam
     double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
     float* lam32 = nullptr;   // 9 n_c: float(Lam)
-    float* G32 = nullptr;     // n_o x 27: rows of Lam G_o in float32 (row a scaled by Lam_cam(o),a)
+    float* G32 = nullptr;     // n_o x 27: G_o = J_p^T A_o in float32 (from the float32 Jacobians)
     float* aux32 = nullptr;   // n_c x 24: the camera's aux block in float32
     float* PY32 = nullptr;    // n_o x 6: P = R X + t and Y = R X in float32 (formed in float64)
     float* L32 = nullptr;     // n_l x 6: L (packed as above) in float32
@@ -177,6 +190,8 @@ struct SolveArgs {
     int64_t max_history = 0;
     int item_blocks = 0;    // blocks per work item of the block-sparse products (0: 512)
     int wait_polls = kDefaultWaitPolls;   // tile-copy waits: polls before giving up (0: give up at once)
+    int host_loop = 0;      // 1: the loops run from the host (plain graphs), for profilers
+    int spmv_cfg = 0;       // shape of the tile-streaming one-column products (0, 1, 2)
 };
 
 struct ProbOut {
@@ -218,11 +233,10 @@ int solver_history(const Solver* w, int problem, const double** hist);
 // Mean ms of one launch of the PCG product q = S p over all problems (float64 or float32 system),
 // L2 flushed between launches; item_blocks as in SolveArgs.
 double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int item_blocks,
-                        cudaStream_t st);
-// Blocks per work item (32 .. 1024) that makes the PCG product fastest; *best_ms its time; trace
-// (optional) receives every (candidate, ms).
-int solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, double* best_ms,
-                    cudaStream_t st, std::vector<std::pair<int, double>>* trace);
+                        int spmv_cfg, cudaStream_t st);
+// Shape (0..2) and blocks per work item (32 .. 1024) that make the PCG product fastest; *best_ms its time.
+void solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int* best_cfg,
+                     int* best_cb, double* best_ms, cudaStream_t st);
 void flush_l2(cudaStream_t st);
 
 // ---- learned pose grouping (k_learn.cu) -------------------------------------------------------

@@ -19,8 +19,8 @@
 //   k_cam_rhs       one CTA per camera (float64): b~ = sum_o J_p^T (r - J_l V^-1 b_l), lambda D_p
 //   k_schur_diag32  one CTA per camera (float32): S_jj = sum_o J_p^T (I - A A^T) J_p + lambda D_p,
 //                   A = J_l L^{-T} (each term is positive semi-definite: no cancellation)
-//   k_obs_G32       one thread per observation (float32): rows of Lam J_p^T A, the G of the
-//                   off-diagonal blocks
+//                   (the same pass writes G_o = J_p^T A in float32 for the off-diagonal blocks,
+//                   which are scaled by Lam_j, Lam_k after their sums)
 // S is written in the tiled layout of ba_internal.cuh (s_at).
 // Every kernel uses grid-stride loops and 64-bit indices.
 #include <cuda_runtime.h>
@@ -596,13 +596,14 @@ __device__ __forceinline__ void lds9(const float* p, float* v) {
 // flight together, no staging registers; lane p fetches the indices of pair p), each 9-value
 // part on a 16-byte boundary.  48 registers let five CTAs share an SM.  The three slices are added in slice order through shuffles,
 // the block is assembled in shared memory and written with coalesced stores to (j, k) and,
-// transposed, to (k, j).  For the scaled float32 system G holds the rows of Lam G (k_scaled_g32),
-// so the same sums give Lam_j S_jk Lam_k.
+// transposed, to (k, j), and to (j, k) of the upper-triangle copy Su.  The float32 system is the scaled
+// Lam S Lam: each block is multiplied by Lam_j (rows) and Lam_k (columns) after its sum.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
     int64_t n_up, const int64_t* __restrict__ up_dst, const int64_t* __restrict__ up_mdst,
-    const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs, const T* __restrict__ G,
-    T* __restrict__ S) {
+    const int64_t* __restrict__ up_udst, const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
+    const int32_t* __restrict__ oc, const T* __restrict__ lam, const T* __restrict__ G, T* __restrict__ S,
+    T* __restrict__ Su) {
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
     constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
     constexpr int kPart = 12;                          // stride of a 9-value part (16-byte aligned)
@@ -657,14 +658,23 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
             acc[i] = (acc[i] + v1) + v2;
         }
         if (lane < 9) {
+            // the block's cameras from its first pair: rows scale by Lam_j, columns by Lam_k
+            const int2 p0 = pairs[pb];
+            const T* lj = lam + 9 * int64_t(oc[p0.x]);
+            const T* lk = lam + 9 * int64_t(oc[p0.y]);
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) sb[wid][(3 * A + r) * 9 + 3 * B + c] = acc[3 * r + c];
+                for (int c = 0; c < 3; ++c)
+                    sb[wid][(3 * A + r) * 9 + 3 * B + c] = acc[3 * r + c] * lj[3 * A + r] * lk[3 * B + c];
         }
         __syncwarp();
-        const int64_t dj = up_dst[u], dk = up_mdst[u];
-        for (int e = lane; e < 81; e += 32) S[dj + e] = -sb[wid][e];
+        const int64_t dj = up_dst[u], dk = up_mdst[u], du = up_udst[u];
+        for (int e = lane; e < 81; e += 32) {
+            const T v = -sb[wid][e];
+            S[dj + e] = v;
+            Su[du + e] = v;
+        }
         for (int e = lane; e < 81; e += 32) {
             const int b = e / 9, a = e - 9 * (e / 9);   // entry e = 9 b + a of (k, j) is (a, b) of (j, k)
             S[dk + e] = -sb[wid][9 * a + b];
@@ -673,17 +683,20 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
     }
 }
 
-// S_jj into the tiled S: float64 copy, or (lam != nullptr) float(Lam S_jj Lam) for the scaled system.
+// S_jj into the tiled S: float64 copy, or (lam != nullptr) float(Lam S_jj Lam) for the scaled system,
+// then also into the upper-triangle copy Su (may be null), where it opens block-row j.
 template <typename T>
 __global__ void k_put_diag(int32_t n_c, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr,
                            const int32_t* __restrict__ diag_pos, const double* __restrict__ Sd,
-                           const double* __restrict__ lam, T* __restrict__ S) {
+                           const double* __restrict__ lam, T* __restrict__ S, const int64_t* __restrict__ tile_ptr_u,
+                           T* __restrict__ Su) {
     for (int64_t i = gtid(); i < int64_t(n_c) * 81; i += gstride()) {
         const int64_t j = i / 81;
         const int e = int(i - j * 81);
         double v = Sd[i];
         if (lam) v *= lam[9 * j + e / 9] * lam[9 * j + e % 9];
         S[s_at(tile_ptr, j, diag_pos[j] - row_ptr[j], e)] = T(v);
+        if (Su) Su[s_at(tile_ptr_u, j, 0, e)] = T(v);
     }
 }
 
@@ -752,13 +765,16 @@ constexpr int kDiagThreads = 256;
 
 // Mixed precision, one CTA per camera: S_jj = sum_{o in j} J_p^T (I - A A^T) J_p + lambda D_p (Eq. 13 on
 // the diagonal: U_j - sum_o G_o G_o^T with G_o = J_p^T A_o), from float32 Jacobians formed in float32
-// from the camera and the float32 point in the camera frame.  I - A A^T = I - J_l V^-1 J_l^T is positive semi-definite, so the terms
-// add without cancellation; each thread sums its observations in float32, the threads' sums are
-// added in float64 (fixed order), and the float64 damping is added last.  Sd receives float64.
+// from the camera and the float32 point in the camera frame.  I - A A^T = I - J_l V^-1 J_l^T is
+// positive semi-definite, so the terms add without cancellation; each thread sums its observations
+// in float32, the threads' sums are added in float64 (fixed order), and the float64 damping is added
+// last.  Sd receives float64.  The same pass writes G_o = J_p^T A_o (9x3, unscaled) of every
+// observation to G32 for the off-diagonal blocks.
 __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
     int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
     const int32_t* __restrict__ op, const float* __restrict__ aux32, const float* __restrict__ PY32,
-    const float* __restrict__ L32, const double* __restrict__ dadd, double* __restrict__ Sd) {
+    const float* __restrict__ L32, const double* __restrict__ dadd, double* __restrict__ Sd,
+    float* __restrict__ G32) {
     constexpr int NW = kDiagThreads / 32;
     __shared__ double red[NW][45];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -782,6 +798,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
             const float m00 = 1.f - (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
             const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
             const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
+            float* g = G32 + 27 * o;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g[3 * a + c] = jc[a] * A[0][c] + jc[9 + a] * A[1][c];
             float B0[9], B1[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
@@ -810,33 +831,6 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
             Sd[81 * int64_t(j) + threadIdx.x] = v;
         }
         __syncthreads();
-    }
-}
-
-// Mixed precision, one thread per observation: the rows of Lam_j G_o in float32, G_o = J_p^T A_o =
-// W_o L^{-T} (9x3), from float32 Jacobians formed in float32 from the camera and the float32 point in
-// the camera frame; the off-diagonal sums over these rows give Lam_j S_jk Lam_k directly.
-__global__ void k_obs_G32(int64_t n_o, const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
-                          const float* __restrict__ aux32, const float* __restrict__ PY32,
-                          const float* __restrict__ L32, const float* __restrict__ lam32, float* __restrict__ G32) {
-    for (int64_t o = gtid(); o < n_o; o += gstride()) {
-        const int64_t j = oc[o], l = op[o];
-        float ax[24], PY[6], Lp[6], jc[18], jl[6], A[2][3];
-#pragma unroll
-        for (int k = 0; k < 24; ++k) ax[k] = __ldg(aux32 + 24 * j + k);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * o + k);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
-        bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
-        rows_A(jl, Lp, A);
-        float* g = G32 + 27 * o;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            const float la = __ldg(lam32 + 9 * j + a);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g[3 * a + c] = la * (jc[a] * A[0][c] + jc[9 + a] * A[1][c]);
-        }
     }
 }
 
@@ -1166,7 +1160,7 @@ void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, c
 
 void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st) {
     k_schur_diag32<<<cam_grid(s), kDiagThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.aux32, y.PY32,
-                                                         y.L32, y.dadd, y.Sd);
+                                                         y.L32, y.dadd, y.Sd, y.G32);
 }
 
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
@@ -1174,17 +1168,16 @@ void launch_schur(const Structure& s, System& y, cudaStream_t st) {
         k_schur_off_rows<double><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
             s.n_up, s.up_dst, s.up_mdst, s.up_pair_ptr, s.pairs, y.G, y.S);
     k_put_diag<double><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
-        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S);
+        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, nullptr, y.S, nullptr, nullptr);
 }
 
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
-    k_obs_G32<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, s.obs_cam, s.obs_pt, y.aux32, y.PY32, y.L32,
-                                                               y.lam32, y.G32);
     if (s.n_up > 0)
         k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_dst, s.up_mdst, s.up_pair_ptr, s.pairs, y.G32, y.S32);
+            s.n_up, s.up_dst, s.up_mdst, s.up_udst, s.up_pair_ptr, s.pairs, s.obs_cam, y.lam32, y.G32, y.S32,
+            y.S32u);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
-        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32);
+        s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32, s.tile_ptr_u, y.S32u);
 }
 
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,

@@ -343,24 +343,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int po
     return false;
 }
 
-// warps per CTA and copy stages of the tile-streaming product (one CTA per SM: the stages use
-// 162 KB of shared memory in both precisions).  float32: 16 warps with one stage each measured
-// faster than 8 with two (more warps cover the gathers of p; the others' copies cover a warp's
-// wait for its next tile).
-template <typename T>
-struct SpmvCfg;
-template <>
-struct SpmvCfg<float> {
-    static constexpr int kWarps = 16, kStages = 1;
-};
-template <>
-struct SpmvCfg<double> {
-    static constexpr int kWarps = 4, kStages = 2;
-};
-template <typename T>
+// Warps per CTA and copy stages of the tile-streaming one-column product, one CTA per SM.  Three
+// shapes per precision (ba_options.spmv_config, chosen by ba_autotune); shape 0 is the default:
+// float32 16 warps x 1 stage (measured faster than 8 x 2 for the full-pattern product: more warps
+// cover the gathers of p), float64 4 x 2.  Every shape keeps its stages within 207 KB.
+template <typename T, int CFG>
+struct SpmvShape;
+template <> struct SpmvShape<float, 0> { static constexpr int kWarps = 16, kStages = 1; };
+template <> struct SpmvShape<float, 1> { static constexpr int kWarps = 8, kStages = 2; };
+template <> struct SpmvShape<float, 2> { static constexpr int kWarps = 20, kStages = 1; };
+template <> struct SpmvShape<double, 0> { static constexpr int kWarps = 4, kStages = 2; };
+template <> struct SpmvShape<double, 1> { static constexpr int kWarps = 8, kStages = 1; };
+template <> struct SpmvShape<double, 2> { static constexpr int kWarps = 2, kStages = 4; };
+constexpr int kSpmvShapes = 3;
+template <typename T, int CFG>
 constexpr size_t spmv_smem() {
-    return sizeof(T) * SpmvCfg<T>::kWarps * SpmvCfg<T>::kStages * kTileElems +
-           sizeof(uint64_t) * SpmvCfg<T>::kWarps * SpmvCfg<T>::kStages;
+    return sizeof(T) * SpmvShape<T, CFG>::kWarps * SpmvShape<T, CFG>::kStages * kTileElems +
+           sizeof(uint64_t) * SpmvShape<T, CFG>::kWarps * SpmvShape<T, CFG>::kStages;
 }
 
 
@@ -398,12 +397,15 @@ __device__ __forceinline__ void cursor_seek(TileCursor& c, const ItemList& L, co
 // MODE 1 (Algorithm 1): q = y (Q column 0) and, per camera, the sums of q^T p and p^T r
 //         (Delta and gamma of Algorithm 1, before the sum over cameras).
 // MODE 2 (Algorithm 2, width 1): y goes to column new_off of Q.
-template <typename T, int MODE, bool ZH>
-__global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
+// SYM: S is the upper triangle (row j: S_jj, then S_jk for k > j).  Each lane's block also gives the
+// transposed term S_jk^T z_j of row k, written to tb at the block's index (9 values), which
+// k_spmv_col adds to row k; in MODE 1 the per-camera sums then move to k_spmv_col as well.
+template <typename T, int MODE, bool ZH, bool SYM, int CFG>
+__global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
     const T* __restrict__ S, const T* __restrict__ z, ItemList L, int sel, T* __restrict__ out,
-    const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl) {
-    constexpr int NW = SpmvCfg<T>::kWarps, NS = SpmvCfg<T>::kStages;
+    const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl, T* __restrict__ tb) {
+    constexpr int NW = SpmvShape<T, CFG>::kWarps, NS = SpmvShape<T, CFG>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (nothing_selected(ctl, L, sel)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -444,6 +446,9 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
         T acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
+        T zr[9];   // SYM: z of the row camera, the factor of every transposed term of the item
+#pragma unroll
+        for (int b = 0; b < 9; ++b) zr[b] = SYM ? z[zoff + 9 * int64_t(it.row) + b] : T(0);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
             // the 9 entries of z this lane needs for tile t, fetched one tile ahead
@@ -479,10 +484,29 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
                 const int q = t * 32 + lane;
                 if (q >= it.q0 && q < it.q1) {
                     const T* blk = tile + lane * 81;
+                    if (SYM) {
+                        T v[9];
 #pragma unroll
-                    for (int a = 0; a < 9; ++a)
+                        for (int b = 0; b < 9; ++b) v[b] = T(0);
 #pragma unroll
-                        for (int b = 0; b < 9; ++b) acc[a] += blk[9 * a + b] * zv[b];
+                        for (int a = 0; a < 9; ++a)
+#pragma unroll
+                            for (int b = 0; b < 9; ++b) {
+                                const T sab = blk[9 * a + b];
+                                acc[a] += sab * zv[b];
+                                v[b] += sab * zr[a];
+                            }
+                        if (q > 0) {   // q = 0 is S_jj, whose row term covers it
+                            T* dst = tb + (rj + q) * 9;
+#pragma unroll
+                            for (int b = 0; b < 9; ++b) dst[b] = v[b];
+                        }
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a)
+#pragma unroll
+                            for (int b = 0; b < 9; ++b) acc[a] += blk[9 * a + b] * zv[b];
+                    }
                 }
                 __syncwarp();
                 if (f.item < L.n) {
@@ -522,7 +546,7 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
         if (fin) {
             const int64_t rowi = 9 * int64_t(it.row) + lane;
             if (lane < 9) out[ooff + rowi] = val;
-            if (MODE == 1) {
+            if (MODE == 1 && !SYM) {
                 double dq = 0.0, dr = 0.0;
                 if (lane < 9) {
                     const double pv = double(z[zoff + rowi]);
@@ -544,6 +568,77 @@ __global__ void __launch_bounds__(SpmvCfg<T>::kWarps * 32, 1) k_spmv(
         if (lane == 0) atomicExch(&ctl[bad_prob].status, BA_ERR_TIMEOUT);
         for (int st = 0; st < NS; ++st)
             if (inflight & (1u << st)) mbar_wait(&bars[st], (parity >> st) & 1u, kDefaultWaitPolls);
+    }
+}
+
+// Second pass of the symmetric product: y_k += sum over the stored blocks (j, k), j < k, of their
+// transposed terms S_jk^T z_j (in j order, so the sum does not depend on scheduling), then in MODE 1
+// the per-camera sums q^T p and p^T r.  One warp per camera; grid: CTAs x problems.
+template <typename T, int MODE, bool ZH>
+__global__ void __launch_bounds__(kThreads) k_spmv_col(const int64_t* __restrict__ qptr,
+                                                       const int32_t* __restrict__ qlist, const T* __restrict__ tb,
+                                                       const T* __restrict__ z, int sel, T* __restrict__ out,
+                                                       const T* __restrict__ rvec, double* __restrict__ camdot,
+                                                       const Ctl* __restrict__ ctl) {
+    const int p = blockIdx.y;
+    if (!selected(ctl, p, sel)) return;
+    const Ctl& c = ctl[p];
+    const int lane = threadIdx.x & 31;
+    const int64_t n = int64_t(c.lay.nc) * 9;
+    const int64_t hb = c.lay.hoff - 9 * int64_t(c.lay.c0);
+    const int64_t zoff = ZH ? hb + int64_t(MODE == 2 ? c.new_off : 0) * n : 0;
+    const int64_t ooff = hb + int64_t(MODE == 1 ? 0 : c.new_off) * n;
+    const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t jl = w0; jl < c.lay.nc; jl += nw) {
+        const int64_t j = c.lay.c0 + jl;
+        T acc[9];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) acc[b] = T(0);
+        // four entries per lane in flight (their list indices first, then the terms)
+        int64_t e = qptr[j] + lane;
+        const int64_t e1 = qptr[j + 1];
+        for (; e + 96 < e1; e += 128) {
+            int64_t q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = qlist[e + 32 * u];
+            T v[4][9];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int b = 0; b < 9; ++b) v[u][b] = tb[q[u] * 9 + b];
+#pragma unroll
+            for (int b = 0; b < 9; ++b) acc[b] += (v[0][b] + v[1][b]) + (v[2][b] + v[3][b]);
+        }
+        for (; e < e1; e += 32) {
+            const T* t = tb + int64_t(qlist[e]) * 9;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) acc[b] += t[b];
+        }
+#pragma unroll
+        for (int b = 0; b < 9; ++b) acc[b] = warp_sum(acc[b]);
+        T val = acc[0];
+#pragma unroll
+        for (int b = 1; b < 9; ++b) if (lane == b) val = acc[b];
+        const int64_t rowi = 9 * j + lane;
+        if (lane < 9) {
+            val = out[ooff + rowi] + val;
+            out[ooff + rowi] = val;
+        }
+        if (MODE == 1) {
+            double dq = 0.0, dr = 0.0;
+            if (lane < 9) {
+                const double pv = double(z[zoff + rowi]);
+                dq = double(val) * pv;
+                dr = pv * double(rvec[rowi]);
+            }
+            dq = warp_sum(dq);
+            dr = warp_sum(dr);
+            if (lane == 0) {
+                camdot[2 * j] = dq;
+                camdot[2 * j + 1] = dr;
+            }
+        }
     }
 }
 
@@ -844,9 +939,10 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
 
 // Condition of the Krylov WHILE loop: continue while a problem is not done.  first = 1 (before the
 // loop) starts the sweep's pass count; otherwise one body pass has ended.  `bound` passes (every
-// problem stops by its iteration budget well before) end the loop in any case.
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Ctl* __restrict__ ctl, int nb, Loops* lp, int first,
-                            int chunk, const Params* __restrict__ prm) {
+// problem stops by its iteration budget well before) end the loop in any case.  use_handle = 0 when
+// the loop runs from the host (the kernel then only counts).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int use_handle, const Ctl* __restrict__ ctl, int nb,
+                            Loops* lp, int first, int chunk, const Params* __restrict__ prm) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -867,7 +963,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const Ctl* __restrict_
             if (go) lp->capped = 1;
             go = 0;
         }
-        cudaGraphSetConditional(h, go ? 1u : 0u);
+        if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
     }
 }
 
@@ -1826,7 +1922,7 @@ __global__ void k_outer_init(const Layout* __restrict__ lay, const double* __res
 // aims 3x past it so that it is the last one.  One CTA over all problems; sets the refinement
 // loop's condition: another sweep when any problem takes part (count = 1: a loop pass has ended).
 __global__ void k_refine_plan(Outer* outer, int nb, const Params* __restrict__ prm, cudaGraphConditionalHandle h,
-                              Loops* lp, int count) {
+                              int use_handle, Loops* lp, int count) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -1852,7 +1948,7 @@ __global__ void k_refine_plan(Outer* outer, int nb, const Params* __restrict__ p
     __syncthreads();
     if (threadIdx.x == 0) {
         if (count) lp->outer += 1;
-        cudaGraphSetConditional(h, any ? 1u : 0u);
+        if (use_handle) cudaGraphSetConditional(h, any ? 1u : 0u);
     }
 }
 
@@ -1894,12 +1990,13 @@ __global__ void k_refine_after(const Ctl* __restrict__ ctl, Outer* outer, const 
 // What a captured solve graph depends on besides the per-solve Params: the algorithm, precision,
 // loop body, work lists, wait bound and every buffer address (a reallocation bumps `allocs`).
 struct GraphKey {
-    int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1, polls = -1, nb = -1;
+    int mcg = -1, fp32 = -1, chunk = 0, mi1 = 0, use_l = -1, epoch = -1, polls = -1, nb = -1, host = -1, cfg = -1;
     uint64_t allocs = ~uint64_t(0);   // buffer generation (any reallocation invalidates the graph)
     const void* ptrs[4] = {};
     bool operator==(const GraphKey& o) const {
         if (mcg != o.mcg || fp32 != o.fp32 || chunk != o.chunk || mi1 != o.mi1 || use_l != o.use_l ||
-            epoch != o.epoch || polls != o.polls || nb != o.nb || allocs != o.allocs)
+            epoch != o.epoch || polls != o.polls || nb != o.nb || host != o.host || cfg != o.cfg ||
+            allocs != o.allocs)
             return false;
         for (int i = 0; i < 4; ++i) if (ptrs[i] != o.ptrs[i]) return false;
         return true;
@@ -1946,12 +2043,15 @@ struct Solver {
     int64_t launches = 0;     // kernel executions issued by the current solve
     cudaStream_t cap_stream = nullptr, cap2 = nullptr, cap3 = nullptr;   // capture streams (nested loops)
     std::vector<SolveExec*> execs;   // instantiated solve graphs
-    // work lists of the block-sparse products: whole rows, and rows split by pose subset
-    ItemList items_g, items_l;
+    // work lists of the block-sparse products: whole rows, rows split by pose subset, and whole rows of
+    // the upper triangle (the symmetric one-column products of mixed precision)
+    ItemList items_g, items_l, items_u;
+    Buf tb;                    // transposed terms of the symmetric product (9 per stored upper block)
     int items_cb = -1;         // item chunk rule the lists were built with (0 = the default)
     int items_l_dirs = -1;
     bool use_l = false;        // the current MCG solve splits rows by pose subset (n_dirs > 1)
     int epoch = 0;             // incremented whenever a work list is rebuilt (captured graphs hold them)
+    int spmv_cfg = 0;          // shape of the one-column products (SpmvShape)
     void* mm_part = nullptr;   // k_spmm partials: items_g.n x 16 x 9
 };
 
@@ -1992,7 +2092,8 @@ constexpr int kItemBlocks = 512;
 // split = false: one segment per row; otherwise segment s of a row of problem b holds the blocks
 // whose column camera lies in [c0 + s sz, c0 + (s + 1) sz), for s < n_eff (empty segments get
 // one empty item, which writes zeros).
-static std::vector<SpItem> build_items(const Structure& s, const std::vector<Layout>& lay, bool split, int forced_cb) {
+static std::vector<SpItem> build_items(const std::vector<int64_t>& h_row_ptr, const std::vector<int32_t>& h_col,
+                                       const std::vector<Layout>& lay, bool split, int forced_cb) {
     std::vector<SpItem> out;
     int grp = 0;
     for (size_t b = 0; b < lay.size(); ++b) {
@@ -2000,8 +2101,8 @@ static std::vector<SpItem> build_items(const Structure& s, const std::vector<Lay
         const int cb = forced_cb > 0 ? forced_cb : kItemBlocks;
         const int nseg = split ? L.n_eff : 1;
         for (int32_t j = L.c0; j < L.c0 + L.nc; ++j) {
-            const int64_t rj = s.h_row_ptr[j], nj = s.h_row_ptr[j + 1] - rj;
-            const int32_t* cj = s.h_col.data() + rj;
+            const int64_t rj = h_row_ptr[j], nj = h_row_ptr[j + 1] - rj;
+            const int32_t* cj = h_col.data() + rj;
             for (int g = 0; g < nseg; ++g) {
                 int q0 = 0, q1 = int(nj);
                 if (split) {
@@ -2051,15 +2152,28 @@ static void upload_items(ItemList& L, const std::vector<SpItem>& v) {
     BA_CUDA_TRY(cudaMalloc(&L.part, sizeof(double) * 9 * (v.size() > 0 ? v.size() : 1)));
 }
 
+// The tile-streaming products of every mode, precision and shape used here.
+template <typename T, int MODE, bool ZH, bool SYM, int CFG>
+static void set_spmv_attr() {
+    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<T, MODE, ZH, SYM, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(spmv_smem<T, CFG>())));
+}
+template <int CFG>
+static void set_spmv_attrs() {
+    set_spmv_attr<float, 0, true, true, CFG>();
+    set_spmv_attr<float, 1, true, true, CFG>();
+    set_spmv_attr<float, 2, true, true, CFG>();
+    set_spmv_attr<double, 0, true, false, CFG>();
+    set_spmv_attr<double, 0, false, false, CFG>();
+    set_spmv_attr<double, 1, true, false, CFG>();
+}
+
 static void set_smem_attrs() {
     static bool done = false;
     if (done) return;
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<float>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
-    BA_CUDA_TRY(cudaFuncSetAttribute(k_spmv<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmv_smem<double>())));
+    set_spmv_attrs<0>();
+    set_spmv_attrs<1>();
+    set_spmv_attrs<2>();
     BA_CUDA_TRY(cudaFuncSetAttribute(k_spmm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(spmm_smem<float>())));
     done = true;
 }
@@ -2068,7 +2182,8 @@ static void set_smem_attrs() {
 static void ensure_items(Solver* w, const Structure& s, int n_dirs, int forced_cb) {
     const int cb = forced_cb > 0 ? forced_cb : 0;
     if (!w->items_g.items || w->items_cb != cb) {
-        upload_items(w->items_g, build_items(s, w->lay, false, cb));
+        upload_items(w->items_g, build_items(s.h_row_ptr, s.h_col, w->lay, false, cb));
+        if (!s.h_row_ptr_u.empty()) upload_items(w->items_u, build_items(s.h_row_ptr_u, s.h_col_u, w->lay, false, cb));
         if (w->mm_part) cudaFree(w->mm_part);
         w->mm_part = nullptr;
         BA_CUDA_TRY(cudaMalloc(&w->mm_part, sizeof(double) * kMaxDirs * 9 * size_t(w->items_g.n > 0 ? w->items_g.n : 1)));
@@ -2077,7 +2192,7 @@ static void ensure_items(Solver* w, const Structure& s, int n_dirs, int forced_c
         ++w->epoch;
     }
     if (n_dirs > 1 && w->items_l_dirs != n_dirs) {
-        upload_items(w->items_l, build_items(s, w->lay, true, cb));
+        upload_items(w->items_l, build_items(s.h_row_ptr, s.h_col, w->lay, true, cb));
         w->items_l_dirs = n_dirs;
         ++w->epoch;
     }
@@ -2188,6 +2303,9 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     ensure_items(w, s, a.mcg ? n_dirs : 1, a.item_blocks);
     w->items_g.polls = a.wait_polls;
     w->items_l.polls = a.wait_polls;
+    w->items_u.polls = a.wait_polls;
+    w->spmv_cfg = a.spmv_cfg >= 0 && a.spmv_cfg < kSpmvShapes ? a.spmv_cfg : 0;
+    if (fp32 && s.nnzb_u > 0) grow(w->tb, size_t(s.nnzb_u) * 9 * sizeof(float));
 }
 
 static void free_buf(Buf& b) {
@@ -2209,6 +2327,8 @@ void solver_destroy(Solver* w) {
     }
     free_items(w->items_g);
     free_items(w->items_l);
+    free_items(w->items_u);
+    free_buf(w->tb);
     if (w->mm_part) cudaFree(w->mm_part);
     if (w->h_ctl) cudaFreeHost(w->h_ctl);
     if (w->h_outer) cudaFreeHost(w->h_outer);
@@ -2230,10 +2350,52 @@ int solver_history(const Solver* w, int problem, const double** hist) {
     return static_cast<int>(w->host_hist[problem].size());
 }
 
-// Enqueue one iteration of the chosen algorithm for every problem on `st`.
+// One launch of k_spmv in shape `cfg` (one CTA per SM).
+template <typename T, int MODE, bool ZH, bool SYM, int CFG>
+static void launch_spmv_cfg(cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
+                            const T* S, const T* z, const ItemList& L, int sel, T* out, const T* rvec, double* camdot,
+                            Ctl* ctl, T* tb) {
+    k_spmv<T, MODE, ZH, SYM, CFG><<<num_sms(), SpmvShape<T, CFG>::kWarps * 32, spmv_smem<T, CFG>(), st>>>(
+        row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+}
+template <typename T, int MODE, bool ZH, bool SYM>
+static void launch_spmv(int cfg, cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
+                        const T* S, const T* z, const ItemList& L, int sel, T* out, const T* rvec, double* camdot,
+                        Ctl* ctl, T* tb) {
+    if (cfg == 1)
+        launch_spmv_cfg<T, MODE, ZH, SYM, 1>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+    else if (cfg == 2)
+        launch_spmv_cfg<T, MODE, ZH, SYM, 2>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+    else
+        launch_spmv_cfg<T, MODE, ZH, SYM, 0>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+}
+
+// A one-column product y = S z, z a column of the direction history (modes of k_spmv).  With the upper
+// triangle Su (float32) it is the symmetric product in two launches; float64 streams the full
+// pattern (its products are bound by the float64 pipe, which halving the bytes would not relieve).
+// Returns the launches.
+template <typename T, int MODE>
+static int enqueue_product(Solver* w, const Structure& s, const T* S, const T* Su, const T* zsrc, int sel, T* out,
+                           const T* rvec, cudaStream_t st) {
+    Ctl* ctl = ptr<Ctl>(w->ctl);
+    double* camdot = MODE == 1 ? ptr<double>(w->camdot) : nullptr;
+    if (Su) {
+        T* tb = ptr<T>(w->tb);
+        launch_spmv<T, MODE, true, true>(w->spmv_cfg, st, s.row_ptr_u, s.tile_ptr_u, s.col_u, Su, zsrc, w->items_u,
+                                         sel, out, rvec, camdot, ctl, tb);
+        k_spmv_col<T, MODE, true><<<dim3(w->gq, w->nb), kThreads, 0, st>>>(s.qptr, s.qlist, tb, zsrc, sel, out, rvec,
+                                                                            camdot, ctl);
+        return 2;
+    }
+    launch_spmv<T, MODE, true, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, zsrc, w->items_g, sel, out,
+                                      rvec, camdot, ctl, nullptr);
+    return 1;
+}
+
+// Enqueue one iteration of the chosen algorithm for every problem on `st`; returns the launches.
 template <typename T>
-static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const double* Dinv, T* x, bool mcg,
-                              cudaStream_t st) {
+static int enqueue_iteration(Solver* w, const Structure& s, const T* S, const T* Su, const double* Dinv, T* x,
+                             bool mcg, cudaStream_t st) {
     const int nb = w->nb;
     T* P = ptr<T>(w->P);
     T* Q = ptr<T>(w->Q);
@@ -2243,13 +2405,12 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
     double* totals = ptr<double>(w->totals);
     int* dcnt = ptr<int>(w->dcnt);
     const int Gt = num_sms();   // tile-streaming products: one CTA per SM
-    const size_t sm = spmv_smem<T>();
     if (!mcg) {
-        k_spmv<T, 1, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
-            s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelLive, Q, r, ptr<double>(w->camdot), ctl);
+        const int np = enqueue_product<T, 1>(w, s, S, Su, P, kSelLive, Q, r, st);
         k_pcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
                                                                ptr<double>(w->dpart), dcnt, ptr<double>(w->hist), ctl);
         k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
+        return np + 2;
     } else {
         k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
         k_mcg_small<T><<<nb, kSmallThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv),
@@ -2265,42 +2426,35 @@ static void enqueue_iteration(Solver* w, const Structure& s, const T* S, const d
         if constexpr (sizeof(T) == 8) {
             // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}; S Z over whole rows for the
             // problems forming a global block, over the subset segments for the local ones
-            k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g, w->use_l ? kSelGlobal : kSelLive, Q, nullptr,
-                nullptr, ctl);
+            launch_spmv<T, 0, false, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, z, w->items_g,
+                                            w->use_l ? kSelGlobal : kSelLive, Q, nullptr, nullptr, ctl, nullptr);
             if (w->use_l)
-                k_spmv<T, 0, false><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
-                    s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l, kSelLocal, Q, nullptr, nullptr, ctl);
+                launch_spmv<T, 0, false, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l,
+                                                kSelLocal, Q, nullptr, nullptr, ctl, nullptr);
             k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, nullptr, ctl);
+            return w->use_l ? 8 : 7;
         } else {
             // Algorithm 2: Q_{i+1} = S P_{i+1}
             k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, ptr<T>(w->PT), ctl);
-            k_spmv<T, 2, true><<<Gt, SpmvCfg<T>::kWarps * 32, sm, st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, P, w->items_g, kSelW1, Q, nullptr, nullptr, ctl);
+            const int np = enqueue_product<T, 2>(w, s, S, Su, P, kSelW1, Q, nullptr, st);
             k_spmm<T><<<Gt, SpmmCfg::kWarps * 32, spmm_smem<T>(), st>>>(
                 s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->PT), w->items_g, static_cast<T*>(w->mm_part), Q, ctl);
+            return 7 + np;
         }
     }
 }
 
-static int iteration_launches(bool mcg, bool fp32, bool two_lists) {
-    if (!mcg) return 3;
-    return fp32 ? 8 : (two_lists ? 8 : 7);
-}
-
-// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0 (3 launches).
+// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0; returns the launches.
 template <typename T>
-static void krylov_init(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs, double sign,
-                        const double* scale, T* x, const Outer* outer, cudaStream_t st) {
+static int krylov_init(Solver* w, const Structure& s, const T* S, const T* Su, const double* Dinv, const double* rhs,
+                       double sign, const double* scale, T* x, const Outer* outer, cudaStream_t st) {
     const int nb = w->nb;
     k_init_vec<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(ptr<Layout>(w->lay_d), rhs, sign, scale, Dinv, x, ptr<T>(w->r),
                                                          ptr<T>(w->z), ptr<T>(w->P), ptr<double>(w->part_b));
     k_init_ctl<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Layout>(w->lay_d), ptr<double>(w->part_b), w->gx,
                                   ptr<Params>(w->params), sizeof(T) == 4 ? kStagnation : 0.0, sizeof(T) == 4 ? 1 : 0,
                                   outer, ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1);
-    k_spmv<T, 0, true><<<num_sms(), SpmvCfg<T>::kWarps * 32, spmv_smem<T>(), st>>>(
-        s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->P), w->items_g, kSelLive, ptr<T>(w->Q), nullptr, nullptr,
-        ptr<Ctl>(w->ctl));
+    return 2 + enqueue_product<T, 0>(w, s, S, Su, ptr<T>(w->P), kSelLive, ptr<T>(w->Q), nullptr, st);
 }
 
 // true residual t = -b~ - S x into out (may be null) and, per problem, its norms into ctl (true_rr,
@@ -2353,18 +2507,20 @@ static cudaGraphConditionalHandle capture_handle(cudaStream_t cs) {
 
 // The Krylov loop of one sweep, captured on cs: the sweep's start, then WHILE(any problem running) {
 // chunk iterations; loop condition } on the body stream cb.
+// Sets *pre (launches before the loop) and *per_pass (launches per pass of the loop).
 template <typename T>
-static void capture_krylov(Solver* w, const Structure& s, const T* S, const double* Dinv, const double* rhs,
-                           double sign, const double* scale, T* x, const Outer* outer, bool mcg, int chunk,
-                           cudaStream_t cs, cudaStream_t cb) {
+static void capture_krylov(Solver* w, const Structure& s, const T* S, const T* Su, const double* Dinv,
+                           const double* rhs, double sign, const double* scale, T* x, const Outer* outer, bool mcg,
+                           int chunk, cudaStream_t cs, cudaStream_t cb, int* pre, int* per_pass) {
     const cudaGraphConditionalHandle h = capture_handle(cs);
-    krylov_init<T>(w, s, S, Dinv, rhs, sign, scale, x, outer, cs);
-    k_loop_cond<<<1, kThreads, 0, cs>>>(h, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 1, chunk,
+    *pre = krylov_init<T>(w, s, S, Su, Dinv, rhs, sign, scale, x, outer, cs) + 1;
+    k_loop_cond<<<1, kThreads, 0, cs>>>(h, 1, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 1, chunk,
                                         ptr<Params>(w->params));
     cudaGraph_t body = capture_while(cs, h);
     BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < chunk; ++k) enqueue_iteration<T>(w, s, S, Dinv, x, mcg, cb);
-    k_loop_cond<<<1, kThreads, 0, cb>>>(h, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 0, chunk,
+    *per_pass = 1;
+    for (int k = 0; k < chunk; ++k) *per_pass += enqueue_iteration<T>(w, s, S, Su, Dinv, x, mcg, cb);
+    k_loop_cond<<<1, kThreads, 0, cb>>>(h, 1, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 0, chunk,
                                         ptr<Params>(w->params));
     cudaGraph_t done = nullptr;
     cudaError_t e = cudaStreamEndCapture(cb, &done);
@@ -2384,31 +2540,31 @@ static cudaGraphExec_t build_solve_graph(Solver* w, const Structure& s, const Sy
     const int64_t n = int64_t(s.n_c) * 9;
     cudaStream_t cs = w->cap_stream;
     gc = GraphCounts();
-    gc.body = a.chunk * iteration_launches(mcg, fp32, w->use_l) + 1;
     BA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     try {
         if (!fp32) {
-            capture_krylov<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, mcg, a.chunk, cs, w->cap2);
-            gc.pre = 4;
+            capture_krylov<double>(w, s, y.S, nullptr, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, mcg, a.chunk, cs,
+                                   w->cap2, &gc.pre, &gc.body);
             gc.post = true_residual(w, s, y, x, nullptr, cs);
         } else {
             k_start_refine<<<grid_for_host(n), kThreads, 0, cs>>>(n, y.bt, x, ptr<double>(w->rt));
             k_outer_init<<<nb, kThreads, 0, cs>>>(ptr<Layout>(w->lay_d), y.bt, ptr<Outer>(w->outer));
             const cudaGraphConditionalHandle ho = capture_handle(cs);
-            k_refine_plan<<<1, kThreads, 0, cs>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho,
+            k_refine_plan<<<1, kThreads, 0, cs>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho, 1,
                                                   ptr<Loops>(w->loops), 0);
             gc.pre = 3;
             cudaGraph_t body = capture_while(cs, ho);
             cudaStream_t c2 = w->cap2;
             BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(c2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            capture_krylov<float>(w, s, y.S32, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw),
-                                  ptr<Outer>(w->outer), mcg, a.chunk, c2, w->cap3);
+            int kpre = 0;
+            capture_krylov<float>(w, s, y.S32, y.S32u, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw),
+                                  ptr<Outer>(w->outer), mcg, a.chunk, c2, w->cap3, &kpre, &gc.body);
             k_accumulate<<<grid_for_host(n), kThreads, 0, c2>>>(n, ptr<float>(w->xw), y.lam, x);
             const int tr = true_residual(w, s, y, x, ptr<double>(w->rt), c2);
             k_refine_after<<<nb, 32, 0, c2>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), ptr<Params>(w->params));
-            k_refine_plan<<<1, kThreads, 0, c2>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho,
+            k_refine_plan<<<1, kThreads, 0, c2>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho, 1,
                                                   ptr<Loops>(w->loops), 1);
-            gc.sweep = 4 + 1 + tr + 2;
+            gc.sweep = kpre + 1 + tr + 2;
             cudaGraph_t done = nullptr;
             cudaError_t e = cudaStreamEndCapture(c2, &done);
             if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("refinement body capture: ") + cudaGetErrorString(e));
@@ -2430,6 +2586,91 @@ static cudaGraphExec_t build_solve_graph(Solver* w, const Structure& s, const Sy
     return exec;
 }
 
+// Host-driven loops (ba_options.host_loop): a plain graph of chunk iterations and the pass counter,
+// launched by the host until every problem is done.  gc.body receives its launches.
+static cudaGraphExec_t build_chunk_graph(Solver* w, const Structure& s, const System& y, const SolveArgs& a,
+                                         double* x, GraphCounts& gc) {
+    const bool fp32 = a.precision == BA_PRECISION_MIXED;
+    cudaStream_t cs = w->cap_stream;
+    gc = GraphCounts();
+    gc.body = 1;
+    BA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < a.chunk; ++k)
+        gc.body += fp32 ? enqueue_iteration<float>(w, s, y.S32, y.S32u, y.Dhat, ptr<float>(w->xw), a.mcg != 0, cs)
+                        : enqueue_iteration<double>(w, s, y.S, nullptr, y.Dinv, x, a.mcg != 0, cs);
+    k_loop_cond<<<1, kThreads, 0, cs>>>(cudaGraphConditionalHandle(), 0, ptr<Ctl>(w->ctl), w->nb,
+                                        ptr<Loops>(w->loops), 0, a.chunk, ptr<Params>(w->params));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("chunk graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("chunk graph instantiate: ") + cudaGetErrorString(e));
+    return exec;
+}
+
+// Launch the chunk graph until every problem's Ctl says done (at most the loop bound); returns the
+// launches and counts the host waits.
+static int64_t host_krylov_loop(Solver* w, cudaGraphExec_t chunk_exec, const GraphCounts& gc, const SolveArgs& a,
+                                cudaStream_t st, int* waits) {
+    const int nb = w->nb;
+    const int bound = a.max_iters / a.chunk + 2;
+    int64_t launches = 0;
+    for (int c = 0; c <= bound; ++c) {
+        BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
+        BA_CUDA_TRY(cudaStreamSynchronize(st));
+        ++*waits;
+        bool all_done = true;
+        for (int b = 0; b < nb && all_done; ++b) all_done = w->h_ctl[b].done != 0;
+        if (all_done || c == bound) break;
+        BA_CUDA_TRY(cudaGraphLaunch(chunk_exec, st));
+        launches += gc.body;
+    }
+    return launches;
+}
+
+static void run_host_loops(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x,
+                           cudaGraphExec_t chunk_exec, const GraphCounts& gc, cudaStream_t st, int* waits) {
+    const bool fp32 = a.precision == BA_PRECISION_MIXED;
+    const int nb = w->nb;
+    const int64_t n = int64_t(s.n_c) * 9;
+    Loops* lp = ptr<Loops>(w->loops);
+    const Params* prm = ptr<Params>(w->params);
+    const cudaGraphConditionalHandle none = cudaGraphConditionalHandle();
+    int64_t launches = 0;
+    if (!fp32) {
+        launches += krylov_init<double>(w, s, y.S, nullptr, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, st);
+        k_loop_cond<<<1, kThreads, 0, st>>>(none, 0, ptr<Ctl>(w->ctl), nb, lp, 1, a.chunk, prm);
+        launches += 1 + host_krylov_loop(w, chunk_exec, gc, a, st, waits);
+        launches += true_residual(w, s, y, x, nullptr, st);
+    } else {
+        k_start_refine<<<grid_for_host(n), kThreads, 0, st>>>(n, y.bt, x, ptr<double>(w->rt));
+        k_outer_init<<<nb, kThreads, 0, st>>>(ptr<Layout>(w->lay_d), y.bt, ptr<Outer>(w->outer));
+        k_refine_plan<<<1, kThreads, 0, st>>>(ptr<Outer>(w->outer), nb, prm, none, 0, lp, 0);
+        launches += 3;
+        for (int sweep = 0; sweep <= a.max_refine; ++sweep) {
+            BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
+            BA_CUDA_TRY(cudaStreamSynchronize(st));
+            ++*waits;
+            bool any = false;
+            for (int b = 0; b < nb && !any; ++b) any = w->h_outer[b].swept != 0;
+            if (!any) break;
+            launches += krylov_init<float>(w, s, y.S32, y.S32u, y.Dhat, ptr<double>(w->rt), 1.0, y.lam,
+                                           ptr<float>(w->xw), ptr<Outer>(w->outer), st);
+            k_loop_cond<<<1, kThreads, 0, st>>>(none, 0, ptr<Ctl>(w->ctl), nb, lp, 1, a.chunk, prm);
+            launches += 1 + host_krylov_loop(w, chunk_exec, gc, a, st, waits);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x);
+            launches += 1 + true_residual(w, s, y, x, ptr<double>(w->rt), st);
+            k_refine_after<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), prm);
+            k_refine_plan<<<1, kThreads, 0, st>>>(ptr<Outer>(w->outer), nb, prm, none, 0, lp, 1);
+            launches += 2;
+        }
+    }
+    BA_CUDA_TRY(cudaGetLastError());
+    w->launches = launches;
+}
+
 // The instantiated graph for this solve (kept for the next solve of the same kind; a few kinds are
 // kept, e.g. PCG and MCG in turn, and graphs that hold freed buffers are dropped).
 static cudaGraphExec_t solve_graph(Solver* w, const Structure& s, const System& y, const SolveArgs& a, double* x,
@@ -2444,6 +2685,8 @@ static cudaGraphExec_t solve_graph(Solver* w, const Structure& s, const System& 
     key.epoch = w->epoch;
     key.polls = a.wait_polls;
     key.nb = w->nb;
+    key.host = a.host_loop;
+    key.cfg = a.spmv_cfg;
     key.allocs = g_allocs.load();
     const void* ptrs[4] = {x, fp32 ? (const void*)y.S32 : (const void*)y.S, w->items_g.items, w->items_l.items};
     for (int i = 0; i < 4; ++i) key.ptrs[i] = ptrs[i];
@@ -2464,7 +2707,7 @@ static cudaGraphExec_t solve_graph(Solver* w, const Structure& s, const System& 
     SolveExec* e = new SolveExec();
     e->key = key;
     try {
-        e->exec = build_solve_graph(w, s, y, a, x, e->gc);
+        e->exec = a.host_loop ? build_chunk_graph(w, s, y, a, x, e->gc) : build_solve_graph(w, s, y, a, x, e->gc);
     } catch (...) {
         delete e;
         throw;
@@ -2507,14 +2750,16 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     hp->pad = 0;
     BA_CUDA_TRY(cudaMemcpyAsync(w->params.p, hp, sizeof(Params), cudaMemcpyHostToDevice, st));
     BA_CUDA_TRY(cudaMemsetAsync(w->loops.p, 0, sizeof(Loops), st));
-    BA_CUDA_TRY(cudaGraphLaunch(exec, st));
+    int host_waits = 0;
+    if (a.host_loop) run_host_loops(w, s, y, a, x, exec, gc, st, &host_waits);
+    else BA_CUDA_TRY(cudaGraphLaunch(exec, st));
     BA_CUDA_TRY(cudaMemcpyAsync(w->h_ctl, w->ctl.p, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, st));
     if (fp32) BA_CUDA_TRY(cudaMemcpyAsync(w->h_outer, w->outer.p, sizeof(Outer) * nb, cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaMemcpyAsync(w->h_loops, w->loops.p, sizeof(Loops), cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaMemcpyAsync(w->h_hist, w->hist.p, sizeof(double) * size_t(nb) * w->mi1, cudaMemcpyDeviceToHost, st));
     BA_CUDA_TRY(cudaEventRecord(e1, st));
     BA_CUDA_TRY(cudaEventSynchronize(e1));
-    int host_waits = 1;
+    ++host_waits;
     BA_CUDA_TRY(cudaGetLastError());
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -2522,7 +2767,7 @@ void solver_run(Solver* w, const Structure& s, const System& y, const SolveArgs&
     cudaEventDestroy(e1);
 
     const Loops lp = *w->h_loops;
-    w->launches = gc.pre + int64_t(lp.outer) * gc.sweep + int64_t(lp.inner) * gc.body + gc.post;
+    if (!a.host_loop) w->launches = gc.pre + int64_t(lp.outer) * gc.sweep + int64_t(lp.inner) * gc.body + gc.post;
     out = SolveOut();
     out.probs.assign(nb, ProbOut());
     bool timed_out = false;
@@ -2594,14 +2839,15 @@ void flush_l2(cudaStream_t st) {
     BA_CUDA_TRY(cudaMemsetAsync(buf, 0, bytes, st));
 }
 
-// The PCG product q = S p of every problem (k_spmv MODE 1, the kernel of Algorithm 1),
-// set up as at the start of a PCG solve (p = D^{-1} b~).
+// The PCG product q = S p of every problem (k_spmv MODE 1, the kernel of Algorithm 1; in float32 the
+// symmetric product, both of its launches), set up as at the start of a PCG solve (p = D^{-1} b~).
 double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int item_blocks,
-                        cudaStream_t st) {
+                        int spmv_cfg, cudaStream_t st) {
     SolveArgs a;
     a.mcg = 0;
     a.max_iters = 1;
     a.item_blocks = item_blocks;
+    a.spmv_cfg = spmv_cfg;
     a.precision = fp32 ? BA_PRECISION_MIXED : BA_PRECISION_FP64;
     prepare(w, s, a, 1, fp32);
     Params* hp = w->h_params;
@@ -2610,9 +2856,9 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
     hp->max_iters = 1;
     BA_CUDA_TRY(cudaMemcpyAsync(w->params.p, hp, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (fp32)
-        krylov_init<float>(w, s, y.S32, y.Dhat, y.bt, -1.0, y.lam, ptr<float>(w->xw), nullptr, st);
+        krylov_init<float>(w, s, y.S32, y.S32u, y.Dhat, y.bt, -1.0, y.lam, ptr<float>(w->xw), nullptr, st);
     else
-        krylov_init<double>(w, s, y.S, y.Dinv, y.bt, -1.0, nullptr, ptr<double>(w->xw), nullptr, st);
+        krylov_init<double>(w, s, y.S, nullptr, y.Dinv, y.bt, -1.0, nullptr, ptr<double>(w->xw), nullptr, st);
     BA_CUDA_TRY(cudaGetLastError());
     cudaEvent_t e0, e1;
     BA_CUDA_TRY(cudaEventCreate(&e0));
@@ -2622,13 +2868,11 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
         flush_l2(st);
         BA_CUDA_TRY(cudaEventRecord(e0, st));
         if (fp32)
-            k_spmv<float, 1, true><<<num_sms(), SpmvCfg<float>::kWarps * 32, spmv_smem<float>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, y.S32, ptr<float>(w->P), w->items_g, kSelLive, ptr<float>(w->Q),
-                ptr<float>(w->r), ptr<double>(w->camdot), ptr<Ctl>(w->ctl));
+            enqueue_product<float, 1>(w, s, y.S32, y.S32u, ptr<float>(w->P), kSelLive, ptr<float>(w->Q),
+                                      ptr<float>(w->r), st);
         else
-            k_spmv<double, 1, true><<<num_sms(), SpmvCfg<double>::kWarps * 32, spmv_smem<double>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, y.S, ptr<double>(w->P), w->items_g, kSelLive, ptr<double>(w->Q),
-                ptr<double>(w->r), ptr<double>(w->camdot), ptr<Ctl>(w->ctl));
+            enqueue_product<double, 1>(w, s, y.S, nullptr, ptr<double>(w->P), kSelLive, ptr<double>(w->Q),
+                                       ptr<double>(w->r), st);
         BA_CUDA_TRY(cudaEventRecord(e1, st));
         BA_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -2640,24 +2884,27 @@ double solver_time_spmv(Solver* w, const Structure& s, const System& y, bool fp3
     return total / reps;
 }
 
-// Item chunk chosen by timing the PCG product: candidates cb = 32 .. 1024 blocks per work item,
-// `reps` launches each; ties keep the smaller chunk.  The lists are left built for the winner.
-int solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, double* best_ms,
-                    cudaStream_t st, std::vector<std::pair<int, double>>* trace) {
+// Shape and item chunk chosen by timing the PCG product: every shape with every chunk of 32 .. 1024
+// blocks per work item, `reps` launches each; ties keep the earlier candidate.  The lists are left
+// built for the winner.
+void solver_autotune(Solver* w, const Structure& s, const System& y, bool fp32, int reps, int* best_cfg,
+                     int* best_cb, double* best_ms, cudaStream_t st) {
     const int cands[] = {32, 64, 128, 256, 512, 1024};
-    int best = 0;
+    int bcfg = 0, bcb = 0;
     double bms = 0.0;
-    for (int cb : cands) {
-        const double ms = solver_time_spmv(w, s, y, fp32, reps, cb, st);
-        if (trace) trace->push_back({cb, ms});
-        if (best == 0 || ms < bms) {
-            best = cb;
-            bms = ms;
+    for (int cfg = 0; cfg < kSpmvShapes; ++cfg)
+        for (int cb : cands) {
+            const double ms = solver_time_spmv(w, s, y, fp32, reps, cb, cfg, st);
+            if (bcb == 0 || ms < bms) {
+                bcfg = cfg;
+                bcb = cb;
+                bms = ms;
+            }
         }
-    }
-    solver_time_spmv(w, s, y, fp32, 1, best, st);
-    if (best_ms) *best_ms = bms;
-    return best;
+    solver_time_spmv(w, s, y, fp32, 1, bcb, bcfg, st);
+    *best_cfg = bcfg;
+    *best_cb = bcb;
+    *best_ms = bms;
 }
 
 }  // namespace ba

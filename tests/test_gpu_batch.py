@@ -145,11 +145,16 @@ def test_autotune_picks_a_candidate_and_keeps_results(precision):
     pb.ba_build_normal(LAM)
     st0 = pb.ba_solve_mcg(1e-6, 1000, 4, 10.0)
     x0 = pb.ba_get_delta()
-    cb, ms = pb.ba_autotune(reps=3)
-    assert cb in (32, 64, 128, 256, 512, 1024) and ms > 0
+    cb, ms, cfg = pb.ba_autotune(reps=3)
+    assert cb in (32, 64, 128, 256, 512, 1024) and ms > 0 and cfg in (0, 1, 2)
     st1 = pb.ba_solve_mcg(1e-6, 1000, 4, 10.0)
     x1 = pb.ba_get_delta()
     pb.close()
+    # the choice is kept for handles of the same precision and size: taken again without timing
+    pc = problem.from_scenes(scs, precision=precision)
+    pc.ba_build_normal(LAM)
+    assert pc.ba_autotune(reps=3) == (cb, ms, cfg)
+    pc.close()
     assert st1["status"] == 0 and st1["true_rel_residual"] <= 1e-6
     # another work-item size changes only the summation order of the products
     assert abs(st1["iters"] - st0["iters"]) <= max(1, st0["iters"] // 10)

@@ -317,14 +317,15 @@ def test_a_solve_is_one_graph_launch_with_one_host_wait(precision, chunk):
     """The iteration loop (and the float64 refinement loop of mixed precision) runs on the device:
     a solve waits on the host once, for its results, and launches exactly the kernels of the passes
     its device-side loop made: 4 before the loop, chunk iterations plus the loop condition per pass,
-    and the 2 of the float64 true residual after it (float64); in mixed precision 3 before the
-    refinement loop and 10 around each sweep's Krylov loop."""
+    and the 2 of the float64 true residual after it (float64: 3 launches per PCG and 8 per MCG
+    iteration); in mixed precision 3 before the refinement loop and 11 around each sweep's Krylov
+    loop (4 per PCG and 9 per MCG iteration: the symmetric float32 product takes two)."""
     import math
 
     sc = scene("seq-small")
     with problem.from_scene(sc, precision=precision, chunk_iters=chunk) as p:
         p.ba_build_normal(1e-4)
-        for kind, per in (("pcg", 3), ("mcg", 8)):
+        for kind, per in (("pcg", 3 if precision == "fp64" else 4), ("mcg", 8 if precision == "fp64" else 9)):
             l0 = p.ba_get_launch_count()
             st = p.ba_solve_pcg(1e-6, 1000) if kind == "pcg" else p.ba_solve_mcg(1e-6, 1000, 16, 10.0)
             launched = p.ba_get_launch_count() - l0
@@ -333,4 +334,25 @@ def test_a_solve_is_one_graph_launch_with_one_host_wait(precision, chunk):
             if precision == "fp64":
                 assert launched == 4 + math.ceil(st["iters"] / chunk) * body + 2, (kind, launched, st)
             elif st["refinements"] == 1:
-                assert launched == 3 + 10 + math.ceil(st["iters"] / chunk) * body, (kind, launched, st)
+                assert launched == 3 + 11 + math.ceil(st["iters"] / chunk) * body, (kind, launched, st)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_driven_loop_gives_the_same_bits(precision):
+    """host_loop = 1 runs the same kernels with the loops driven from the host (for profilers that
+    cannot see kernels inside conditional graphs): the same iterates to the bit, more host waits."""
+    sc = scene("seq-small")
+    xy = problem.device_measurements(sc)
+    out = {}
+    for hl in (0, 1):
+        with problem.from_scene(sc, precision=precision, xy=xy, host_loop=hl, chunk_iters=4) as p:
+            p.ba_build_normal(1e-4)
+            a = p.ba_solve_pcg(1e-6, 1000)
+            xa = p.ba_get_delta().copy()
+            b = p.ba_solve_mcg(1e-6, 1000, 16, 10.0)
+            xb = p.ba_get_delta().copy()
+            out[hl] = (a, xa, b, xb)
+    (a0, xa0, b0, xb0), (a1, xa1, b1, xb1) = out[0], out[1]
+    assert a0["iters"] == a1["iters"] and b0["iters"] == b1["iters"]
+    assert np.array_equal(xa0, xa1) and np.array_equal(xb0, xb1)
+    assert a0["host_waits"] == 1 and a1["host_waits"] > 1
