@@ -93,7 +93,7 @@ typedef struct ba_options {
                                   wait gives up at once (tests the timeout path) */
     int32_t spmv_config;       /* warps x copy stages per CTA of the tile-streaming one-column product:
                                   0 (default) = float32 16 x 1, float64 4 x 2; 1 = 8 x 2 / 8 x 1;
-                                  2 = 20 x 1 / 2 x 4; ba_autotune sets it */
+                                  2 = 10 x 2 / 2 x 4; ba_autotune sets it */
     int32_t host_loop;         /* 1: drive the iteration and refinement loops from the host (a plain
                                   graph of chunk_iters iterations per launch, the stop flags read back
                                   after each) instead of the solve graph's device-side loops; the same

@@ -255,6 +255,17 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     s.perm = upload(p, perm);
     s.obs_xy = upload(p, sxy);
     s.pt_ptr = upload(p, pt_ptr);
+    {
+        // landmarks by decreasing track length, stable (counting sort on the length)
+        int64_t tmax = 0;
+        for (int32_t l = 0; l < n_l; ++l) tmax = std::max(tmax, pt_ptr[l + 1] - pt_ptr[l]);
+        std::vector<int64_t> cnt(size_t(tmax) + 2, 0);
+        for (int32_t l = 0; l < n_l; ++l) cnt[size_t(tmax - (pt_ptr[l + 1] - pt_ptr[l])) + 1]++;
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        std::vector<int32_t> order(n_l);
+        for (int32_t l = 0; l < n_l; ++l) order[cnt[size_t(tmax - (pt_ptr[l + 1] - pt_ptr[l]))]++] = l;
+        s.lm_order = upload(p, order);
+    }
     s.cam_ptr = upload(p, cam_ptr);
     s.cam_obs = upload(p, cam_obs);
     s.nnzb = nnzb;
@@ -358,7 +369,7 @@ void alloc_system(ba_problem* p) {
         BA_CUDA_TRY(cudaMemset(y.S32, 0, sizeof(float) * size_t(s.n_tiles) * ba::kTileElems));
         y.S32u = dev_alloc<float>(p, size_t(s.n_tiles_u) * ba::kTileElems);
         BA_CUDA_TRY(cudaMemset(y.S32u, 0, sizeof(float) * size_t(s.n_tiles_u) * ba::kTileElems));
-        y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 27);
+        y.G32 = dev_alloc<float>(p, size_t(s.n_o) * 36);   // three 16-byte aligned parts of 9 per row
         y.aux32 = dev_alloc<float>(p, size_t(s.n_c) * 24);
         y.PY32 = dev_alloc<float>(p, size_t(s.n_o) * 6);
         y.L32 = dev_alloc<float>(p, size_t(s.n_l) * 6);

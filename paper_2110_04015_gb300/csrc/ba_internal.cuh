@@ -67,6 +67,9 @@ struct Structure {
     int32_t* perm = nullptr;      // n_o: point-order slot -> caller index
     double* obs_xy = nullptr;     // n_o x 2
     int64_t* pt_ptr = nullptr;    // n_l + 1
+    int32_t* lm_order = nullptr;  // n_l: landmarks by decreasing track length (ties by index); the
+                                  // per-landmark kernels take them in this order so that the lanes of a
+                                  // warp loop over equally many observations
     int64_t* cam_ptr = nullptr;   // n_c + 1
     int32_t* cam_obs = nullptr;   // n_o: point-order slots grouped by camera
     // S pattern (full)
@@ -130,7 +133,8 @@ struct System {
     double* lam = nullptr;    // 9 n_c: Lam
     double* Dhat = nullptr;   // n_c x 81: inverses of the diagonal blocks of S^
     float* lam32 = nullptr;   // 9 n_c: float(Lam)
-    float* G32 = nullptr;     // n_o x 27: G_o = J_p^T A_o in float32 (from the float32 Jacobians)
+    float* G32 = nullptr;     // n_o x 36: G_o = J_p^T A_o in float32 (from the float32 Jacobians), rows
+                              // 3P..3P+2 at offset 12 P (three 16-byte aligned parts)
     float* aux32 = nullptr;   // n_c x 24: the camera's aux block in float32
     float* PY32 = nullptr;    // n_o x 6: P = R X + t and Y = R X in float32 (formed in float64)
     float* L32 = nullptr;     // n_l x 6: L (packed as above) in float32

@@ -33,6 +33,10 @@ namespace ba {
 
 namespace {
 
+// a float32 G row: the 9x3 values in three parts of 9 (rows 3P..3P+2), each starting on a 16-byte boundary
+constexpr int kG32Part = 12;
+constexpr int kG32Row = 3 * kG32Part;
+
 inline int grid_for(int64_t n, int threads) {
     int64_t g = (n + threads - 1) / threads;
     int cap = num_sms() * 16;
@@ -273,11 +277,13 @@ __global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const d
 // (1 / l00, l10, 1 / l11, l20, l21, 1 / l22): every later use multiplies by the reciprocal diagonal.
 // Mixed precision (L32 != null) also writes L in float32 (same packing) and y_l = V^{-1} b_l =
 // L^{-T} e in float64 (for b~ in the form sum J_p^T (r - J_l y_l)).
-__global__ void k_landmarks(int32_t n_l, const int64_t* __restrict__ pt_ptr, const double* __restrict__ r,
-                            const double* __restrict__ Jl, int damping, double lambda, double* __restrict__ Vout,
-                            double* __restrict__ Lout, double* __restrict__ blout, double* __restrict__ eout,
-                            float* __restrict__ L32, double* __restrict__ yout, int* status) {
-    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+__global__ void k_landmarks(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                            const double* __restrict__ r, const double* __restrict__ Jl, int damping, double lambda,
+                            double* __restrict__ Vout, double* __restrict__ Lout, double* __restrict__ blout,
+                            double* __restrict__ eout, float* __restrict__ L32, double* __restrict__ yout,
+                            int* status) {
+    for (int64_t t = gtid(); t < n_l; t += gstride()) {
+        const int64_t l = order[t];
         double v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, b0 = 0, b1 = 0, b2 = 0;
         for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
             const double* j = Jl + 6 * o;
@@ -569,9 +575,10 @@ __global__ void __launch_bounds__(kThreads) k_schur_off_rows(
     }
 }
 
-// 4-byte asynchronous copy global -> shared (cp.async, completion awaited by cp_async_wait_all).
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+// 16-byte asynchronous copy global -> shared (cp.async, completion awaited by cp_async_wait_all); both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
                  "l"(src)
                  : "memory");
 }
@@ -591,10 +598,11 @@ __device__ __forceinline__ void lds9(const float* p, float* v) {
 // (k, j).  Lane 9 g + 3 A + B (g < 3) accumulates the 3x3 sub-block at rows 3A.., columns 3B.. over the
 // pairs p = g (mod 3): it needs rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok, nine consecutive
 // values each, so one pair costs the lane two runs of vector shared loads for 27 fused
-// multiply-adds.  The warp takes the pairs kChunk at a time: lanes 0..26 copy the two 27-value G
-// blocks of every pair of the chunk into shared memory with 4-byte asynchronous copies (all in
-// flight together, no staging registers; lane p fetches the indices of pair p), each 9-value
-// part on a 16-byte boundary.  48 registers let five CTAs share an SM.  The three slices are added in slice order through shuffles,
+// multiply-adds.  The warp takes the pairs kChunk at a time and copies the two G rows of every pair
+// of the chunk into shared memory with 16-byte asynchronous copies (a row is three 9-value parts on
+// 16-byte boundaries, laid out in shared memory as in global memory: 9 copies per row, all in flight
+// together, no staging registers; lane p fetches the indices of pair p).  The three slices are added
+// in slice order through shuffles,
 // the block is assembled in shared memory and written with coalesced stores to (j, k) and,
 // transposed, to (k, j), and to (j, k) of the upper-triangle copy Su.  The float32 system is the scaled
 // Lam S Lam: each block is multiplied by Lam_j (rows) and Lam_k (columns) after its sum.
@@ -606,14 +614,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
     T* __restrict__ Su) {
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
     constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
-    constexpr int kPart = 12;                          // stride of a 9-value part (16-byte aligned)
-    __shared__ __align__(16) T sg[kThreads / 32][kChunk][2][3 * kPart];
+    constexpr int kPart = kG32Part;
+    __shared__ __align__(16) T sg[kThreads / 32][kChunk][2][kG32Row];
     __shared__ T sb[kThreads / 32][81];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = gstride() >> 5;
     const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31 only load
     const int A = sub / 3, B = sub - 3 * (sub / 3);
-    const int stage = (lane / 9) * kPart + lane % 9;   // where G entry `lane` (< 27) is staged
     for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
         T acc[9];
 #pragma unroll
@@ -624,15 +631,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
             int2 pr = make_int2(0, 0);
             if (lane < np) pr = pairs[q + lane];
             __syncwarp();   // every lane is done with the previous chunk's staging area
-            // the chunk's G rows go straight to shared memory as 4-byte asynchronous copies (no
-            // staging registers, all copies in flight together); pairs past np are not read
-#pragma unroll
-            for (int p = 0; p < kChunk; ++p) {
-                const int ox = __shfl_sync(0xffffffffu, pr.x, p);
-                const int oy = __shfl_sync(0xffffffffu, pr.y, p);
-                if (p < np && lane < 27) {
-                    cp_async4(&sg[wid][p][0][stage], G + 27 * int64_t(ox) + lane);
-                    cp_async4(&sg[wid][p][1][stage], G + 27 * int64_t(oy) + lane);
+            // copy (pair, side, 16-byte piece) = (it / 18, it % 18 / 9, it % 9) of the chunk; pieces
+            // 0..8 of a row are parts it % 9 / 3 at stride kPart, 4 values each
+#pragma unroll 1
+            for (int it0 = 0; it0 < kChunk * 18; it0 += 32) {
+                const int it = it0 + lane;
+                const int pp = it / 18, rem = it - 18 * (it / 18);
+                const int side = rem / 9, piece = rem - 9 * side;
+                const int ox = __shfl_sync(0xffffffffu, pr.x, pp & 31);
+                const int oy = __shfl_sync(0xffffffffu, pr.y, pp & 31);
+                if (pp < np) {
+                    const int off = (piece / 3) * kPart + (piece % 3) * 4;
+                    cp_async16(&sg[wid][pp][side][off], G + int64_t(kG32Row) * (side ? oy : ox) + off);
                 }
             }
             cp_async_wait_all();
@@ -798,11 +808,13 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
             const float m00 = 1.f - (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
             const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
             const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
-            float* g = G32 + 27 * o;
+            // G_o row-major 9x3, stored as three parts of rows 3P..3P+2 at stride kG32Part (16-byte aligned)
+            float* g = G32 + kG32Row * o;
 #pragma unroll
             for (int a = 0; a < 9; ++a)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) g[3 * a + c] = jc[a] * A[0][c] + jc[9 + a] * A[1][c];
+                for (int c = 0; c < 3; ++c)
+                    g[(a / 3) * kG32Part + (a % 3) * 3 + c] = jc[a] * A[0][c] + jc[9 + a] * A[1][c];
             float B0[9], B1[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
@@ -848,10 +860,12 @@ __device__ __forceinline__ void solve_V(const double* L, double s0, double s1, d
 // Mixed precision true residual, float64, landmark pass (one thread per landmark, its observations
 // are contiguous): u_o = J_p x_cam(o), y_l = V_l^-1 sum_o J_l^T u_o, and v_o = u_o - J_l y_l into uv.
 // Then (S x)_j = sum_{o in j} J_p^T v_o + lambda D_p x_j = U_j x_j - (W V^-1 W^T x)_j (Eq. 13).
-__global__ void k_jres_land(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
-                            const double* __restrict__ Jc, const double* __restrict__ Jl,
-                            const double* __restrict__ Lall, const double* __restrict__ x, double* __restrict__ uv) {
-    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+__global__ void k_jres_land(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                            const int32_t* __restrict__ oc, const double* __restrict__ Jc,
+                            const double* __restrict__ Jl, const double* __restrict__ Lall,
+                            const double* __restrict__ x, double* __restrict__ uv) {
+    for (int64_t t = gtid(); t < n_l; t += gstride()) {
+        const int64_t l = order[t];
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         const int64_t o0 = pt_ptr[l], o1 = pt_ptr[l + 1];
         for (int64_t o = o0; o < o1; ++o) {
@@ -932,11 +946,12 @@ __global__ void __launch_bounds__(kCamThreads) k_jres_cam(
 
 // Back-substitution without G (mixed precision): dx_l = -V_l^{-1} (b_l + sum_o J_l^T J_p dx_p,cam(o))
 // (Eq. 15 with the sign that follows from Eq. 6).
-__global__ void k_back_sub_J(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
-                             const double* __restrict__ Jc, const double* __restrict__ Jl,
-                             const double* __restrict__ Lall, const double* __restrict__ bl,
-                             const double* __restrict__ dxp, double* __restrict__ dxl) {
-    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+__global__ void k_back_sub_J(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                             const int32_t* __restrict__ oc, const double* __restrict__ Jc,
+                             const double* __restrict__ Jl, const double* __restrict__ Lall,
+                             const double* __restrict__ bl, const double* __restrict__ dxp, double* __restrict__ dxl) {
+    for (int64_t t = gtid(); t < n_l; t += gstride()) {
+        const int64_t l = order[t];
         double s0 = bl[3 * l], s1 = bl[3 * l + 1], s2 = bl[3 * l + 2];
         for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
             const double* xc = dxp + 9 * int64_t(oc[o]);
@@ -1020,11 +1035,12 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
 }
 
 // dx_l = -L^{-T} (e_l + sum_o G_o^T dx_p,cam(o))
-__global__ void k_back_substitute(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ oc,
-                                  const double* __restrict__ G, const double* __restrict__ Lall,
-                                  const double* __restrict__ e, const double* __restrict__ dxp,
-                                  double* __restrict__ dxl) {
-    for (int64_t l = gtid(); l < n_l; l += gstride()) {
+__global__ void k_back_substitute(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                                  const int32_t* __restrict__ oc, const double* __restrict__ G,
+                                  const double* __restrict__ Lall, const double* __restrict__ e,
+                                  const double* __restrict__ dxp, double* __restrict__ dxl) {
+    for (int64_t t = gtid(); t < n_l; t += gstride()) {
+        const int64_t l = order[t];
         double a0 = e[3 * l], a1 = e[3 * l + 1], a2 = e[3 * l + 2];
         for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
             const double* g = G + 27 * o;
@@ -1129,8 +1145,8 @@ void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
 }
 
 void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
-    k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, y.r, y.Jl, damping, lambda, y.V,
-                                                                 y.L, y.bl, y.e, y.L32, y.yl, y.status);
+    k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, y.r, y.Jl, damping,
+                                                                 lambda, y.V, y.L, y.bl, y.e, y.L32, y.yl, y.status);
 }
 
 void launch_obs_G(const Structure& s, System& y, cudaStream_t st) {
@@ -1182,7 +1198,8 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
 
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st) {
-    k_jres_land<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.Jc, y.Jl, y.L, x, y.uv);
+    k_jres_land<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.Jc, y.Jl,
+                                                                 y.L, x, y.uv);
     k_jres_cam<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.Jc, y.uv, y.dadd, x, y.bt, out,
                                                     partial);
 }
@@ -1203,11 +1220,11 @@ void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st) {
 
 void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl, cudaStream_t st) {
     if (y.G)
-        k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.G, y.L, y.e,
-                                                                           dxp, dxl);
+        k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.G,
+                                                                           y.L, y.e, dxp, dxl);
     else
-        k_back_sub_J<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.obs_cam, y.Jc, y.Jl, y.L, y.bl,
-                                                                      dxp, dxl);
+        k_back_sub_J<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.Jc,
+                                                                      y.Jl, y.L, y.bl, dxp, dxl);
 }
 
 void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial, int nparts,

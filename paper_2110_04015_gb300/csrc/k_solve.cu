@@ -346,12 +346,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int po
 // Warps per CTA and copy stages of the tile-streaming one-column product, one CTA per SM.  Three
 // shapes per precision (ba_options.spmv_config, chosen by ba_autotune); shape 0 is the default:
 // float32 16 warps x 1 stage (measured faster than 8 x 2 for the full-pattern product: more warps
-// cover the gathers of p), float64 4 x 2.  Every shape keeps its stages within 207 KB.
+// cover the gathers of p), float64 4 x 2.  The symmetric product does twice the arithmetic per tile,
+// so a second stage per warp keeps the next copy in flight during it (shapes 1 and 2).  Every shape
+// keeps its stages within 207 KB.
 template <typename T, int CFG>
 struct SpmvShape;
 template <> struct SpmvShape<float, 0> { static constexpr int kWarps = 16, kStages = 1; };
 template <> struct SpmvShape<float, 1> { static constexpr int kWarps = 8, kStages = 2; };
-template <> struct SpmvShape<float, 2> { static constexpr int kWarps = 20, kStages = 1; };
+template <> struct SpmvShape<float, 2> { static constexpr int kWarps = 10, kStages = 2; };
 template <> struct SpmvShape<double, 0> { static constexpr int kWarps = 4, kStages = 2; };
 template <> struct SpmvShape<double, 1> { static constexpr int kWarps = 8, kStages = 1; };
 template <> struct SpmvShape<double, 2> { static constexpr int kWarps = 2, kStages = 4; };
@@ -572,36 +574,39 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
 }
 
 // Second pass of the symmetric product: y_k += sum over the stored blocks (j, k), j < k, of their
-// transposed terms S_jk^T z_j (in j order, so the sum does not depend on scheduling), then in MODE 1
-// the per-camera sums q^T p and p^T r.  One warp per camera; grid: CTAs x problems.
+// transposed terms S_jk^T z_j (a fixed order: lane-strided sums in each warp's share of the list,
+// then the warps' sums in warp order), then in MODE 1 the per-camera sums q^T p and p^T r.  One CTA
+// of kColWarps warps per camera (the list of a camera holds up to n_c - 1 terms of 36 bytes, read
+// through an index); grid: CTAs x problems.
+constexpr int kColWarps = 8;
 template <typename T, int MODE, bool ZH>
-__global__ void __launch_bounds__(kThreads) k_spmv_col(const int64_t* __restrict__ qptr,
-                                                       const int32_t* __restrict__ qlist, const T* __restrict__ tb,
-                                                       const T* __restrict__ z, int sel, T* __restrict__ out,
-                                                       const T* __restrict__ rvec, double* __restrict__ camdot,
-                                                       const Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kColWarps * 32) k_spmv_col(const int64_t* __restrict__ qptr,
+                                                             const int32_t* __restrict__ qlist, const T* __restrict__ tb,
+                                                             const T* __restrict__ z, int sel, T* __restrict__ out,
+                                                             const T* __restrict__ rvec, double* __restrict__ camdot,
+                                                             const Ctl* __restrict__ ctl) {
     const int p = blockIdx.y;
     if (!selected(ctl, p, sel)) return;
     const Ctl& c = ctl[p];
-    const int lane = threadIdx.x & 31;
+    __shared__ T red[kColWarps][9];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t n = int64_t(c.lay.nc) * 9;
     const int64_t hb = c.lay.hoff - 9 * int64_t(c.lay.c0);
     const int64_t zoff = ZH ? hb + int64_t(MODE == 2 ? c.new_off : 0) * n : 0;
     const int64_t ooff = hb + int64_t(MODE == 1 ? 0 : c.new_off) * n;
-    const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t jl = w0; jl < c.lay.nc; jl += nw) {
+    for (int64_t jl = blockIdx.x; jl < c.lay.nc; jl += gridDim.x) {
         const int64_t j = c.lay.c0 + jl;
         T acc[9];
 #pragma unroll
         for (int b = 0; b < 9; ++b) acc[b] = T(0);
-        // four entries per lane in flight (their list indices first, then the terms)
-        int64_t e = qptr[j] + lane;
+        // warp w takes entries w * 32 + lane + k * kColWarps * 32; four per lane in flight
+        constexpr int step = kColWarps * 32;
+        int64_t e = qptr[j] + wid * 32 + lane;
         const int64_t e1 = qptr[j + 1];
-        for (; e + 96 < e1; e += 128) {
+        for (; e + 3 * step < e1; e += 4 * step) {
             int64_t q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = qlist[e + 32 * u];
+            for (int u = 0; u < 4; ++u) q[u] = qlist[e + u * step];
             T v[4][9];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -610,35 +615,45 @@ __global__ void __launch_bounds__(kThreads) k_spmv_col(const int64_t* __restrict
 #pragma unroll
             for (int b = 0; b < 9; ++b) acc[b] += (v[0][b] + v[1][b]) + (v[2][b] + v[3][b]);
         }
-        for (; e < e1; e += 32) {
+        for (; e < e1; e += step) {
             const T* t = tb + int64_t(qlist[e]) * 9;
 #pragma unroll
             for (int b = 0; b < 9; ++b) acc[b] += t[b];
         }
 #pragma unroll
         for (int b = 0; b < 9; ++b) acc[b] = warp_sum(acc[b]);
-        T val = acc[0];
+        if (lane == 0)
 #pragma unroll
-        for (int b = 1; b < 9; ++b) if (lane == b) val = acc[b];
-        const int64_t rowi = 9 * j + lane;
-        if (lane < 9) {
-            val = out[ooff + rowi] + val;
-            out[ooff + rowi] = val;
-        }
-        if (MODE == 1) {
-            double dq = 0.0, dr = 0.0;
+            for (int b = 0; b < 9; ++b) red[wid][b] = acc[b];
+        __syncthreads();
+        if (wid == 0) {
+            T val = T(0);
             if (lane < 9) {
-                const double pv = double(z[zoff + rowi]);
-                dq = double(val) * pv;
-                dr = pv * double(rvec[rowi]);
+                val = red[0][lane];
+#pragma unroll
+                for (int w = 1; w < kColWarps; ++w) val += red[w][lane];
             }
-            dq = warp_sum(dq);
-            dr = warp_sum(dr);
-            if (lane == 0) {
-                camdot[2 * j] = dq;
-                camdot[2 * j + 1] = dr;
+            const int64_t rowi = 9 * j + lane;
+            if (lane < 9) {
+                val = out[ooff + rowi] + val;
+                out[ooff + rowi] = val;
+            }
+            if (MODE == 1) {
+                double dq = 0.0, dr = 0.0;
+                if (lane < 9) {
+                    const double pv = double(z[zoff + rowi]);
+                    dq = double(val) * pv;
+                    dr = pv * double(rvec[rowi]);
+                }
+                dq = warp_sum(dq);
+                dr = warp_sum(dr);
+                if (lane == 0) {
+                    camdot[2 * j] = dq;
+                    camdot[2 * j + 1] = dr;
+                }
             }
         }
+        __syncthreads();
     }
 }
 
@@ -2030,6 +2045,7 @@ struct Solver {
     int gq = 1;               // grid width of the per-row kernels
     int gpq = 1;              // grid width of the reorthogonalisation (32-row blocks)
     int gphi = 1, gb = 1;     // Phi and beta grid widths
+    int gcol = 1;             // grid width of the column pass of the symmetric product (a CTA per camera)
     std::vector<Layout> lay;  // of the current solve
     Buf P, Q, r, z, xw, PT, part_a, part_b, part_cam, dpinv, beta, betaf, phip, hist, blk_off, blk_w, ctl, outer, rt,
         lay_d, totals, dpart, dcnt, camdot, params, loops;
@@ -2249,6 +2265,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     w->gpq = int(std::max<int64_t>(1, std::min<int64_t>((9 * int64_t(nc_max) + 31) / 32, 4 * G / nb)));
     w->gphi = std::max(1, 4 * G / nb);
     w->gb = std::max(1, G / nb);
+    w->gcol = std::min(nc_max, std::max(1, 8 * G / nb));
     if (!w->h_ctl || int(w->lay.size()) != nb) {
         if (w->h_ctl) cudaFreeHost(w->h_ctl);
         if (w->h_outer) cudaFreeHost(w->h_outer);
@@ -2383,8 +2400,8 @@ static int enqueue_product(Solver* w, const Structure& s, const T* S, const T* S
         T* tb = ptr<T>(w->tb);
         launch_spmv<T, MODE, true, true>(w->spmv_cfg, st, s.row_ptr_u, s.tile_ptr_u, s.col_u, Su, zsrc, w->items_u,
                                          sel, out, rvec, camdot, ctl, tb);
-        k_spmv_col<T, MODE, true><<<dim3(w->gq, w->nb), kThreads, 0, st>>>(s.qptr, s.qlist, tb, zsrc, sel, out, rvec,
-                                                                            camdot, ctl);
+        k_spmv_col<T, MODE, true><<<dim3(w->gcol, w->nb), kColWarps * 32, 0, st>>>(s.qptr, s.qlist, tb, zsrc, sel,
+                                                                                    out, rvec, camdot, ctl);
         return 2;
     }
     launch_spmv<T, MODE, true, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, zsrc, w->items_g, sel, out,
