@@ -763,7 +763,9 @@ def run_batched(a):
     nnzb = pb.ba_get_schur_nnzb()
     peaks = load_peaks()
     elt = 8 if a.precision == "fp64" else 4
-    spmv_bytes = nnzb * (81 * elt + 4) + 8 * (n_cams + 1) + 3 * 9 * n_cams * elt
+    # float64 streams every stored block; float32 the upper triangle (the symmetric product)
+    blocks = nnzb if a.precision == "fp64" else (nnzb + n_cams) // 2
+    spmv_bytes = blocks * (81 * elt + 4) + 8 * (n_cams + 1) + 3 * 9 * n_cams * elt
     pb.close()
 
     tl = []
@@ -800,7 +802,8 @@ def run_batched(a):
         "looped_single_ms": ms_l, "speedup_vs_loop": ms_l / ms_b if ms_l else None,
         "per_problem_iters": [s["iters"] for s in per],
         "autotune": {"item_blocks": cb, "spmv_config": cfg, "spmv_ms_tuned": t_tuned, "spmv_ms_heuristic": t_heur},
-        "roofline": {"kernel": "k_spmv<T,1> over all problems", "bound": "hbm" if elt == 4 else "alu",
+        "roofline": {"kernel": "q = S p over all problems (float32: the symmetric product over the upper triangle)",
+                     "bound": "hbm" if elt == 4 else "alu", "bytes_per_launch": spmv_bytes,
                      "achieved_gbs": spmv_bytes / t_tuned / 1e6, "peak_gbs": peaks["hbm_gbs"],
                      "frac": spmv_bytes / t_tuned / 1e6 / peaks["hbm_gbs"]},
         "gpu_launches_per_step": int(launches), "clocks": clk,

@@ -293,6 +293,21 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         s.up_mdst = upload(p, mdst);
     }
     s.up_pair_ptr = upload(p, up_pp);
+    if (p->opt.precision == BA_PRECISION_MIXED) {
+        // the float32 per-observation arrays are kept in camera order (cam_obs order), so that the
+        // per-camera kernels read and write them contiguously
+        std::vector<int32_t> cpos(n_o), cam_lm(n_o);
+        for (int64_t q = 0; q < n_o; ++q) {
+            cpos[cam_obs[q]] = int32_t(q);
+            cam_lm[q] = spt[cam_obs[q]];
+        }
+        for (int64_t q = 0; q < n_pairs; ++q) pr[q] = make_int2(cpos[pr[q].x], cpos[pr[q].y]);
+        std::vector<int2> ucams(n_up > 0 ? n_up : 1);
+        for (int64_t u = 0; u < n_up; ++u) ucams[u] = make_int2(up_j[u], up_k[u]);
+        s.cpos = upload(p, cpos);
+        s.cam_lm = upload(p, cam_lm);
+        s.up_cams = upload(p, ucams);
+    }
     s.pairs = upload(p, pr);
     if (p->opt.precision == BA_PRECISION_MIXED) {
         // upper pattern: the diagonal block first, then the upper blocks in (j, k) order

@@ -85,7 +85,11 @@ struct Structure {
     int64_t* up_dst = nullptr;    // n_up: element offset of block (j, k) in the tiled S (s_at(.., 0))
     int64_t* up_mdst = nullptr;   // n_up: element offset of its mirror (k, j)
     int64_t* up_pair_ptr = nullptr;  // n_up + 1
-    int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark
+    int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark (mixed precision:
+                                  // their camera-order positions, where the float32 G rows are kept)
+    int2* up_cams = nullptr;      // n_up (mixed precision): the cameras (j, k) of each upper block
+    int32_t* cpos = nullptr;      // n_o (mixed precision): camera-order position of each point-order slot
+    int32_t* cam_lm = nullptr;    // n_o (mixed precision): landmark of each camera-order position
     // upper triangle of S (mixed precision's one-column products): row j holds S_jj, then S_jk, k > j,
     // tiled like the full pattern; qptr/qlist list, per camera k, the stored blocks (j, k), j < k
     int64_t nnzb_u = 0, n_tiles_u = 0;

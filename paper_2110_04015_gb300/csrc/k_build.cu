@@ -239,12 +239,13 @@ __global__ void k_project(int64_t n_o, const double* __restrict__ cams, const do
 }
 
 // Float64 residuals and Jacobians per observation; mixed precision (PY32 != null) also keeps P and
-// Y = R X in float32 (6 per observation), from which the float32 Jacobians are formed (forming P = Y + t
-// in float32 would lose digits when |Y|, |t| >> |P|, and Y = P - t when |P|, |t| >> |Y|).
+// Y = R X in float32 (6 per observation, in camera order), from which the float32 Jacobians are
+// formed (forming P = Y + t in float32 would lose digits when |Y|, |t| >> |P|, and Y = P - t when
+// |P|, |t| >> |Y|).
 __global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const double* __restrict__ pts,
                             const int32_t* __restrict__ oc, const int32_t* __restrict__ op,
                             const double* __restrict__ xy, double* __restrict__ r, double* __restrict__ Jc,
-                            double* __restrict__ Jl, float* __restrict__ PY32) {
+                            double* __restrict__ Jl, float* __restrict__ PY32, const int32_t* __restrict__ cpos) {
     for (int64_t i = gtid(); i < n_o; i += gstride()) {
         double ax[24], X[3], Y[3], P[3], m[2], rr[2], jc[18], jl[6];
         const double* cp = aux + int64_t(oc[i]) * 24;
@@ -263,11 +264,12 @@ __global__ void k_linearize(int64_t n_o, const double* __restrict__ aux, const d
         for (int k = 0; k < 18; ++k) Jc[18 * i + k] = jc[k];
 #pragma unroll
         for (int k = 0; k < 6; ++k) Jl[6 * i + k] = jl[k];
-        if (PY32) {
+        if (PY32) {   // at the observation's camera-order position
+            float* py = PY32 + 6 * int64_t(cpos[i]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                PY32[6 * i + k] = float(P[k]);
-                PY32[6 * i + 3 + k] = float(Y[k]);
+                py[k] = float(P[k]);
+                py[3 + k] = float(Y[k]);
             }
         }
     }
@@ -610,7 +612,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
     int64_t n_up, const int64_t* __restrict__ up_dst, const int64_t* __restrict__ up_mdst,
     const int64_t* __restrict__ up_udst, const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
-    const int32_t* __restrict__ oc, const T* __restrict__ lam, const T* __restrict__ G, T* __restrict__ S,
+    const int2* __restrict__ up_cams, const T* __restrict__ lam, const T* __restrict__ G, T* __restrict__ S,
     T* __restrict__ Su) {
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
     constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
@@ -621,6 +623,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
     const int64_t nw = gstride() >> 5;
     const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31 only load
     const int A = sub / 3, B = sub - 3 * (sub / 3);
+    // copy role of lanes 0..17: side (row of o_j or o_k) and 16-byte piece of the 36-float row,
+    // piece c = part c / 3 at stride kPart, values 4 (c % 3) .. + 3
+    const int cside = lane >= 9 ? 1 : 0, cpiece = lane - 9 * cside;
+    const int coff = (cpiece / 3) * kPart + (cpiece % 3) * 4;
     for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
         T acc[9];
 #pragma unroll
@@ -631,19 +637,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
             int2 pr = make_int2(0, 0);
             if (lane < np) pr = pairs[q + lane];
             __syncwarp();   // every lane is done with the previous chunk's staging area
-            // copy (pair, side, 16-byte piece) = (it / 18, it % 18 / 9, it % 9) of the chunk; pieces
-            // 0..8 of a row are parts it % 9 / 3 at stride kPart, 4 values each
-#pragma unroll 1
-            for (int it0 = 0; it0 < kChunk * 18; it0 += 32) {
-                const int it = it0 + lane;
-                const int pp = it / 18, rem = it - 18 * (it / 18);
-                const int side = rem / 9, piece = rem - 9 * side;
-                const int ox = __shfl_sync(0xffffffffu, pr.x, pp & 31);
-                const int oy = __shfl_sync(0xffffffffu, pr.y, pp & 31);
-                if (pp < np) {
-                    const int off = (piece / 3) * kPart + (piece % 3) * 4;
-                    cp_async16(&sg[wid][pp][side][off], G + int64_t(kG32Row) * (side ? oy : ox) + off);
-                }
+            // lanes 0..17 copy the 16-byte piece `cpiece` of side `cside` of every pair of the chunk
+            // (np is the same in every lane: the loop stops at the chunk's last pair)
+#pragma unroll 4
+            for (int p = 0; p < np; ++p) {
+                const int ox = __shfl_sync(0xffffffffu, pr.x, p);
+                const int oy = __shfl_sync(0xffffffffu, pr.y, p);
+                if (lane < 18) cp_async16(&sg[wid][p][cside][coff], G + int64_t(kG32Row) * (cside ? oy : ox) + coff);
             }
             cp_async_wait_all();
             __syncwarp();
@@ -668,10 +668,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
             acc[i] = (acc[i] + v1) + v2;
         }
         if (lane < 9) {
-            // the block's cameras from its first pair: rows scale by Lam_j, columns by Lam_k
-            const int2 p0 = pairs[pb];
-            const T* lj = lam + 9 * int64_t(oc[p0.x]);
-            const T* lk = lam + 9 * int64_t(oc[p0.y]);
+            // rows scale by Lam_j, columns by Lam_k
+            const int2 jk = up_cams[u];
+            const T* lj = lam + 9 * int64_t(jk.x);
+            const T* lk = lam + 9 * int64_t(jk.y);
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -773,20 +773,33 @@ __device__ __forceinline__ void rows_A(const float* jl, const float* Lp, float (
 
 constexpr int kDiagThreads = 256;
 
+// A float32 sum carried as an unevaluated pair hi + lo: adding (h, l) is an error-free two-sum of
+// the high parts with the low parts added, about 48 significant bits without float64 arithmetic.
+struct FloatPair {
+    float hi, lo;
+    __device__ __forceinline__ void add(float h, float l) {
+        const float t = __fadd_rn(hi, h);
+        const float bv = __fsub_rn(t, hi);
+        const float te = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(h, bv));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(te, l));
+    }
+};
+
 // Mixed precision, one CTA per camera: S_jj = sum_{o in j} J_p^T (I - A A^T) J_p + lambda D_p (Eq. 13 on
 // the diagonal: U_j - sum_o G_o G_o^T with G_o = J_p^T A_o), from float32 Jacobians formed in float32
 // from the camera and the float32 point in the camera frame.  I - A A^T = I - J_l V^-1 J_l^T is
 // positive semi-definite, so the terms add without cancellation; each thread sums its observations
 // in float32, the threads' sums are added in float64 (fixed order), and the float64 damping is added
 // last.  Sd receives float64.  The same pass writes G_o = J_p^T A_o (9x3, unscaled) of every
-// observation to G32 for the off-diagonal blocks.
+// observation to G32 for the off-diagonal blocks.  PY32, cam_lm and G32 are in camera order, so the
+// CTA of camera j reads and writes rows cam_ptr[j] .. cam_ptr[j + 1] contiguously.
 __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
-    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
-    const int32_t* __restrict__ op, const float* __restrict__ aux32, const float* __restrict__ PY32,
-    const float* __restrict__ L32, const double* __restrict__ dadd, double* __restrict__ Sd,
-    float* __restrict__ G32) {
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_lm,
+    const float* __restrict__ aux32, const float* __restrict__ PY32, const float* __restrict__ L32,
+    const double* __restrict__ dadd, double* __restrict__ Sd, float* __restrict__ G32) {
     constexpr int NW = kDiagThreads / 32;
-    __shared__ double red[NW][45];
+    __shared__ FloatPair red[NW][45];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
         float ax[24];
@@ -796,11 +809,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
 #pragma unroll
         for (int k = 0; k < 45; ++k) acc[k] = 0.f;
         for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
-            const int64_t o = cam_obs[q];
-            const int64_t l = op[o];
+            const int64_t l = cam_lm[q];
             float PY[6], Lp[6], jc[18], jl[6], A[2][3];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * o + k);
+            for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * q + k);
 #pragma unroll
             for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
             bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
@@ -809,7 +821,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
             const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
             const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
             // G_o row-major 9x3, stored as three parts of rows 3P..3P+2 at stride kG32Part (16-byte aligned)
-            float* g = G32 + kG32Row * o;
+            float* g = G32 + kG32Row * q;
 #pragma unroll
             for (int a = 0; a < 9; ++a)
 #pragma unroll
@@ -827,9 +839,13 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
 #pragma unroll
                 for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
         }
+        // the threads' sums meet as float pairs (error-free two-sums on the float32 pipe) in a fixed
+        // tree: across the warp, then across the warps in warp order; float64 only at the end
 #pragma unroll
         for (int k = 0; k < 45; ++k) {
-            const double v = warp_sum(double(acc[k]));
+            FloatPair v{acc[k], 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v.add(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
             if (lane == 0) red[wid][k] = v;
         }
         __syncthreads();
@@ -837,10 +853,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
             const int a = threadIdx.x / 9, b = threadIdx.x % 9;
             const int lo = a < b ? a : b, hi = a < b ? b : a;
             const int idx = lo * 9 - lo * (lo - 1) / 2 + (hi - lo);
-            double v = ((red[0][idx] + red[1][idx]) + (red[2][idx] + red[3][idx])) +
-                       ((red[4][idx] + red[5][idx]) + (red[6][idx] + red[7][idx]));
-            if (a == b) v += dadd[9 * int64_t(j) + a];
-            Sd[81 * int64_t(j) + threadIdx.x] = v;
+            FloatPair v = red[0][idx];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) v.add(red[w][idx].hi, red[w][idx].lo);
+            double d = double(v.hi) + double(v.lo);
+            if (a == b) d += dadd[9 * int64_t(j) + a];
+            Sd[81 * int64_t(j) + threadIdx.x] = d;
         }
         __syncthreads();
     }
@@ -993,17 +1011,19 @@ __global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, doubl
             for (int a = 0; a < 9; ++a)
                 for (int b = 0; b < 9; ++b) L[9 * a + b] *= sc[a] * sc[b];
         }
+        // Cholesky with reciprocal square roots: L[c][c] keeps 1 / l_cc (the exact float64 divisions
+        // and square roots are long dependent chains on this GPU's narrow float64 pipe)
         bool ok = true;
         for (int c = 0; c < 9; ++c) {
             double d = L[9 * c + c];
             for (int k = 0; k < c; ++k) d -= L[9 * c + k] * L[9 * c + k];
             if (!(d > 0.0)) { ok = false; d = 1.0; }
-            double lc = sqrt(d);
-            L[9 * c + c] = lc;
+            const double ic = rsqrt_fast(d);
+            L[9 * c + c] = ic;
             for (int a = c + 1; a < 9; ++a) {
                 double v = L[9 * a + c];
                 for (int k = 0; k < c; ++k) v -= L[9 * a + k] * L[9 * c + k];
-                L[9 * a + c] = v / lc;
+                L[9 * a + c] = v * ic;
             }
         }
         if (!ok) atomicExch(status, BA_ERR_SINGULAR);
@@ -1011,11 +1031,11 @@ __global__ void k_block_jacobi(int32_t n_c, const double* __restrict__ Sd, doubl
         double Li[81];
         for (int k = 0; k < 81; ++k) Li[k] = 0.0;
         for (int c = 0; c < 9; ++c) {
-            Li[9 * c + c] = 1.0 / L[9 * c + c];
+            Li[9 * c + c] = L[9 * c + c];
             for (int a = c + 1; a < 9; ++a) {
                 double v = 0.0;
                 for (int k = c; k < a; ++k) v -= L[9 * a + k] * Li[9 * k + c];
-                Li[9 * a + c] = v / L[9 * a + a];
+                Li[9 * a + c] = v * L[9 * a + a];
             }
         }
         double* D = Dinv + 81 * j;
@@ -1141,7 +1161,7 @@ void launch_project(int64_t n_o, const double* cams, const double* pts, const in
 
 void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
     k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.aux, y.pts, s.obs_cam, s.obs_pt,
-                                                                 s.obs_xy, y.r, y.Jc, y.Jl, y.PY32);
+                                                                 s.obs_xy, y.r, y.Jc, y.Jl, y.PY32, s.cpos);
 }
 
 void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
@@ -1175,8 +1195,8 @@ void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, c
 }
 
 void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st) {
-    k_schur_diag32<<<cam_grid(s), kDiagThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.aux32, y.PY32,
-                                                         y.L32, y.dadd, y.Sd, y.G32);
+    k_schur_diag32<<<cam_grid(s), kDiagThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_lm, y.aux32, y.PY32, y.L32, y.dadd,
+                                                         y.Sd, y.G32);
 }
 
 void launch_schur(const Structure& s, System& y, cudaStream_t st) {
@@ -1190,7 +1210,7 @@ void launch_schur(const Structure& s, System& y, cudaStream_t st) {
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
     if (s.n_up > 0)
         k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_dst, s.up_mdst, s.up_udst, s.up_pair_ptr, s.pairs, s.obs_cam, y.lam32, y.G32, y.S32,
+            s.n_up, s.up_dst, s.up_mdst, s.up_udst, s.up_pair_ptr, s.pairs, s.up_cams, y.lam32, y.G32, y.S32,
             y.S32u);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32, s.tile_ptr_u, y.S32u);
