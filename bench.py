@@ -593,7 +593,8 @@ def run_kernel_case(a):
     from paper_2110_04015_gb300 import problem
 
     sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
-    p = problem.from_scene(sc, precision=a.precision, host_loop=int(a.host_loop))
+    # work items of 256 blocks: what ba_autotune picks for this problem
+    p = problem.from_scene(sc, precision=a.precision, host_loop=int(a.host_loop), item_blocks=256)
     p.ba_build_normal(LAMBDA)
     if a.kernel_case == "build":
         import torch as _t

@@ -308,7 +308,14 @@ typedef enum ba_kernel {
     BA_KERNEL_SCHUR = 1,       /* the S_jk = delta U_j - sum G G^T block build (Eq. 13); mixed precision:
                                   the float32 diagonal blocks and G rows, the preconditioner and the
                                   scaled off-diagonal blocks */
-    BA_KERNEL_LINEARIZE = 2    /* residuals and Jacobians of every observation (Eqs. 2-4) */
+    BA_KERNEL_LINEARIZE = 2,   /* residuals and Jacobians of every observation (Eqs. 2-4) */
+    /* the build's kernels one by one (Eqs. 8-14), each recomputing what the last build wrote: */
+    BA_KERNEL_LANDMARKS = 3,   /* per landmark: V_lambda, its Cholesky factor and b_l */
+    BA_KERNEL_CAM_RHS = 4,     /* per camera: b~ (Eq. 14) and the damping; FP64 also U_lambda, b_p and
+                                  the observations' G = W L^-T */
+    BA_KERNEL_SCHUR_DIAG = 5,  /* the diagonal blocks S_jj; mixed precision also the float32 G rows */
+    BA_KERNEL_SCHUR_OFF = 6,   /* the off-diagonal blocks S_jk, j != k, and the diagonal put in place */
+    BA_KERNEL_BLOCK_JACOBI = 7 /* the preconditioner's inverse blocks (mixed precision: of the scaled S) */
 } ba_kernel;
 
 /*

@@ -109,7 +109,8 @@ _SIGNATURES = {
     "ba_gnn_launch_count": (_I32, [_P, _P]),
 }
 BA_STATIC_MAX_CAMS = 65536
-KERNEL = {"spmv": 0, "schur": 1, "linearize": 2}
+KERNEL = {"spmv": 0, "schur": 1, "linearize": 2, "landmarks": 3, "cam_rhs": 4, "schur_diag": 5, "schur_off": 6,
+          "block_jacobi": 7}
 
 _lib = None
 

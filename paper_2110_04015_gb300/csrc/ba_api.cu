@@ -307,6 +307,16 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         s.cpos = upload(p, cpos);
         s.cam_lm = upload(p, cam_lm);
         s.up_cams = upload(p, ucams);
+        // the upper blocks by decreasing pair count, stable (counting sort)
+        if (n_up >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
+        int64_t pmax = 0;
+        for (int64_t u = 0; u < n_up; ++u) pmax = std::max(pmax, up_pp[u + 1] - up_pp[u]);
+        std::vector<int64_t> pc(size_t(pmax) + 2, 0);
+        for (int64_t u = 0; u < n_up; ++u) pc[size_t(pmax - (up_pp[u + 1] - up_pp[u])) + 1]++;
+        for (size_t k = 1; k < pc.size(); ++k) pc[k] += pc[k - 1];
+        std::vector<int32_t> uorder(n_up > 0 ? n_up : 1);
+        for (int64_t u = 0; u < n_up; ++u) uorder[pc[size_t(pmax - (up_pp[u + 1] - up_pp[u]))]++] = int32_t(u);
+        s.up_order = upload(p, uorder);
     }
     s.pairs = upload(p, pr);
     if (p->opt.precision == BA_PRECISION_MIXED) {
@@ -320,7 +330,7 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
             col_u[row_u[j]] = j;
             tile_u[j + 1] = tile_u[j] + (row_u[j + 1] - row_u[j] + ba::kTile - 1) / ba::kTile;
         }
-        std::vector<int64_t> udst(n_up), qpos(n_up);
+        std::vector<int64_t> udst(n_up);
         {
             std::vector<int64_t> ufill(n_c);
             for (int32_t j = 0; j < n_c; ++j) ufill[j] = row_u[j] + 1;
@@ -328,7 +338,6 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
                 const int32_t j = up_j[u];
                 const int64_t pos = ufill[j]++;
                 col_u[pos] = up_k[u];
-                qpos[u] = pos;
                 udst[u] = (tile_u[j] * ba::kTile + (pos - row_u[j])) * 81;
             }
         }
@@ -339,9 +348,9 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         std::vector<int32_t> qlist(n_up > 0 ? n_up : 1);
         {
             std::vector<int64_t> fill(qptr.begin(), qptr.end() - 1);
-            for (int64_t u = 0; u < n_up; ++u) qlist[fill[up_k[u]]++] = int32_t(qpos[u]);
+            for (int64_t u = 0; u < n_up; ++u) qlist[fill[up_k[u]]++] = int32_t(udst[u] / 81);
         }
-        if (nnzb_u >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
+        if (tile_u[n_c] * ba::kTile >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
         s.nnzb_u = nnzb_u;
         s.row_ptr_u = upload(p, row_u);
         s.col_u = upload(p, col_u);
@@ -433,7 +442,7 @@ void do_build(ba_problem* p, double lambda) {
         ba::launch_schur_diag32(s, y, st);
         ba::launch_block_jacobi(s, y, st);
         ba::launch_schur_mixed(s, y, st);    // off-diagonal and diagonal blocks of S^ (float32)
-        p->launches += 9;
+        p->launches += 8;
     }
     check_launch();
     int status = 0;
@@ -872,6 +881,12 @@ int ba_get_preconditioner(const ba_problem* pc, double* Dinv) {
     if (!p || !Dinv) return BA_ERR_INVALID_ARG;
     try {
         if (!p->y.built) throw Error(BA_ERR_STATE, "nothing built");
+        if (p->opt.precision == BA_PRECISION_MIXED) {
+            // the mixed build inverts only the scaled blocks; D^{-1} of S itself is formed here
+            ba::launch_block_jacobi_plain(p->s, p->y, p->stream);
+            check_launch();
+            ++p->launches;
+        }
         copy_out(Dinv, p->y.Dinv, sizeof(double) * 81 * size_t(p->s.n_c), p->stream);
         return BA_OK;
     } catch (const Error& e) {
@@ -1121,7 +1136,8 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
                                      p->opt.item_blocks, p->opt.spmv_config, st);
             return BA_OK;
         }
-        if (kernel != BA_KERNEL_SCHUR && kernel != BA_KERNEL_LINEARIZE) throw Error(BA_ERR_INVALID_ARG, "unknown kernel");
+        if (kernel < BA_KERNEL_SCHUR || kernel > BA_KERNEL_BLOCK_JACOBI) throw Error(BA_ERR_INVALID_ARG, "unknown kernel");
+        const bool fp64 = p->opt.precision == BA_PRECISION_FP64;
         cudaEvent_t a, b;
         BA_CUDA_TRY(cudaEventCreate(&a));
         BA_CUDA_TRY(cudaEventCreate(&b));
@@ -1129,18 +1145,43 @@ int ba_time_kernel(ba_problem* p, int32_t kernel, int32_t reps, double* ms) {
         for (int k = 0; k < reps; ++k) {
             ba::flush_l2(st);
             BA_CUDA_TRY(cudaEventRecord(a, st));
-            if (kernel == BA_KERNEL_SCHUR) {
-                if (p->opt.precision == BA_PRECISION_FP64) ba::launch_schur(p->s, p->y, st);
-                else {
-                    // the float32 Schur complement from the float32 Jacobians: diagonal blocks and G
-                    // rows, Lam and the preconditioner, off-diagonal blocks
-                    ba::launch_schur_diag32(p->s, p->y, st);
+            switch (kernel) {
+                case BA_KERNEL_SCHUR:
+                    if (fp64) ba::launch_schur(p->s, p->y, st);
+                    else {
+                        // the float32 Schur complement from the float32 Jacobians: diagonal blocks and G
+                        // rows, Lam and the preconditioner, off-diagonal blocks
+                        ba::launch_schur_diag32(p->s, p->y, st);
+                        ba::launch_block_jacobi(p->s, p->y, st);
+                        ba::launch_schur_mixed(p->s, p->y, st);
+                    }
+                    break;
+                case BA_KERNEL_LINEARIZE:
+                    ba::launch_cam_prep(p->s, p->y, st);
+                    ba::launch_linearize(p->s, p->y, st);
+                    break;
+                case BA_KERNEL_LANDMARKS:
+                    ba::launch_landmarks(p->s, p->y, p->opt.damping, p->y.lambda, st);
+                    break;
+                case BA_KERNEL_CAM_RHS:
+                    if (fp64) {
+                        ba::launch_obs_G(p->s, p->y, st);
+                        ba::launch_cameras(p->s, p->y, p->opt.damping, p->y.lambda, st);
+                    } else {
+                        ba::launch_cam_rhs(p->s, p->y, p->opt.damping, p->y.lambda, st);
+                    }
+                    break;
+                case BA_KERNEL_SCHUR_DIAG:
+                    if (fp64) ba::launch_schur_diag(p->s, p->y, st);
+                    else ba::launch_schur_diag32(p->s, p->y, st);
+                    break;
+                case BA_KERNEL_SCHUR_OFF:
+                    if (fp64) ba::launch_schur(p->s, p->y, st);
+                    else ba::launch_schur_mixed(p->s, p->y, st);
+                    break;
+                default:
                     ba::launch_block_jacobi(p->s, p->y, st);
-                    ba::launch_schur_mixed(p->s, p->y, st);
-                }
-            } else {
-                ba::launch_cam_prep(p->s, p->y, st);
-                ba::launch_linearize(p->s, p->y, st);
+                    break;
             }
             BA_CUDA_TRY(cudaEventRecord(b, st));
             BA_CUDA_TRY(cudaEventSynchronize(b));

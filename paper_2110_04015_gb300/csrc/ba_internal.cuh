@@ -88,6 +88,7 @@ struct Structure {
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark (mixed precision:
                                   // their camera-order positions, where the float32 G rows are kept)
     int2* up_cams = nullptr;      // n_up (mixed precision): the cameras (j, k) of each upper block
+    int32_t* up_order = nullptr;  // n_up (mixed precision): the upper blocks by decreasing pair count
     int32_t* cpos = nullptr;      // n_o (mixed precision): camera-order position of each point-order slot
     int32_t* cam_lm = nullptr;    // n_o (mixed precision): landmark of each camera-order position
     // upper triangle of S (mixed precision's one-column products): row j holds S_jj, then S_jk, k > j,
@@ -98,7 +99,8 @@ struct Structure {
     int64_t* tile_ptr_u = nullptr;   // n_c + 1
     int64_t* up_udst = nullptr;      // n_up: element offset of block (j, k) in the tiled upper S
     int64_t* qptr = nullptr;         // n_c + 1
-    int32_t* qlist = nullptr;        // nnzb_u - n_c: upper-pattern indices of the blocks (j, k), j < k, by k
+    int32_t* qlist = nullptr;        // nnzb_u - n_c: tiled indices (32 tile_ptr_u[j] + position in row j)
+                                     // of the blocks (j, k), j < k, by k
     // batch: problem b owns cameras [h_cam_off[b], h_cam_off[b + 1]); one problem: {0, n_c}
     std::vector<int32_t> h_cam_off;
     // host copies of the pattern (work lists of the block-sparse products are built from them)
@@ -172,6 +174,7 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st);
 void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st);
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st);
+void launch_block_jacobi_plain(const Structure& s, System& y, cudaStream_t st);
 void launch_to_float(const double* in, float* out, int64_t n, cudaStream_t st);
 void launch_back_substitute(const Structure& s, const System& y, const double* dxp, double* dxl,
                             cudaStream_t st);

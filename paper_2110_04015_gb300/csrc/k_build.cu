@@ -11,11 +11,10 @@
 //                   three entries per lane (_rows), float32: a 3x3 sub-block and a third of the
 //                   pairs per lane (_sub)
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
-//   k_scaled_g32    float32 rows of Lam G for the scaled float32 system
-//   k_implicit_*    the float64 product S x = U x - G (G^T x) without an explicit S
 // Mixed precision builds no float64 U, G or S_jj: float64 keeps r, J_p, J_l (for b~ and the true
 // residual S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x, k_jres_*), and the
-// float32 system comes from float32 Jacobians recomputed from float32 parameters:
+// float32 system comes from float32 Jacobians formed from P = R X + t and R X, which k_linearize
+// keeps in float32 (camera order):
 //   k_cam_rhs       one CTA per camera (float64): b~ = sum_o J_p^T (r - J_l V^-1 b_l), lambda D_p
 //   k_schur_diag32  one CTA per camera (float32): S_jj = sum_o J_p^T (I - A A^T) J_p + lambda D_p,
 //                   A = J_l L^{-T} (each term is positive semi-definite: no cancellation)
@@ -595,99 +594,119 @@ __device__ __forceinline__ void lds9(const float* p, float* v) {
     v[8] = p[8];
 }
 
-// Off-diagonal blocks in float32: one warp per upper block (j < k), S_jk = - sum over the
-// observation pairs (o_j, o_k) of its landmarks of G_oj G_ok^T, written to (j, k) and transposed to
-// (k, j).  Lane 9 g + 3 A + B (g < 3) accumulates the 3x3 sub-block at rows 3A.., columns 3B.. over the
-// pairs p = g (mod 3): it needs rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok, nine consecutive
-// values each, so one pair costs the lane two runs of vector shared loads for 27 fused
-// multiply-adds.  The warp takes the pairs kChunk at a time and copies the two G rows of every pair
-// of the chunk into shared memory with 16-byte asynchronous copies (a row is three 9-value parts on
-// 16-byte boundaries, laid out in shared memory as in global memory: 9 copies per row, all in flight
-// together, no staging registers; lane p fetches the indices of pair p).  The three slices are added
-// in slice order through shuffles,
-// the block is assembled in shared memory and written with coalesced stores to (j, k) and,
-// transposed, to (k, j), and to (j, k) of the upper-triangle copy Su.  The float32 system is the scaled
-// Lam S Lam: each block is multiplied by Lam_j (rows) and Lam_k (columns) after its sum.
+// Off-diagonal blocks in float32: S_jk = - Lam_j (sum over the observation pairs (o_j, o_k) of the
+// landmarks j and k share of G_oj G_ok^T) Lam_k, written to (j, k), transposed to (k, j), and to the
+// upper-triangle copy.  Most blocks have few pairs (a dense problem of 1000 cameras: 7.5 on average,
+// 87 % of the blocks 5 or fewer), so a warp takes three blocks at once, one per group of 9 lanes
+// (lanes 27..31 idle): lane 9 g + 3 A + B sums the 3x3 sub-block at rows 3A.., columns 3B.. of its
+// group's block over all its pairs, from rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok (nine
+// consecutive values each: vector shared loads for 27 fused multiply-adds).  Blocks go in
+// decreasing pair count (up_order), so the three blocks of a warp have about as many pairs and the
+// largest start first.  A group copies the G rows of its pairs into shared memory kOffChunk pairs at
+// a time with 16-byte asynchronous copies, double-buffered (lane 3A + B copies piece 3A + B of
+// both rows of every pair; a row is three 9-value parts on 16-byte boundaries).  The three blocks
+// then meet in shared memory, and the warp writes their 3 x 81 values per destination together.
+constexpr int kOffChunk = 3;
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 5) k_schur_off_sub(
-    int64_t n_up, const int64_t* __restrict__ up_dst, const int64_t* __restrict__ up_mdst,
-    const int64_t* __restrict__ up_udst, const int64_t* __restrict__ pair_ptr, const int2* __restrict__ pairs,
-    const int2* __restrict__ up_cams, const T* __restrict__ lam, const T* __restrict__ G, T* __restrict__ S,
-    T* __restrict__ Su) {
+__global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
+    int64_t n_up, const int32_t* __restrict__ up_order, const int64_t* __restrict__ up_dst,
+    const int64_t* __restrict__ up_mdst, const int64_t* __restrict__ up_udst, const int64_t* __restrict__ pair_ptr,
+    const int2* __restrict__ pairs, const int2* __restrict__ up_cams, const T* __restrict__ lam,
+    const T* __restrict__ G, T* __restrict__ S, T* __restrict__ Su) {
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
-    constexpr int kChunk = 12;                         // a multiple of the 3 pair slices
-    constexpr int kPart = kG32Part;
-    __shared__ __align__(16) T sg[kThreads / 32][kChunk][2][kG32Row];
-    __shared__ T sb[kThreads / 32][81];
+    constexpr int kBuf = kOffChunk * 2 * kG32Row;      // one buffer of a group: the chunk's row pairs
+    __shared__ __align__(16) T sg[kThreads / 32][3][2 * kBuf];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t nw = gstride() >> 5;
-    const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31 only load
+    const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31
     const int A = sub / 3, B = sub - 3 * (sub / 3);
-    // copy role of lanes 0..17: side (row of o_j or o_k) and 16-byte piece of the 36-float row,
-    // piece c = part c / 3 at stride kPart, values 4 (c % 3) .. + 3
-    const int cside = lane >= 9 ? 1 : 0, cpiece = lane - 9 * cside;
-    const int coff = (cpiece / 3) * kPart + (cpiece % 3) * 4;
-    for (int64_t u = gtid() >> 5; u < n_up; u += nw) {
+    const int coff = A * kG32Part + B * 4;             // piece `sub` of a 36-float row
+    T* const area = &sg[wid][g < 3 ? g : 0][0];
+    const int64_t n_tri = (n_up + 2) / 3;
+    const int64_t nw = gstride() >> 5;
+    for (int64_t w = gtid() >> 5; w < n_tri; w += nw) {
+        const int64_t slot = 3 * w + g;
+        const bool has = g < 3 && slot < n_up;
+        const int64_t u = has ? up_order[slot] : 0;
+        const int64_t pb = has ? pair_ptr[u] : 0, pe = has ? pair_ptr[u + 1] : 0;
+        const int nch = int((pe - pb + kOffChunk - 1) / kOffChunk);
+        int nmax = nch;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        // chunk c of this group's pairs into buffer c & 1 (nothing past the group's last chunk)
+        auto issue = [&](int c) {
+            if (c < nch) {
+                T* buf = area + (c & 1) * kBuf;
+                const int64_t q0 = pb + int64_t(c) * kOffChunk;
+                const int n = pe - q0 < kOffChunk ? int(pe - q0) : kOffChunk;
+                for (int i = 0; i < n; ++i) {
+                    const int2 pr = pairs[q0 + i];
+                    cp_async16(buf + (2 * i) * kG32Row + coff, G + int64_t(kG32Row) * pr.x + coff);
+                    cp_async16(buf + (2 * i + 1) * kG32Row + coff, G + int64_t(kG32Row) * pr.y + coff);
+                }
+            }
+            cp_async_commit();
+        };
         T acc[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) acc[i] = T(0);
-        const int64_t pb = pair_ptr[u], pe = pair_ptr[u + 1];
-        for (int64_t q = pb; q < pe; q += kChunk) {
-            const int np = int(pe - q < kChunk ? pe - q : kChunk);
-            int2 pr = make_int2(0, 0);
-            if (lane < np) pr = pairs[q + lane];
-            __syncwarp();   // every lane is done with the previous chunk's staging area
-            // lanes 0..17 copy the 16-byte piece `cpiece` of side `cside` of every pair of the chunk
-            // (np is the same in every lane: the loop stops at the chunk's last pair)
-#pragma unroll 4
-            for (int p = 0; p < np; ++p) {
-                const int ox = __shfl_sync(0xffffffffu, pr.x, p);
-                const int oy = __shfl_sync(0xffffffffu, pr.y, p);
-                if (lane < 18) cp_async16(&sg[wid][p][cside][coff], G + int64_t(kG32Row) * (cside ? oy : ox) + coff);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            if (g < 3) {
-                for (int p = g; p < np; p += 3) {
+        issue(0);
+        for (int c = 0; c < nmax; ++c) {
+            issue(c + 1);
+            cp_async_wait_prev();   // this lane's copies of chunk c have landed
+            __syncwarp();           // and every lane's
+            if (c < nch) {
+                const T* buf = area + (c & 1) * kBuf;
+                const int64_t q0 = pb + int64_t(c) * kOffChunk;
+                const int n = pe - q0 < kOffChunk ? int(pe - q0) : kOffChunk;
+                for (int i = 0; i < n; ++i) {
                     T x[9], y[9];
-                    lds9(&sg[wid][p][0][A * kPart], x);
-                    lds9(&sg[wid][p][1][B * kPart], y);
+                    lds9(buf + (2 * i) * kG32Row + A * kG32Part, x);
+                    lds9(buf + (2 * i + 1) * kG32Row + B * kG32Part, y);
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            acc[3 * r + c] += x[3 * r] * y[3 * c] + x[3 * r + 1] * y[3 * c + 1] + x[3 * r + 2] * y[3 * c + 2];
+                        for (int cc = 0; cc < 3; ++cc)
+                            acc[3 * r + cc] += x[3 * r] * y[3 * cc] + x[3 * r + 1] * y[3 * cc + 1] + x[3 * r + 2] * y[3 * cc + 2];
                 }
             }
+            __syncwarp();           // buffer c & 1 is refilled by issue(c + 2)
         }
-        // slices 1 and 2 (lanes 9..26) onto slice 0 (lanes 0..8)
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const T v1 = __shfl_down_sync(0xffffffffu, acc[i], 9);
-            const T v2 = __shfl_down_sync(0xffffffffu, acc[i], 18);
-            acc[i] = (acc[i] + v1) + v2;
-        }
-        if (lane < 9) {
-            // rows scale by Lam_j, columns by Lam_k
+        // the group's block, scaled (rows by Lam_j, columns by Lam_k) and negated, into its area
+        int64_t dj = 0, dk = 0, du = 0;
+        if (has) {
             const int2 jk = up_cams[u];
             const T* lj = lam + 9 * int64_t(jk.x);
             const T* lk = lam + 9 * int64_t(jk.y);
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    sb[wid][(3 * A + r) * 9 + 3 * B + c] = acc[3 * r + c] * lj[3 * A + r] * lk[3 * B + c];
+                for (int cc = 0; cc < 3; ++cc)
+                    area[(3 * A + r) * 9 + 3 * B + cc] = -(acc[3 * r + cc] * lj[3 * A + r] * lk[3 * B + cc]);
+            dj = up_dst[u];
+            dk = up_mdst[u];
+            du = up_udst[u];
         }
         __syncwarp();
-        const int64_t dj = up_dst[u], dk = up_mdst[u], du = up_udst[u];
-        for (int e = lane; e < 81; e += 32) {
-            const T v = -sb[wid][e];
-            S[dj + e] = v;
-            Su[du + e] = v;
-        }
-        for (int e = lane; e < 81; e += 32) {
-            const int b = e / 9, a = e - 9 * (e / 9);   // entry e = 9 b + a of (k, j) is (a, b) of (j, k)
-            S[dk + e] = -sb[wid][9 * a + b];
+        // the warp writes the three blocks: entry e of 3 x 81 is entry e % 81 of group e / 81's block
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = lane + 32 * it;
+            const int gg = e < 243 ? e / 81 : 0, ee = e - 81 * gg;
+            const int64_t ej = __shfl_sync(0xffffffffu, dj, 9 * gg);
+            const int64_t ek = __shfl_sync(0xffffffffu, dk, 9 * gg);
+            const int64_t eu = __shfl_sync(0xffffffffu, du, 9 * gg);
+            if (e < 243 && 3 * w + gg < n_up) {
+                const T* blk = &sg[wid][gg][0];
+                const T v = blk[ee];
+                S[ej + ee] = v;
+                Su[eu + ee] = v;
+                const int b = ee / 9, a = ee - 9 * (ee / 9);   // entry 9 b + a of (k, j) is (a, b) of (j, k)
+                S[ek + ee] = blk[9 * a + b];
+            }
         }
         __syncwarp();
     }
@@ -772,35 +791,26 @@ __device__ __forceinline__ void rows_A(const float* jl, const float* Lp, float (
 }
 
 constexpr int kDiagThreads = 256;
-
-// A float32 sum carried as an unevaluated pair hi + lo: adding (h, l) is an error-free two-sum of
-// the high parts with the low parts added, about 48 significant bits without float64 arithmetic.
-struct FloatPair {
-    float hi, lo;
-    __device__ __forceinline__ void add(float h, float l) {
-        const float t = __fadd_rn(hi, h);
-        const float bv = __fsub_rn(t, hi);
-        const float te = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(h, bv));
-        hi = t;
-        lo = __fadd_rn(lo, __fadd_rn(te, l));
-    }
-};
+// the 45 sums of S_jj's upper triangle across the CTA: 5 threads per sum, each adding a 52-thread
+// slice of the staged partials (the last slice 48)
+constexpr int kDiagSlices = 5, kDiagSlice = 52;
 
 // Mixed precision, one CTA per camera: S_jj = sum_{o in j} J_p^T (I - A A^T) J_p + lambda D_p (Eq. 13 on
 // the diagonal: U_j - sum_o G_o G_o^T with G_o = J_p^T A_o), from float32 Jacobians formed in float32
 // from the camera and the float32 point in the camera frame.  I - A A^T = I - J_l V^-1 J_l^T is
-// positive semi-definite, so the terms add without cancellation; each thread sums its observations
-// in float32, the threads' sums are added in float64 (fixed order), and the float64 damping is added
-// last.  Sd receives float64.  The same pass writes G_o = J_p^T A_o (9x3, unscaled) of every
+// positive semi-definite, so the terms add without cancellation: an entry's rounding errors are at
+// most a few float32 units of sqrt(S_aa S_bb) (each term obeys |t_ab| <= sqrt(t_aa t_bb)), the
+// accuracy of the float32 system.  Each thread sums its observations, the threads' partials meet in
+// shared memory and are added in a fixed order (slices, then the slices' sums), and the float64
+// damping is added last.  Sd receives float64.  The same pass writes G_o = J_p^T A_o (9x3, unscaled) of every
 // observation to G32 for the off-diagonal blocks.  PY32, cam_lm and G32 are in camera order, so the
 // CTA of camera j reads and writes rows cam_ptr[j] .. cam_ptr[j + 1] contiguously.
 __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
     int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_lm,
     const float* __restrict__ aux32, const float* __restrict__ PY32, const float* __restrict__ L32,
     const double* __restrict__ dadd, double* __restrict__ Sd, float* __restrict__ G32) {
-    constexpr int NW = kDiagThreads / 32;
-    __shared__ FloatPair red[NW][45];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ float stage[45][kDiagThreads + 1];
+    __shared__ float slice[45][kDiagSlices];
     for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
         float ax[24];
 #pragma unroll
@@ -839,24 +849,29 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
 #pragma unroll
                 for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
         }
-        // the threads' sums meet as float pairs (error-free two-sums on the float32 pipe) in a fixed
-        // tree: across the warp, then across the warps in warp order; float64 only at the end
+        // the threads' partials: staged (stride kDiagThreads + 1 keeps the column reads apart in the
+        // banks), 5 slices per entry with 4 interleaved sums each, then the slices in order
 #pragma unroll
-        for (int k = 0; k < 45; ++k) {
-            FloatPair v{acc[k], 0.f};
+        for (int k = 0; k < 45; ++k) stage[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        if (threadIdx.x < 45 * kDiagSlices) {
+            const int k = threadIdx.x / kDiagSlices, sl = threadIdx.x % kDiagSlices;
+            const int t0 = sl * kDiagSlice, t1 = min(t0 + kDiagSlice, kDiagThreads);
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int t = t0; t < t1; t += 4)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v.add(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-            if (lane == 0) red[wid][k] = v;
+                for (int u = 0; u < 4; ++u) s4[u] += stage[k][t + u];
+            slice[k][sl] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
         __syncthreads();
         if (threadIdx.x < 81) {
             const int a = threadIdx.x / 9, b = threadIdx.x % 9;
             const int lo = a < b ? a : b, hi = a < b ? b : a;
             const int idx = lo * 9 - lo * (lo - 1) / 2 + (hi - lo);
-            FloatPair v = red[0][idx];
+            float v = slice[idx][0];
 #pragma unroll
-            for (int w = 1; w < NW; ++w) v.add(red[w][idx].hi, red[w][idx].lo);
-            double d = double(v.hi) + double(v.lo);
+            for (int sl = 1; sl < kDiagSlices; ++sl) v += slice[idx][sl];
+            double d = double(v);
             if (a == b) d += dadd[9 * int64_t(j) + a];
             Sd[81 * int64_t(j) + threadIdx.x] = d;
         }
@@ -1209,9 +1224,9 @@ void launch_schur(const Structure& s, System& y, cudaStream_t st) {
 
 void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
     if (s.n_up > 0)
-        k_schur_off_sub<float><<<grid_for(s.n_up * 32, kThreads), kThreads, 0, st>>>(
-            s.n_up, s.up_dst, s.up_mdst, s.up_udst, s.up_pair_ptr, s.pairs, s.up_cams, y.lam32, y.G32, y.S32,
-            y.S32u);
+        k_schur_off_sub<float><<<grid_for((s.n_up + 2) / 3 * 32, kThreads), kThreads, 0, st>>>(
+            s.n_up, s.up_order, s.up_dst, s.up_mdst, s.up_udst, s.up_pair_ptr, s.pairs, s.up_cams, y.lam32, y.G32,
+            y.S32, y.S32u);
     k_put_diag<float><<<grid_for(int64_t(s.n_c) * 81, kThreads), kThreads, 0, st>>>(
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32, s.tile_ptr_u, y.S32u);
 }
@@ -1228,9 +1243,15 @@ void launch_cam_prep(const Structure& s, System& y, cudaStream_t st) {
     k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux, y.aux32);
 }
 
+// Float64: D^{-1}.  Mixed precision: Lam and the inverse blocks of the scaled system only (its solves
+// use no other; launch_block_jacobi_plain forms D^{-1} when it is asked for).
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st) {
-    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dinv, nullptr, nullptr, y.status);
     if (y.S32) k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dhat, y.lam, y.lam32, y.status);
+    else launch_block_jacobi_plain(s, y, st);
+}
+
+void launch_block_jacobi_plain(const Structure& s, System& y, cudaStream_t st) {
+    k_block_jacobi<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.Sd, y.Dinv, nullptr, nullptr, y.status);
 }
 
 
