@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: relative residual reduction of one float32 sweep (library default)")
     ap.add_argument("--tau", type=float, default=10.0)
-    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg", "build", "pcg"],
+    ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg", "build", "pcg", "step"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
                          "400k landmarks, ~1.6M observations) and exit; 'mcg' runs one MCG solve (N = 16) "
                          "with every step local, so each iteration launches the 16-column kernels; 'build' "
@@ -117,6 +117,56 @@ SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = None
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
 # NVIDIA's nominal figure for the part is 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.06
+# Float32 FMA peak (nominal: 128 FMA per clock per SM, 152 SMs, 2.07 GHz; no measured figure).
+FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
+
+# The mixed-precision build kernel by kernel (ba_time_kernel keys), with the work of one launch in the
+# counts of the problem: o observations, l landmarks, c cameras, p observation pairs of shared landmarks
+# (the terms of the off-diagonal Schur blocks), u stored upper blocks off the diagonal.  Bytes: every
+# array element the kernel reads or writes, once (gathered rows counted once).  Operations: floating-
+# point operations per unit, FMA counted twice; for the float64 kernels and the float32 diagonal pass
+# the executed counts of an ncu capture of the 1000-camera dense build (DFMA x 2 + DADD + DMUL per
+# observation, FFMA x 2 + FADD + FMUL), for the off-diagonal blocks the algorithm's 243 FMA per pair
+# and the scaling (2 multiplies per entry of a block).
+BUILD_WORK = [
+    ("linearize", "k_cam_prep + k_linearize: r, J_p, J_l per observation (Eqs. 2-4)",
+     lambda n: 260 * n["o"] + 24 * n["l"], lambda n: 158.0 * n["o"], None),
+    ("landmarks", "k_landmarks: V_lambda, its Cholesky factor, b_l per landmark",
+     lambda n: 64 * n["o"] + 228 * n["l"], lambda n: 51.5 * n["o"], None),
+    ("cam_rhs", "k_cam_rhs: b~ (Eq. 14) and the damping per camera",
+     lambda n: 216 * n["o"] + 24 * n["l"] + 144 * n["c"], lambda n: 91.2 * n["o"], None),
+    ("schur_diag", "k_schur_diag32: S_jj and the float32 G rows (Eq. 13)",
+     lambda n: 136 * n["o"] + 24 * n["l"] + 816 * n["c"], None, lambda n: 765.0 * n["o"]),
+    ("block_jacobi", "k_block_jacobi: Lam and the inverse scaled diagonal blocks",
+     lambda n: 1400 * n["c"], None, None),
+    ("schur_off", "k_schur_off_sub + k_put_diag: the float32 blocks of Lam S Lam (Eq. 13)",
+     lambda n: 8 * n["p"] + 108 * n["o"] + 1012 * n["u"] + 1944 * n["c"], None,
+     lambda n: 486.0 * n["p"] + 162.0 * n["u"]),
+]
+
+
+def build_roofline(p, counts, peaks, reps=3):
+    """Each kernel of the mixed build timed alone (ba_time_kernel, L2 evicted before each launch),
+    against the HBM copy peak and the arithmetic peak of its precision; `bound` is the larger fraction."""
+    out = []
+    for key, what, fbytes, f64, f32 in BUILD_WORK:
+        t = p.ba_time_kernel(key, reps)
+        e = {"kernel": what, "ms_per_launch": t, "bytes_per_launch": fbytes(counts)}
+        e["achieved_gbs"] = e["bytes_per_launch"] / t / 1e6
+        e["frac_hbm"] = e["achieved_gbs"] / peaks["hbm_gbs"]
+        fr = {"hbm": e["frac_hbm"]}
+        if f64:
+            e["fp64_ops_per_launch"] = f64(counts)
+            e["achieved_fp64_tflops"] = e["fp64_ops_per_launch"] / t / 1e9
+            e["frac_fp64"] = fr["fp64"] = e["achieved_fp64_tflops"] / FP64_PEAK_TFLOPS
+        if f32:
+            e["fp32_ops_per_launch"] = f32(counts)
+            e["achieved_fp32_tflops"] = e["fp32_ops_per_launch"] / t / 1e9
+            e["frac_fp32"] = fr["fp32"] = e["achieved_fp32_tflops"] / FP32_PEAK_TFLOPS
+        e["bound"] = max(fr, key=fr.get)
+        e["frac"] = fr[e["bound"]]
+        out.append(e)
+    return out
 
 
 class ClockSampler:
@@ -465,9 +515,13 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                 "bytes_moved_model": spmv_bytes + 72 * (nnzb_u - sc.n_cams),
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
-    # build: one pair of observations of a landmark feeds 81 entries of a 9x9 block (243 FMA)
-    roof_schur = {"kernel": "float32 Schur blocks: k_scaled_g32 + k_schur_off_sub + k_put_diag (Eq. 13)",
-                  "ms_per_launch": t_schur}
+    # the build kernel by kernel (mixed precision)
+    roof_build = None
+    if a.precision == "mixed":
+        track = np.bincount(sc.obs_pt, minlength=sc.n_pts).astype(np.int64)
+        counts = {"o": sc.n_obs, "l": sc.n_pts, "c": sc.n_cams, "p": int((track * (track - 1) // 2).sum()),
+                  "u": (nnzb - sc.n_cams) // 2}
+        roof_build = {"counts": counts, "schur_ms": t_schur, "kernels": build_roofline(p, counts, peaks)}
 
     # end to end through the host-buffer API: parameters in, both solutions out
     e2e = None
@@ -575,7 +629,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                 "build_ms": T / a.steps - s_pcg["ms"] - s_mcg["ms"],
             },
             "roofline": roof,
-            "roofline_build": roof_schur,
+            "roofline_build": roof_build,
             "fp64": fp64,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -587,11 +641,28 @@ def run_ours(a, rank: int, world: int, local_rank: int):
 
 
 def run_kernel_case(a):
-    """A problem small enough for multi-pass ncu captures (S ~0.3 GB float32), larger than L2."""
+    """A problem small enough for multi-pass ncu captures (S ~0.3 GB float32), larger than L2; or
+    (`step`) two steps of the benchmark's own workload with the solve loops driven from the host, for
+    a profiler's launch list (ncu does not profile kernels in graphs with conditional nodes)."""
     import torch
 
     from paper_2110_04015_gb300 import problem
 
+    if a.kernel_case == "step":
+        gen, kw, _ = WORKLOADS[a.workload]
+        sc = synthetic.make(gen, 0, **kw)
+        p = problem.from_scene(sc, precision=a.precision, host_loop=1, item_blocks=256)
+        for rep in range(2):
+            t0 = time.perf_counter()
+            p.ba_build_normal(LAMBDA)
+            s1 = p.ba_solve_pcg(TOL, MAX_ITERS)
+            s2 = p.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
+            torch.cuda.synchronize()
+            print(json.dumps({"kernel_case": "step", "workload": a.workload, "rep": rep,
+                              "host_ms": (time.perf_counter() - t0) * 1e3, "pcg_iters": s1["iters"],
+                              "mcg_iters": s2["iters"], "mcg_local": s2["local_steps"]}), flush=True)
+        p.close()
+        return
     sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
     # work items of 256 blocks: what ba_autotune picks for this problem
     p = problem.from_scene(sc, precision=a.precision, host_loop=int(a.host_loop), item_blocks=256)

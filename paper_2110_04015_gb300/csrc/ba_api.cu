@@ -345,12 +345,12 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         std::vector<int64_t> qptr(size_t(n_c) + 1, 0);
         for (int64_t u = 0; u < n_up; ++u) qptr[up_k[u] + 1]++;
         for (int32_t k = 0; k < n_c; ++k) qptr[k + 1] += qptr[k];
-        std::vector<int32_t> qlist(n_up > 0 ? n_up : 1);
+        if (n_up >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
+        std::vector<int32_t> cslot(size_t(tile_u[n_c]) * ba::kTile, -1);
         {
             std::vector<int64_t> fill(qptr.begin(), qptr.end() - 1);
-            for (int64_t u = 0; u < n_up; ++u) qlist[fill[up_k[u]]++] = int32_t(udst[u] / 81);
+            for (int64_t u = 0; u < n_up; ++u) cslot[udst[u] / 81] = int32_t(fill[up_k[u]]++);
         }
-        if (tile_u[n_c] * ba::kTile >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
         s.nnzb_u = nnzb_u;
         s.row_ptr_u = upload(p, row_u);
         s.col_u = upload(p, col_u);
@@ -358,7 +358,7 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         s.n_tiles_u = tile_u[n_c];
         s.up_udst = upload(p, udst);
         s.qptr = upload(p, qptr);
-        s.qlist = upload(p, qlist);
+        s.cslot = upload(p, cslot);
         s.h_row_ptr_u = row_u;
         s.h_col_u = col_u;
         s.h_tile_ptr_u = tile_u;

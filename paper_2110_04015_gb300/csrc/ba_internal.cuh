@@ -92,15 +92,16 @@ struct Structure {
     int32_t* cpos = nullptr;      // n_o (mixed precision): camera-order position of each point-order slot
     int32_t* cam_lm = nullptr;    // n_o (mixed precision): landmark of each camera-order position
     // upper triangle of S (mixed precision's one-column products): row j holds S_jj, then S_jk, k > j,
-    // tiled like the full pattern; qptr/qlist list, per camera k, the stored blocks (j, k), j < k
+    // tiled like the full pattern; qptr/cslot number, per camera k, the stored blocks (j, k), j < k
     int64_t nnzb_u = 0, n_tiles_u = 0;
     int64_t* row_ptr_u = nullptr;    // n_c + 1
     int32_t* col_u = nullptr;        // nnzb_u
     int64_t* tile_ptr_u = nullptr;   // n_c + 1
     int64_t* up_udst = nullptr;      // n_up: element offset of block (j, k) in the tiled upper S
     int64_t* qptr = nullptr;         // n_c + 1
-    int32_t* qlist = nullptr;        // nnzb_u - n_c: tiled indices (32 tile_ptr_u[j] + position in row j)
-                                     // of the blocks (j, k), j < k, by k
+    int32_t* cslot = nullptr;        // n_tiles_u x 32: for the block at tiled index 32 tile_ptr_u[j] + q
+                                     // (q > 0), its slot among the blocks (j', k), j' < k, ordered by
+                                     // (k, j'): column k owns slots qptr[k] .. qptr[k + 1] - 1; -1 elsewhere
     // batch: problem b owns cameras [h_cam_off[b], h_cam_off[b + 1]); one problem: {0, n_c}
     std::vector<int32_t> h_cam_off;
     // host copies of the pattern (work lists of the block-sparse products are built from them)

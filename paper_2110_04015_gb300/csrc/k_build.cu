@@ -576,14 +576,13 @@ __global__ void __launch_bounds__(kThreads) k_schur_off_rows(
     }
 }
 
-// 16-byte asynchronous copy global -> shared (cp.async, completion awaited by cp_async_wait_all); both
+// 16-byte asynchronous copy global -> shared (cp.async, completion awaited by cp.async.wait_group); both
 // addresses 16-byte aligned.
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
                  "l"(src)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Nine consecutive values from a 16-byte aligned shared-memory address.
 __device__ __forceinline__ void lds9(const float* p, float* v) {
@@ -804,13 +803,20 @@ constexpr int kDiagSlices = 5, kDiagSlice = 52;
 // shared memory and are added in a fixed order (slices, then the slices' sums), and the float64
 // damping is added last.  Sd receives float64.  The same pass writes G_o = J_p^T A_o (9x3, unscaled) of every
 // observation to G32 for the off-diagonal blocks.  PY32, cam_lm and G32 are in camera order, so the
-// CTA of camera j reads and writes rows cam_ptr[j] .. cam_ptr[j + 1] contiguously.
+// CTA of camera j reads and writes rows cam_ptr[j] .. cam_ptr[j + 1] contiguously: a warp takes 32
+// consecutive observations, stages their G rows in shared memory and writes the 32 rows (4.6 KB) as
+// 16-byte stores (a thread writing its own row made 27 scattered 4-byte stores per observation).
 __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
     int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_lm,
     const float* __restrict__ aux32, const float* __restrict__ PY32, const float* __restrict__ L32,
     const double* __restrict__ dadd, double* __restrict__ Sd, float* __restrict__ G32) {
-    __shared__ float stage[45][kDiagThreads + 1];
+    // the partials at the end of a camera; during the observation loop the same memory stages each
+    // warp's 32 G rows (8 x 32 x 36 floats fit in 45 x 257)
+    __shared__ __align__(16) float stage[45][kDiagThreads + 1];
     __shared__ float slice[45][kDiagSlices];
+    static_assert((kDiagThreads / 32) * 32 * kG32Row <= 45 * (kDiagThreads + 1), "G staging fits");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* const grows = &stage[0][0] + wid * (32 * kG32Row);
     for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
         float ax[24];
 #pragma unroll
@@ -818,37 +824,50 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
         float acc[45];
 #pragma unroll
         for (int k = 0; k < 45; ++k) acc[k] = 0.f;
-        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
-            const int64_t l = cam_lm[q];
-            float PY[6], Lp[6], jc[18], jl[6], A[2][3];
+        const int64_t q0 = cam_ptr[j], q1 = cam_ptr[j + 1];
+        for (int64_t qw = q0 + 32 * wid; qw < q1; qw += blockDim.x) {   // warp-uniform
+            const int64_t q = qw + lane;
+            const bool act = q < q1;
+            float* g = grows + lane * kG32Row;
+            if (act) {
+                const int64_t l = cam_lm[q];
+                float PY[6], Lp[6], jc[18], jl[6], A[2][3];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * q + k);
+                for (int k = 0; k < 6; ++k) PY[k] = __ldg(PY32 + 6 * q + k);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
-            bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
-            rows_A(jl, Lp, A);
-            const float m00 = 1.f - (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
-            const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
-            const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
-            // G_o row-major 9x3, stored as three parts of rows 3P..3P+2 at stride kG32Part (16-byte aligned)
-            float* g = G32 + kG32Row * q;
+                for (int k = 0; k < 6; ++k) Lp[k] = __ldg(L32 + 6 * l + k);
+                bal_jacobian_P<float>(ax, PY + 3, PY, nullptr, nullptr, jc, jl);
+                rows_A(jl, Lp, A);
+                const float m00 = 1.f - (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
+                const float m01 = -(A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
+                const float m11 = 1.f - (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
+                // G_o row-major 9x3 as three parts of rows 3P..3P+2 at stride kG32Part (16-byte aligned)
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
+                for (int a = 0; a < 9; ++a)
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    g[(a / 3) * kG32Part + (a % 3) * 3 + c] = jc[a] * A[0][c] + jc[9 + a] * A[1][c];
-            float B0[9], B1[9];
+                    for (int c = 0; c < 3; ++c)
+                        g[(a / 3) * kG32Part + (a % 3) * 3 + c] = jc[a] * A[0][c] + jc[9 + a] * A[1][c];
+                float B0[9], B1[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                B0[a] = m00 * jc[a] + m01 * jc[9 + a];
-                B1[a] = m01 * jc[a] + m11 * jc[9 + a];
+                for (int a = 0; a < 9; ++a) {
+                    B0[a] = m00 * jc[a] + m01 * jc[9 + a];
+                    B1[a] = m01 * jc[a] + m11 * jc[9 + a];
+                }
+                int t = 0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+#pragma unroll
+                    for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
             }
-            int t = 0;
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-#pragma unroll
-                for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
+            __syncwarp();
+            // the warp's rows qw .. qw + n - 1, 9 16-byte pieces each (the padding of a part included)
+            const int n = q1 - qw < 32 ? int(q1 - qw) : 32;
+            float4* dst = reinterpret_cast<float4*>(G32 + kG32Row * qw);
+            const float4* src = reinterpret_cast<const float4*>(grows);
+            for (int i = lane; i < 9 * n; i += 32) dst[i] = src[i];
+            __syncwarp();
         }
+        __syncthreads();   // every warp is done with its G staging before the partials take the memory
         // the threads' partials: staged (stride kDiagThreads + 1 keeps the column reads apart in the
         // banks), 5 slices per entry with 4 interleaved sums each, then the slices in order
 #pragma unroll

@@ -393,13 +393,17 @@ template <> struct SpmvShape<double, 0> { static constexpr int kWarps = 4, kStag
 template <> struct SpmvShape<double, 1> { static constexpr int kWarps = 8, kStages = 1; };
 template <> struct SpmvShape<double, 2> { static constexpr int kWarps = 2, kStages = 4; };
 constexpr int kSpmvShapes = 3;
-// Shared memory of k_spmv: the warps' tile stages, then one tile's transposed terms per warp (the
-// symmetric product stages them for 16-byte stores), then the stages' barriers.
+// Shared memory of k_spmv: the warps' tile stages, then the stages' barriers.
 template <typename T, int CFG>
 constexpr size_t spmv_smem() {
-    return sizeof(T) * SpmvShape<T, CFG>::kWarps * (SpmvShape<T, CFG>::kStages * kTileElems + kTile * 9) +
+    return sizeof(T) * SpmvShape<T, CFG>::kWarps * SpmvShape<T, CFG>::kStages * kTileElems +
            sizeof(uint64_t) * SpmvShape<T, CFG>::kWarps * SpmvShape<T, CFG>::kStages;
 }
+
+// The transposed terms of the symmetric product, one slot per stored upper block: values 0..7 of slot
+// e at tb[8 e ..] (one 32-byte sector in float32, written whole by two 16-byte stores, so that L2
+// never fills a partly written sector from DRAM) and value 8 at tb[8 n_slots + e].
+constexpr int kTbHead = 8;
 
 
 // Tile cursor of a warp: the tiles of its selected items (WarpItems) in order, skipping empty
@@ -443,22 +447,21 @@ __device__ __forceinline__ void cursor_start(TileCursor& c, const ItemList& L, c
 //         (Delta and gamma of Algorithm 1, before the sum over cameras).
 // MODE 2 (Algorithm 2, width 1): y goes to column new_off of Q.
 // SYM: S is the upper triangle (row j: S_jj, then S_jk for k > j).  Each lane's block also gives the
-// transposed term S_jk^T z_j of row k, written to tb at the block's tiled index (32 tile_ptr[j] + q,
-// 9 values; a whole tile's 288 values go out as 16-byte stores through shared memory), which
-// k_spmv_col adds to row k; in MODE 1 the per-camera sums then move to k_spmv_col as well.
+// transposed term S_jk^T z_j of row k, written to slot cslot[32 tile_ptr[j] + q] of tb/tb8 (the terms
+// of column k are consecutive there, in row order), which k_spmv_col adds to row k; in MODE 1 the
+// per-camera sums then move to k_spmv_col as well.
 template <typename T, int MODE, bool ZH, bool SYM, int CFG>
 __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
     const T* __restrict__ S, const T* __restrict__ z, ItemList L, int sel, T* __restrict__ out,
-    const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl, T* __restrict__ tb) {
+    const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl, T* __restrict__ tb, T* __restrict__ tb8,
+    const int32_t* __restrict__ cslot) {
     constexpr int NW = SpmvShape<T, CFG>::kWarps, NS = SpmvShape<T, CFG>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (nothing_selected(ctl, L, sel)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* tiles = reinterpret_cast<T*>(smem_raw) + size_t(wid) * NS * kTileElems;
-    T* tstage = reinterpret_cast<T*>(smem_raw) + size_t(NW) * NS * kTileElems + wid * (kTile * 9);
-    uint64_t* bars =
-        reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * (NS * kTileElems + kTile * 9)) + wid * NS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NW * NS * kTileElems) + wid * NS;
     T* part = static_cast<T*>(L.part);
     constexpr uint32_t tile_bytes = sizeof(T) * kTileElems;
 
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
         const int64_t zoff = ZH ? hb + int64_t(MODE == 2 ? c.new_off : 0) * n : 0;
         const int64_t ooff = hb + int64_t(MODE == 1 ? 0 : (MODE == 2 ? c.new_off : c.new_off + it.seg)) * n;
         const int64_t rj = row_ptr[it.row];
-        const int64_t tb0 = SYM ? tile_ptr[it.row] * kTile : 0;
+        const int64_t tb0 = SYM ? tile_ptr[it.row] * kTile : 0;   // tiled index of the row's first block
         T acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc[a] = T(0);
@@ -508,25 +511,30 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
         for (int b = 0; b < 9; ++b) zr[b] = SYM ? z[zoff + 9 * int64_t(it.row) + b] : T(0);
         if (it.q1 > it.q0) {
             const int t0 = it.q0 >> 5, t1 = (it.q1 + 31) >> 5;
-            // the 9 entries of z this lane needs for tile t, fetched one tile ahead
+            // the 9 entries of z this lane needs for tile t (and SYM: the slot of its transposed
+            // term, -1 for none), fetched one tile ahead
             T zn[9];
+            int csn = -1;
             {
                 const int q = t0 * 32 + lane;
                 const bool in = q >= it.q0 && q < it.q1;
                 const T* zk = z + zoff + int64_t(in ? col[rj + q] : it.row) * 9;
 #pragma unroll
                 for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
+                if (SYM && in) csn = cslot[tb0 + q];
             }
             for (int t = t0; t < t1; ++t) {
                 T zv[9];
 #pragma unroll
                 for (int b = 0; b < 9; ++b) zv[b] = zn[b];
+                const int csv = csn;
                 if (t + 1 < t1) {
                     const int qn = (t + 1) * 32 + lane;
                     const bool in = qn < it.q1;
                     const T* zk = z + zoff + int64_t(in ? col[rj + qn] : it.row) * 9;
 #pragma unroll
                     for (int b = 0; b < 9; ++b) zn[b] = in ? zk[b] : T(0);
+                    csn = SYM && in ? cslot[tb0 + qn] : -1;
                 }
                 // every lane observes the phase (visibility of the copied bytes); the warp agrees
                 const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u, L.polls);
@@ -555,20 +563,17 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
                                 v[b] += sab * zr[a];
                             }
                     }
-                    // q = 0 is S_jj, whose row term covers it; its slot of tb is never read
-                    T* dst = tb + (tb0 + int64_t(t) * kTile) * 9;
-                    if (t * 32 >= it.q0 && t * 32 + 32 <= it.q1) {   // the whole tile: 16-byte stores
+                    // q = 0 is S_jj, whose row term covers it (its slot is -1)
+                    if (csv >= 0) {
+                        T* dst = tb + int64_t(csv) * kTbHead;
+                        if constexpr (sizeof(T) == 4) {
+                            reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                            reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+                        } else {
 #pragma unroll
-                        for (int b = 0; b < 9; ++b) tstage[lane * 9 + b] = v[b];
-                        __syncwarp();
-                        constexpr int n16 = kTile * 9 * int(sizeof(T)) / 16;
-                        const int4* src4 = reinterpret_cast<const int4*>(tstage);
-                        int4* dst4 = reinterpret_cast<int4*>(dst);
-#pragma unroll
-                        for (int u = lane; u < n16; u += 32) dst4[u] = src4[u];
-                    } else if (inq && q > 0) {
-#pragma unroll
-                        for (int b = 0; b < 9; ++b) dst[lane * 9 + b] = v[b];
+                            for (int b = 0; b < 8; ++b) dst[b] = v[b];
+                        }
+                        tb8[csv] = v[8];
                     }
                 } else if (inq) {
                     const T* blk = tile + lane * 81;
@@ -640,14 +645,14 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
 }
 
 // Second pass of the symmetric product: y_k += sum over the stored blocks (j, k), j < k, of their
-// transposed terms S_jk^T z_j (a fixed order: lane-strided sums in each warp's share of the list,
-// then the warps' sums in warp order), then in MODE 1 the per-camera sums q^T p and p^T r.  One CTA
-// of kColWarps warps per camera (the list of a camera holds up to n_c - 1 terms of 36 bytes, read
-// through an index); grid: CTAs x problems.
+// transposed terms S_jk^T z_j (a fixed order: lane-strided sums in each warp's share of the column's
+// slots, then the warps' sums in warp order), then in MODE 1 the per-camera sums q^T p and p^T r.
+// One CTA of kColWarps warps per camera (its slots qptr[k] .. qptr[k + 1] - 1 of tb are consecutive,
+// up to n_c - 1 of them); grid: CTAs x problems.
 constexpr int kColWarps = 8;
 template <typename T, int MODE, bool ZH>
 __global__ void __launch_bounds__(kColWarps * 32) k_spmv_col(const int64_t* __restrict__ qptr,
-                                                             const int32_t* __restrict__ qlist, const T* __restrict__ tb,
+                                                             const T* __restrict__ tb, const T* __restrict__ tb8,
                                                              const T* __restrict__ z, int sel, T* __restrict__ out,
                                                              const T* __restrict__ rvec, double* __restrict__ camdot,
                                                              const Ctl* __restrict__ ctl) {
@@ -665,19 +670,32 @@ __global__ void __launch_bounds__(kColWarps * 32) k_spmv_col(const int64_t* __re
         T acc[9];
 #pragma unroll
         for (int b = 0; b < 9; ++b) acc[b] = T(0);
-        // warp w takes entries w * 32 + lane + k * kColWarps * 32, four per lane in flight (the
-        // indices of a round first, then their terms; entries past the end add exact zeros)
+        // warp w takes slots w * 32 + lane + k * kColWarps * 32, four per lane in flight (slots past
+        // the end add exact zeros)
         constexpr int step = kColWarps * 32;
         const int64_t e1 = qptr[j + 1];
         for (int64_t e = qptr[j] + wid * 32 + lane; e < e1; e += 4 * step) {
-            int64_t q[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = e + u * step < e1 ? int64_t(qlist[e + u * step]) : int64_t(-1);
             T v[4][9];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                const int64_t eu = e + u * step;
+                const T* t = tb + eu * kTbHead;
+                if (eu < e1) {
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 a = reinterpret_cast<const float4*>(t)[0];
+                        const float4 c = reinterpret_cast<const float4*>(t)[1];
+                        v[u][0] = a.x, v[u][1] = a.y, v[u][2] = a.z, v[u][3] = a.w;
+                        v[u][4] = c.x, v[u][5] = c.y, v[u][6] = c.z, v[u][7] = c.w;
+                    } else {
 #pragma unroll
-                for (int b = 0; b < 9; ++b) v[u][b] = q[u] >= 0 ? tb[q[u] * 9 + b] : T(0);
+                        for (int b = 0; b < 8; ++b) v[u][b] = t[b];
+                    }
+                    v[u][8] = tb8[eu];
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 9; ++b) v[u][b] = T(0);
+                }
+            }
 #pragma unroll
             for (int b = 0; b < 9; ++b) acc[b] += (v[0][b] + v[1][b]) + (v[2][b] + v[3][b]);
         }
@@ -2122,7 +2140,7 @@ struct Solver {
     // work lists of the block-sparse products: whole rows, rows split by pose subset, and whole rows of
     // the upper triangle (the symmetric one-column products of mixed precision)
     ItemList items_g, items_l, items_u;
-    Buf tb;                    // transposed terms of the symmetric product (9 per tiled slot of the upper S)
+    Buf tb;                    // transposed terms of the symmetric product (kTbHead + 1 values per upper block)
     int items_cb = -1;         // item chunk rule the lists were built with (0 = the default)
     int items_l_dirs = -1;
     bool use_l = false;        // the current MCG solve splits rows by pose subset (n_dirs > 1)
@@ -2450,7 +2468,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     w->items_g.polls = a.wait_polls;
     w->items_l.polls = a.wait_polls;
     w->items_u.polls = a.wait_polls;
-    if (fp32 && s.nnzb_u > 0) grow(w->tb, size_t(s.n_tiles_u) * kTile * 9 * sizeof(float));
+    if (fp32 && s.n_up > 0) grow(w->tb, size_t(s.n_up) * (kTbHead + 1) * sizeof(float));
 }
 
 static void free_buf(Buf& b) {
@@ -2499,20 +2517,20 @@ int solver_history(const Solver* w, int problem, const double** hist) {
 template <typename T, int MODE, bool ZH, bool SYM, int CFG>
 static void launch_spmv_cfg(cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
                             const T* S, const T* z, const ItemList& L, int sel, T* out, const T* rvec, double* camdot,
-                            Ctl* ctl, T* tb) {
+                            Ctl* ctl, T* tb, T* tb8, const int32_t* cslot) {
     k_spmv<T, MODE, ZH, SYM, CFG><<<num_sms(), SpmvShape<T, CFG>::kWarps * 32, spmv_smem<T, CFG>(), st>>>(
-        row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+        row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8, cslot);
 }
 template <typename T, int MODE, bool ZH, bool SYM>
 static void launch_spmv(int cfg, cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
                         const T* S, const T* z, const ItemList& L, int sel, T* out, const T* rvec, double* camdot,
-                        Ctl* ctl, T* tb) {
+                        Ctl* ctl, T* tb, T* tb8 = nullptr, const int32_t* cslot = nullptr) {
     if (cfg == 1)
-        launch_spmv_cfg<T, MODE, ZH, SYM, 1>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+        launch_spmv_cfg<T, MODE, ZH, SYM, 1>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8, cslot);
     else if (cfg == 2)
-        launch_spmv_cfg<T, MODE, ZH, SYM, 2>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+        launch_spmv_cfg<T, MODE, ZH, SYM, 2>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8, cslot);
     else
-        launch_spmv_cfg<T, MODE, ZH, SYM, 0>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb);
+        launch_spmv_cfg<T, MODE, ZH, SYM, 0>(st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8, cslot);
 }
 
 // A one-column product y = S z, z a column of the direction history (modes of k_spmv).  With the upper
@@ -2526,9 +2544,10 @@ static int enqueue_product(Solver* w, const Structure& s, const T* S, const T* S
     double* camdot = MODE == 1 ? ptr<double>(w->camdot) : nullptr;
     if (Su) {
         T* tb = ptr<T>(w->tb);
+        T* tb8 = tb + kTbHead * s.n_up;
         launch_spmv<T, MODE, true, true>(w->spmv_cfg, st, s.row_ptr_u, s.tile_ptr_u, s.col_u, Su, zsrc, w->items_u,
-                                         sel, out, rvec, camdot, ctl, tb);
-        k_spmv_col<T, MODE, true><<<dim3(w->gcol, w->nb), kColWarps * 32, 0, st>>>(s.qptr, s.qlist, tb, zsrc, sel,
+                                         sel, out, rvec, camdot, ctl, tb, tb8, s.cslot);
+        k_spmv_col<T, MODE, true><<<dim3(w->gcol, w->nb), kColWarps * 32, 0, st>>>(s.qptr, tb, tb8, zsrc, sel,
                                                                                     out, rvec, camdot, ctl);
         return 2;
     }
