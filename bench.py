@@ -81,6 +81,8 @@ def parse():
                     help="training problems per family (each gives 10 normal equations)")
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--no-loop", action="store_true", help="batch mode: skip the looped single-problem solves")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default line: skip the batched 64-problem measurement reported under `batched`")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="landmarks per camera x this factor")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -108,10 +110,9 @@ def load_peaks() -> dict:
 
 
 # DRAM bytes per stored upper 9x9 block of one float32 symmetric product (k_spmv<float,1,true,true> and
-# k_spmv_col together: dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of the
-# 1000-camera dense case; traffic grows with the stored blocks).  None until that capture is taken
-# of the current kernels.
-SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = None
+# k_spmv_col together: dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the dense
+# 1936-camera product timed by ba_time_kernel: 594.4 + 12.5 + 0.6 + 0.8 MB over 1,755,926 upper blocks).
+SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = 346.4
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
@@ -136,7 +137,7 @@ BUILD_WORK = [
     ("cam_rhs", "k_cam_rhs: b~ (Eq. 14) and the damping per camera",
      lambda n: 216 * n["o"] + 24 * n["l"] + 144 * n["c"], lambda n: 91.2 * n["o"], None),
     ("schur_diag", "k_schur_diag32: S_jj and the float32 G rows (Eq. 13)",
-     lambda n: 136 * n["o"] + 24 * n["l"] + 816 * n["c"], None, lambda n: 765.0 * n["o"]),
+     lambda n: 136 * n["o"] + 24 * n["l"] + 816 * n["c"], None, lambda n: 483.0 * n["o"]),
     ("block_jacobi", "k_block_jacobi: Lam and the inverse scaled diagonal blocks",
      lambda n: 1400 * n["c"], None, None),
     ("schur_off", "k_schur_off_sub + k_put_diag: the float32 blocks of Lam S Lam (Eq. 13)",
@@ -510,7 +511,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
         roof = {"kernel": "k_spmv<float,1,true,true> + k_spmv_col (q = S p from the upper triangle of S, Algorithm 1)",
                 "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": traffic,
-                "traffic_source": "ncu dram bytes of the 1000-camera case scaled by stored upper blocks",
+                "traffic_source": "ncu dram bytes of this product on dense-1936 (both launches), per upper block",
                 "bytes_per_launch": spmv_bytes, "upper_blocks": nnzb_u,
                 "bytes_moved_model": spmv_bytes + 72 * (nnzb_u - sc.n_cams),
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
@@ -599,6 +600,12 @@ def run_ours(a, rank: int, world: int, local_rank: int):
                 "mixed_vs_fp64": mixed_err}
         q.close()
 
+    # 64 uneven problems in one handle against a loop over 64 handles (the batched solve of the
+    # hot path), on rank 0 of a one-GPU run
+    batched = None
+    if rank == 0 and world == 1 and not a.no_batched:
+        batched = measure_batched(a, 3, 1, True)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         if a.cpu_sample:
@@ -636,6 +643,7 @@ def run_ours(a, rank: int, world: int, local_rank: int):
             "gpu_launches": int(launches),
             "clocks": clk,
             "autotune": tuned,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
 
@@ -785,6 +793,11 @@ def run_lm(a):
 
 
 def run_batched(a):
+    """Batched uneven problems (`--batched`): one JSON line."""
+    print(json.dumps(measure_batched(a, a.steps, a.warmup, not a.no_loop)), flush=True)
+
+
+def measure_batched(a, steps, warmup, loop):
     """Batched uneven problems: one handle (ba_batch_create) against a loop over single-problem handles.
 
     A step is the build and the MCG solve of every problem to the float64 tolerance; both arms use
@@ -819,17 +832,17 @@ def run_batched(a):
         pb.ba_build_normal(LAMBDA)
         return pb.ba_solve_mcg(TOL, MAX_ITERS, a.n_dirs, a.tau)
 
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         step_batch()
     l0 = pb.ba_get_launch_count()
     clocks = ClockSampler(0)
     clocks.start()
     tb = []
-    for _ in range(a.steps):
+    for _ in range(steps):
         t, st = timed(step_batch)
         tb.append(t)
     clk = clocks.stop()
-    launches = (pb.ba_get_launch_count() - l0) // a.steps
+    launches = (pb.ba_get_launch_count() - l0) // steps
     per = pb.ba_get_batch_stats()
     assert all(s["status"] == 0 and s["true_rel_residual"] <= 1.5e-6 for s in per), per
     nnzb = pb.ba_get_schur_nnzb()
@@ -841,7 +854,7 @@ def run_batched(a):
     pb.close()
 
     tl = []
-    if not a.no_loop:
+    if loop:
         singles = [problem.from_scene(sc, precision=a.precision) for sc in scs]
         for q in singles:
             q.ba_set_stream(stream)
@@ -854,7 +867,7 @@ def run_batched(a):
             return out
 
         step_loop()
-        for _ in range(max(1, min(a.steps, 3))):
+        for _ in range(max(1, min(steps, 3))):
             t, sts = timed(step_loop)
             tl.append(t)
         assert all(s["status"] == 0 for s in sts)
@@ -865,7 +878,7 @@ def run_batched(a):
     ms_l = float(np.mean(tl)) if tl else None
     line = {
         "mode": "batched", "metric": "time to rel. residual 1e-6, all problems of a batch (MCG)",
-        "value": ms_b, "unit": "ms/batch", "higher_is_better": False, "steps": a.steps, "warmup": a.warmup,
+        "value": ms_b, "unit": "ms/batch", "higher_is_better": False, "steps": steps, "warmup": warmup,
         "dtype": "f64" if a.precision == "fp64" else "f32+f64", "data": "synthetic (seeded generator)",
         "config": {"workload": f"batched-{len(scs)}", "n_problems": len(scs),
                    "cams": [sc.n_cams for sc in scs], "n_cams": n_cams, "n_obs": n_obs, "nnzb": nnzb,
@@ -881,7 +894,7 @@ def run_batched(a):
         "gpu_launches_per_step": int(launches), "clocks": clk,
         "step_ms": [round(x, 3) for x in tb], "loop_ms": [round(x, 3) for x in tl],
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_learned(a):

@@ -649,9 +649,9 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
 // slots, then the warps' sums in warp order), then in MODE 1 the per-camera sums q^T p and p^T r.
 // One CTA of kColWarps warps per camera (its slots qptr[k] .. qptr[k + 1] - 1 of tb are consecutive,
 // up to n_c - 1 of them); grid: CTAs x problems.
-constexpr int kColWarps = 8;
+constexpr int kColWarps = 4;   // 12 CTAs per SM: 1824 cameras in flight
 template <typename T, int MODE, bool ZH>
-__global__ void __launch_bounds__(kColWarps * 32) k_spmv_col(const int64_t* __restrict__ qptr,
+__global__ void __launch_bounds__(kColWarps * 32, 12) k_spmv_col(const int64_t* __restrict__ qptr,
                                                              const T* __restrict__ tb, const T* __restrict__ tb8,
                                                              const T* __restrict__ z, int sel, T* __restrict__ out,
                                                              const T* __restrict__ rvec, double* __restrict__ camdot,
@@ -2225,13 +2225,14 @@ static std::vector<SpItem> build_items(const std::vector<int64_t>& h_row_ptr, co
     return out;
 }
 
-// Order the items for a launch of W warps by the longest-processing-time rule: in decreasing cost
-// (tiles of S, in quarter tiles, plus a quarter for the item's own sums and output), each item goes
-// to the warp with the least cost so far (ties: the lower warp).  Warp g's items then follow in
-// their original order at wptr[g].  Chunks and slots are unchanged, so the sums are too.
-// (Round-robin over the 1936-camera upper triangle left the longest warp 1.4x the mean; this
-// rule, 1.05x.)
-static std::vector<int64_t> balance_items(std::vector<SpItem>& v, int64_t W) {
+// Order the items for a launch of W warps, NW per CTA, by the longest-processing-time rule: in
+// decreasing cost (tiles of S, in quarter tiles, plus a quarter for the item's own sums and output),
+// each item goes to the bin with the least cost so far (ties: the lower bin).  Bin b is run by warp
+// (b % C) * NW + b / C of the C = W / NW CTAs, so that the largest items, which go to the first bins,
+// are spread over the SMs instead of filling the first CTAs.  Warp g's items follow in their
+// original order at wptr[g].  Chunks and slots are unchanged, so the sums are too.  (Round-robin
+// over the 1936-camera upper triangle left the longest warp 1.4x the mean; this rule, 1.05x.)
+static std::vector<int64_t> balance_items(std::vector<SpItem>& v, int64_t W, int64_t NW) {
     const int64_t n = int64_t(v.size());
     std::vector<int64_t> cost(n), idx(n);
     for (int64_t i = 0; i < n; ++i) {
@@ -2244,13 +2245,15 @@ static std::vector<int64_t> balance_items(std::vector<SpItem>& v, int64_t W) {
     using Load = std::pair<int64_t, int64_t>;   // (cost so far, warp)
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int64_t g = 0; g < W; ++g) heap.push({0, g});
+    const int64_t C = W / NW;
     std::vector<int64_t> owner(n), wptr(W + 1, 0);
     for (const int64_t i : idx) {
         const Load l = heap.top();
         heap.pop();
-        owner[i] = l.second;
-        heap.push({l.first + cost[i], l.second});
-        ++wptr[l.second + 1];
+        const int64_t b = l.second;
+        owner[i] = (b % C) * NW + b / C;
+        heap.push({l.first + cost[i], b});
+        ++wptr[owner[i] + 1];
     }
     for (int64_t g = 0; g < W; ++g) wptr[g + 1] += wptr[g];
     std::vector<int64_t> pos(wptr.begin(), wptr.end() - 1);
@@ -2268,11 +2271,11 @@ static void free_items(ItemList& L) {
     L = ItemList();
 }
 
-// Upload a list, in the balanced order for W warps (W > 0).
-static void upload_items(ItemList& L, std::vector<SpItem> v, int64_t W) {
+// Upload a list, in the balanced order for W warps, NW per CTA (W > 0).
+static void upload_items(ItemList& L, std::vector<SpItem> v, int64_t W, int64_t NW) {
     free_items(L);
     std::vector<int64_t> wptr;
-    if (W > 0) wptr = balance_items(v, W);
+    if (W > 0) wptr = balance_items(v, W, NW);
     SpItem* d = nullptr;
     BA_CUDA_TRY(cudaMalloc(&d, sizeof(SpItem) * (v.empty() ? 1 : v.size())));
     if (!v.empty()) BA_CUDA_TRY(cudaMemcpy(d, v.data(), sizeof(SpItem) * v.size(), cudaMemcpyHostToDevice));
@@ -2334,19 +2337,19 @@ static int spmv_warps(int cfg) {
 static void ensure_items(Solver* w, const Structure& s, int n_dirs, int forced_cb, bool fp32, int cfg) {
     const int cb = forced_cb > 0 ? forced_cb : 0;
     const int64_t sms = num_sms();
-    const int64_t wg = sms * (fp32 ? SpmmCfg::kWarps : spmv_warps<double>(cfg));
-    const int64_t wu = sms * spmv_warps<float>(cfg);
-    const int64_t wl = sms * spmv_warps<double>(cfg);
+    const int64_t ng = fp32 ? SpmmCfg::kWarps : spmv_warps<double>(cfg);
+    const int64_t nu = spmv_warps<float>(cfg), nl = spmv_warps<double>(cfg);
+    const int64_t wg = sms * ng, wu = sms * nu, wl = sms * nl;
     const bool fresh = !w->items_g.items || w->items_cb != cb;
     if (fresh || w->items_g.nw != wg) {
-        upload_items(w->items_g, build_items(s.h_row_ptr, s.h_col, w->lay, false, cb), wg);
+        upload_items(w->items_g, build_items(s.h_row_ptr, s.h_col, w->lay, false, cb), wg, ng);
         if (w->mm_part) cudaFree(w->mm_part);
         w->mm_part = nullptr;
         BA_CUDA_TRY(cudaMalloc(&w->mm_part, sizeof(double) * kMaxDirs * 9 * size_t(w->items_g.n > 0 ? w->items_g.n : 1)));
         ++w->epoch;
     }
     if (!s.h_row_ptr_u.empty() && (fresh || w->items_u.nw != wu)) {
-        upload_items(w->items_u, build_items(s.h_row_ptr_u, s.h_col_u, w->lay, false, cb), wu);
+        upload_items(w->items_u, build_items(s.h_row_ptr_u, s.h_col_u, w->lay, false, cb), wu, nu);
         ++w->epoch;
     }
     if (fresh) {
@@ -2354,7 +2357,7 @@ static void ensure_items(Solver* w, const Structure& s, int n_dirs, int forced_c
         w->items_cb = cb;
     }
     if (n_dirs > 1 && (w->items_l_dirs != n_dirs || w->items_l.nw != wl)) {
-        upload_items(w->items_l, build_items(s.h_row_ptr, s.h_col, w->lay, true, cb), wl);
+        upload_items(w->items_l, build_items(s.h_row_ptr, s.h_col, w->lay, true, cb), wl, nl);
         w->items_l_dirs = n_dirs;
         ++w->epoch;
     }
@@ -2411,7 +2414,7 @@ static void prepare(Solver* w, const Structure& s, const SolveArgs& a, int n_dir
     w->gpq = int(std::max<int64_t>(1, std::min<int64_t>((9 * int64_t(nc_max) + 31) / 32, 4 * G / nb)));
     w->gphi = std::max(1, 4 * G / nb);
     w->gb = std::max(1, G / nb);
-    w->gcol = std::min(nc_max, std::max(1, 8 * G / nb));
+    w->gcol = std::min(nc_max, std::max(1, 16 * G / nb));
     if (!w->h_ctl || int(w->lay.size()) != nb) {
         if (w->h_ctl) cudaFreeHost(w->h_ctl);
         if (w->h_outer) cudaFreeHost(w->h_outer);
