@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: relative residual reduction of one float32 sweep (library default)")
     ap.add_argument("--tau", type=float, default=10.0)
+    ap.add_argument("--full-size", action="store_true",
+                    help="kernel cases: the benchmark's workload (--workload) instead of the 1000-camera problem")
     ap.add_argument("--kernel-case", choices=["spmv", "schur", "linearize", "mcg", "build", "pcg", "step"],
                     help="profiling mode: time one kernel on a mid-size dense problem (1000 cameras, "
                          "400k landmarks, ~1.6M observations) and exit; 'mcg' runs one MCG solve (N = 16) "
@@ -671,8 +673,12 @@ def run_kernel_case(a):
                               "mcg_iters": s2["iters"], "mcg_local": s2["local_steps"]}), flush=True)
         p.close()
         return
-    sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
-    # work items of 256 blocks: what ba_autotune picks for this problem
+    if a.full_size:
+        gen, kw, _ = WORKLOADS[a.workload]
+        sc = synthetic.make(gen, 0, **kw)
+    else:
+        sc = synthetic.dense(seed=0, n_cams=1000, n_pts=400_000, n_clusters=33)
+    # work items of 256 blocks: what ba_autotune picks for the 1000-camera problem
     p = problem.from_scene(sc, precision=a.precision, host_loop=int(a.host_loop), item_blocks=256)
     p.ba_build_normal(LAMBDA)
     if a.kernel_case == "build":

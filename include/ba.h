@@ -397,9 +397,8 @@ int ba_gnn_launch_count(const ba_gnn* g, int64_t* n);
 /*
  * |-b~ - S x| and |b~| for a block-sparse S that the caller holds in device memory, computed
  * without allocating anything.  The paper has no counterpart; this exists for callers that
- * cannot call cudaMalloc where they check a solution: code running while a CUDA graph is being
- * captured, loops whose device memory is fixed up front, or hosts whose allocator owns all
- * device memory.
+ * cannot call cudaMalloc where they check a solution: loops whose device memory is fixed up
+ * front, or hosts whose allocator owns all device memory.
  *   n_cams   block rows of S, 1 .. BA_STATIC_MAX_CAMS (larger: INVALID_ARG, nothing launched)
  *   row_ptr  n_cams + 1 int64 block offsets, device
  *   col      block column indices (int32), device

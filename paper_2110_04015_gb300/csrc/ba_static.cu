@@ -1,8 +1,8 @@
 // Allocation-free true-residual check: ba_schur_residual_static (declared in include/ba.h).
 //
 // Some callers cannot allocate device memory at the point where they want to check a
-// solution: code running while a CUDA graph is being captured, real-time loops whose memory
-// budget is fixed up front, or hosts whose allocator owns all device memory.  This entry point
+// solution: real-time loops whose memory budget is fixed up front, or hosts whose allocator owns
+// all device memory.  This entry point
 // computes |-b~ - S x| and |b~| for a block-sparse S the caller already holds on the device,
 // without any allocation: its only working memory is the file-scope device array below.
 //

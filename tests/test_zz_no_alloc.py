@@ -1,8 +1,8 @@
 """The allocation-free residual check agrees with the solver's own float64 true residual.
 
 ``ba_schur_residual_static`` is for callers that cannot allocate device memory where they
-check a solution (inside a CUDA graph capture, under a fixed memory budget, or behind an
-allocator that owns the device).  It works in a file-scope device array instead of allocating.
+check a solution (under a fixed memory budget, or behind an allocator that owns the device).
+It works in a file-scope device array instead of allocating.
 This file is named to be collected last, so a run that stops at its first failure has already
 run every other test; it also passes on its own in a fresh process.
 """
