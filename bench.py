@@ -127,17 +127,18 @@ FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.07e9 / 1e12
 # counts of the problem: o observations, l landmarks, c cameras, p observation pairs of shared landmarks
 # (the terms of the off-diagonal Schur blocks), u stored upper blocks off the diagonal.  Bytes: every
 # array element the kernel reads or writes, once (gathered rows counted once).  Operations: floating-
-# point operations per unit, FMA counted twice; for the float64 kernels and the float32 diagonal pass
-# the executed counts of an ncu capture of the 1000-camera dense build (DFMA x 2 + DADD + DMUL per
-# observation, FFMA x 2 + FADD + FMUL), for the off-diagonal blocks the algorithm's 243 FMA per pair
-# and the scaling (2 multiplies per entry of a block).
+# point operations per unit, FMA counted twice.  The double-float kernels (the float64 parts of the
+# mixed build, on the float32 pipe) and the float32 diagonal pass count the float32 instructions they
+# execute (FFMA x 2 + FADD + FMUL per observation, ncu on the 1000-camera dense build); the
+# off-diagonal blocks count the algorithm's 243 FMA per pair and the scaling (2 multiplies per entry
+# of a block).
 BUILD_WORK = [
-    ("linearize", "k_cam_prep + k_linearize: r, J_p, J_l per observation (Eqs. 2-4)",
-     lambda n: 260 * n["o"] + 24 * n["l"], lambda n: 158.0 * n["o"], None),
-    ("landmarks", "k_landmarks: V_lambda, its Cholesky factor, b_l per landmark",
-     lambda n: 64 * n["o"] + 228 * n["l"], lambda n: 51.5 * n["o"], None),
-    ("cam_rhs", "k_cam_rhs: b~ (Eq. 14) and the damping per camera",
-     lambda n: 216 * n["o"] + 24 * n["l"] + 144 * n["c"], lambda n: 91.2 * n["o"], None),
+    ("linearize", "k_cam_prep + k_linearize_df: r, J_p, J_l per observation in double-float (Eqs. 2-4)",
+     lambda n: 260 * n["o"] + 48 * n["l"], None, lambda n: 1548.0 * n["o"]),
+    ("landmarks", "k_landmarks_df: V_lambda, its Cholesky factor, b_l, y_l per landmark (double-float)",
+     lambda n: 64 * n["o"] + 132 * n["l"], None, lambda n: 510.0 * n["o"]),
+    ("cam_rhs", "k_cam_rhs_df: b~ (Eq. 14) and the damping per camera (double-float)",
+     lambda n: 216 * n["o"] + 24 * n["l"] + 144 * n["c"], None, lambda n: 1009.0 * n["o"]),
     ("schur_diag", "k_schur_diag32: S_jj and the float32 G rows (Eq. 13)",
      lambda n: 136 * n["o"] + 24 * n["l"] + 816 * n["c"], None, lambda n: 483.0 * n["o"]),
     ("block_jacobi", "k_block_jacobi: Lam and the inverse scaled diagonal blocks",

@@ -254,6 +254,15 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
     s.obs_pt = upload(p, spt);
     s.perm = upload(p, perm);
     s.obs_xy = upload(p, sxy);
+    if (p->opt.precision == BA_PRECISION_MIXED) {
+        // double-float measurements: the nearest float, then the nearest float to the remainder
+        std::vector<float2> xyd(sxy.size());
+        for (size_t k = 0; k < sxy.size(); ++k) {
+            const float h = static_cast<float>(sxy[k]);
+            xyd[k] = make_float2(h, static_cast<float>(sxy[k] - static_cast<double>(h)));
+        }
+        s.obs_xyd = upload(p, xyd);
+    }
     s.pt_ptr = upload(p, pt_ptr);
     {
         // landmarks by decreasing track length, stable (counting sort on the length)
@@ -398,6 +407,9 @@ void alloc_system(ba_problem* p) {
         y.PY32 = dev_alloc<float>(p, size_t(s.n_o) * 6);
         y.L32 = dev_alloc<float>(p, size_t(s.n_l) * 6);
         y.yl = dev_alloc<double>(p, size_t(s.n_l) * 3);
+        y.auxd = dev_alloc<float2>(p, size_t(s.n_c) * 24);
+        y.ptsd = dev_alloc<float2>(p, size_t(s.n_l) * 3);
+        y.xd = dev_alloc<float2>(p, size_t(s.n_c) * 9);
         y.dadd = dev_alloc<double>(p, size_t(s.n_c) * 9);
         y.uv = dev_alloc<double>(p, size_t(s.n_o) * 2);
         y.lam = dev_alloc<double>(p, size_t(s.n_c) * 9);
@@ -696,7 +708,7 @@ int ba_get_delta(ba_problem* p, double* dxp, double* dxl) {
         if (dxl) {
             ba::launch_back_substitute(p->s, p->y, p->dxp, p->dxl, p->stream);
             check_launch();
-            p->launches += 1;
+            p->launches += p->y.G ? 1 : 2;   // mixed: the split of dx_p, then the landmarks
             copy_out(dxl, p->dxl, sizeof(double) * 3 * size_t(p->s.n_l), p->stream);
         }
         return BA_OK;
@@ -754,7 +766,7 @@ int ba_lm_step(ba_problem* p, int32_t solver, double lambda0, double tol, int32_
             ba::launch_add_params(p->y.cams, p->dxp, p->tmp_cams, int64_t(p->s.n_c) * 9, p->stream);
             ba::launch_add_params(p->y.pts, p->dxl, p->tmp_pts, int64_t(p->s.n_l) * 3, p->stream);
             check_launch();
-            p->launches += 3;
+            p->launches += p->y.G ? 3 : 4;
             s.cost_after = do_cost(p, p->tmp_cams, p->tmp_pts);
         } else {
             s.cost_after = s.cost_before;
@@ -813,6 +825,8 @@ int ba_get_linearization(const ba_problem* pc, double* r, double* Jp, double* Jl
             double* tmp = nullptr;
             BA_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * n_o * width[k]));
             ba::launch_unpermute(src[k], p->s.perm, tmp, n_o, width[k], p->stream);
+            // mixed precision keeps these in double-float (8 bytes per value, moved as such above)
+            if (p->opt.precision == BA_PRECISION_MIXED) ba::launch_df_to_double(tmp, n_o * width[k], p->stream);
             cudaError_t e = cudaMemcpyAsync(dst[k], tmp, sizeof(double) * n_o * width[k], cudaMemcpyDefault, p->stream);
             cudaStreamSynchronize(p->stream);
             cudaFree(tmp);
@@ -829,16 +843,41 @@ int ba_get_normal(const ba_problem* pc, double* U, double* V, double* b_p, doubl
     if (!p) return BA_ERR_INVALID_ARG;
     try {
         if (!p->y.built) throw Error(BA_ERR_STATE, "nothing built");
-        if (p->opt.precision == BA_PRECISION_MIXED && (U || b_p)) {
-            // the mixed build needs neither U nor b_p: form them from the stored Jacobians on request
-            ba::launch_cameras_U(p->s, p->y, p->opt.damping, p->y.lambda, p->stream);
-            check_launch();
-            p->launches += 1;
+        const ba::Structure& s = p->s;
+        if (p->opt.precision == BA_PRECISION_MIXED) {
+            // the mixed build keeps r, J_p, J_l in double-float and needs none of U, V, b_p, b_l in
+            // float64: form them on request from float64 copies, with the kernels of the float64 build
+            const size_t n_o = size_t(s.n_o), n_l = size_t(s.n_l);
+            const size_t sizes[7] = {2 * n_o, 18 * n_o, 6 * n_o, 9 * n_l, 6 * n_l, 3 * n_l, 3 * n_l};
+            double* t[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaMalloc(&t[k], sizeof(double) * (sizes[k] ? sizes[k] : 1));
+            if (e == cudaSuccess) {
+                ba::launch_normal_request(s, p->y, p->opt.damping, p->y.lambda, t[0], t[1], t[2], t[3], t[4], t[5],
+                                          t[6], p->stream);
+                e = cudaGetLastError();
+                p->launches += 8;
+            }
+            if (e == cudaSuccess) {
+                try {
+                    copy_out(U, p->y.U, sizeof(double) * 81 * size_t(s.n_c), p->stream);
+                    copy_out(V, t[3], sizeof(double) * 9 * n_l, p->stream);
+                    copy_out(b_p, p->y.bp, sizeof(double) * 9 * size_t(s.n_c), p->stream);
+                    copy_out(b_l, t[5], sizeof(double) * 3 * n_l, p->stream);
+                } catch (...) {
+                    for (double* q : t) if (q) cudaFree(q);
+                    throw;
+                }
+            }
+            cudaStreamSynchronize(p->stream);
+            for (double* q : t) if (q) cudaFree(q);
+            if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("normal equation on request: ") + cudaGetErrorString(e));
+            return BA_OK;
         }
-        copy_out(U, p->y.U, sizeof(double) * 81 * size_t(p->s.n_c), p->stream);
-        copy_out(V, p->y.V, sizeof(double) * 9 * size_t(p->s.n_l), p->stream);
-        copy_out(b_p, p->y.bp, sizeof(double) * 9 * size_t(p->s.n_c), p->stream);
-        copy_out(b_l, p->y.bl, sizeof(double) * 3 * size_t(p->s.n_l), p->stream);
+        copy_out(U, p->y.U, sizeof(double) * 81 * size_t(s.n_c), p->stream);
+        copy_out(V, p->y.V, sizeof(double) * 9 * size_t(s.n_l), p->stream);
+        copy_out(b_p, p->y.bp, sizeof(double) * 9 * size_t(s.n_c), p->stream);
+        copy_out(b_l, p->y.bl, sizeof(double) * 3 * size_t(s.n_l), p->stream);
         return BA_OK;
     } catch (const Error& e) {
         return fail(p, e);

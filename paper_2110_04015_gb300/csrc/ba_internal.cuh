@@ -66,6 +66,7 @@ struct Structure {
     int32_t* obs_pt = nullptr;    // n_o
     int32_t* perm = nullptr;      // n_o: point-order slot -> caller index
     double* obs_xy = nullptr;     // n_o x 2
+    float2* obs_xyd = nullptr;    // n_o x 2 (mixed precision): the measurements in double-float
     int64_t* pt_ptr = nullptr;    // n_l + 1
     int32_t* lm_order = nullptr;  // n_l: landmarks by decreasing track length (ties by index); the
                                   // per-landmark kernels take them in this order so that the lanes of a
@@ -148,6 +149,11 @@ struct System {
     double* yl = nullptr;     // n_l x 3: V_l^{-1} b_l
     double* dadd = nullptr;   // n_c x 9: the damping lambda D_p^T D_p added to the diagonal of U_j
     double* uv = nullptr;     // n_o x 2: per-observation terms of the float64 true residual
+    // mixed precision keeps r, Jc, Jl, L, bl, yl and uv above as double-float (float2 (hi, lo) in the
+    // same 8 bytes per value, df64.cuh), and its own double-float inputs:
+    float2* auxd = nullptr;   // n_c x 24: the aux block
+    float2* ptsd = nullptr;   // n_l x 3: the points
+    float2* xd = nullptr;     // n_c x 9: x of the true residual (or dx_p of the back-substitution)
     int* status = nullptr;    // device error word of the build
     double lambda = 0.0;
     bool built = false;
@@ -163,7 +169,9 @@ void launch_obs_G(const Structure& s, System& y, cudaStream_t st);
 void launch_cameras(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
 void launch_schur_diag(const Structure& s, System& y, cudaStream_t st);
 // U_lambda and b_p only (mixed precision forms them on request)
-void launch_cameras_U(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
+void launch_normal_request(const Structure& s, System& y, int damping, double lambda, double* r64, double* Jc64,
+                           double* Jl64, double* V64, double* L64, double* bl64, double* e64, cudaStream_t st);
+void launch_df_to_double(double* buf, int64_t n, cudaStream_t st);
 // mixed precision: b~ and lambda D_p in float64, then the float32 diagonal blocks into Sd
 void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, cudaStream_t st);
 void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st);
@@ -172,7 +180,7 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st);
 // out = -b~ - S x with the implicit float64 operator (mixed precision, no explicit S)
 // S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x;
 // partial[2 j], partial[2 j + 1] receive camera j's sums of out^2 and b~^2 (2 n_c values)
-void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
+int launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
                               cudaStream_t st);
 void launch_block_jacobi(const Structure& s, System& y, cudaStream_t st);
 void launch_block_jacobi_plain(const Structure& s, System& y, cudaStream_t st);

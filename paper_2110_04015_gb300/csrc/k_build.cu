@@ -6,16 +6,18 @@
 //   k_obs_G         one thread per observation: G_o = (J_p^T J_l) L^{-T}
 //   k_cameras       one CTA per camera: U_lambda, b_p, b~ = b_p - sum G_o e_l
 //   k_schur_diag    one CTA per camera: S_jj = U_j - sum_o G_o G_o^T (float64)
-//   k_schur_off_*   one warp per upper block (j < k): S_jk = - sum G_oj G_ok^T over the observation
-//                   pairs of shared landmarks, written to (j, k) and transposed to (k, j); float64:
-//                   three entries per lane (_rows), float32: a 3x3 sub-block and a third of the
-//                   pairs per lane (_sub)
+//   k_schur_off_*   S_jk = - sum G_oj G_ok^T over the observation pairs of shared landmarks, written
+//                   to (j, k) and transposed to (k, j); float64: a warp per upper block, three
+//                   entries per lane (_rows); float32: three blocks per warp, a 3x3 sub-block per
+//                   lane (_sub)
 //   k_block_jacobi  one thread per camera: D_j^{-1} = (S_jj)^{-1} through Cholesky
-// Mixed precision builds no float64 U, G or S_jj: float64 keeps r, J_p, J_l (for b~ and the true
-// residual S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x, k_jres_*), and the
-// float32 system comes from float32 Jacobians formed from P = R X + t and R X, which k_linearize
-// keeps in float32 (camera order):
-//   k_cam_rhs       one CTA per camera (float64): b~ = sum_o J_p^T (r - J_l V^-1 b_l), lambda D_p
+// Mixed precision builds no float64 U, G or S_jj.  r, J_p, J_l (for b~ and the true residual
+// S x = sum_o J_p^T (J_p x - J_l V^-1 sum J_l^T J_p x) + lambda D_p x) are formed and used in
+// double-float arithmetic on the float32 pipe (df64.cuh; the *_df kernels), and the float32 system
+// comes from float32 Jacobians formed from P = R X + t and R X, which k_linearize_df keeps in
+// float32 (camera order):
+//   k_landmarks_df  one thread per landmark: V_lambda, b_l, L, y_l = V^-1 b_l
+//   k_cam_rhs_df    one CTA per camera: b~ = sum_o J_p^T (r - J_l V^-1 b_l), lambda D_p
 //   k_schur_diag32  one CTA per camera (float32): S_jj = sum_o J_p^T (I - A A^T) J_p + lambda D_p,
 //                   A = J_l L^{-T} (each term is positive semi-definite: no cancellation)
 //                   (the same pass writes G_o = J_p^T A in float32 for the off-diagonal blocks,
@@ -27,6 +29,7 @@
 #include <cstdint>
 
 #include "ba_internal.cuh"
+#include "df64.cuh"
 
 namespace ba {
 
@@ -96,9 +99,14 @@ __device__ __forceinline__ void bal_project(const double* c, const double* X, do
 // Per-camera part of the linearisation, shared by all observations of the camera:
 // aux = (R[9], RJ[9], t[3], f, k1, k2), RJ = R J_r(omega) with J_r = I - B [w]x + C [w]x^2 the
 // right Jacobian of the rotation exponential, so that d(R X)/d omega = -R [X]x J_r = -[R X]x RJ
-// (R [X]x = [R X]x R for a rotation).  aux32 (may be null) receives the same values in float32.
+// (R [X]x = [R X]x R for a rotation).  aux32 and auxd (may be null) receive the same values in
+// float32 and in double-float; with ptsd, the same launch also splits the n_pv point coordinates
+// into double-float (mixed precision, whose per-observation kernels take no float64 input).
 __global__ void k_cam_prep(int32_t n_c, const double* __restrict__ cams, double* __restrict__ aux,
-                           float* __restrict__ aux32) {
+                           float* __restrict__ aux32, float2* __restrict__ auxd, int64_t n_pv,
+                           const double* __restrict__ pts, float2* __restrict__ ptsd) {
+    if (ptsd)
+        for (int64_t i = gtid(); i < n_pv; i += gstride()) df_st(ptsd + i, df_from(pts[i]));
     for (int64_t j = gtid(); j < n_c; j += gstride()) {
         const double* c = cams + 9 * j;
         double w[3] = {c[0], c[1], c[2]};
@@ -130,6 +138,10 @@ __global__ void k_cam_prep(int32_t n_c, const double* __restrict__ cams, double*
         if (aux32) {
 #pragma unroll
             for (int k = 0; k < 24; ++k) aux32[24 * j + k] = float(o[k]);
+        }
+        if (auxd) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) df_st(auxd + 24 * j + k, df_from(o[k]));
         }
     }
 }
@@ -734,51 +746,6 @@ __device__ __forceinline__ double damp_add(double d, int damping, double lambda)
     return damping == BA_DAMPING_IDENTITY ? lambda : lambda * fmin(fmax(d, 1e-6), 1e32);
 }
 
-// Mixed precision, one CTA per camera, float64: b~_j = sum_{o in j} J_p^T (r_o - J_l y_l) (Eq. 14, with
-// W V^-1 b_l = sum_o J_p^T J_l y_l and y_l = V_l^-1 b_l), and dadd_j = the damping lambda D_p^T D_p
-// added to the diagonal of U_j.
-__global__ void __launch_bounds__(kCamThreads) k_cam_rhs(
-    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
-    const int32_t* __restrict__ op, const double* __restrict__ r, const double* __restrict__ Jc,
-    const double* __restrict__ Jl, const double* __restrict__ yl, int damping, double lambda,
-    double* __restrict__ btout, double* __restrict__ dadd) {
-    __shared__ double red[kCamThreads / 32][18];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
-        double bt[9], dg[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) bt[a] = dg[a] = 0.0;
-        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
-            const int64_t o = cam_obs[q];
-            const double* y = yl + 3 * int64_t(op[o]);
-            const double* jl = Jl + 6 * o;
-            const double y0 = y[0], y1 = y[1], y2 = y[2];
-            const double s0 = r[2 * o] - (jl[0] * y0 + jl[1] * y1 + jl[2] * y2);
-            const double s1 = r[2 * o + 1] - (jl[3] * y0 + jl[4] * y1 + jl[5] * y2);
-            const double* jc = Jc + 18 * o;
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const double c0 = jc[a], c1 = jc[9 + a];
-                bt[a] += c0 * s0 + c1 * s1;
-                dg[a] += c0 * c0 + c1 * c1;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 18; ++k) {
-            const double v = warp_sum(k < 9 ? bt[k] : dg[k - 9]);
-            if (lane == 0) red[wid][k] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 18) {
-            const int k = threadIdx.x;
-            const double v = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
-            if (k < 9) btout[9 * int64_t(j) + k] = v;
-            else dadd[9 * int64_t(j) + k - 9] = damp_add(v, damping, lambda);
-        }
-        __syncthreads();
-    }
-}
-
 // Row a of A_o = J_l L^{-T} (2x3) from L packed with its reciprocal diagonal (float32).
 __device__ __forceinline__ void rows_A(const float* jl, const float* Lp, float (&A)[2][3]) {
 #pragma unroll
@@ -898,86 +865,320 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
     }
 }
 
-// V_l^{-1} s from L packed with its reciprocal diagonal: L z = s, then L^T y = z.
-__device__ __forceinline__ void solve_V(const double* L, double s0, double s1, double s2, double& y0, double& y1,
-                                        double& y2) {
-    const double z0 = s0 * L[0];
-    const double z1 = (s1 - L[1] * z0) * L[2];
-    const double z2 = (s2 - L[3] * z0 - L[4] * z1) * L[5];
-    y2 = z2 * L[5];
-    y1 = (z1 - L[4] * y2) * L[2];
-    y0 = (z0 - L[1] * y1 - L[3] * y2) * L[0];
+
+// ---------------------------------------------------------------------------------------
+// Mixed precision: the float64 parts of the build, the true residual and the back-substitution in
+// double-float arithmetic (df64.cuh) on the float32 pipe.  r, J_p, J_l (per observation), L, b_l,
+// y_l (per landmark) and the true residual's terms uv are stored as float2 (hi, lo) in the same
+// buffers as their float64 counterparts of the float64 precision.  Float64 values enter per camera
+// (the aux block), per landmark (the points, split by k_cam_prep), per camera again (x, split by
+// the refinement's accumulation) or once at create (the measurements), and results leave per camera
+// (b~, the damping, the true residual) or per landmark (the back-substitution); the conversions run
+// on the float64 pipe, the arithmetic per observation does not.
+
+__device__ __forceinline__ df64 ldd(const float2* p) { return df_ld(p); }
+// two consecutive double-float values in one 16-byte load (p 16-byte aligned)
+__device__ __forceinline__ void ldd2(const float2* p, df64& a, df64& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = df64(v.x, v.y);
+    b = df64(v.z, v.w);
+}
+// n (even) consecutive double-float values from a 16-byte aligned address
+template <int N>
+__device__ __forceinline__ void lddn(const float2* p, df64 (&v)[N]) {
+    static_assert(N % 2 == 0, "pairs");
+#pragma unroll
+    for (int k = 0; k < N; k += 2) ldd2(p + k, v[k], v[k + 1]);
+}
+__device__ __forceinline__ df64 ldg_d(const float2* p) {
+    const float2 v = __ldg(p);
+    return df64(v.x, v.y);
 }
 
-// Mixed precision true residual, float64, landmark pass (one thread per landmark, its observations
-// are contiguous): u_o = J_p x_cam(o), y_l = V_l^-1 sum_o J_l^T u_o, and v_o = u_o - J_l y_l into uv.
-// Then (S x)_j = sum_{o in j} J_p^T v_o + lambda D_p x_j = U_j x_j - (W V^-1 W^T x)_j (Eq. 13).
-__global__ void k_jres_land(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
-                            const int32_t* __restrict__ oc, const double* __restrict__ Jc,
-                            const double* __restrict__ Jl, const double* __restrict__ Lall,
-                            const double* __restrict__ x, double* __restrict__ uv) {
+// damp() of the float64 build in double-float: d + lambda clamp(d, 1e-6, 1e32) (Marquardt) or d + lambda;
+// lam = lambda split into double-float
+__device__ __forceinline__ df64 damp_df(df64 d, int damping, df64 lam) {
+    if (damping == BA_DAMPING_IDENTITY) return d + lam;
+    const df64 c = d.hi < 1e-6f ? df64(1e-6f) : (d.hi > 1e32f ? df64(1e32f) : d);
+    return d + lam * c;
+}
+
+// V_l^{-1} s from L (packed with its reciprocal diagonal), double-float
+__device__ __forceinline__ void solve_V_df(const float2* L, df64 s0, df64 s1, df64 s2, df64& y0, df64& y1, df64& y2) {
+    const df64 L0 = ldd(L), L1 = ldd(L + 1), L2 = ldd(L + 2), L3 = ldd(L + 3), L4 = ldd(L + 4), L5 = ldd(L + 5);
+    const df64 z0 = s0 * L0;
+    const df64 z1 = (s1 - L1 * z0) * L2;
+    const df64 z2 = (s2 - L3 * z0 - L4 * z1) * L5;
+    y2 = z2 * L5;
+    y1 = (z1 - L4 * y2) * L2;
+    y0 = (z0 - L1 * y1 - L3 * y2) * L0;
+}
+
+// r, J_p, J_l per observation in double-float (bal_jacobian_P on df64), and P, Y = R X in float32
+// (their high parts) at the observation's camera-order position.  A warp takes 32 consecutive
+// observations and writes their rows of J_p (32 x 144 B), J_l and r through shared memory as 16-byte
+// stores: a thread storing its own 144-byte row made every store instruction touch 32 sectors.
+constexpr int kLinThreads = 256;
+__global__ void __launch_bounds__(kLinThreads) k_linearize_df(
+    int64_t n_o, const float2* __restrict__ auxd, const float2* __restrict__ ptsd, const int32_t* __restrict__ oc,
+    const int32_t* __restrict__ op, const float2* __restrict__ xyd, float2* __restrict__ r, float2* __restrict__ Jc,
+    float2* __restrict__ Jl, float* __restrict__ PY32, const int32_t* __restrict__ cpos) {
+    __shared__ __align__(16) float2 stage[kLinThreads / 32][32 * 18];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float2* const sw = stage[wid];
+    const int64_t nwarps = gstride() >> 5;
+    for (int64_t base = (gtid() >> 5) * 32; base < n_o; base += nwarps * 32) {   // warp-uniform
+        const int64_t i = base + lane;
+        const bool act = i < n_o;
+        const int n = n_o - base < 32 ? int(n_o - base) : 32;
+        df64 rr[2], jc[18], jl[6];
+        if (act) {
+            df64 ax[24], X[3], Y[3], P[3], m[2];
+            const float2* cp = auxd + int64_t(oc[i]) * 24;
+            const float2* xp = ptsd + int64_t(op[i]) * 3;
+#pragma unroll
+            for (int k = 0; k < 24; k += 2) {   // 16-byte loads of the camera's 192-byte aux block
+                const float4 v = __ldg(reinterpret_cast<const float4*>(cp + k));
+                ax[k] = df64(v.x, v.y);
+                ax[k + 1] = df64(v.z, v.w);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) X[k] = ldg_d(xp + k);
+            lddn<2>(xyd + 2 * i, m);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Y[a] = ax[3 * a] * X[0] + ax[3 * a + 1] * X[1] + ax[3 * a + 2] * X[2];
+                P[a] = Y[a] + ax[18 + a];
+            }
+            bal_jacobian_P<df64>(ax, Y, P, m, rr, jc, jl);
+            float* py = PY32 + 6 * int64_t(cpos[i]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                py[k] = P[k].hi;
+                py[3 + k] = Y[k].hi;
+            }
+        }
+        // J_p: 32 rows of 18 values (144 B each), then J_l (48 B) with r (16 B) after it
+#pragma unroll
+        for (int k = 0; k < 18; ++k) sw[18 * lane + k] = make_float2(jc[k].hi, jc[k].lo);
+        __syncwarp();
+        {
+            const float4* src = reinterpret_cast<const float4*>(sw);
+            float4* dst = reinterpret_cast<float4*>(Jc + 18 * base);
+            for (int u = lane; u < 9 * n; u += 32) dst[u] = src[u];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sw[6 * lane + k] = make_float2(jl[k].hi, jl[k].lo);
+        sw[6 * 32 + 2 * lane] = make_float2(rr[0].hi, rr[0].lo);
+        sw[6 * 32 + 2 * lane + 1] = make_float2(rr[1].hi, rr[1].lo);
+        __syncwarp();
+        {
+            const float4* src = reinterpret_cast<const float4*>(sw);
+            float4* dl = reinterpret_cast<float4*>(Jl + 6 * base);
+            for (int u = lane; u < 3 * n; u += 32) dl[u] = src[u];
+            const float4* srr = reinterpret_cast<const float4*>(sw + 6 * 32);
+            float4* dr = reinterpret_cast<float4*>(r + 2 * base);
+            for (int u = lane; u < n; u += 32) dr[u] = srr[u];
+        }
+        __syncwarp();
+    }
+}
+
+// Per landmark in double-float: V_lambda = sum J_l^T J_l + damping, b_l = sum J_l^T r, V = L L^T
+// (L packed with its reciprocal diagonal), y_l = V^{-1} b_l; L also in float32 (its high parts).
+// The float64 V and e of the float64 build are not needed here (the getters form V on request).
+__global__ void k_landmarks_df(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                               const float2* __restrict__ r, const float2* __restrict__ Jl, int damping, float lam_hi,
+                               float lam_lo, float2* __restrict__ Lout, float2* __restrict__ blout,
+                               float* __restrict__ L32, float2* __restrict__ yout, int* status) {
+    const df64 lam(lam_hi, lam_lo);
     for (int64_t t = gtid(); t < n_l; t += gstride()) {
         const int64_t l = order[t];
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        const int64_t o0 = pt_ptr[l], o1 = pt_ptr[l + 1];
-        for (int64_t o = o0; o < o1; ++o) {
-            const double* xc = x + 9 * int64_t(oc[o]);
-            const double* jc = Jc + 18 * o;
-            double u0 = 0.0, u1 = 0.0;
+        df64 v00(0.f), v01(0.f), v02(0.f), v11(0.f), v12(0.f), v22(0.f), b0(0.f), b1(0.f), b2(0.f);
+#pragma unroll 4
+        for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
+            df64 jv[6], rv[2];
+            lddn<6>(Jl + 6 * o, jv);
+            lddn<2>(r + 2 * o, rv);
+            const df64 a0 = jv[0], a1 = jv[1], a2 = jv[2], c0 = jv[3], c1 = jv[4], c2 = jv[5];
+            const df64 r0 = rv[0], r1 = rv[1];
+            v00 += a0 * a0 + c0 * c0;
+            v01 += a0 * a1 + c0 * c1;
+            v02 += a0 * a2 + c0 * c2;
+            v11 += a1 * a1 + c1 * c1;
+            v12 += a1 * a2 + c1 * c2;
+            v22 += a2 * a2 + c2 * c2;
+            b0 += a0 * r0 + c0 * r1;
+            b1 += a1 * r0 + c1 * r1;
+            b2 += a2 * r0 + c2 * r1;
+        }
+        v00 = damp_df(v00, damping, lam);
+        v11 = damp_df(v11, damping, lam);
+        v22 = damp_df(v22, damping, lam);
+        const df64 i00 = rsqrt_fast(v00);
+        const df64 l10 = v01 * i00, l20 = v02 * i00;
+        const df64 i11 = rsqrt_fast(v11 - l10 * l10);
+        const df64 l21 = (v12 - l20 * l10) * i11;
+        const df64 i22 = rsqrt_fast(v22 - l20 * l20 - l21 * l21);
+        if (!(df_positive(i00) && df_positive(i11) && df_positive(i22))) atomicExch(status, BA_ERR_SINGULAR);
+        const df64 Lv[6] = {i00, l10, i11, l20, l21, i22};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            df_st(Lout + 6 * l + k, Lv[k]);
+            L32[6 * l + k] = Lv[k].hi;
+        }
+        df_st(blout + 3 * l, b0);
+        df_st(blout + 3 * l + 1, b1);
+        df_st(blout + 3 * l + 2, b2);
+        const df64 e0 = b0 * i00;
+        const df64 e1 = (b1 - l10 * e0) * i11;
+        const df64 e2 = (b2 - l20 * e0 - l21 * e1) * i22;
+        const df64 y2 = e2 * i22;
+        const df64 y1 = (e1 - l21 * y2) * i11;
+        const df64 y0 = (e0 - l10 * y1 - l20 * y2) * i00;
+        df_st(yout + 3 * l, y0);
+        df_st(yout + 3 * l + 1, y1);
+        df_st(yout + 3 * l + 2, y2);
+    }
+}
+
+// Sum of a double-float value over the CTA's kCamThreads threads in a fixed order (warp shuffle
+// tree, then the warps in order); red: [kCamThreads / 32] per value.  Every thread gets the sum.
+template <int NV>
+__device__ __forceinline__ void cta_sum_df(df64 (&v)[NV], df64 (*red)[NV]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += df_shfl_xor(v[k], o);
+        if (lane == 0) red[wid][k] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        df64 t = red[0][k];
+#pragma unroll
+        for (int w = 1; w < kCamThreads / 32; ++w) t += red[w][k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+// Per camera in double-float: b~_j = sum_o J_p^T (r_o - J_l y_l) (Eq. 14) and the damping
+// lambda D_p^T D_p from sum_o diag(J_p^T J_p); both leave as float64.
+__global__ void __launch_bounds__(kCamThreads) k_cam_rhs_df(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const int32_t* __restrict__ op, const float2* __restrict__ r, const float2* __restrict__ Jc,
+    const float2* __restrict__ Jl, const float2* __restrict__ yl, int damping, double lambda,
+    double* __restrict__ btout, double* __restrict__ dadd) {
+    __shared__ df64 red[kCamThreads / 32][18];
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        df64 v[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) v[k] = df64(0.f);
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            const float2* y = yl + 3 * int64_t(op[o]);
+            const df64 y0 = ldd(y), y1 = ldd(y + 1), y2 = ldd(y + 2);
+            df64 jl[6], rv[2], jc[18];
+            lddn<6>(Jl + 6 * o, jl);
+            lddn<2>(r + 2 * o, rv);
+            lddn<18>(Jc + 18 * o, jc);
+            const df64 s0 = rv[0] - (jl[0] * y0 + jl[1] * y1 + jl[2] * y2);
+            const df64 s1 = rv[1] - (jl[3] * y0 + jl[4] * y1 + jl[5] * y2);
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                const double xa = xc[a];
-                u0 += jc[a] * xa;
-                u1 += jc[9 + a] * xa;
+                const df64 c0 = jc[a], c1 = jc[9 + a];
+                v[a] += c0 * s0 + c1 * s1;
+                v[9 + a] += c0 * c0 + c1 * c1;
             }
-            uv[2 * o] = u0;
-            uv[2 * o + 1] = u1;
-            const double* jl = Jl + 6 * o;
-            s0 += jl[0] * u0 + jl[3] * u1;
-            s1 += jl[1] * u0 + jl[4] * u1;
-            s2 += jl[2] * u0 + jl[5] * u1;
         }
-        double y0, y1, y2;
-        solve_V(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
-        for (int64_t o = o0; o < o1; ++o) {
-            const double* jl = Jl + 6 * o;
-            uv[2 * o] -= jl[0] * y0 + jl[1] * y1 + jl[2] * y2;
-            uv[2 * o + 1] -= jl[3] * y0 + jl[4] * y1 + jl[5] * y2;
+        cta_sum_df<18>(v, red);
+        if (threadIdx.x < 18) {
+            const int k = threadIdx.x;
+            const double d = df_to(v[k]);
+            if (k < 9) btout[9 * int64_t(j) + k] = d;
+            else dadd[9 * int64_t(j) + k - 9] = damp_add(d, damping, lambda);
         }
     }
 }
 
-// Camera pass of the true residual: out_j = -b~_j - (S x)_j; camera j's sums of |out_j|^2 and |b~_j|^2
-// into partial[2 j], partial[2 j + 1] (one CTA per camera).
-__global__ void __launch_bounds__(kCamThreads) k_jres_cam(
-    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
-    const double* __restrict__ Jc, const double* __restrict__ uv, const double* __restrict__ dadd,
-    const double* __restrict__ x, const double* __restrict__ bt, double* __restrict__ out,
-    double* __restrict__ partial) {
-    __shared__ double red[kCamThreads / 32][9];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
-        double acc[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) acc[a] = 0.0;
-        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
-            const int64_t o = cam_obs[q];
-            const double v0 = uv[2 * o], v1 = uv[2 * o + 1];
-            const double* jc = Jc + 18 * o;
-#pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] += jc[a] * v0 + jc[9 + a] * v1;
-        }
+// True residual, observation pass, double-float: u_o = J_p x_cam(o) into uv (xd: x split into
+// double-float per camera).  Thread = observation, so a warp reads 32 consecutive J_p rows.
+__global__ void k_jres_obs_df(int64_t n_o, const int32_t* __restrict__ oc, const float2* __restrict__ Jc,
+                              const float2* __restrict__ xd, float2* __restrict__ uv) {
+    for (int64_t o = gtid(); o < n_o; o += gstride()) {
+        const float2* xc = xd + 9 * int64_t(oc[o]);
+        df64 jc[18];
+        lddn<18>(Jc + 18 * o, jc);
+        df64 u0(0.f), u1(0.f);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const double v = warp_sum(acc[a]);
-            if (lane == 0) red[wid][a] = v;
+            const df64 xa = ldg_d(xc + a);
+            u0 += jc[a] * xa;
+            u1 += jc[9 + a] * xa;
         }
-        __syncthreads();
+        *reinterpret_cast<float4*>(uv + 2 * o) = make_float4(u0.hi, u0.lo, u1.hi, u1.lo);
+    }
+}
+
+// True residual, landmark pass: y_l = V_l^-1 sum_o J_l^T u_o and v_o = u_o - J_l y_l in place of u_o.
+__global__ void k_jres_land_df(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                               const float2* __restrict__ Jl, const float2* __restrict__ Lall,
+                               float2* __restrict__ uv) {
+    for (int64_t t = gtid(); t < n_l; t += gstride()) {
+        const int64_t l = order[t];
+        df64 s0(0.f), s1(0.f), s2(0.f);
+        const int64_t o0 = pt_ptr[l], o1 = pt_ptr[l + 1];
+#pragma unroll 4
+        for (int64_t o = o0; o < o1; ++o) {
+            df64 jl[6], u[2];
+            lddn<6>(Jl + 6 * o, jl);
+            lddn<2>(uv + 2 * o, u);
+            s0 += jl[0] * u[0] + jl[3] * u[1];
+            s1 += jl[1] * u[0] + jl[4] * u[1];
+            s2 += jl[2] * u[0] + jl[5] * u[1];
+        }
+        df64 y0, y1, y2;
+        solve_V_df(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
+        for (int64_t o = o0; o < o1; ++o) {
+            df64 jl[6], u[2];
+            lddn<6>(Jl + 6 * o, jl);
+            lddn<2>(uv + 2 * o, u);
+            const df64 v0 = u[0] - (jl[0] * y0 + jl[1] * y1 + jl[2] * y2);
+            const df64 v1 = u[1] - (jl[3] * y0 + jl[4] * y1 + jl[5] * y2);
+            *reinterpret_cast<float4*>(uv + 2 * o) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+        }
+    }
+}
+
+// True residual, camera pass: out_j = -b~_j - (S x)_j with (S x)_j = sum_{o in j} J_p^T v_o (double-float)
+// + lambda D_p x_j (float64); camera j's |out_j|^2 and |b~_j|^2 into partial[2 j], partial[2 j + 1].
+__global__ void __launch_bounds__(kCamThreads) k_jres_cam_df(
+    int32_t n_c, const int64_t* __restrict__ cam_ptr, const int32_t* __restrict__ cam_obs,
+    const float2* __restrict__ Jc, const float2* __restrict__ uv, const double* __restrict__ dadd,
+    const double* __restrict__ x, const double* __restrict__ bt, double* __restrict__ out,
+    double* __restrict__ partial) {
+    __shared__ df64 red[kCamThreads / 32][9];
+    for (int j = blockIdx.x; j < n_c; j += gridDim.x) {
+        df64 acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = df64(0.f);
+        for (int64_t q = cam_ptr[j] + threadIdx.x; q < cam_ptr[j + 1]; q += blockDim.x) {
+            const int64_t o = cam_obs[q];
+            df64 u[2], jc[18];
+            lddn<2>(uv + 2 * o, u);
+            lddn<18>(Jc + 18 * o, jc);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] += jc[a] * u[0] + jc[9 + a] * u[1];
+        }
+        cta_sum_df<9>(acc, red);
         double tt = 0.0, bb = 0.0;
         if (threadIdx.x < 9) {
             const int a = threadIdx.x;
             const int64_t i = 9 * int64_t(j) + a;
-            const double sx = ((red[0][a] + red[1][a]) + (red[2][a] + red[3][a])) + dadd[i] * x[i];
+            const double sx = df_to(acc[a]) + dadd[i] * x[i];
             const double b_ = bt[i];
             const double rv = -b_ - sx;
             if (out) out[i] = rv;
@@ -996,34 +1197,50 @@ __global__ void __launch_bounds__(kCamThreads) k_jres_cam(
     }
 }
 
-// Back-substitution without G (mixed precision): dx_l = -V_l^{-1} (b_l + sum_o J_l^T J_p dx_p,cam(o))
-// (Eq. 15 with the sign that follows from Eq. 6).
-__global__ void k_back_sub_J(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
-                             const int32_t* __restrict__ oc, const double* __restrict__ Jc,
-                             const double* __restrict__ Jl, const double* __restrict__ Lall,
-                             const double* __restrict__ bl, const double* __restrict__ dxp, double* __restrict__ dxl) {
+// Back-substitution in double-float: dx_l = -V_l^{-1} (b_l + sum_o J_l^T J_p dx_p,cam(o)) (Eq. 15 with
+// the sign that follows from Eq. 6); dxpd: dx_p split into double-float per camera.
+__global__ void k_back_sub_df(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
+                              const int32_t* __restrict__ oc, const float2* __restrict__ Jc,
+                              const float2* __restrict__ Jl, const float2* __restrict__ Lall,
+                              const float2* __restrict__ bl, const float2* __restrict__ dxpd,
+                              double* __restrict__ dxl) {
     for (int64_t t = gtid(); t < n_l; t += gstride()) {
         const int64_t l = order[t];
-        double s0 = bl[3 * l], s1 = bl[3 * l + 1], s2 = bl[3 * l + 2];
+        df64 s0 = ldd(bl + 3 * l), s1 = ldd(bl + 3 * l + 1), s2 = ldd(bl + 3 * l + 2);
         for (int64_t o = pt_ptr[l]; o < pt_ptr[l + 1]; ++o) {
-            const double* xc = dxp + 9 * int64_t(oc[o]);
-            const double* jc = Jc + 18 * o;
-            double u0 = 0.0, u1 = 0.0;
+            const float2* xc = dxpd + 9 * int64_t(oc[o]);
+            df64 jc[18], jl[6];
+            lddn<18>(Jc + 18 * o, jc);
+            lddn<6>(Jl + 6 * o, jl);
+            df64 u0(0.f), u1(0.f);
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                u0 += jc[a] * xc[a];
-                u1 += jc[9 + a] * xc[a];
+                const df64 xa = ldg_d(xc + a);
+                u0 += jc[a] * xa;
+                u1 += jc[9 + a] * xa;
             }
-            const double* jl = Jl + 6 * o;
             s0 += jl[0] * u0 + jl[3] * u1;
             s1 += jl[1] * u0 + jl[4] * u1;
             s2 += jl[2] * u0 + jl[5] * u1;
         }
-        double y0, y1, y2;
-        solve_V(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
-        dxl[3 * l] = -y0;
-        dxl[3 * l + 1] = -y1;
-        dxl[3 * l + 2] = -y2;
+        df64 y0, y1, y2;
+        solve_V_df(Lall + 6 * l, s0, s1, s2, y0, y1, y2);
+        dxl[3 * l] = -df_to(y0);
+        dxl[3 * l + 1] = -df_to(y1);
+        dxl[3 * l + 2] = -df_to(y2);
+    }
+}
+
+// float64 -> double-float, elementwise
+__global__ void k_split_df(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) df_st(out + i, df_from(in[i]));
+}
+// double-float -> float64 in place (the buffer holds n float2 values; each becomes the double at
+// the same index, of the same size)
+__global__ void k_df_to_double(double* __restrict__ buf, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const float2 v = reinterpret_cast<const float2*>(buf)[i];
+        buf[i] = double(v.x) + double(v.y);
     }
 }
 
@@ -1194,11 +1411,25 @@ void launch_project(int64_t n_o, const double* cams, const double* pts, const in
 }
 
 void launch_linearize(const Structure& s, System& y, cudaStream_t st) {
+    if (y.S32) {   // mixed precision: double-float
+        k_linearize_df<<<grid_for(s.n_o, kLinThreads), kLinThreads, 0, st>>>(
+            s.n_o, y.auxd, y.ptsd, s.obs_cam, s.obs_pt, s.obs_xyd, reinterpret_cast<float2*>(y.r),
+            reinterpret_cast<float2*>(y.Jc), reinterpret_cast<float2*>(y.Jl), y.PY32, s.cpos);
+        return;
+    }
     k_linearize<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(s.n_o, y.aux, y.pts, s.obs_cam, s.obs_pt,
                                                                  s.obs_xy, y.r, y.Jc, y.Jl, y.PY32, s.cpos);
 }
 
 void launch_landmarks(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
+    if (y.S32) {   // mixed precision: double-float
+        const float lh = float(lambda), ll = float(lambda - double(lh));
+        k_landmarks_df<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(
+            s.n_l, s.pt_ptr, s.lm_order, reinterpret_cast<const float2*>(y.r), reinterpret_cast<const float2*>(y.Jl),
+            damping, lh, ll, reinterpret_cast<float2*>(y.L), reinterpret_cast<float2*>(y.bl), y.L32,
+            reinterpret_cast<float2*>(y.yl), y.status);
+        return;
+    }
     k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, y.r, y.Jl, damping,
                                                                  lambda, y.V, y.L, y.bl, y.e, y.L32, y.yl, y.status);
 }
@@ -1214,9 +1445,29 @@ void launch_cameras(const Structure& s, System& y, int damping, double lambda, c
                                                    lambda, y.U, y.bp, y.bt);
 }
 
-void launch_cameras_U(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
-    k_cameras<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, nullptr, y.e,
+// Mixed precision, on request (ba_get_normal): the float64 U, b_p, V, b_l of the last build, from
+// float64 copies of its double-float r, J_p, J_l (r64, Jc64, Jl64, n_o x 2 / 18 / 6) with the kernels
+// of the float64 build; V, L, b_l, e go to V64, L64, bl64, e64 (n_l x 9 / 6 / 3 / 3), U and b_p to
+// y.U, y.bp.
+void launch_normal_request(const Structure& s, System& y, int damping, double lambda, double* r64, double* Jc64,
+                           double* Jl64, double* V64, double* L64, double* bl64, double* e64, cudaStream_t st) {
+    const int64_t n[3] = {2 * s.n_o, 18 * s.n_o, 6 * s.n_o};
+    const double* src[3] = {y.r, y.Jc, y.Jl};
+    double* dst[3] = {r64, Jc64, Jl64};
+    for (int k = 0; k < 3; ++k) {
+        cudaMemcpyAsync(dst[k], src[k], sizeof(double) * n[k], cudaMemcpyDeviceToDevice, st);
+        k_df_to_double<<<grid_for(n[k], kThreads), kThreads, 0, st>>>(dst[k], n[k]);
+    }
+    k_landmarks<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, r64, Jl64, damping,
+                                                                 lambda, V64, L64, bl64, e64, nullptr, nullptr,
+                                                                 y.status);
+    k_cameras<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, r64, Jc64, nullptr, e64,
                                                    damping, lambda, y.U, y.bp, nullptr);
+}
+
+// double-float -> float64 in place, n values
+void launch_df_to_double(double* buf, int64_t n, cudaStream_t st) {
+    k_df_to_double<<<grid_for(n, kThreads), kThreads, 0, st>>>(buf, n);
 }
 
 void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
@@ -1224,8 +1475,11 @@ void launch_schur_diag(const Structure& s, System& y, cudaStream_t st) {
 }
 
 void launch_cam_rhs(const Structure& s, System& y, int damping, double lambda, cudaStream_t st) {
-    k_cam_rhs<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, y.r, y.Jc, y.Jl, y.yl,
-                                                   damping, lambda, y.bt, y.dadd);
+    // mixed precision only (the float64 build forms b~ from G): double-float
+    k_cam_rhs_df<<<cam_grid(s), kCamThreads, 0, st>>>(
+        s.n_c, s.cam_ptr, s.cam_obs, s.obs_pt, reinterpret_cast<const float2*>(y.r),
+        reinterpret_cast<const float2*>(y.Jc), reinterpret_cast<const float2*>(y.Jl),
+        reinterpret_cast<const float2*>(y.yl), damping, lambda, y.bt, y.dadd);
 }
 
 void launch_schur_diag32(const Structure& s, System& y, cudaStream_t st) {
@@ -1250,16 +1504,30 @@ void launch_schur_mixed(const Structure& s, System& y, cudaStream_t st) {
         s.n_c, s.row_ptr, s.tile_ptr, s.diag_pos, y.Sd, y.lam, y.S32, s.tile_ptr_u, y.S32u);
 }
 
-void launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
-                              cudaStream_t st) {
-    k_jres_land<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.Jc, y.Jl,
-                                                                 y.L, x, y.uv);
-    k_jres_cam<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs, y.Jc, y.uv, y.dadd, x, y.bt, out,
-                                                    partial);
+// Mixed precision's true residual in double-float (three launches); y.xd must hold x split into
+// double-float (the refinement's accumulation, which forms x, writes it).
+int launch_implicit_residual(const Structure& s, const System& y, const double* x, double* out, double* partial,
+                             cudaStream_t st) {
+    k_jres_obs_df<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(
+        s.n_o, s.obs_cam, reinterpret_cast<const float2*>(y.Jc), y.xd, reinterpret_cast<float2*>(y.uv));
+    k_jres_land_df<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(
+        s.n_l, s.pt_ptr, s.lm_order, reinterpret_cast<const float2*>(y.Jl), reinterpret_cast<const float2*>(y.L),
+        reinterpret_cast<float2*>(y.uv));
+    k_jres_cam_df<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs,
+                                                       reinterpret_cast<const float2*>(y.Jc),
+                                                       reinterpret_cast<const float2*>(y.uv), y.dadd, x, y.bt, out,
+                                                       partial);
+    return 3;
 }
 
 void launch_cam_prep(const Structure& s, System& y, cudaStream_t st) {
-    k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux, y.aux32);
+    if (y.ptsd) {   // mixed precision: also the double-float aux blocks and points
+        const int64_t n_pv = int64_t(s.n_l) * 3;
+        k_cam_prep<<<grid_for(n_pv > s.n_c ? n_pv : s.n_c, 256), 256, 0, st>>>(s.n_c, y.cams, y.aux, y.aux32, y.auxd,
+                                                                              n_pv, y.pts, y.ptsd);
+        return;
+    }
+    k_cam_prep<<<grid_for(s.n_c, 64), 64, 0, st>>>(s.n_c, y.cams, y.aux, y.aux32, nullptr, 0, nullptr, nullptr);
 }
 
 // Float64: D^{-1}.  Mixed precision: Lam and the inverse blocks of the scaled system only (its solves
@@ -1282,9 +1550,14 @@ void launch_back_substitute(const Structure& s, const System& y, const double* d
     if (y.G)
         k_back_substitute<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.G,
                                                                            y.L, y.e, dxp, dxl);
-    else
-        k_back_sub_J<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, y.Jc,
-                                                                      y.Jl, y.L, y.bl, dxp, dxl);
+    else {
+        // mixed precision: dx_p split into double-float (the true residual's buffer, idle here)
+        k_split_df<<<grid_for(int64_t(s.n_c) * 9, kThreads), kThreads, 0, st>>>(dxp, y.xd, int64_t(s.n_c) * 9);
+        k_back_sub_df<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(
+            s.n_l, s.pt_ptr, s.lm_order, s.obs_cam, reinterpret_cast<const float2*>(y.Jc),
+            reinterpret_cast<const float2*>(y.Jl), reinterpret_cast<const float2*>(y.L),
+            reinterpret_cast<const float2*>(y.bl), y.xd, dxl);
+    }
 }
 
 void launch_cost(const Structure& s, const double* cams, const double* pts, double* partial, int nparts,

@@ -1975,9 +1975,16 @@ __global__ void k_true_reduce(Ctl* ctl, const double* __restrict__ partial) {
 }
 
 // mixed precision: x64 += Lam (double) d32, the inner solution mapped back from the scaled system
+// x += Lam d (a float32 sweep's correction, unscaled), and x split into double-float for the true
+// residual that follows (its per-observation products take no float64 input)
 __global__ void k_accumulate(int64_t n, const float* __restrict__ d, const double* __restrict__ lam,
-                             double* __restrict__ x) {
-    for (int64_t i = gtid(); i < n; i += gstride()) x[i] += lam[i] * double(d[i]);
+                             double* __restrict__ x, float2* __restrict__ xd) {
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const double v = x[i] + lam[i] * double(d[i]);
+        x[i] = v;
+        const float h = __double2float_rn(v);
+        xd[i] = make_float2(h, __double2float_rn(v - double(h)));
+    }
 }
 
 // refinement start: x = 0 and rt = -b~
@@ -2634,8 +2641,7 @@ static int true_residual(Solver* w, const Structure& s, const System& y, const d
             s.n_c, s.row_ptr, s.tile_ptr, s.col, y.S, x, y.bt, out, ptr<double>(w->part_cam));
         n = 1;
     } else {
-        launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
-        n = 2;
+        n = launch_implicit_residual(s, y, x, out, ptr<double>(w->part_cam), st);
     }
     k_true_reduce<<<w->nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<double>(w->part_cam));
     return n + 1;
@@ -2726,7 +2732,7 @@ static cudaGraphExec_t build_solve_graph(Solver* w, const Structure& s, const Sy
             int kpre = 0;
             capture_krylov<float>(w, s, y.S32, y.S32u, y.Dhat, ptr<double>(w->rt), 1.0, y.lam, ptr<float>(w->xw),
                                   ptr<Outer>(w->outer), mcg, a.chunk, c2, w->cap3, &kpre, &gc.body);
-            k_accumulate<<<grid_for_host(n), kThreads, 0, c2>>>(n, ptr<float>(w->xw), y.lam, x);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, c2>>>(n, ptr<float>(w->xw), y.lam, x, y.xd);
             const int tr = true_residual(w, s, y, x, ptr<double>(w->rt), c2);
             k_refine_after<<<nb, 32, 0, c2>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), ptr<Params>(w->params));
             k_refine_plan<<<1, kThreads, 0, c2>>>(ptr<Outer>(w->outer), nb, ptr<Params>(w->params), ho, 1,
@@ -2827,7 +2833,7 @@ static void run_host_loops(Solver* w, const Structure& s, const System& y, const
                                            ptr<float>(w->xw), ptr<Outer>(w->outer), st);
             k_loop_cond<<<1, kThreads, 0, st>>>(none, 0, ptr<Ctl>(w->ctl), nb, lp, 1, a.chunk, prm);
             launches += 1 + host_krylov_loop(w, chunk_exec, gc, a, st, waits);
-            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x);
+            k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x, y.xd);
             launches += 1 + true_residual(w, s, y, x, ptr<double>(w->rt), st);
             k_refine_after<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Outer>(w->outer), prm);
             k_refine_plan<<<1, kThreads, 0, st>>>(ptr<Outer>(w->outer), nb, prm, none, 0, lp, 1);
