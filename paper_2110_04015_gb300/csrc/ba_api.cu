@@ -316,15 +316,23 @@ void build_structure(ba_problem* p, int32_t n_c, int32_t n_l, int64_t n_o, const
         s.cpos = upload(p, cpos);
         s.cam_lm = upload(p, cam_lm);
         s.up_cams = upload(p, ucams);
-        // the upper blocks by decreasing pair count, stable (counting sort)
+        // the upper blocks by decreasing pair-count class floor(log2(count)), stable: a warp's three
+        // blocks differ by at most 2x in pairs, and within a class the blocks keep their (j, k) order,
+        // in which the G rows of the blocks in flight are shared (one row serves the blocks of its
+        // camera's row j, and the blocks (j', k) of the cameras j' that see its landmark)
         if (n_up >= (int64_t(1) << 31)) throw Error(BA_ERR_INVALID_ARG, "too many blocks in S");
-        int64_t pmax = 0;
-        for (int64_t u = 0; u < n_up; ++u) pmax = std::max(pmax, up_pp[u + 1] - up_pp[u]);
-        std::vector<int64_t> pc(size_t(pmax) + 2, 0);
-        for (int64_t u = 0; u < n_up; ++u) pc[size_t(pmax - (up_pp[u + 1] - up_pp[u])) + 1]++;
+        auto cls = [&](int64_t u) {
+            int64_t c = up_pp[u + 1] - up_pp[u], b = 0;
+            while (c > 1) { c >>= 1; ++b; }
+            return b;
+        };
+        int64_t bmax = 0;
+        for (int64_t u = 0; u < n_up; ++u) bmax = std::max(bmax, cls(u));
+        std::vector<int64_t> pc(size_t(bmax) + 2, 0);
+        for (int64_t u = 0; u < n_up; ++u) pc[size_t(bmax - cls(u)) + 1]++;
         for (size_t k = 1; k < pc.size(); ++k) pc[k] += pc[k - 1];
         std::vector<int32_t> uorder(n_up > 0 ? n_up : 1);
-        for (int64_t u = 0; u < n_up; ++u) uorder[pc[size_t(pmax - (up_pp[u + 1] - up_pp[u]))]++] = int32_t(u);
+        for (int64_t u = 0; u < n_up; ++u) uorder[pc[size_t(bmax - cls(u))]++] = int32_t(u);
         s.up_order = upload(p, uorder);
     }
     s.pairs = upload(p, pr);

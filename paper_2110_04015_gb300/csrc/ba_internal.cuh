@@ -89,7 +89,7 @@ struct Structure {
     int2* pairs = nullptr;        // n_pairs: (o_j, o_k) point-order slots of one landmark (mixed precision:
                                   // their camera-order positions, where the float32 G rows are kept)
     int2* up_cams = nullptr;      // n_up (mixed precision): the cameras (j, k) of each upper block
-    int32_t* up_order = nullptr;  // n_up (mixed precision): the upper blocks by decreasing pair count
+    int32_t* up_order = nullptr;  // n_up (mixed precision): the upper blocks by decreasing pair-count class
     int32_t* cpos = nullptr;      // n_o (mixed precision): camera-order position of each point-order slot
     int32_t* cam_lm = nullptr;    // n_o (mixed precision): landmark of each camera-order position
     // upper triangle of S (mixed precision's one-column products): row j holds S_jj, then S_jk, k > j,

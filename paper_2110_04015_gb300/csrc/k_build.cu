@@ -612,8 +612,9 @@ __device__ __forceinline__ void lds9(const float* p, float* v) {
 // (lanes 27..31 idle): lane 9 g + 3 A + B sums the 3x3 sub-block at rows 3A.., columns 3B.. of its
 // group's block over all its pairs, from rows 3A..3A+2 of G_oj and 3B..3B+2 of G_ok (nine
 // consecutive values each: vector shared loads for 27 fused multiply-adds).  Blocks go in
-// decreasing pair count (up_order), so the three blocks of a warp have about as many pairs and the
-// largest start first.  A group copies the G rows of its pairs into shared memory kOffChunk pairs at
+// decreasing pair-count class (up_order: floor(log2(pairs)), (j, k) order within a class), so the
+// three blocks of a warp have about as many pairs, the largest start first, and the blocks in flight
+// share their G rows in L2.  A group copies the G rows of its pairs into shared memory kOffChunk pairs at
 // a time with 16-byte asynchronous copies, double-buffered (lane 3A + B copies piece 3A + B of
 // both rows of every pair; a row is three 9-value parts on 16-byte boundaries).  The three blocks
 // then meet in shared memory, and the warp writes their 3 x 81 values per destination together.
