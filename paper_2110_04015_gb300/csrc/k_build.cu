@@ -1125,11 +1125,13 @@ __global__ void k_jres_obs_df(int64_t n_o, const int32_t* __restrict__ oc, const
 }
 
 // True residual, landmark pass: y_l = V_l^-1 sum_o J_l^T u_o and v_o = u_o - J_l y_l in place of u_o.
-__global__ void k_jres_land_df(int32_t n_l, const int64_t* __restrict__ pt_ptr, const int32_t* __restrict__ order,
-                               const float2* __restrict__ Jl, const float2* __restrict__ Lall,
-                               float2* __restrict__ uv) {
-    for (int64_t t = gtid(); t < n_l; t += gstride()) {
-        const int64_t l = order[t];
+// Landmarks in index order (not by track length): neighbouring lanes then read neighbouring rows,
+// which on the 1000-camera case cut the DRAM reads from 184 to 125 MB and the time from 90 to 66 µs
+// despite the lanes' unequal loop lengths (the landmark factors, heavier per observation, run
+// faster in track-length order).
+__global__ void k_jres_land_df(int32_t n_l, const int64_t* __restrict__ pt_ptr, const float2* __restrict__ Jl,
+                               const float2* __restrict__ Lall, float2* __restrict__ uv) {
+    for (int64_t l = gtid(); l < n_l; l += gstride()) {
         df64 s0(0.f), s1(0.f), s2(0.f);
         const int64_t o0 = pt_ptr[l], o1 = pt_ptr[l + 1];
 #pragma unroll 4
@@ -1512,7 +1514,7 @@ int launch_implicit_residual(const Structure& s, const System& y, const double* 
     k_jres_obs_df<<<grid_for(s.n_o, kThreads), kThreads, 0, st>>>(
         s.n_o, s.obs_cam, reinterpret_cast<const float2*>(y.Jc), y.xd, reinterpret_cast<float2*>(y.uv));
     k_jres_land_df<<<grid_for(s.n_l, kThreads), kThreads, 0, st>>>(
-        s.n_l, s.pt_ptr, s.lm_order, reinterpret_cast<const float2*>(y.Jl), reinterpret_cast<const float2*>(y.L),
+        s.n_l, s.pt_ptr, reinterpret_cast<const float2*>(y.Jl), reinterpret_cast<const float2*>(y.L),
         reinterpret_cast<float2*>(y.uv));
     k_jres_cam_df<<<cam_grid(s), kCamThreads, 0, st>>>(s.n_c, s.cam_ptr, s.cam_obs,
                                                        reinterpret_cast<const float2*>(y.Jc),

@@ -36,6 +36,7 @@
 #include <functional>
 #include <numeric>
 #include <queue>
+#include <utility>
 #include <vector>
 
 #include "ba_internal.cuh"
@@ -365,6 +366,12 @@ __device__ __forceinline__ void bulk_load_ef(void* dst, const void* src, uint32_
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
+// First statement of the kernels of a solve iteration, which are launched chained (launch_chained):
+// such a kernel may be scheduled while the previous kernel on the stream drains, and waits here for
+// that kernel to complete and its writes to be visible.  Without the chained attribute it returns
+// at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls) {
     for (int i = 0; i < polls; ++i) {
         uint32_t ok;
@@ -456,6 +463,7 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
     const T* __restrict__ S, const T* __restrict__ z, ItemList L, int sel, T* __restrict__ out,
     const T* __restrict__ rvec, double* __restrict__ camdot, Ctl* ctl, T* __restrict__ tb, T* __restrict__ tb8,
     const int32_t* __restrict__ cslot) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     constexpr int NW = SpmvShape<T, CFG>::kWarps, NS = SpmvShape<T, CFG>::kStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (nothing_selected(ctl, L, sel)) return;
@@ -656,6 +664,7 @@ __global__ void __launch_bounds__(kColWarps * 32, 12) k_spmv_col(const int64_t* 
                                                              const T* __restrict__ z, int sel, T* __restrict__ out,
                                                              const T* __restrict__ rvec, double* __restrict__ camdot,
                                                              const Ctl* __restrict__ ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.y;
     if (!selected(ctl, p, sel)) return;
     const Ctl& c = ctl[p];
@@ -773,6 +782,7 @@ __global__ void __launch_bounds__(SpmmCfg::kWarps * 32, 1) k_spmm(
     const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ col,
     const T* __restrict__ S, const T* __restrict__ PT, ItemList L, T* __restrict__ part, T* __restrict__ Q,
     Ctl* ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     static_assert(sizeof(T) == 4, "the multi-column product serves the float32 sweeps");
     constexpr int NW = SpmmCfg::kWarps, NS = SpmmCfg::kStages;
     constexpr int sel = kSelWide;
@@ -1036,6 +1046,7 @@ __global__ void k_init_ctl(Ctl* ctl, const Layout* __restrict__ lay, const doubl
 // the loop runs from the host (the kernel then only counts).
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, int use_handle, const Ctl* __restrict__ ctl, int nb,
                             Loops* lp, int first, int chunk, const Params* __restrict__ prm) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -1118,6 +1129,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(const double* __restric
                                                          double* __restrict__ totals, double* __restrict__ dpart,
                                                          int* __restrict__ dcnt, double* __restrict__ hist,
                                                          Ctl* ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1203,6 +1215,7 @@ __device__ void pcg_decide(Ctl* c, const double* tot, double* hist, int p, int n
 // p = z - beta p (rows of the problem)
 template <typename T>
 __global__ void k_pcg_dir(const T* __restrict__ z, T* __restrict__ P, const Ctl* __restrict__ ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
     const T beta = T(c.beta);
@@ -1225,6 +1238,7 @@ __device__ __forceinline__ int gram_ctas(int64_t n, int gx) {
 template <typename T>
 __global__ void k_mcg_gram(const T* __restrict__ P, const T* __restrict__ Q, const T* __restrict__ r,
                            double* __restrict__ partial, const Ctl* __restrict__ ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1461,6 +1475,7 @@ constexpr int kSmallThreads = 1024;
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads) k_mcg_small(Ctl* ctl, const double* __restrict__ partial, int gx, double* __restrict__ dpinv,
                             int mi1) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.x;
     Ctl* c = ctl + p;
     if (c->done) return;
@@ -1561,6 +1576,7 @@ __global__ void __launch_bounds__(kThreads) k_mcg_update(const double* __restric
                                                          double* __restrict__ totals, double* __restrict__ hist,
                                                          int* __restrict__ blk_off, int* __restrict__ blk_w, int mi1,
                                                          Ctl* ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1672,6 +1688,7 @@ __device__ void mcg_decide(Ctl* c, const double* tot, double* hist, int* blk_off
 template <typename T>
 __global__ void k_mcg_phi(const T* __restrict__ Q, const T* __restrict__ z, double* __restrict__ phip,
                           const Ctl* __restrict__ ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
     const int lane = threadIdx.x & 31;
@@ -1710,6 +1727,7 @@ template <typename T>
 __global__ void k_mcg_beta(const double* __restrict__ phip, const double* __restrict__ dpinv,
                            const int* __restrict__ blk_off, const int* __restrict__ blk_w, double* __restrict__ beta,
                            T* __restrict__ betat, const Ctl* __restrict__ ctl, int mi1) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const int p = blockIdx.y;
     const Ctl& c = ctl[p];
     if (c.done) return;
@@ -1811,6 +1829,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPqSlices * 32) k_mcg_pq(T* __restrict__ P, T* __restrict__ Q,
                                                             const T* __restrict__ z, const T* __restrict__ beta,
                                                             T* __restrict__ PT, const Ctl* __restrict__ ctl) {
+    wait_prior_grid();   // chained launch: the previous kernel's results are visible from here
     const Ctl& c = ctl[blockIdx.y];
     if (c.done) return;
     constexpr int TC = 64;
@@ -2524,12 +2543,31 @@ int solver_history(const Solver* w, int problem, const double** hist) {
 }
 
 // One launch of k_spmv in shape `cfg` (one CTA per SM).
+// Launch with programmatic stream serialization (the kernels of a solve iteration): the kernel may
+// be scheduled while the previous kernel on the stream drains and waits for it in wait_prior_grid,
+// its first statement, instead of starting only after the previous grid has retired.
+template <typename... K, typename... A>
+static void launch_chained(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...));
+}
+
 template <typename T, int MODE, bool ZH, bool SYM, int CFG>
 static void launch_spmv_cfg(cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
                             const T* S, const T* z, const ItemList& L, int sel, T* out, const T* rvec, double* camdot,
                             Ctl* ctl, T* tb, T* tb8, const int32_t* cslot) {
-    k_spmv<T, MODE, ZH, SYM, CFG><<<num_sms(), SpmvShape<T, CFG>::kWarps * 32, spmv_smem<T, CFG>(), st>>>(
-        row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8, cslot);
+    launch_chained(k_spmv<T, MODE, ZH, SYM, CFG>, dim3(num_sms()), dim3(SpmvShape<T, CFG>::kWarps * 32),
+                   spmv_smem<T, CFG>(), st, row_ptr, tile_ptr, col, S, z, L, sel, out, rvec, camdot, ctl, tb, tb8,
+                   cslot);
 }
 template <typename T, int MODE, bool ZH, bool SYM>
 static void launch_spmv(int cfg, cudaStream_t st, const int64_t* row_ptr, const int64_t* tile_ptr, const int32_t* col,
@@ -2557,8 +2595,8 @@ static int enqueue_product(Solver* w, const Structure& s, const T* S, const T* S
         T* tb8 = tb + kTbHead * s.n_up;
         launch_spmv<T, MODE, true, true>(w->spmv_cfg, st, s.row_ptr_u, s.tile_ptr_u, s.col_u, Su, zsrc, w->items_u,
                                          sel, out, rvec, camdot, ctl, tb, tb8, s.cslot);
-        k_spmv_col<T, MODE, true><<<dim3(w->gcol, w->nb), kColWarps * 32, 0, st>>>(s.qptr, tb, tb8, zsrc, sel,
-                                                                                    out, rvec, camdot, ctl);
+        launch_chained(k_spmv_col<T, MODE, true>, dim3(w->gcol, w->nb), dim3(kColWarps * 32), 0, st, s.qptr,
+                       (const T*)tb, (const T*)tb8, zsrc, sel, out, rvec, camdot, ctl);
         return 2;
     }
     launch_spmv<T, MODE, true, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, zsrc, w->items_g, sel, out,
@@ -2581,22 +2619,22 @@ static int enqueue_iteration(Solver* w, const Structure& s, const T* S, const T*
     const int Gt = num_sms();   // tile-streaming products: one CTA per SM
     if (!mcg) {
         const int np = enqueue_product<T, 1>(w, s, S, Su, P, kSelLive, Q, r, st);
-        k_pcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(Dinv, P, Q, x, r, z, ptr<double>(w->camdot), totals,
-                                                               ptr<double>(w->dpart), dcnt, ptr<double>(w->hist), ctl);
-        k_pcg_dir<T><<<dim3(w->gq, nb), kThreads, 0, st>>>(z, P, ctl);
+        launch_chained(k_pcg_update<T>, dim3(w->gu, nb), dim3(kThreads), 0, st, Dinv, P, Q, x, r, z,
+                       ptr<double>(w->camdot), totals, ptr<double>(w->dpart), dcnt, ptr<double>(w->hist), ctl);
+        launch_chained(k_pcg_dir<T>, dim3(w->gq, nb), dim3(kThreads), 0, st, z, P, ctl);
         return np + 2;
     } else {
-        k_mcg_gram<T><<<dim3(w->gg, nb), kThreads, 0, st>>>(P, Q, r, ptr<double>(w->part_a), ctl);
-        k_mcg_small<T><<<nb, kSmallThreads, 0, st>>>(ctl, ptr<double>(w->part_a), w->gg, ptr<double>(w->dpinv),
-                                                     w->mi1);
-        k_mcg_update<T><<<dim3(w->gu, nb), kThreads, 0, st>>>(
-            Dinv, P, Q, x, r, z, ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu, dcnt, totals, ptr<double>(w->hist),
-            ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1, ctl);
-        k_mcg_phi<T><<<dim3(w->gphi, nb), kThreads, 0, st>>>(Q, z, ptr<double>(w->phip), ctl);
+        launch_chained(k_mcg_gram<T>, dim3(w->gg, nb), dim3(kThreads), 0, st, P, Q, r, ptr<double>(w->part_a), ctl);
+        launch_chained(k_mcg_small<T>, dim3(nb), dim3(kSmallThreads), 0, st, ctl, ptr<double>(w->part_a), w->gg,
+                       ptr<double>(w->dpinv), w->mi1);
+        launch_chained(k_mcg_update<T>, dim3(w->gu, nb), dim3(kThreads), 0, st, Dinv, P, Q, x, r, z,
+                       ptr<double>(w->dpart) + 3 * size_t(nb) * w->gu, dcnt, totals, ptr<double>(w->hist),
+                       ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1, ctl);
+        launch_chained(k_mcg_phi<T>, dim3(w->gphi, nb), dim3(kThreads), 0, st, Q, z, ptr<double>(w->phip), ctl);
         T* betat = sizeof(T) == 8 ? ptr<T>(w->beta) : ptr<T>(w->betaf);
-        k_mcg_beta<T><<<dim3(w->gb, nb), kThreads, 0, st>>>(ptr<double>(w->phip), ptr<double>(w->dpinv),
-                                                            ptr<int>(w->blk_off), ptr<int>(w->blk_w),
-                                                            ptr<double>(w->beta), betat, ctl, w->mi1);
+        launch_chained(k_mcg_beta<T>, dim3(w->gb, nb), dim3(kThreads), 0, st, ptr<double>(w->phip),
+                       ptr<double>(w->dpinv), ptr<int>(w->blk_off), ptr<int>(w->blk_w), ptr<double>(w->beta), betat,
+                       ctl, w->mi1);
         if constexpr (sizeof(T) == 8) {
             // Eq. 18: Q_{i+1} = S Z_{i+1} - sum_j Q_j beta_{i,j}; S Z over whole rows for the
             // problems forming a global block, over the subset segments for the local ones
@@ -2605,14 +2643,16 @@ static int enqueue_iteration(Solver* w, const Structure& s, const T* S, const T*
             if (w->use_l)
                 launch_spmv<T, 0, false, false>(w->spmv_cfg, st, s.row_ptr, s.tile_ptr, s.col, S, z, w->items_l,
                                                 kSelLocal, Q, nullptr, nullptr, ctl, nullptr);
-            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, nullptr, ctl);
+            launch_chained(k_mcg_pq<T>, dim3(w->gpq, nb), dim3(kPqSlices * 32), 0, st, P, Q, z, betat, (T*)nullptr,
+                           ctl);
             return w->use_l ? 8 : 7;
         } else {
             // Algorithm 2: Q_{i+1} = S P_{i+1}
-            k_mcg_pq<T><<<dim3(w->gpq, nb), kPqSlices * 32, 0, st>>>(P, Q, z, betat, ptr<T>(w->PT), ctl);
+            launch_chained(k_mcg_pq<T>, dim3(w->gpq, nb), dim3(kPqSlices * 32), 0, st, P, Q, z, betat, ptr<T>(w->PT),
+                           ctl);
             const int np = enqueue_product<T, 2>(w, s, S, Su, P, kSelW1, Q, nullptr, st);
-            k_spmm<T><<<Gt, SpmmCfg::kWarps * 32, spmm_smem<T>(), st>>>(
-                s.row_ptr, s.tile_ptr, s.col, S, ptr<T>(w->PT), w->items_g, static_cast<T*>(w->mm_part), Q, ctl);
+            launch_chained(k_spmm<T>, dim3(Gt), dim3(SpmmCfg::kWarps * 32), spmm_smem<T>(), st, s.row_ptr, s.tile_ptr,
+                           s.col, S, ptr<T>(w->PT), w->items_g, static_cast<T*>(w->mm_part), Q, ctl);
             return 7 + np;
         }
     }
@@ -2693,8 +2733,8 @@ static void capture_krylov(Solver* w, const Structure& s, const T* S, const T* S
     BA_CUDA_TRY(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     *per_pass = 1;
     for (int k = 0; k < chunk; ++k) *per_pass += enqueue_iteration<T>(w, s, S, Su, Dinv, x, mcg, cb);
-    k_loop_cond<<<1, kThreads, 0, cb>>>(h, 1, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 0, chunk,
-                                        ptr<Params>(w->params));
+    launch_chained(k_loop_cond, dim3(1), dim3(kThreads), 0, cb, h, 1, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 0,
+                   chunk, ptr<Params>(w->params));
     cudaGraph_t done = nullptr;
     cudaError_t e = cudaStreamEndCapture(cb, &done);
     if (e != cudaSuccess) throw Error(BA_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(e));
