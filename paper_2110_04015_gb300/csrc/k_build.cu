@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc)
-                            acc[3 * r + cc] += x[3 * r] * y[3 * cc] + x[3 * r + 1] * y[3 * cc + 1] + x[3 * r + 2] * y[3 * cc + 2];
+                            acc[3 * r + cc] = fmaf(x[3 * r + 2], y[3 * cc + 2],
+                                                   fmaf(x[3 * r + 1], y[3 * cc + 1], fmaf(x[3 * r], y[3 * cc], acc[3 * r + cc])));
                 }
             }
             __syncwarp();           // buffer c & 1 is refilled by issue(c + 2)
@@ -825,7 +826,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_schur_diag32(
 #pragma unroll
                 for (int a = 0; a < 9; ++a)
 #pragma unroll
-                    for (int b = a; b < 9; ++b) acc[t++] += jc[a] * B0[b] + jc[9 + a] * B1[b];
+                    for (int b = a; b < 9; ++b, ++t) acc[t] = fmaf(jc[9 + a], B1[b], fmaf(jc[a], B0[b], acc[t]));
             }
             __syncwarp();
             // the warp's rows qw .. qw + n - 1, 9 16-byte pieces each (the padding of a part included)
