@@ -113,8 +113,9 @@ def load_peaks() -> dict:
 
 # DRAM bytes per stored upper 9x9 block of one float32 symmetric product (k_spmv<float,1,true,true> and
 # k_spmv_col together: dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the dense
-# 1936-camera product timed by ba_time_kernel: 594.6 + 11.6 + 0.6 + 1.0 MB over 1,755,926 upper blocks).
-SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = 346.2
+# 1936-camera product timed by ba_time_kernel, mean of two launch pairs: 594.5 + 11.4 + 0.2 + 0.6 MB
+# over 1,755,926 upper blocks).
+SPMV_F32_TRAFFIC_PER_UPPER_BLOCK = 345.5
 
 # FP64 arithmetic peak of this GB300: 1.06 TFLOP/s measured with an FMA-chain kernel
 # (1216 CTAs x 256 threads x 8 independent chains; 1.69 FMA per clock per SM at 2.07 GHz).
