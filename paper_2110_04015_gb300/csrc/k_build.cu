@@ -632,6 +632,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
     static_assert(sizeof(T) == 4, "float32 build (float64 uses k_schur_off_rows)");
     constexpr int kBuf = kOffChunk * 2 * kG32Row;      // one buffer of a group: the chunk's row pairs
     __shared__ __align__(16) T sg[kThreads / 32][3][2 * kBuf];
+    __shared__ int64_t sdst[kThreads / 32][3][3];   // per group: offsets of (j, k), (k, j), upper (j, k)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int g = lane / 9, sub = lane - 9 * g;        // g == 3: lanes 27..31
     const int A = sub / 3, B = sub - 3 * (sub / 3);
@@ -689,7 +690,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
             __syncwarp();           // buffer c & 1 is refilled by issue(c + 2)
         }
         // the group's block, scaled (rows by Lam_j, columns by Lam_k) and negated, into its area
-        int64_t dj = 0, dk = 0, du = 0;
         if (has) {
             const int2 jk = up_cams[u];
             const T* lj = lam + 9 * int64_t(jk.x);
@@ -699,26 +699,27 @@ __global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
                     area[(3 * A + r) * 9 + 3 * B + cc] = -(acc[3 * r + cc] * lj[3 * A + r] * lk[3 * B + cc]);
-            dj = up_dst[u];
-            dk = up_mdst[u];
-            du = up_udst[u];
+            if (sub == 0) {
+                sdst[wid][g][0] = up_dst[u];
+                sdst[wid][g][1] = up_mdst[u];
+                sdst[wid][g][2] = up_udst[u];
+            }
         }
         __syncwarp();
-        // the warp writes the three blocks: entry e of 3 x 81 is entry e % 81 of group e / 81's block
+        // the warp writes the blocks one after the other, 81 consecutive values per destination
+        for (int gg = 0; gg < 3 && 3 * w + gg < n_up; ++gg) {
+            const int64_t ej = sdst[wid][gg][0], ek = sdst[wid][gg][1], eu = sdst[wid][gg][2];
+            const T* blk = &sg[wid][gg][0];
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int e = lane + 32 * it;
-            const int gg = e < 243 ? e / 81 : 0, ee = e - 81 * gg;
-            const int64_t ej = __shfl_sync(0xffffffffu, dj, 9 * gg);
-            const int64_t ek = __shfl_sync(0xffffffffu, dk, 9 * gg);
-            const int64_t eu = __shfl_sync(0xffffffffu, du, 9 * gg);
-            if (e < 243 && 3 * w + gg < n_up) {
-                const T* blk = &sg[wid][gg][0];
-                const T v = blk[ee];
-                S[ej + ee] = v;
-                Su[eu + ee] = v;
-                const int b = ee / 9, a = ee - 9 * (ee / 9);   // entry 9 b + a of (k, j) is (a, b) of (j, k)
-                S[ek + ee] = blk[9 * a + b];
+            for (int it = 0; it < 3; ++it) {
+                const int ee = lane + 32 * it;
+                if (ee < 81) {
+                    const T v = blk[ee];
+                    S[ej + ee] = v;
+                    Su[eu + ee] = v;
+                    const int b = ee / 9, a = ee - 9 * (ee / 9);   // entry 9 b + a of (k, j) is (a, b) of (j, k)
+                    S[ek + ee] = blk[9 * a + b];
+                }
             }
         }
         __syncwarp();
