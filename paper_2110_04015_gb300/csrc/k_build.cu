@@ -649,16 +649,33 @@ __global__ void __launch_bounds__(kThreads, 4) k_schur_off_sub(
         int nmax = nch;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        // The observation pairs of a chunk are loaded one chunk ahead, pair i by lane 9 g + i of the
+        // group, so that the copies of a chunk start without waiting on its pair indices.
+        const int src = 9 * (g < 3 ? g : 0);
+        auto load_pairs = [&](int c) {
+            const int64_t q = pb + int64_t(c) * kOffChunk + sub;
+            return (c < nch && sub < kOffChunk && q < pe) ? pairs[q] : make_int2(0, 0);
+        };
+        int2 pnext = load_pairs(0);
         // chunk c of this group's pairs into buffer c & 1 (nothing past the group's last chunk)
         auto issue = [&](int c) {
+            int2 pr[kOffChunk];
+#pragma unroll
+            for (int i = 0; i < kOffChunk; ++i) {
+                pr[i].x = __shfl_sync(0xffffffffu, pnext.x, src + i);
+                pr[i].y = __shfl_sync(0xffffffffu, pnext.y, src + i);
+            }
+            pnext = load_pairs(c + 1);
             if (c < nch) {
                 T* buf = area + (c & 1) * kBuf;
                 const int64_t q0 = pb + int64_t(c) * kOffChunk;
                 const int n = pe - q0 < kOffChunk ? int(pe - q0) : kOffChunk;
-                for (int i = 0; i < n; ++i) {
-                    const int2 pr = pairs[q0 + i];
-                    cp_async16(buf + (2 * i) * kG32Row + coff, G + int64_t(kG32Row) * pr.x + coff);
-                    cp_async16(buf + (2 * i + 1) * kG32Row + coff, G + int64_t(kG32Row) * pr.y + coff);
+#pragma unroll
+                for (int i = 0; i < kOffChunk; ++i) {
+                    if (i < n) {
+                        cp_async16(buf + (2 * i) * kG32Row + coff, G + int64_t(kG32Row) * pr[i].x + coff);
+                        cp_async16(buf + (2 * i + 1) * kG32Row + coff, G + int64_t(kG32Row) * pr[i].y + coff);
+                    }
                 }
             }
             cp_async_commit();
