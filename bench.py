@@ -150,6 +150,18 @@ BUILD_WORK = [
 ]
 
 
+def spmv_bytes(precision: str, nnzb: int, n_cams: int) -> int:
+    """Algorithmic bytes of one product q = S p: the stored blocks of S once (81 values and a 4-byte
+    column index each; float64 streams every block, the float32 symmetric product the upper triangle
+    with the diagonal, (nnzb + n_cams) / 2 blocks, each serving S_jk p_k and S_jk^T p_j), the row
+    pointers, and three vectors of 9 n_cams values (p read, q written, one more read for the
+    per-camera sums).  The transposed terms the symmetric product writes and reads back are
+    implementation traffic, not counted."""
+    elt = 8 if precision == "fp64" else 4
+    blocks = nnzb if precision == "fp64" else (nnzb + n_cams) // 2
+    return blocks * (81 * elt + 4) + 8 * (n_cams + 1) + 3 * 9 * n_cams * elt
+
+
 def build_roofline(p, counts, peaks, reps=3):
     """Each kernel of the mixed build timed alone (ba_time_kernel, L2 evicted before each launch),
     against the HBM copy peak and the arithmetic peak of its precision; `bound` is the larger fraction."""
@@ -490,34 +502,28 @@ def run_ours(a, rank: int, world: int, local_rank: int):
     # roofline of the dominant kernel: the product q = S p of the Krylov solves
     nnzb = p.ba_get_schur_nnzb()
     nnzb_u = (nnzb + sc.n_cams) // 2       # upper triangle with the diagonal
-    n = 9 * sc.n_cams
     t_spmv = p.ba_time_kernel("spmv", reps=10)
     t_schur = p.ba_time_kernel("schur", reps=3)
     peaks = load_peaks()
-    elt = 8 if a.precision == "fp64" else 4
     spmv_flops = 162.0 * nnzb
-    if a.precision == "fp64":
-        spmv_bytes = nnzb * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
-    else:
-        # the symmetric product streams the upper triangle once (each block serves S_jk p_k and
-        # S_jk^T p_j); the 9 transposed terms per strict upper block it writes and reads back
-        # (72 B) are not counted as algorithmic
-        spmv_bytes = nnzb_u * (81 * elt + 4) + 8 * (sc.n_cams + 1) + 3 * n * elt
+    # the float32 symmetric product streams the upper triangle once; the 9 transposed terms per
+    # strict upper block it writes and reads back (72 B) are not counted as algorithmic
+    sbytes = spmv_bytes(a.precision, nnzb, sc.n_cams)
     if a.precision == "fp64":
         roof = {"kernel": "k_spmv<double,1,true> (q = S p, Algorithm 1)", "bound": "alu", "achieved": spmv_flops / t_spmv / 1e9,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
-                "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "ms_per_launch": t_spmv,
-                "achieved_gbs": spmv_bytes / t_spmv / 1e6, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "bytes_per_launch": sbytes, "flops_per_launch": spmv_flops, "ms_per_launch": t_spmv,
+                "achieved_gbs": sbytes / t_spmv / 1e6, "hbm_peak_gbs": peaks["hbm_gbs"],
                 "peak_source": "measured FP64 FMA throughput 1.06 TFLOP/s (nominal 1.25)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         traffic = None if SPMV_F32_TRAFFIC_PER_UPPER_BLOCK is None else SPMV_F32_TRAFFIC_PER_UPPER_BLOCK * nnzb_u
         roof = {"kernel": "k_spmv<float,1,true,true> + k_spmv_col (q = S p from the upper triangle of S, Algorithm 1)",
-                "bound": "hbm", "achieved": spmv_bytes / t_spmv / 1e6,
+                "bound": "hbm", "achieved": sbytes / t_spmv / 1e6,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": traffic,
                 "traffic_source": "ncu dram bytes of this product on dense-1936 (both launches), per upper block",
-                "bytes_per_launch": spmv_bytes, "upper_blocks": nnzb_u,
-                "bytes_moved_model": spmv_bytes + 72 * (nnzb_u - sc.n_cams),
+                "bytes_per_launch": sbytes, "upper_blocks": nnzb_u,
+                "bytes_moved_model": sbytes + 72 * (nnzb_u - sc.n_cams),
                 "ms_per_launch": t_spmv, "peak_source": peaks["source"]}
         roof["frac"] = roof["achieved"] / roof["peak"]
     # the build kernel by kernel (mixed precision)
@@ -856,9 +862,7 @@ def measure_batched(a, steps, warmup, loop):
     nnzb = pb.ba_get_schur_nnzb()
     peaks = load_peaks()
     elt = 8 if a.precision == "fp64" else 4
-    # float64 streams every stored block; float32 the upper triangle (the symmetric product)
-    blocks = nnzb if a.precision == "fp64" else (nnzb + n_cams) // 2
-    spmv_bytes = blocks * (81 * elt + 4) + 8 * (n_cams + 1) + 3 * 9 * n_cams * elt
+    sbytes = spmv_bytes(a.precision, nnzb, n_cams)
     pb.close()
 
     tl = []
@@ -896,9 +900,9 @@ def measure_batched(a, steps, warmup, loop):
         "per_problem_iters": [s["iters"] for s in per],
         "autotune": {"item_blocks": cb, "spmv_config": cfg, "spmv_ms_tuned": t_tuned, "spmv_ms_heuristic": t_heur},
         "roofline": {"kernel": "q = S p over all problems (float32: the symmetric product over the upper triangle)",
-                     "bound": "hbm" if elt == 4 else "alu", "bytes_per_launch": spmv_bytes,
-                     "achieved_gbs": spmv_bytes / t_tuned / 1e6, "peak_gbs": peaks["hbm_gbs"],
-                     "frac": spmv_bytes / t_tuned / 1e6 / peaks["hbm_gbs"]},
+                     "bound": "hbm" if elt == 4 else "alu", "bytes_per_launch": sbytes,
+                     "achieved_gbs": sbytes / t_tuned / 1e6, "peak_gbs": peaks["hbm_gbs"],
+                     "frac": sbytes / t_tuned / 1e6 / peaks["hbm_gbs"]},
         "gpu_launches_per_step": int(launches), "clocks": clk,
         "step_ms": [round(x, 3) for x in tb], "loop_ms": [round(x, 3) for x in tl],
     }
