@@ -62,7 +62,9 @@ typedef enum ba_damping {
 typedef enum ba_precision {
     BA_PRECISION_FP64 = 0,     /* every array and product in float64 */
     BA_PRECISION_MIXED = 1     /* float32 S, directions and Krylov products; float64 outer
-                                  refinement on the true residual, small solves in float64 */
+                                  refinement on the true residual, small solves in float64;
+                                  residuals, Jacobians, landmark factors, b~ and the true
+                                  residual in double-float (float32 pairs, ~48 bits) */
 } ba_precision;
 
 typedef enum ba_solver {
@@ -201,7 +203,10 @@ int ba_get_params(const ba_problem* p, double* cams, double* pts);
  * V_lambda (Marquardt or identity damping), b_p, b_l, the block-sparse S with its
  * 9x9 blocks for every co-visible camera pair, b~, and the inverses of the diagonal
  * blocks of S for the block-Jacobi preconditioner (Section 3.2).  In MIXED precision
- * a float32 copy of S is made as well (the preconditioner stays float64).  Errors:
+ * S itself is built in float32 as Lam S Lam (Lam = diag(S)^-1/2, full pattern and upper
+ * triangle) from float32 Jacobians, the diagonal blocks of S in float64, and the
+ * residuals, Jacobians, landmark factors and b~ in double-float arithmetic; the
+ * preconditioner holds the inverses of the scaled diagonal blocks.  Errors:
  * INVALID_ARG (lambda <= 0 or not finite), SINGULAR (a V_lambda or S_jj not positive
  * definite; the system is left unusable), CUDA.
  */

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kCamThreads) k_cameras(
             Uout[81 * int64_t(j) + threadIdx.x] = v;
         }
         __syncthreads();
-        if (!G) {   // U and b_p only (mixed precision builds b~ in k_cam_rhs)
+        if (!G) {   // U and b_p only (mixed precision builds b~ in k_cam_rhs_df)
             if (threadIdx.x < 9) bpout[9 * int64_t(j) + threadIdx.x] = fin[45 + threadIdx.x];
             __syncthreads();
             continue;

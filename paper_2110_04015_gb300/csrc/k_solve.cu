@@ -2674,7 +2674,7 @@ static int krylov_init(Solver* w, const Structure& s, const T* S, const T* Su, c
 }
 
 // true residual t = -b~ - S x into out (may be null) and, per problem, its norms into ctl (true_rr,
-// bb): explicit tiled S in float64 precision, the implicit float64 operator in mixed precision.
+// bb): explicit tiled S in float64 precision, the implicit operator (double-float arithmetic) in mixed precision.
 static int true_residual(Solver* w, const Structure& s, const System& y, const double* x, double* out,
                          cudaStream_t st) {
     int n = 0;
