@@ -658,7 +658,9 @@ __global__ void __launch_bounds__(SpmvShape<T, CFG>::kWarps * 32, 1) k_spmv(
 // transposed terms S_jk^T z_j (a fixed order: lane-strided sums in each warp's share of the column's
 // slots, then the warps' sums in warp order), then in MODE 1 the per-camera sums q^T p and p^T r.
 // One CTA of kColWarps warps per camera (its slots qptr[k] .. qptr[k + 1] - 1 of tb are consecutive,
-// up to n_c - 1 of them); grid: CTAs x problems.
+// up to n_c - 1 of them); grid: CTAs x problems.  CTAs take the cameras from the last one down:
+// camera k's column holds the blocks (j, k), j < k, so on a dense pattern the long columns start
+// in the first wave and the short ones fill the tail.
 constexpr int kColWarps = 4;   // 12 CTAs per SM: 1824 cameras in flight
 template <typename T, int MODE, bool ZH>
 __global__ void __launch_bounds__(kColWarps * 32, 12) k_spmv_col(const int64_t* __restrict__ qptr,
@@ -676,8 +678,8 @@ __global__ void __launch_bounds__(kColWarps * 32, 12) k_spmv_col(const int64_t* 
     const int64_t hb = c.lay.hoff - 9 * int64_t(c.lay.c0);
     const int64_t zoff = ZH ? hb + int64_t(MODE == 2 ? c.new_off : 0) * n : 0;
     const int64_t ooff = hb + int64_t(MODE == 1 ? 0 : c.new_off) * n;
-    for (int64_t jl = blockIdx.x; jl < c.lay.nc; jl += gridDim.x) {
-        const int64_t j = c.lay.c0 + jl;
+    for (int64_t jr = blockIdx.x; jr < c.lay.nc; jr += gridDim.x) {
+        const int64_t j = c.lay.c0 + (c.lay.nc - 1 - jr);
         T acc[9];
 #pragma unroll
         for (int b = 0; b < 9; ++b) acc[b] = T(0);
