@@ -2662,17 +2662,19 @@ static int enqueue_iteration(Solver* w, const Structure& s, const T* S, const T*
     }
 }
 
-// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and Q_0 = S P_0; returns the launches.
+// x = 0, r = sign * rhs, z = D^{-1} r, P_0 = z, the control blocks and (q0) Q_0 = S P_0; returns the
+// launches.  Algorithm 2 starts its iterations from Q_0; Algorithm 1 forms Q = S P first in every
+// iteration, so its solves pass q0 = false.
 template <typename T>
 static int krylov_init(Solver* w, const Structure& s, const T* S, const T* Su, const double* Dinv, const double* rhs,
-                       double sign, const double* scale, T* x, const Outer* outer, cudaStream_t st) {
+                       double sign, const double* scale, T* x, const Outer* outer, cudaStream_t st, bool q0 = true) {
     const int nb = w->nb;
     k_init_vec<T><<<dim3(w->gx, nb), kThreads, 0, st>>>(ptr<Layout>(w->lay_d), rhs, sign, scale, Dinv, x, ptr<T>(w->r),
                                                          ptr<T>(w->z), ptr<T>(w->P), ptr<double>(w->part_b));
     k_init_ctl<<<nb, 32, 0, st>>>(ptr<Ctl>(w->ctl), ptr<Layout>(w->lay_d), ptr<double>(w->part_b), w->gx,
                                   ptr<Params>(w->params), sizeof(T) == 4 ? kStagnation : 0.0, sizeof(T) == 4 ? 1 : 0,
                                   outer, ptr<int>(w->blk_off), ptr<int>(w->blk_w), w->mi1);
-    return 2 + enqueue_product<T, 0>(w, s, S, Su, ptr<T>(w->P), kSelLive, ptr<T>(w->Q), nullptr, st);
+    return 2 + (q0 ? enqueue_product<T, 0>(w, s, S, Su, ptr<T>(w->P), kSelLive, ptr<T>(w->Q), nullptr, st) : 0);
 }
 
 // true residual t = -b~ - S x into out (may be null) and, per problem, its norms into ctl (true_rr,
@@ -2730,7 +2732,7 @@ static void capture_krylov(Solver* w, const Structure& s, const T* S, const T* S
                            const double* rhs, double sign, const double* scale, T* x, const Outer* outer, bool mcg,
                            int chunk, cudaStream_t cs, cudaStream_t cb, int* pre, int* per_pass) {
     const cudaGraphConditionalHandle h = capture_handle(cs);
-    *pre = krylov_init<T>(w, s, S, Su, Dinv, rhs, sign, scale, x, outer, cs) + 1;
+    *pre = krylov_init<T>(w, s, S, Su, Dinv, rhs, sign, scale, x, outer, cs, mcg) + 1;
     k_loop_cond<<<1, kThreads, 0, cs>>>(h, 1, ptr<Ctl>(w->ctl), w->nb, ptr<Loops>(w->loops), 1, chunk,
                                         ptr<Params>(w->params));
     cudaGraph_t body = capture_while(cs, h);
@@ -2857,7 +2859,7 @@ static void run_host_loops(Solver* w, const Structure& s, const System& y, const
     const cudaGraphConditionalHandle none = cudaGraphConditionalHandle();
     int64_t launches = 0;
     if (!fp32) {
-        launches += krylov_init<double>(w, s, y.S, nullptr, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, st);
+        launches += krylov_init<double>(w, s, y.S, nullptr, y.Dinv, y.bt, -1.0, nullptr, x, nullptr, st, a.mcg != 0);
         k_loop_cond<<<1, kThreads, 0, st>>>(none, 0, ptr<Ctl>(w->ctl), nb, lp, 1, a.chunk, prm);
         launches += 1 + host_krylov_loop(w, chunk_exec, gc, a, st, waits);
         launches += true_residual(w, s, y, x, nullptr, st);
@@ -2874,7 +2876,7 @@ static void run_host_loops(Solver* w, const Structure& s, const System& y, const
             for (int b = 0; b < nb && !any; ++b) any = w->h_outer[b].swept != 0;
             if (!any) break;
             launches += krylov_init<float>(w, s, y.S32, y.S32u, y.Dhat, ptr<double>(w->rt), 1.0, y.lam,
-                                           ptr<float>(w->xw), ptr<Outer>(w->outer), st);
+                                           ptr<float>(w->xw), ptr<Outer>(w->outer), st, a.mcg != 0);
             k_loop_cond<<<1, kThreads, 0, st>>>(none, 0, ptr<Ctl>(w->ctl), nb, lp, 1, a.chunk, prm);
             launches += 1 + host_krylov_loop(w, chunk_exec, gc, a, st, waits);
             k_accumulate<<<grid_for_host(n), kThreads, 0, st>>>(n, ptr<float>(w->xw), y.lam, x, y.xd);

@@ -316,11 +316,12 @@ def test_tight_tolerance_solution_matches_dense_solve_elementwise(case, dense_re
 def test_a_solve_is_one_graph_launch_with_one_host_wait(precision, chunk):
     """The iteration loop (and the float64 refinement loop of mixed precision) runs on the device:
     a solve waits on the host once, for its results, and launches exactly the kernels of the passes
-    its device-side loop made: 4 before the loop, chunk iterations plus the loop condition per pass,
-    and the 2 of the float64 true residual after it (float64: 3 launches per PCG and 8 per MCG
-    iteration); in mixed precision 3 before the refinement loop and 12 around each sweep's Krylov
-    loop (the double-float true residual takes 4 of them; 4 per PCG and 9 per MCG iteration: the
-    symmetric float32 product takes two)."""
+    its device-side loop made: before the loop the start (2) and the loop condition, plus for MCG
+    the product Q_0 = S P_0 (PCG forms Q = S P first in every iteration); chunk iterations plus the
+    loop condition per pass; and the 2 of the float64 true residual after it (float64: 3 launches
+    per PCG and 8 per MCG iteration). In mixed precision 3 before the refinement loop and, around
+    each sweep's Krylov loop, 10 (PCG) or 12 (MCG: the symmetric float32 product takes two) (the
+    double-float true residual takes 4 of them; 4 per PCG and 9 per MCG iteration)."""
     import math
 
     sc = scene("seq-small")
@@ -333,9 +334,11 @@ def test_a_solve_is_one_graph_launch_with_one_host_wait(precision, chunk):
             assert st["status"] == 0 and st["host_waits"] == 1, st
             body = chunk * per + 1
             if precision == "fp64":
-                assert launched == 4 + math.ceil(st["iters"] / chunk) * body + 2, (kind, launched, st)
+                pre = 3 if kind == "pcg" else 4
+                assert launched == pre + math.ceil(st["iters"] / chunk) * body + 2, (kind, launched, st)
             elif st["refinements"] == 1:
-                assert launched == 3 + 12 + math.ceil(st["iters"] / chunk) * body, (kind, launched, st)
+                sweep = 10 if kind == "pcg" else 12
+                assert launched == 3 + sweep + math.ceil(st["iters"] / chunk) * body, (kind, launched, st)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
